@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark: 1080p 8-level Oriented FAST, frames/s and Mpix/s on GB300.
+
+Workload (one step): a batch of B synthetic 1920x1080 uint8 frames (1/f-noise
+background, 200 rectangles, 30 checkerboards, blur sigma 1, noise sigma 3),
+each through the whole chain -- 8-level bilinear pyramid at scale 1.2 (border
+19), FAST-9 score with t=20 and fallback t=7 per 30x30 cell, strict 3x3 NMS,
+Harris 7x7 with k=0.04, top 1000 per frame split by level area, centroid
+orientation with radius 15.
+
+Reported:
+  value        batched path, frames/s (inputs resident in HBM, one
+               of_detect_batch call per step, B frames)
+  plain        per-frame path (one of_detect_batch call per frame), frames/s
+  e2e          batched path with host buffers: pinned H2D of the frames and
+               D2H of keypoints + counts inside the timed region
+  roofline     dominant stage: algorithmic bytes per launch / its mean
+               CUDA-event duration over the timed region, vs measured HBM peak
+  cpu_baseline the CPU oracle on a bounded sample, all host cores (N=1, rank 0)
+
+--impl reference runs the CPU oracle as the reference arm (bounded samples).
+Multi-GPU (torchrun): replicas only, each rank runs the same per-GPU workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+W_, H_, LEVELS, SCALE, FAST_T, FAST_T_LO, HARRIS_K, NFEAT = 1920, 1080, 8, 1.2, 20, 7, 0.04, 1000
+BORDER = 19
+WORKLOAD = ("1920x1080 u8 frames, 8-level bilinear pyramid scale 1.2, FAST-9 t=20 (fallback t=7 "
+            "per 30x30 cell), strict 3x3 NMS, Harris 7x7 k=0.04, top 1000 per frame by level "
+            "area, centroid r=15")
+METRIC = "1080p 8-level Oriented FAST frames/s"
+
+
+def _gen(seed: int):
+    import synth
+
+    return synth.scene(W_, H_, seed, background="pink")
+
+
+def _oracle_detect(img):
+    import oracle
+
+    return len(oracle.detect(img, levels=LEVELS, scale=SCALE, fast_t=FAST_T, fast_t_lo=FAST_T_LO,
+                             harris_k=HARRIS_K, n_features=NFEAT))
+
+
+def make_frames(n: int, pool=None):
+    seeds = list(range(n))
+    if pool is not None:
+        return pool.map(_gen, seeds)
+    return [_gen(s) for s in seeds]
+
+
+def cpu_baseline(pool, cores: int, frames, n_frames: int):
+    """The oracle as it stands, frame-parallel over `cores` processes (detect only)."""
+    import oracle
+
+    oracle.build()
+    work = [frames[i % len(frames)] for i in range(n_frames)]
+    pool.map(_oracle_detect, work[:cores])  # warm the workers
+    t0 = time.perf_counter()
+    pool.map(_oracle_detect, work)
+    wall = time.perf_counter() - t0
+    return {"value": round(n_frames / wall, 4), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_frames} frames of the timed workload ({len(frames)} distinct), one oracle "
+                      f"process per core, wall {wall:.1f} s"}
+
+
+def sample_clocks(stop_path: str, out_path: str):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "100", "-i", os.environ.get("LOCAL_RANK", "0")],
+                                stdout=open(out_path, "w"), stderr=subprocess.DEVNULL)
+    except (OSError, FileNotFoundError):
+        return None
+
+
+def summarize_clocks(path: str):
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def stage_bytes(levels_w, levels_h, cand_counts, kept_counts):
+    """Algorithmic HBM bytes per frame for each stage (see the design notes)."""
+    lw, lh = levels_w, levels_h
+    px = [w * h for w, h in zip(lw, lh)]
+    det = [max(0, w - 2 * BORDER) * max(0, h - 2 * BORDER) for w, h in zip(lw, lh)]
+    pyr = sum(px[:-1]) + sum(px[1:])                      # read l-1, write l
+    fast = sum(px) + sum(det)                             # read levels, write score maps
+    nmsh = sum(det) + sum(px) + 12 * sum(cand_counts)     # read scores + levels, write candidates
+    sel = 12 * sum(cand_counts) + 12 * sum(kept_counts)   # read candidates, write kept
+    orient = (709 + 81 + 12 + 64) * sum(kept_counts)      # disc + footprint + kept + record
+    return [pyr, fast, nmsh, sel, orient]
+
+
+def run_reference(args, rank: int, world: int):
+    """Reference arm: the CPU oracle, bounded sample per step."""
+    if rank != 0:
+        return 0
+    import multiprocessing as mp
+
+    cores = min(os.cpu_count() or 1, 16)
+    ctx = mp.get_context("spawn")
+    frames_per_step = cores
+    with ctx.Pool(cores) as pool:
+        import oracle
+
+        oracle.build()
+        frames = make_frames(frames_per_step, pool)
+        for _ in range(args.warmup):
+            pool.map(_oracle_detect, frames)
+        per_step = []
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_detect, frames)
+            per_step.append(time.perf_counter() - t0)
+    tot = sum(per_step)
+    value = frames_per_step * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "frames/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * tot / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_step": frames_per_step},
+            "cpu_baseline": {"value": round(value, 4), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{frames_per_step} distinct 1920x1080 frames per step, one "
+                                       "oracle process per core"},
+            "e2e": {"value": round(value, 4), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=128, help="frames per step")
+    ap.add_argument("--distinct", type=int, default=16, help="distinct synthetic frames")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frames", type=int, default=0, help="oracle sample size (0: 2 x cores)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(min(cores, 16))
+    frames_np = make_frames(args.distinct, pool)
+
+    import numpy as np
+    import torch
+
+    import paper_2506_07164_gb300 as ofg
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ofg.build()
+    ofg.load()
+    B = args.batch
+    stream = torch.cuda.Stream()
+    dev_frames = [torch.from_numpy(frames_np[i % len(frames_np)]).cuda() for i in range(B)]
+    torch.cuda.synchronize()
+    batched = ofg.Detector(W_, H_, max_levels=LEVELS, max_features=NFEAT, max_batch=B, fast_t_lo=FAST_T_LO,
+                           stream=stream)
+    plain = ofg.Detector(W_, H_, max_levels=LEVELS, max_features=NFEAT, max_batch=1, fast_t_lo=FAST_T_LO,
+                         stream=stream)
+    frames = [(t, W_, H_, W_) for t in dev_frames]
+
+    def step_batched(events=None):
+        if events is not None:
+            ofg.of_time_stages(batched.h, events)
+        ofg.of_detect_batch(batched.h, frames, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, batched.out,
+                            batched.counts)
+
+    def step_plain():
+        for f in frames:
+            ofg.of_detect_batch(plain.h, [f], LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, plain.out, plain.counts)
+
+    def timed(fn, steps, warmup, per_step_events=False):
+        for _ in range(warmup):
+            fn() if not per_step_events else fn(None)
+        barrier()
+        evs = None
+        if per_step_events:
+            evs = [[torch.cuda.Event(enable_timing=True) for _ in range(ofg.OF_N_STAGES + 1)]
+                   for _ in range(steps)]
+            for row in evs:
+                for e in row:
+                    e.record(stream)
+        barrier()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for k in range(steps):
+            fn(evs[k]) if per_step_events else fn()
+        end.record(stream)
+        end.synchronize()
+        barrier()
+        ms = start.elapsed_time(end)
+        stage_ms = None
+        if evs:
+            stage_ms = [statistics.mean(row[i].elapsed_time(row[i + 1]) for row in evs)
+                        for i in range(ofg.OF_N_STAGES)]
+        return ms, stage_ms
+
+    clock_file = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/ofast_clocks_{os.getpid()}.csv"
+    smi = sample_clocks("", clock_file)
+    time.sleep(0.3)
+    ms_b, stage_ms = timed(step_batched, args.steps, args.warmup, per_step_events=True)
+    if smi is not None:
+        smi.terminate()
+        smi.wait()
+    clocks = summarize_clocks(clock_file)
+    plain_steps = max(2, args.steps // 4)
+    ms_p, _ = timed(step_plain, plain_steps, 2)
+
+    # End to end through the public API with host buffers.
+    host = [torch.from_numpy(frames_np[i % len(frames_np)]).pin_memory() for i in range(B)]
+    out_host = torch.empty(B * NFEAT * 64, dtype=torch.uint8).pin_memory()
+    cnt_host = torch.empty(B, dtype=torch.int32).pin_memory()
+
+    def step_e2e():
+        with torch.cuda.stream(stream):
+            for hsrc, d in zip(host, dev_frames):
+                d.copy_(hsrc, non_blocking=True)
+            step_batched()
+            cnt_host.copy_(batched.counts[:B], non_blocking=True)
+            out_host.copy_(batched.out[: B * NFEAT * 64], non_blocking=True)
+        stream.synchronize()
+
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(2):
+        step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_e2e()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+
+    # Correctness spot check of the timed configuration: frame 0 vs frame 0 of a single call.
+    torch.cuda.synchronize()
+    counts = batched.counts[:B].cpu().numpy()
+
+    # Plan geometry and candidate counts for the algorithmic byte model.
+    lw, lh, _ = ofg.of_plan_levels(W_, H_, LEVELS, SCALE, NFEAT)
+    cand = []
+    kept = []
+    for l in range(LEVELS):
+        _, dims = ofg.of_inspect(batched.h, ofg.OF_BUF_CAND, 0, l)
+        cand.append(dims[2])
+    recs = ofg.keypoints_to_numpy(batched.out[: NFEAT * 64])[: int(counts[0])]
+    for l in range(LEVELS):
+        kept.append(int((recs["level"] == l).sum()))
+    per_frame = stage_bytes(lw, lh, cand, kept)
+
+    # Max over ranks.
+    vals = torch.tensor([ms_b, ms_p, e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms_b, ms_p, e2e_s = vals.tolist()
+
+    frames_total = B * args.steps * world
+    value = frames_total / (ms_b / 1000.0)
+    plain_fps = B * plain_steps * world / (ms_p / 1000.0)
+    e2e_fps = B * e2e_steps * world / e2e_s
+    mpix = W_ * H_ / 1e6
+
+    peak, peak_kind = measured_peaks()
+    shares = [m / sum(stage_ms) for m in stage_ms]
+    dom = int(np.argmax(stage_ms))
+    achieved = per_frame[dom] * B / (stage_ms[dom] / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": ofg.STAGE_NAMES[dom], "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None,
+                "stage_ms_per_step": {n: round(m, 4) for n, m in zip(ofg.STAGE_NAMES, stage_ms)},
+                "stage_share": {n: round(s, 4) for n, s in zip(ofg.STAGE_NAMES, shares)},
+                "stage_frac_of_hbm": {n: round(per_frame[i] * B / (stage_ms[i] / 1000.0) / 1e9 / peak, 4)
+                                      for i, n in enumerate(ofg.STAGE_NAMES)},
+                "algorithmic_bytes_per_frame": dict(zip(ofg.STAGE_NAMES, per_frame))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n = args.cpu_frames or 2 * min(cores, 16)
+        cpu = cpu_baseline(pool, min(cores, 16), frames_np, n)
+    pool.close()
+
+    kernels_per_step = (LEVELS - 1) + 4
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_b / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": B, "distinct_frames": len(frames_np),
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2: {B} frames x {W_ * H_ / 1e6:.2f} MB per step"},
+        "mpix_per_s": round(value * mpix, 1),
+        "plain": {"value": round(plain_fps, 2), "unit": "frames/s", "mpix_per_s": round(plain_fps * mpix, 1),
+                  "steps": plain_steps, "launch": "one of_detect_batch call (one graph) per frame"},
+        "batched_vs_plain": round(value / plain_fps, 3),
+        "e2e": {"value": round(e2e_fps, 2), "unit": "frames/s", "h2d_bytes_per_step": B * W_ * H_,
+                "d2h_bytes_per_step": B * NFEAT * 64 + 4 * B, "steps": e2e_steps},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": kernels_per_step * args.steps,
+        "keypoints_per_frame": float(np.mean(counts)),
+        "candidates_frame0": cand,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batched.close()
+    plain.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

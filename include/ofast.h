@@ -1,0 +1,170 @@
+/*
+ * ofast.h — C ABI of the GB300 (sm_103a) Oriented FAST detector.
+ *
+ * Method: "Faster than Fast: Accelerating Oriented FAST Feature Detection on
+ * Low-end Embedded GPUs" (arXiv 2506.07164).  One call runs, on the GPU, the
+ * whole detection chain of an ORB front end:
+ *
+ *   1. pyramid: level l is a bilinear resize of level l-1, sizes
+ *      w_l = floor(W / scale^l + 0.5) (Sec. 1; Sec. 6.1 "decrease exponentially");
+ *   2. FAST-9 segment test with a score (Eq. 1, Sec. 3.1, Alg. 2, Fig. 3);
+ *   3. per-cell threshold fallback and strict 3x3 non-maximum suppression
+ *      (Fig. 1 "NMS");
+ *   4. Harris response from separable Sobel gradients and 7x7 window sums
+ *      (Eqs. 2-4, Alg. 3, Fig. 4);
+ *   5. top-N per level by Harris response (Sec. 1: Harris "screens" the FAST
+ *      points; Sec. 3.2);
+ *   6. intensity-centroid orientation (Fig. 1 "Centroid").
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked [device] are CUDA device pointers (e.g. torch tensors'
+ *     data_ptr()); [host] pointers are ordinary host memory.
+ *   - Images are uint8, row-major, `pitch` bytes between rows; the caller
+ *     guarantees `h * pitch` readable bytes.  Level 0 is read in place when
+ *     its address and pitch are multiples of 16, otherwise it is first copied
+ *     into the handle's scratch (same results, one extra copy).
+ *   - The caller owns every buffer it passes; the handle owns all scratch
+ *     (pyramid, score maps, candidate lists), allocated once by of_create.
+ *   - Work is ordered on the handle's stream (of_params.stream; NULL means the
+ *     CUDA default stream).  Nothing traps the GPU: errors are
+ *     negative return codes, with a message from of_last_error().
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef OFAST_H
+#define OFAST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OF_VERSION 1
+
+/* Return codes (negative = error). */
+#define OF_OK 0
+#define OF_ERR_ARG (-1)           /* invalid argument (null pointer, size, range) */
+#define OF_ERR_TOO_LARGE (-2)     /* request exceeds what the handle was created for */
+#define OF_ERR_CUDA (-3)          /* a CUDA runtime call failed (message in of_last_error) */
+#define OF_ERR_TIMEOUT (-4)       /* a bounded device-side wait expired */
+#define OF_ERR_UNSUPPORTED (-5)   /* valid but not implemented (e.g. harris_block != 7) */
+
+typedef struct of_handle of_handle;
+
+/* Creation parameters.  Zero fields take the default shown. */
+typedef struct of_params {
+    int32_t max_w, max_h;     /* largest level-0 frame accepted (required, > 0) */
+    int32_t max_levels;       /* pyramid levels per frame, 1..16 (default 8) */
+    int32_t max_features;     /* largest n_features per frame (default 1000, <= 8192) */
+    int32_t max_batch;        /* largest number of frames per call (default 1) */
+    float min_scale;          /* smallest pyramid scale accepted, > 1 (default 1.2);
+                                 scratch is sized for pyramids of this scale */
+    int32_t fast_t_lo;        /* per-cell fallback FAST threshold: a 30x30 cell with no
+                                 pixel scoring >= fast_t uses fast_t_lo instead.
+                                 0 (default) disables the fallback. */
+    int32_t cell;             /* fallback cell side in pixels (default 30) */
+    int32_t border;           /* pixels excluded at each level edge (default 19; >= orient_radius, >= 4) */
+    int32_t harris_block;     /* Harris window side (default 7; only 7 is implemented) */
+    int32_t orient_radius;    /* centroid disc radius (default 15; 1..15) */
+    void* stream;             /* cudaStream_t to order work on; NULL = the CUDA default stream */
+} of_params;
+
+/* One detected keypoint, 64 bytes.  Level-major, rank order within a level
+ * (Harris key descending, then y ascending, then x ascending). */
+typedef struct of_keypoint {
+    float x, y;           /* level-0 coordinates: (x_l, y_l) * scale^l */
+    int32_t x_l, y_l;     /* pixel position in its level */
+    int32_t level;
+    int32_t fast_score;   /* s(p): largest FAST threshold at which p passes */
+    float response;       /* Harris score det(M) - k trace(M)^2 times (1/(4*7*255))^4 */
+    float angle;          /* atan2(m01, m10), radians in (-pi, pi]; 0 when both are 0 */
+    int32_t A, B, C;      /* exact window sums of gx^2, gy^2, gx*gy */
+    int32_t m10, m01;     /* exact centroid moments over the disc */
+    int32_t reserved;
+    int64_t key;          /* exact integer Harris key: den*det(M) - num*trace(M)^2, k = num/den */
+} of_keypoint;
+
+/* One input frame for of_detect_batch. */
+typedef struct of_frame {
+    const uint8_t* img;   /* [device] uint8 image */
+    int32_t w, h, pitch;
+} of_frame;
+
+/* Create a handle; allocates all device scratch for max_batch frames of
+ * max_w x max_h with max_levels levels at min_scale.  Returns NULL on failure
+ * (message in of_last_error()). */
+of_handle* of_create(const of_params* p);
+
+/* Free the handle and its scratch.  NULL is ignored. */
+void of_destroy(of_handle* h);
+
+/* Detect keypoints in one frame.
+ *   img [device]          uint8 frame, w x h_px, `pitch` bytes per row (pitch >= w)
+ *   levels                pyramid levels, 1..max_levels
+ *   scale                 pyramid scale between levels, min_scale <= scale <= 4
+ *   fast_t                FAST threshold t of Eq. 1, 1..255
+ *   harris_k              Harris k of Eq. 3, 0 <= k <= 0.25, rounded to a multiple of 1e-6
+ *                         whose reduced denominator must be <= 3000 (e.g. 0.04 = 1/25)
+ *   n_features            keypoints per frame, split over levels by area, 0..max_features
+ *   out_kpts [device]     room for n_features records
+ * Returns the number of keypoints written (>= 0) or a negative OF_ERR_*.
+ * Synchronises the handle's stream to read the count back. */
+int of_detect(of_handle* h, const uint8_t* img, int w, int h_px, int pitch, int levels,
+              float scale, int fast_t, float harris_k, int n_features, of_keypoint* out_kpts);
+
+/* Detect keypoints in n_frames frames of any sizes in one batched launch
+ * sequence (replayed from a cached CUDA graph for a repeated batch shape).
+ *   frames [host]         n_frames descriptors, 1 <= n_frames <= max_batch
+ *   out_kpts [device]     n_frames * n_features records; frame i starts at i * n_features
+ *   out_counts [device]   n_frames int32: keypoints written per frame
+ * Other arguments as of_detect.  Asynchronous: returns OF_OK once the work is
+ * queued on the handle's stream; results are valid after that stream syncs. */
+int of_detect_batch(of_handle* h, const of_frame* frames, int n_frames, int levels,
+                    float scale, int fast_t, float harris_k, int n_features,
+                    of_keypoint* out_kpts, int32_t* out_counts);
+
+/* Copy an intermediate buffer of the most recent detect call into `dst`, for
+ * inspection and parity checks.  what:
+ *   OF_BUF_LEVEL  pyramid level image, w x h bytes, packed rows (pitch = w)
+ *   OF_BUF_SCORE  FAST score map, w x h bytes: s(p) where s(p) >= the lowest
+ *                 threshold in use (fast_t_lo if enabled, else fast_t), else 0;
+ *                 0 outside the detect region
+ *   OF_BUF_CELLT  per-cell threshold, ncx x ncy bytes (fast_t or fast_t_lo)
+ *   OF_BUF_CAND   NMS survivors, count x 16 bytes {int64 key; int32 x; int32 y},
+ *                 in no particular order
+ * dst [device] may be NULL to query the size.  dims [host] receives
+ * {w, h, count_or_ncx, ncy}.  Returns the byte size, or a negative OF_ERR_*.
+ * Synchronises the handle's stream. */
+#define OF_BUF_LEVEL 0
+#define OF_BUF_SCORE 1
+#define OF_BUF_CELLT 2
+#define OF_BUF_CAND 3
+int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int64_t dst_bytes,
+                   int32_t* dims);
+
+/* Stage timing: the next detect call on this handle runs its stages as
+ * separate launches and records events[i] (cudaEvent_t, created by the
+ * caller with timing enabled) on the handle's stream before stage i and
+ * events[5] after the last one:
+ *   0 pyramid (clear + resize)  1 FAST score  2 NMS + Harris  3 top-N  4 orientation.
+ * Results are identical to an untimed call.  Returns OF_OK or OF_ERR_ARG. */
+#define OF_N_STAGES 5
+int of_time_stages(of_handle* h, void* const* events);
+
+/* Host-only: the pyramid plan the detector uses for a W x H frame (no GPU
+ * needed).  ws, hs [host, levels ints] receive level sizes; quota [host,
+ * levels ints] receives the per-level feature quota for n_features.
+ * Returns OF_OK or OF_ERR_ARG. */
+int of_plan_levels(int W, int H, int levels, float scale, int n_features, int32_t* ws,
+                   int32_t* hs, int32_t* quota);
+
+/* Message for the last error on this host thread ("" if none). */
+const char* of_last_error(void);
+
+/* OF_VERSION of the loaded library. */
+int of_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFAST_H */

@@ -1,0 +1,253 @@
+"""Python binding of the GB300 Oriented FAST library (include/ofast.h).
+
+Argument marshalling only: every step of the detection chain runs in the CUDA
+kernels of ``csrc/``.  Functions carry the C names (``of_create``,
+``of_detect``, ``of_detect_batch``, ``of_destroy``, ``of_inspect``,
+``of_plan_levels``, ``of_last_error``, ``of_version``); device buffers are
+passed as torch CUDA tensors (or raw integer device addresses), host arrays
+as numpy arrays.  PyTorch provides device memory and streams, nothing else.
+
+The shared library is built in-tree by ``build.py``.  Loading fails loudly
+when it is missing: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB, build  # noqa: F401
+
+__all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspect", "of_plan_levels",
+           "of_time_stages", "OF_N_STAGES", "STAGE_NAMES",
+           "of_last_error", "of_version", "OfParams", "OfFrame", "OfKeypoint", "KEYPOINT_DTYPE",
+           "OF_BUF_LEVEL", "OF_BUF_SCORE", "OF_BUF_CELLT", "OF_BUF_CAND", "OfError", "load",
+           "Detector", "keypoints_to_numpy"]
+
+OF_OK, OF_ERR_ARG, OF_ERR_TOO_LARGE, OF_ERR_CUDA, OF_ERR_TIMEOUT, OF_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+OF_BUF_LEVEL, OF_BUF_SCORE, OF_BUF_CELLT, OF_BUF_CAND = 0, 1, 2, 3
+
+
+class OfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ofast error {code}: {msg}")
+        self.code = code
+
+
+class OfParams(C.Structure):
+    _fields_ = [("max_w", C.c_int32), ("max_h", C.c_int32), ("max_levels", C.c_int32),
+                ("max_features", C.c_int32), ("max_batch", C.c_int32), ("min_scale", C.c_float),
+                ("fast_t_lo", C.c_int32), ("cell", C.c_int32), ("border", C.c_int32),
+                ("harris_block", C.c_int32), ("orient_radius", C.c_int32), ("stream", C.c_void_p)]
+
+
+class OfKeypoint(C.Structure):
+    _fields_ = [("x", C.c_float), ("y", C.c_float), ("x_l", C.c_int32), ("y_l", C.c_int32),
+                ("level", C.c_int32), ("fast_score", C.c_int32), ("response", C.c_float),
+                ("angle", C.c_float), ("A", C.c_int32), ("B", C.c_int32), ("C", C.c_int32),
+                ("m10", C.c_int32), ("m01", C.c_int32), ("reserved", C.c_int32), ("key", C.c_int64)]
+
+
+class OfFrame(C.Structure):
+    _fields_ = [("img", C.c_void_p), ("w", C.c_int32), ("h", C.c_int32), ("pitch", C.c_int32)]
+
+
+KEYPOINT_DTYPE = np.dtype([("x", "f4"), ("y", "f4"), ("x_l", "i4"), ("y_l", "i4"), ("level", "i4"),
+                           ("fast_score", "i4"), ("response", "f4"), ("angle", "f4"), ("A", "i4"),
+                           ("B", "i4"), ("C", "i4"), ("m10", "i4"), ("m01", "i4"),
+                           ("reserved", "i4"), ("key", "i8")])
+assert KEYPOINT_DTYPE.itemsize == C.sizeof(OfKeypoint) == 64
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (must have been built by ``build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise OfError(OF_ERR_UNSUPPORTED, f"CUDA library not built: {path} (run paper_2506_07164_gb300.build())")
+    L = C.CDLL(path)
+    L.of_create.argtypes = [C.POINTER(OfParams)]
+    L.of_create.restype = C.c_void_p
+    L.of_destroy.argtypes = [C.c_void_p]
+    L.of_destroy.restype = None
+    L.of_detect.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
+                            C.c_int, C.c_float, C.c_int, C.c_void_p]
+    L.of_detect.restype = C.c_int
+    L.of_detect_batch.argtypes = [C.c_void_p, C.POINTER(OfFrame), C.c_int, C.c_int, C.c_float, C.c_int,
+                                  C.c_float, C.c_int, C.c_void_p, C.c_void_p]
+    L.of_detect_batch.restype = C.c_int
+    L.of_inspect.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64,
+                             C.POINTER(C.c_int32)]
+    L.of_inspect.restype = C.c_int64
+    L.of_plan_levels.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, C.c_int, C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.of_plan_levels.restype = C.c_int
+    L.of_last_error.argtypes = []
+    L.of_last_error.restype = C.c_char_p
+    L.of_version.argtypes = []
+    L.of_version.restype = C.c_int
+    L.of_time_stages.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
+    L.of_time_stages.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise OfError(rc, of_last_error())
+    return rc
+
+
+def of_last_error() -> str:
+    return load().of_last_error().decode()
+
+
+def of_version() -> int:
+    return int(load().of_version())
+
+
+def of_create(params: OfParams | None = None, **kw) -> int:
+    """Create a handle; ``kw`` fill an OfParams (``stream`` may be a torch.cuda.Stream)."""
+    p = params or OfParams()
+    for k, v in kw.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = int(v.cuda_stream)
+        setattr(p, k, v)
+    h = load().of_create(C.byref(p))
+    if not h:
+        raise OfError(OF_ERR_ARG, of_last_error())
+    return h
+
+
+def of_destroy(h: int) -> None:
+    load().of_destroy(h)
+
+
+def of_detect(h: int, img, w: int, h_px: int, pitch: int, levels: int, scale: float, fast_t: int,
+              harris_k: float, n_features: int, out_kpts) -> int:
+    return _check(load().of_detect(h, _ptr(img), w, h_px, pitch, levels, scale, fast_t, harris_k,
+                                   n_features, _ptr(out_kpts)))
+
+
+def of_detect_batch(h: int, frames, levels: int, scale: float, fast_t: int, harris_k: float,
+                    n_features: int, out_kpts, out_counts) -> int:
+    """``frames``: sequence of (img, w, h, pitch) with img a device tensor or address."""
+    arr = (OfFrame * len(frames))()
+    for i, (img, w, hh, pitch) in enumerate(frames):
+        arr[i] = OfFrame(_ptr(img), w, hh, pitch)
+    return _check(load().of_detect_batch(h, arr, len(frames), levels, scale, fast_t, harris_k,
+                                         n_features, _ptr(out_kpts), _ptr(out_counts)))
+
+
+def of_inspect(h: int, what: int, frame: int, level: int, dst=None, dst_bytes: int = 0):
+    """Returns (byte size, dims[4])."""
+    dims = (C.c_int32 * 4)()
+    n = _check(int(load().of_inspect(h, what, frame, level, _ptr(dst), dst_bytes, dims)))
+    return n, list(dims)
+
+
+OF_N_STAGES = 5
+STAGE_NAMES = ("pyramid", "fast", "nms_harris", "select", "orient")
+
+
+def of_time_stages(h: int, events) -> int:
+    """Record 6 events around the 5 stages of the next detect call.
+
+    ``events``: raw cudaEvent_t handles, or torch.cuda.Event(enable_timing=True)
+    objects that have been recorded once (torch creates them lazily)."""
+    hs = [e if isinstance(e, int) else int(e.cuda_event) for e in events]
+    if len(hs) != OF_N_STAGES + 1:
+        raise ValueError("need OF_N_STAGES + 1 events")
+    arr = (C.c_void_p * len(hs))(*hs)
+    return _check(load().of_time_stages(h, arr))
+
+
+def of_plan_levels(W: int, H: int, levels: int, scale: float, n_features: int):
+    ws = (C.c_int32 * levels)()
+    hs = (C.c_int32 * levels)()
+    q = (C.c_int32 * levels)()
+    rc = load().of_plan_levels(W, H, levels, scale, n_features, ws, hs, q)
+    if rc != 0:
+        raise OfError(rc, "bad plan arguments")
+    return list(ws), list(hs), list(q)
+
+
+def keypoints_to_numpy(t) -> np.ndarray:
+    """A uint8 torch tensor holding of_keypoint records -> structured numpy array."""
+    b = t.detach().to("cpu").contiguous().numpy().view(np.uint8).reshape(-1)
+    return b.view(KEYPOINT_DTYPE)
+
+
+class Detector:
+    """Convenience owner of a handle and its output buffers (torch CUDA tensors)."""
+
+    def __init__(self, max_w: int, max_h: int, max_levels: int = 8, max_features: int = 1000,
+                 max_batch: int = 1, fast_t_lo: int = 0, min_scale: float = 1.2, border: int = 19,
+                 cell: int = 30, orient_radius: int = 15, stream=None, device="cuda"):
+        """stream: a torch.cuda.Stream (default: the current stream of `device`)."""
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            if stream is None:
+                stream = torch.cuda.current_stream(self.device)
+            self.stream = stream
+            self.h = of_create(max_w=max_w, max_h=max_h, max_levels=max_levels,
+                               max_features=max_features, max_batch=max_batch, fast_t_lo=fast_t_lo,
+                               min_scale=min_scale, border=border, cell=cell,
+                               orient_radius=orient_radius, stream=stream)
+        self.max_features = max_features
+        self.max_batch = max_batch
+        self.out = torch.empty(max_batch * max(max_features, 1) * 64, dtype=torch.uint8, device=self.device)
+        self.counts = torch.zeros(max_batch, dtype=torch.int32, device=self.device)
+
+    def close(self):
+        if self.h:
+            of_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def detect(self, img, levels=8, scale=1.2, fast_t=20, harris_k=0.04, n_features=1000) -> np.ndarray:
+        """One frame (2-D uint8 CUDA tensor, rows may be strided) -> numpy keypoints."""
+        assert img.dtype == self.torch.uint8 and img.is_cuda and img.dim() == 2 and img.stride(1) == 1
+        n = of_detect(self.h, img, img.shape[1], img.shape[0], img.stride(0), levels, scale, fast_t,
+                      harris_k, n_features, self.out)
+        return keypoints_to_numpy(self.out[: n * 64])
+
+    def detect_batch(self, imgs, levels=8, scale=1.2, fast_t=20, harris_k=0.04, n_features=1000):
+        """Queue a batch (list of 2-D uint8 CUDA tensors); returns (records tensor, counts tensor)."""
+        frames = [(im, im.shape[1], im.shape[0], im.stride(0)) for im in imgs]
+        of_detect_batch(self.h, frames, levels, scale, fast_t, harris_k, n_features, self.out, self.counts)
+        return self.out, self.counts
+
+    def batch_results(self, n_frames: int, n_features: int):
+        """Per-frame numpy keypoints of the last batch (synchronises)."""
+        recs = keypoints_to_numpy(self.out[: n_frames * n_features * 64])
+        cnt = self.counts[:n_frames].cpu().numpy()
+        return [recs[i * n_features: i * n_features + int(cnt[i])] for i in range(n_frames)]
+
+    def inspect(self, what: int, frame: int = 0, level: int = 0):
+        n, dims = of_inspect(self.h, what, frame, level)
+        buf = self.torch.empty(max(n, 1), dtype=self.torch.uint8, device=self.device)
+        n, dims = of_inspect(self.h, what, frame, level, buf, n)
+        return buf[:n].cpu().numpy(), dims

@@ -1,0 +1,152 @@
+// Orientation by intensity centroid (Fig. 1 "Centroid") and the output
+// records.  One warp per output slot (frame, level, rank):
+//   - Harris sums A, B, C of the kept keypoint (Eqs. 2-4), lanes over the 49
+//     window positions, warp reduction;
+//   - moments m10 = sum u I, m01 = sum v I over the disc u^2 + v^2 <= r^2,
+//     lane = column u, loop over rows v, warp reduction;
+//   - angle = atan2f(m01, m10) (both moments are exact int32, |m| < 2^24, so
+//     their float conversion is exact);
+//   - response = key / kden * (1 / (4*7*255))^4 in float64, stored as float.
+// Records are level-major in rank order: the slot of a kept keypoint is the
+// number of keypoints kept by the frame's earlier levels plus its rank.
+#include <cuda_runtime.h>
+
+#include "of_internal.h"
+
+namespace ofk {
+
+__global__ void __launch_bounds__(ORIENT_WARPS * 32)
+k_orient(const Img* __restrict__ imgs, int n_img, const Call* __restrict__ call) {
+    const int slot = blockIdx.x * ORIENT_WARPS + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (slot >= call->total_slots) return;
+    int lo = 0, hi = n_img - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (imgs[mid].slot0 <= slot) lo = mid; else hi = mid - 1;
+    }
+    const Img& I = imgs[lo];
+    const int rank = slot - I.slot0;
+    const int levels = call->levels;
+    const Img* F = imgs + I.frame * levels;
+
+    // The frame's first slot publishes its keypoint count.
+    if (slot == I.frame * call->n_features) {
+        if (lane == 0) {
+            int total = 0;
+            for (int l = 0; l < levels; ++l) total += F[l].ctr[1];
+            call->counts[I.frame] = total;
+        }
+    }
+    if (rank >= I.quota || rank >= I.ctr[1]) return;
+    int base = 0;
+    for (int l = 0; l < I.level; ++l) base += F[l].ctr[1];
+
+    const uint32_t yx = I.kyx[rank];
+    const int x = (int)(yx & 0xFFFFu), y = (int)(yx >> 16);
+    const uint8_t* img = I.img;
+    const int pitch = I.pitch;
+
+    // Harris sums over the 7 x 7 window.
+    int a = 0, b = 0, c = 0;
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+        const int p = lane + 32 * rep;
+        if (p < 49) {
+            const int u = p % 7 - 3, v = p / 7 - 3;
+            const uint8_t* q = img + (size_t)(y + v) * pitch + (x + u);
+            const int l0 = __ldg(q - pitch - 1), c0 = __ldg(q - pitch), r0 = __ldg(q - pitch + 1);
+            const int l1 = __ldg(q - 1), r1 = __ldg(q + 1);
+            const int l2 = __ldg(q + pitch - 1), c2 = __ldg(q + pitch), r2 = __ldg(q + pitch + 1);
+            const int gx = (r0 - l0) + 2 * (r1 - l1) + (r2 - l2);
+            const int gy = (l2 - l0) + 2 * (c2 - c0) + (r2 - r0);
+            a += gx * gx;
+            b += gy * gy;
+            c += gx * gy;
+        }
+    }
+    a = __reduce_add_sync(0xFFFFFFFFu, a);
+    b = __reduce_add_sync(0xFFFFFFFFu, b);
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+
+    // Centroid moments.
+    const int R = call->radius;
+    const int u = lane - 15;
+    int m10 = 0, m01 = 0;
+    if (u >= -R && u <= R) {
+        for (int v = -R; v <= R; ++v) {
+            if (u * u + v * v <= R * R) {
+                const int iv = __ldg(img + (size_t)(y + v) * pitch + (x + u));
+                m10 += u * iv;
+                m01 += v * iv;
+            }
+        }
+    }
+    m10 = __reduce_add_sync(0xFFFFFFFFu, m10);
+    m01 = __reduce_add_sync(0xFFFFFFFFu, m01);
+
+    if (lane == 0) {
+        const uint64_t okey = I.kkey[rank];
+        const int64_t key = (int64_t)(okey ^ 0x8000000000000000ull);
+        const double f = 1.0 / (4.0 * 7.0 * 255.0);
+        const double resp = ((double)key / (double)call->kden) * (f * f * f * f);
+        of_keypoint k;
+        k.x = (float)((double)x * I.lscale);
+        k.y = (float)((double)y * I.lscale);
+        k.x_l = x;
+        k.y_l = y;
+        k.level = I.level;
+        k.fast_score = I.score[(size_t)y * I.spitch + x];
+        k.response = (float)resp;
+        k.angle = (m10 == 0 && m01 == 0) ? 0.0f : atan2f((float)m01, (float)m10);
+        k.A = a;
+        k.B = b;
+        k.C = c;
+        k.m10 = m10;
+        k.m01 = m01;
+        k.reserved = 0;
+        k.key = key;
+        of_keypoint* dst = call->out + (size_t)I.frame * call->n_features + base + rank;
+        const uint4* src = reinterpret_cast<const uint4*>(&k);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d4[i] = src[i];
+    }
+}
+
+void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream) {
+    if (total_slots <= 0) return;
+    const int blocks = (total_slots + ORIENT_WARPS - 1) / ORIENT_WARPS;
+    k_orient<<<blocks, ORIENT_WARPS * 32, 0, (cudaStream_t)stream>>>(imgs, n_img, call);
+}
+
+// ---------------------------------------------------------------- inspect
+__global__ void k_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t* dst) {
+    const Img& I = imgs[img];
+    const int n = I.ncx * I.ncy;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = (uint8_t)((t_hi != t_lo && I.cell[i]) ? t_hi : t_lo);
+}
+
+__global__ void k_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst) {
+    const Img& I = imgs[img];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int64_t* d = reinterpret_cast<int64_t*>(dst + 16 * (size_t)i);
+        int32_t* d32 = reinterpret_cast<int32_t*>(dst + 16 * (size_t)i + 8);
+        d[0] = (int64_t)(I.ckey[i] ^ 0x8000000000000000ull);
+        d32[0] = (int32_t)(I.cyx[i] & 0xFFFFu);
+        d32[1] = (int32_t)(I.cyx[i] >> 16);
+    }
+}
+
+void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t* dst,
+                          void* stream) {
+    k_inspect_cells<<<64, 256, 0, (cudaStream_t)stream>>>(imgs, img, t_hi, t_lo, dst);
+}
+
+void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream) {
+    if (n <= 0) return;
+    k_inspect_cands<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(imgs, img, n, dst);
+}
+
+}  // namespace ofk

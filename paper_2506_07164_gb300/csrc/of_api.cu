@@ -1,0 +1,775 @@
+// Runtime behind the C ABI of include/ofast.h: handle and scratch arena,
+// batch plans (level sizes, tiling, resize tables, arena layout), one CUDA
+// graph per plan, pointer rebinding between calls, inspection and errors.
+//
+// A plan is built once per batch shape (frame sizes and pitches, levels,
+// scale, thresholds, k, n_features).  Its kernels read every pointer from a
+// small device-side descriptor block, so a replay with new frame or output
+// pointers only re-uploads that block (from pinned staging memory) before
+// launching the same graph.  The arena is allocated once by of_create for the
+// largest batch the handle accepts; detect calls never allocate device memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "of_internal.h"
+#include "of_plan.h"
+#include "ofast.h"
+
+namespace ofk {
+void set_select_smem_limit(int bytes);
+}
+
+using namespace ofk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define OF_CK(call)                                                                   \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(OF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct FrameKey {
+    int w, h, pitch;
+    bool copy;  // level 0 is copied into the arena (unaligned input)
+    bool operator==(const FrameKey& o) const {
+        return w == o.w && h == o.h && pitch == o.pitch && copy == o.copy;
+    }
+};
+
+struct Settings {
+    int levels;
+    float scale;
+    int t_hi, t_lo;
+    int64_t knum, kden;
+    int n_features;
+    int border, cell, radius;
+};
+
+// Arena layout of one batch.
+struct ImgLayout {
+    int w = 0, h = 0;
+    int pitch = 0, spitch = 0;
+    int ncx = 0, ncy = 0, cap = 0, quota = 0;
+    int tiles_x = 0, tiles_y = 0, tile_x0 = 0;
+    bool det = false;  // detect region not empty
+    size_t lev = 0, score = 0, cell = 0, ckey = 0, cyx = 0, kkey = 0, kyx = 0, ctr = 0;
+    double lscale = 1.0;
+};
+
+struct Layout {
+    std::vector<ImgLayout> img;  // frame-major, level-minor
+    size_t zero_end = 0;         // [0, zero_end) is cleared before every call
+    size_t total = 0;
+};
+
+constexpr size_t kAlign = 256;
+constexpr int kStages = 5;
+
+// Lay out one batch.  `quota_each` overrides the per-level quotas (capacity sizing).
+Layout make_layout(const std::vector<FrameKey>& frames, const Settings& s, int quota_each) {
+    Layout L;
+    const int nl = s.levels;
+    L.img.resize(frames.size() * nl);
+    std::vector<int32_t> ws(nl), hs(nl), q(nl);
+    std::vector<double> ls(nl);
+    ofh::level_quotas(s.n_features, nl, s.scale, q.data());
+    // Pass 1: geometry.
+    for (size_t f = 0; f < frames.size(); ++f) {
+        ofh::level_sizes(frames[f].w, frames[f].h, nl, s.scale, ws.data(), hs.data(), ls.data());
+        bool alive = true;
+        for (int l = 0; l < nl; ++l) {
+            ImgLayout& I = L.img[f * nl + l];
+            if (ws[l] < 1 || hs[l] < 1) alive = false;
+            I.quota = quota_each >= 0 ? quota_each : q[l];
+            I.lscale = ls[l];
+            if (!alive) continue;
+            I.w = ws[l];
+            I.h = hs[l];
+            I.pitch = (l == 0 && !frames[f].copy) ? frames[f].pitch : (int)align_up(I.w, 16);
+            const int rw = I.w - 2 * s.border, rh = I.h - 2 * s.border;
+            if (rw > 0 && rh > 0) {
+                I.det = true;
+                I.spitch = (int)align_up(I.w, 16);
+                I.ncx = (rw + s.cell - 1) / s.cell;
+                I.ncy = (rh + s.cell - 1) / s.cell;
+                I.cap = ((rw + 1) / 2) * ((rh + 1) / 2);
+                I.tile_x0 = s.border & ~15;
+                I.tiles_x = (I.w - s.border - I.tile_x0 + TILE_W - 1) / TILE_W;
+                I.tiles_y = (rh + TILE_H - 1) / TILE_H;
+            }
+        }
+    }
+    // Pass 2: offsets.  Cleared region first: counters, then cell flags.
+    size_t off = 0;
+    for (auto& I : L.img) {
+        I.ctr = off;
+        off += 4 * sizeof(int32_t);
+    }
+    off = align_up(off, kAlign);
+    for (auto& I : L.img) {
+        if (!I.det) continue;
+        I.cell = off;
+        off = align_up(off + sizeof(uint32_t) * I.ncx * I.ncy, 16);
+    }
+    off = align_up(off, kAlign);
+    L.zero_end = off;
+    for (size_t f = 0; f < frames.size(); ++f) {
+        for (int l = 0; l < nl; ++l) {
+            ImgLayout& I = L.img[f * nl + l];
+            if (I.w == 0) continue;
+            if (l > 0 || frames[f].copy) {
+                I.lev = off;
+                off = align_up(off + (size_t)I.pitch * I.h, kAlign);
+            }
+        }
+    }
+    for (auto& I : L.img) {
+        if (!I.det) continue;
+        I.score = off;
+        off = align_up(off + (size_t)I.spitch * I.h, kAlign);
+        I.ckey = off;
+        off = align_up(off + sizeof(uint64_t) * I.cap, kAlign);
+        I.cyx = off;
+        off = align_up(off + sizeof(uint32_t) * I.cap, kAlign);
+        I.kkey = off;
+        off = align_up(off + sizeof(uint64_t) * std::max(I.quota, 1), kAlign);
+        I.kyx = off;
+        off = align_up(off + sizeof(uint32_t) * std::max(I.quota, 1), kAlign);
+    }
+    L.total = off;
+    return L;
+}
+
+struct Plan {
+    std::vector<FrameKey> frames;
+    Settings s{};
+    Layout lay;
+    std::vector<Img> h_img;
+    std::vector<Resize> h_rs;
+    std::vector<int> rs_begin;   // jobs of level l: [rs_begin[l], rs_begin[l+1])
+    std::vector<int> rsp_begin;  // prefix array offset of level l
+    std::vector<int> rs_tiles;   // tiles of level l
+    std::vector<int32_t> rs_prefix, det_list, det_prefix, tables;
+    int det_tiles = 0, max_quota = 0, total_slots = 0, n_img = 0;
+    Call h_call{};
+    uint8_t* dbuf = nullptr;
+    size_t off_call = 0, off_img = 0, off_rs = 0, off_rsp = 0, off_dl = 0, off_dp = 0, off_tab = 0;
+    size_t header_bytes = 0;
+    uint8_t* stage[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int stage_i = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t stage_exec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::vector<const uint8_t*> bound_src;
+    of_keypoint* bound_out = nullptr;
+    int32_t* bound_counts = nullptr;
+    bool bound = false;
+    uint64_t stamp = 0;
+
+    Img* d_img() const { return reinterpret_cast<Img*>(dbuf + off_img); }
+    Resize* d_rs() const { return reinterpret_cast<Resize*>(dbuf + off_rs); }
+    Call* d_call() const { return reinterpret_cast<Call*>(dbuf + off_call); }
+    const int32_t* d_rsp() const { return reinterpret_cast<const int32_t*>(dbuf + off_rsp); }
+    const int32_t* d_dl() const { return reinterpret_cast<const int32_t*>(dbuf + off_dl); }
+    const int32_t* d_dp() const { return reinterpret_cast<const int32_t*>(dbuf + off_dp); }
+};
+
+void free_plan(Plan* p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    for (auto& x : p->stage_exec)
+        if (x) cudaGraphExecDestroy(x);
+    for (int i = 0; i < 2; ++i) {
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+        if (p->stage[i]) cudaFreeHost(p->stage[i]);
+    }
+    if (p->dbuf) cudaFree(p->dbuf);
+    delete p;
+}
+
+}  // namespace
+
+struct of_handle {
+    of_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    uint8_t* arena = nullptr;
+    size_t arena_bytes = 0;
+    int32_t* d_counts = nullptr;  // of_detect's per-frame count
+    int32_t* h_count = nullptr;   // pinned
+    std::vector<Plan*> plans;
+    Plan* last = nullptr;
+    uint64_t clock = 0;
+    cudaEvent_t stage_ev[6] = {};  // when set: recorded around each stage of the next call
+    bool stage_timing = false;
+};
+
+namespace {
+
+constexpr int kMaxPlans = 8;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Enqueue stages [first, last) of a plan on `st`:
+//   0 clear counters and cell flags, resize levels 1..L-1 (pyramid)
+//   1 FAST score + cell flags      2 NMS + Harris keys
+//   3 top-N per level              4 orientation + output records
+void enqueue_stages(of_handle* H, Plan* P, int first, int last, cudaStream_t st) {
+    const Settings& s = P->s;
+    const int nl = s.levels;
+    for (int stage = first; stage < last; ++stage) {
+        switch (stage) {
+            case 0:
+                cudaMemsetAsync(H->arena, 0, P->lay.zero_end, st);
+                for (int l = 1; l < nl; ++l) {
+                    const int nj = P->rs_begin[l + 1] - P->rs_begin[l];
+                    if (nj > 0)
+                        launch_resize(P->d_rs() + P->rs_begin[l], P->d_rsp() + P->rsp_begin[l], nj,
+                                      P->rs_tiles[l], st);
+                }
+                break;
+            case 1:
+                launch_fast(P->d_img(), P->d_dl(), P->d_dp(), (int)P->det_list.size(),
+                            P->det_tiles, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell, st);
+                break;
+            case 2:
+                launch_nms_harris(P->d_img(), P->d_dl(), P->d_dp(), (int)P->det_list.size(),
+                                  P->det_tiles, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell, st);
+                break;
+            case 3:
+                launch_select(P->d_img(), P->n_img, P->d_call(), P->max_quota, st);
+                break;
+            case 4:
+                launch_orient(P->d_img(), P->n_img, P->d_call(), P->total_slots, st);
+                break;
+        }
+    }
+}
+
+cudaError_t capture(of_handle* H, Plan* P, int first, int last, cudaGraph_t* g) {
+    cudaStream_t cs = H->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    enqueue_stages(H, P, first, last, cs);
+    const cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(cs, g);
+    return e != cudaSuccess ? e : le;
+}
+
+int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings& s,
+               Plan** out) {
+    Plan* P = new Plan();
+    P->frames = frames;
+    P->s = s;
+    P->lay = make_layout(frames, s, -1);
+    if (P->lay.total > H->arena_bytes) {
+        free_plan(P);
+        return fail(OF_ERR_TOO_LARGE, "batch needs " + std::to_string(P->lay.total) +
+                                          " bytes of scratch; handle has " +
+                                          std::to_string(H->arena_bytes));
+    }
+    const int nl = s.levels;
+    const int nf = (int)frames.size();
+    P->n_img = nf * nl;
+    uint8_t* A = H->arena;
+
+    // Image descriptors.
+    P->h_img.resize(P->n_img);
+    int slot = 0;
+    for (int f = 0; f < nf; ++f) {
+        for (int l = 0; l < nl; ++l) {
+            const ImgLayout& L = P->lay.img[f * nl + l];
+            Img& I = P->h_img[f * nl + l];
+            std::memset(&I, 0, sizeof(I));
+            I.img = (l == 0 && !frames[f].copy) ? nullptr : A + L.lev;  // bound per call
+            I.w = L.w;
+            I.h = L.h;
+            I.pitch = L.pitch;
+            I.spitch = L.spitch;
+            I.ncx = L.ncx;
+            I.ncy = L.ncy;
+            I.cand_cap = L.cap;
+            I.quota = L.quota;
+            I.frame = f;
+            I.level = l;
+            I.lscale = L.lscale;
+            I.ctr = reinterpret_cast<int32_t*>(A + L.ctr);
+            if (L.det) {
+                I.score = A + L.score;
+                I.cell = reinterpret_cast<uint32_t*>(A + L.cell);
+                I.ckey = reinterpret_cast<uint64_t*>(A + L.ckey);
+                I.cyx = reinterpret_cast<uint32_t*>(A + L.cyx);
+                I.kkey = reinterpret_cast<uint64_t*>(A + L.kkey);
+                I.kyx = reinterpret_cast<uint32_t*>(A + L.kyx);
+                I.tiles_x = L.tiles_x;
+                I.tiles_y = L.tiles_y;
+                I.tile_x0 = L.tile_x0;
+            } else {
+                I.quota = 0;  // an empty level keeps nothing; its share is not redistributed
+            }
+            I.slot0 = slot;
+            slot += L.quota;
+            P->max_quota = std::max(P->max_quota, I.quota);
+        }
+    }
+    P->total_slots = slot;
+
+    // Resize jobs and their tables (deduplicated per (n_src, n_dst)).
+    std::map<std::pair<int, int>, int> tab_of;
+    auto table = [&](int n_src, int n_dst) {
+        auto key = std::make_pair(n_src, n_dst);
+        auto it = tab_of.find(key);
+        if (it != tab_of.end()) return it->second;
+        const int at = (int)P->tables.size();
+        P->tables.resize(at + n_dst);
+        ofh::resize_table(n_src, n_dst, P->tables.data() + at);
+        tab_of[key] = at;
+        return at;
+    };
+    std::vector<std::pair<int, int>> tab_idx;  // (xtab, ytab) offsets per job
+    P->rs_begin.assign(nl + 1, 0);
+    P->rsp_begin.assign(nl + 1, 0);
+    P->rs_tiles.assign(nl + 1, 0);
+    for (int l = 1; l < nl; ++l) {
+        P->rs_begin[l] = (int)P->h_rs.size();
+        P->rsp_begin[l] = (int)P->rs_prefix.size();
+        int tiles = 0;
+        for (int f = 0; f < nf; ++f) {
+            const Img& S = P->h_img[f * nl + l - 1];
+            const Img& D = P->h_img[f * nl + l];
+            if (D.w == 0 || S.w == 0) continue;
+            Resize R;
+            std::memset(&R, 0, sizeof(R));
+            R.src = S.img;  // level 0 bound per call
+            R.dst = const_cast<uint8_t*>(D.img);
+            R.sw = S.w;
+            R.sh = S.h;
+            R.spitch = S.pitch;
+            R.dw = D.w;
+            R.dh = D.h;
+            R.dpitch = D.pitch;
+            R.tiles_x = (D.w + RS_TILE_W - 1) / RS_TILE_W;
+            R.tiles_y = (D.h + RS_TILE_H - 1) / RS_TILE_H;
+            tab_idx.emplace_back(table(S.w, D.w), table(S.h, D.h));
+            P->rs_prefix.push_back(tiles);
+            tiles += R.tiles_x * R.tiles_y;
+            P->h_rs.push_back(R);
+        }
+        P->rs_tiles[l] = tiles;
+    }
+    P->rs_begin[nl] = (int)P->h_rs.size();
+    for (int i = 0; i < P->n_img; ++i) {
+        const Img& I = P->h_img[i];
+        if (I.tiles_x > 0) {
+            P->det_list.push_back(i);
+            P->det_prefix.push_back(P->det_tiles);
+            P->det_tiles += I.tiles_x * I.tiles_y;
+        }
+    }
+
+    Call& C = P->h_call;
+    std::memset(&C, 0, sizeof(C));
+    C.knum = s.knum;
+    C.kden = s.kden;
+    C.n_frames = nf;
+    C.levels = nl;
+    C.n_features = s.n_features;
+    C.t_hi = s.t_hi;
+    C.t_lo = s.t_lo;
+    C.border = s.border;
+    C.cell = s.cell;
+    C.radius = s.radius;
+    C.n_img = P->n_img;
+    C.total_slots = P->total_slots;
+
+    // Device descriptor block: [Call | Img[] | Resize[]] (re-uploaded when
+    // pointers change) then [resize prefix | detect list | detect prefix | tables].
+    size_t off = 0;
+    P->off_call = off;
+    off = align_up(off + sizeof(Call), 16);
+    P->off_img = off;
+    off = align_up(off + sizeof(Img) * P->n_img, 16);
+    P->off_rs = off;
+    off = align_up(off + sizeof(Resize) * std::max<size_t>(P->h_rs.size(), 1), 16);
+    P->header_bytes = off;
+    P->off_rsp = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->rs_prefix.size(), 1), 16);
+    P->off_dl = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->det_list.size(), 1), 16);
+    P->off_dp = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->det_prefix.size(), 1), 16);
+    P->off_tab = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->tables.size(), 1), 16);
+    cudaError_t e = cudaMalloc(&P->dbuf, off);
+    if (e != cudaSuccess) {
+        free_plan(P);
+        return fail(OF_ERR_CUDA, std::string("cudaMalloc(descriptors): ") + cudaGetErrorString(e));
+    }
+    const int32_t* d_tab = reinterpret_cast<const int32_t*>(P->dbuf + P->off_tab);
+    for (size_t i = 0; i < P->h_rs.size(); ++i) {
+        P->h_rs[i].xtab = d_tab + tab_idx[i].first;
+        P->h_rs[i].ytab = d_tab + tab_idx[i].second;
+    }
+    std::vector<uint8_t> blob(off, 0);
+    auto put = [&](size_t at, const void* src, size_t n) {
+        if (n) std::memcpy(blob.data() + at, src, n);
+    };
+    put(P->off_call, &C, sizeof(C));
+    put(P->off_img, P->h_img.data(), sizeof(Img) * P->h_img.size());
+    put(P->off_rs, P->h_rs.data(), sizeof(Resize) * P->h_rs.size());
+    put(P->off_rsp, P->rs_prefix.data(), sizeof(int32_t) * P->rs_prefix.size());
+    put(P->off_dl, P->det_list.data(), sizeof(int32_t) * P->det_list.size());
+    put(P->off_dp, P->det_prefix.data(), sizeof(int32_t) * P->det_prefix.size());
+    put(P->off_tab, P->tables.data(), sizeof(int32_t) * P->tables.size());
+    e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaMallocHost(&P->stage[i], P->header_bytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        free_plan(P);
+        return fail(OF_ERR_CUDA, std::string("plan setup: ") + cudaGetErrorString(e));
+    }
+
+    // Capture the launch sequence once as one graph, and once per stage
+    // (the per-stage graphs serve calls that time each stage with events).
+    cudaGraph_t g = nullptr;
+    e = capture(H, P, 0, kStages, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    for (int st = 0; st < kStages && e == cudaSuccess; ++st) {
+        g = nullptr;
+        e = capture(H, P, st, st + 1, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&P->stage_exec[st], g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    if (e != cudaSuccess) {
+        free_plan(P);
+        return fail(OF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    *out = P;
+    return OF_OK;
+}
+
+// Point the plan at this call's frames and output, re-uploading the
+// descriptor header when anything changed.
+int bind_plan(of_handle* H, Plan* P, const of_frame* frames, of_keypoint* out, int32_t* counts) {
+    const int nl = P->s.levels;
+    const int nf = (int)P->frames.size();
+    bool changed = !P->bound || P->bound_out != out || P->bound_counts != counts;
+    if (!changed)
+        for (int f = 0; f < nf; ++f)
+            if (!P->frames[f].copy && P->bound_src[f] != frames[f].img) changed = true;
+    if (!changed) return OF_OK;
+    P->bound_src.assign(nf, nullptr);
+    for (int f = 0; f < nf; ++f) {
+        if (P->frames[f].copy) continue;
+        P->bound_src[f] = frames[f].img;
+        P->h_img[f * nl].img = frames[f].img;
+    }
+    // Level-1 resize jobs read level 0.
+    if (nl > 1) {
+        for (int i = P->rs_begin[1]; i < P->rs_begin[2]; ++i) {
+            Resize& R = P->h_rs[i];
+            for (int f = 0; f < nf; ++f)
+                if (R.dst == P->h_img[f * nl + 1].img) R.src = P->h_img[f * nl].img;
+        }
+    }
+    P->h_call.out = out;
+    P->h_call.counts = counts;
+    P->bound_out = out;
+    P->bound_counts = counts;
+    P->bound = true;
+    const int si = P->stage_i;
+    P->stage_i ^= 1;
+    OF_CK(cudaEventSynchronize(P->ev[si]));
+    uint8_t* st = P->stage[si];
+    std::memcpy(st + P->off_call, &P->h_call, sizeof(Call));
+    std::memcpy(st + P->off_img, P->h_img.data(), sizeof(Img) * P->h_img.size());
+    std::memcpy(st + P->off_rs, P->h_rs.data(), sizeof(Resize) * P->h_rs.size());
+    OF_CK(cudaMemcpyAsync(P->dbuf, st, P->header_bytes, cudaMemcpyHostToDevice, H->stream));
+    OF_CK(cudaEventRecord(P->ev[si], H->stream));
+    return OF_OK;
+}
+
+Plan* find_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings& s) {
+    for (Plan* P : H->plans) {
+        if (P->frames.size() != frames.size()) continue;
+        const Settings& t = P->s;
+        if (t.levels != s.levels || t.scale != s.scale || t.t_hi != s.t_hi || t.t_lo != s.t_lo ||
+            t.knum != s.knum || t.kden != s.kden || t.n_features != s.n_features)
+            continue;
+        bool same = true;
+        for (size_t i = 0; i < frames.size() && same; ++i) same = P->frames[i] == frames[i];
+        if (same) return P;
+    }
+    return nullptr;
+}
+
+int run_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, float scale,
+              int fast_t, float harris_k, int n_features, of_keypoint* out, int32_t* counts) {
+    if (!H) return fail(OF_ERR_ARG, "null handle");
+    if (!frames || n_frames < 1) return fail(OF_ERR_ARG, "no frames");
+    if (n_frames > H->p.max_batch)
+        return fail(OF_ERR_TOO_LARGE, "n_frames exceeds max_batch");
+    if (levels < 1 || levels > H->p.max_levels) return fail(OF_ERR_ARG, "levels out of range");
+    if (!(scale >= H->p.min_scale && scale <= 4.0f))
+        return fail(OF_ERR_ARG, "scale must be in [min_scale, 4]");
+    if (fast_t < 1 || fast_t > 255) return fail(OF_ERR_ARG, "fast_t must be in 1..255");
+    if (n_features < 0 || n_features > H->p.max_features)
+        return fail(OF_ERR_ARG, "n_features out of range");
+    if (!counts || (n_features > 0 && !out)) return fail(OF_ERR_ARG, "null output pointer");
+    Settings s{};
+    s.levels = levels;
+    s.scale = scale;
+    s.t_hi = fast_t;
+    s.t_lo = (H->p.fast_t_lo > 0 && H->p.fast_t_lo < fast_t) ? H->p.fast_t_lo : fast_t;
+    if (!ofh::k_fraction(harris_k, &s.knum, &s.kden))
+        return fail(OF_ERR_ARG, "harris_k must be in [0, 0.25] with a reduced denominator <= 3000");
+    s.n_features = n_features;
+    s.border = H->p.border;
+    s.cell = H->p.cell;
+    s.radius = H->p.orient_radius;
+    std::vector<FrameKey> keys(n_frames);
+    for (int i = 0; i < n_frames; ++i) {
+        const of_frame& F = frames[i];
+        if (!F.img || F.w < 1 || F.h < 1 || F.pitch < F.w)
+            return fail(OF_ERR_ARG, "bad frame " + std::to_string(i));
+        if (F.w > H->p.max_w || F.h > H->p.max_h)
+            return fail(OF_ERR_TOO_LARGE, "frame larger than max_w x max_h");
+        const bool aligned = ((uintptr_t)F.img % 16 == 0) && (F.pitch % 16 == 0);
+        keys[i] = FrameKey{F.w, F.h, F.pitch, !aligned};
+    }
+    DeviceGuard dg(H->device);
+    Plan* P = find_plan(H, keys, s);
+    if (!P) {
+        if ((int)H->plans.size() >= kMaxPlans) {
+            auto it = std::min_element(H->plans.begin(), H->plans.end(),
+                                       [](Plan* a, Plan* b) { return a->stamp < b->stamp; });
+            OF_CK(cudaStreamSynchronize(H->stream));
+            if (H->last == *it) H->last = nullptr;
+            free_plan(*it);
+            H->plans.erase(it);
+        }
+        const int rc = build_plan(H, keys, s, &P);
+        if (rc != OF_OK) return rc;
+        H->plans.push_back(P);
+    }
+    P->stamp = ++H->clock;
+    for (int i = 0; i < n_frames; ++i) {
+        if (!keys[i].copy) continue;
+        const Img& I = P->h_img[i * levels];
+        OF_CK(cudaMemcpy2DAsync(const_cast<uint8_t*>(I.img), I.pitch, frames[i].img, frames[i].pitch,
+                                frames[i].w, frames[i].h, cudaMemcpyDeviceToDevice, H->stream));
+    }
+    const int rc = bind_plan(H, P, frames, out, counts);
+    if (rc != OF_OK) return rc;
+    if (n_features == 0) OF_CK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_frames, H->stream));
+    if (H->stage_timing) {
+        for (int st = 0; st < kStages; ++st) {
+            OF_CK(cudaEventRecord(H->stage_ev[st], H->stream));
+            OF_CK(cudaGraphLaunch(P->stage_exec[st], H->stream));
+        }
+        OF_CK(cudaEventRecord(H->stage_ev[kStages], H->stream));
+        H->stage_timing = false;
+    } else {
+        OF_CK(cudaGraphLaunch(P->exec, H->stream));
+    }
+    H->last = P;
+    return OF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int of_version(void) { return OF_VERSION; }
+
+const char* of_last_error(void) { return g_err.c_str(); }
+
+of_handle* of_create(const of_params* pin) {
+    if (!pin) {
+        fail(OF_ERR_ARG, "null params");
+        return nullptr;
+    }
+    of_params p = *pin;
+    if (p.max_levels == 0) p.max_levels = 8;
+    if (p.max_features == 0) p.max_features = 1000;
+    if (p.max_batch == 0) p.max_batch = 1;
+    if (p.min_scale == 0.0f) p.min_scale = 1.2f;
+    if (p.cell == 0) p.cell = 30;
+    if (p.border == 0) p.border = 19;
+    if (p.harris_block == 0) p.harris_block = 7;
+    if (p.orient_radius == 0) p.orient_radius = 15;
+    if (p.max_w < 1 || p.max_h < 1 || p.max_w > 65535 || p.max_h > 65535 || p.max_levels < 1 ||
+        p.max_levels > 16 || p.max_features < 0 || p.max_features > 8192 || p.max_batch < 1 ||
+        !(p.min_scale > 1.0f) || p.fast_t_lo < 0 || p.fast_t_lo > 255 || p.cell < 8 ||
+        p.border < 4 || p.orient_radius < 1 || p.orient_radius > 15 ||
+        p.border < p.orient_radius) {
+        fail(OF_ERR_ARG, "invalid of_params");
+        return nullptr;
+    }
+    if (p.harris_block != 7) {
+        fail(OF_ERR_UNSUPPORTED, "only harris_block = 7 is implemented");
+        return nullptr;
+    }
+    of_handle* H = new of_handle();
+    H->p = p;
+    auto bail = [&](cudaError_t e, const char* what) -> of_handle* {
+        fail(OF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+        of_destroy(H);
+        return nullptr;
+    };
+    cudaError_t e = cudaGetDevice(&H->device);
+    if (e != cudaSuccess) return bail(e, "cudaGetDevice");
+    H->stream = (cudaStream_t)p.stream;  // NULL: the CUDA default stream
+    e = cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(e, "cudaStreamCreate");
+    // Scratch for the largest batch: max_batch frames of max_w x max_h.
+    Settings s{};
+    s.levels = p.max_levels;
+    s.scale = p.min_scale;
+    s.n_features = p.max_features;
+    s.border = p.border;
+    s.cell = p.cell;
+    std::vector<FrameKey> worst(p.max_batch, FrameKey{p.max_w, p.max_h, (int)align_up(p.max_w, 16), true});
+    const Layout L = make_layout(worst, s, p.max_features);
+    H->arena_bytes = L.total;
+    e = cudaMalloc(&H->arena, H->arena_bytes);
+    if (e != cudaSuccess) return bail(e, "cudaMalloc(arena)");
+    e = cudaMalloc(&H->d_counts, sizeof(int32_t) * 4);
+    if (e != cudaSuccess) return bail(e, "cudaMalloc(counts)");
+    e = cudaMallocHost(&H->h_count, sizeof(int32_t) * 4);
+    if (e != cudaSuccess) return bail(e, "cudaMallocHost");
+    ofk::set_select_smem_limit(ofk::select_smem_bytes(std::max(p.max_features, 1)));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
+    return H;
+}
+
+void of_destroy(of_handle* H) {
+    if (!H) return;
+    if (H->stream) cudaStreamSynchronize(H->stream);
+    for (Plan* P : H->plans) free_plan(P);
+    if (H->arena) cudaFree(H->arena);
+    if (H->d_counts) cudaFree(H->d_counts);
+    if (H->h_count) cudaFreeHost(H->h_count);
+    if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+    if (H->own_stream && H->stream) cudaStreamDestroy(H->stream);
+    delete H;
+}
+
+int of_detect_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, float scale,
+                    int fast_t, float harris_k, int n_features, of_keypoint* out_kpts,
+                    int32_t* out_counts) {
+    return run_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
+                     out_counts);
+}
+
+int of_time_stages(of_handle* H, void* const* events) {
+    if (!H || !events) return fail(OF_ERR_ARG, "null argument");
+    for (int i = 0; i <= kStages; ++i) {
+        if (!events[i]) return fail(OF_ERR_ARG, "null event");
+        H->stage_ev[i] = (cudaEvent_t)events[i];
+    }
+    H->stage_timing = true;
+    return OF_OK;
+}
+
+int of_detect(of_handle* H, const uint8_t* img, int w, int h_px, int pitch, int levels,
+              float scale, int fast_t, float harris_k, int n_features, of_keypoint* out_kpts) {
+    if (!H) return fail(OF_ERR_ARG, "null handle");
+    of_frame F{img, w, h_px, pitch};
+    const int rc = run_batch(H, &F, 1, levels, scale, fast_t, harris_k, n_features, out_kpts,
+                             H->d_counts);
+    if (rc != OF_OK) return rc;
+    DeviceGuard dg(H->device);
+    OF_CK(cudaMemcpyAsync(H->h_count, H->d_counts, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          H->stream));
+    OF_CK(cudaStreamSynchronize(H->stream));
+    return H->h_count[0];
+}
+
+int64_t of_inspect(of_handle* H, int what, int frame, int level, void* dst, int64_t dst_bytes,
+                   int32_t* dims) {
+    if (!H) return fail(OF_ERR_ARG, "null handle");
+    Plan* P = H->last;
+    if (!P) return fail(OF_ERR_ARG, "no detect call to inspect");
+    const int nl = P->s.levels;
+    if (frame < 0 || frame >= (int)P->frames.size() || level < 0 || level >= nl)
+        return fail(OF_ERR_ARG, "frame/level out of range");
+    DeviceGuard dg(H->device);
+    const Img& I = P->h_img[frame * nl + level];
+    const Settings& s = P->s;
+    int32_t d4[4] = {I.w, I.h, 0, 0};
+    int64_t bytes = 0;
+    if (what == OF_BUF_LEVEL || what == OF_BUF_SCORE) {
+        bytes = (int64_t)I.w * I.h;
+    } else if (what == OF_BUF_CELLT) {
+        d4[2] = I.ncx;
+        d4[3] = I.ncy;
+        bytes = (int64_t)I.ncx * I.ncy;
+    } else if (what == OF_BUF_CAND) {
+        int32_t n = 0;
+        OF_CK(cudaStreamSynchronize(H->stream));
+        OF_CK(cudaMemcpy(&n, I.ctr, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        n = std::min(n, I.cand_cap);
+        d4[2] = n;
+        bytes = 16 * (int64_t)n;
+    } else {
+        return fail(OF_ERR_ARG, "unknown buffer");
+    }
+    if (dims) std::memcpy(dims, d4, sizeof(d4));
+    if (!dst || bytes == 0) return bytes;
+    if (dst_bytes < bytes) return fail(OF_ERR_ARG, "dst too small");
+    uint8_t* d = static_cast<uint8_t*>(dst);
+    cudaStream_t st = H->stream;
+    if (what == OF_BUF_LEVEL) {
+        OF_CK(cudaMemcpy2DAsync(d, I.w, I.img, I.pitch, I.w, I.h, cudaMemcpyDeviceToDevice, st));
+    } else if (what == OF_BUF_SCORE) {
+        OF_CK(cudaMemsetAsync(d, 0, bytes, st));
+        const int rw = I.w - 2 * s.border, rh = I.h - 2 * s.border;
+        if (rw > 0 && rh > 0 && I.score)
+            OF_CK(cudaMemcpy2DAsync(d + (size_t)s.border * I.w + s.border, I.w,
+                                    I.score + (size_t)s.border * I.spitch + s.border, I.spitch, rw,
+                                    rh, cudaMemcpyDeviceToDevice, st));
+    } else if (what == OF_BUF_CELLT) {
+        ofk::launch_inspect_cells(P->d_img(), frame * nl + level, s.t_hi, s.t_lo, d, st);
+        OF_CK(cudaGetLastError());
+    } else {
+        ofk::launch_inspect_cands(P->d_img(), frame * nl + level, (int)(bytes / 16), d, st);
+        OF_CK(cudaGetLastError());
+    }
+    OF_CK(cudaStreamSynchronize(st));
+    return bytes;
+}
+
+}  // extern "C"

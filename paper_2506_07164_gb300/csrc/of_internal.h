@@ -1,0 +1,93 @@
+// Internal descriptors shared by the host runtime and the sm_103a kernels.
+// Not part of the public ABI (include/ofast.h).
+#pragma once
+#include <stdint.h>
+
+#include "ofast.h"
+
+namespace ofk {
+
+// Tile geometry of the detect-stage kernels (FAST score, NMS + Harris).
+// A tile is TILE_W x TILE_H pixels; its x origin is a multiple of 16 so that
+// 16-byte vector loads stay aligned.  256 threads: 32 columns of 4 pixels
+// x 8 rows of RPT pixels.
+constexpr int TILE_W = 128;
+constexpr int TILE_H = 32;
+constexpr int DET_THREADS = 256;
+constexpr int RPT = TILE_H / 8;        // rows per thread
+constexpr int HALO_X = 16;             // left/right staging margin (bytes), keeps alignment
+constexpr int SROW = TILE_W + 2 * HALO_X;  // staged row length (bytes)
+constexpr int MAX_CELLS_LOCAL = 128;   // cells overlapping one tile (+halo); needs cell >= 8
+
+// Resize tile: 128 x 16 output pixels, each thread writes 4 consecutive pixels.
+constexpr int RS_TILE_W = 128;
+constexpr int RS_TILE_H = 16;
+constexpr int RS_THREADS = 512;
+
+constexpr int SELECT_THREADS = 512;
+constexpr int ORIENT_WARPS = 8;        // warps per block in the orientation kernel
+
+// One (frame, level) image of a batch.
+struct Img {
+    const uint8_t* img;  // level pixels (level 0: caller's frame or its aligned copy)
+    uint8_t* score;      // FAST score map, spitch bytes per row
+    uint32_t* cell;      // per-cell "has a strong pixel" flags, ncx * ncy
+    uint64_t* ckey;      // candidates: order-preserving key (signed key ^ 2^63)
+    uint32_t* cyx;       // candidates: (y << 16) | x
+    uint64_t* kkey;      // kept (ranked) keys
+    uint32_t* kyx;       // kept positions
+    int32_t* ctr;        // [0] candidate count, [1] kept count, [2] overflow flag
+    int32_t w, h, pitch, spitch;
+    int32_t ncx, ncy;
+    int32_t cand_cap, quota;
+    int32_t frame, level;
+    int32_t tiles_x, tiles_y;  // detect-stage tiling (0 when the detect region is empty)
+    int32_t tile_x0;           // x origin of tile 0 (multiple of 16)
+    int32_t slot0;             // first output slot of this image (sum of earlier quotas)
+    double lscale;             // scale^level
+};
+
+// One resize job: dst = bilinear(src).  Tables hold (i0 << 12) | a per
+// destination column / row, i0 the first source index and a in [0, 2048].
+struct Resize {
+    const uint8_t* src;
+    uint8_t* dst;
+    const int32_t* xtab;
+    const int32_t* ytab;
+    int32_t sw, sh, spitch;
+    int32_t dw, dh, dpitch;
+    int32_t tiles_x, tiles_y;
+};
+
+// Per-call constants.
+struct Call {
+    of_keypoint* out;     // n_frames * n_features records
+    int32_t* counts;      // n_frames
+    int64_t knum, kden;   // Harris k = knum / kden
+    int32_t n_frames, levels, n_features;
+    int32_t t_hi, t_lo;   // t_lo == t_hi: no per-cell fallback
+    int32_t border, cell, radius;
+    int32_t n_img;        // n_frames * levels
+    int32_t total_slots;  // sum of quotas
+};
+
+}  // namespace ofk
+
+// Kernel launchers (implemented in the .cu files).  All take device pointers
+// to the plan's descriptor arrays and launch on `stream`.
+namespace ofk {
+void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
+                   void* stream);
+void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
+                 int n_list, int n_tiles, const Call* call, int t_hi, int t_lo, int border,
+                 int cell, void* stream);
+void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
+                       int n_list, int n_tiles, const Call* call, int t_hi, int t_lo, int border,
+                       int cell, void* stream);
+void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, void* stream);
+void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
+void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t* dst,
+                          void* stream);
+void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream);
+int select_smem_bytes(int max_quota);
+}  // namespace ofk

@@ -1,0 +1,83 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+entry point that include/*.h declares; host-only plan arithmetic agrees with
+the oracle.  No compute call needs a GPU here."""
+
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2506_07164_gb300 as ofg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(of_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ofg.build()
+    return ofg.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("of_create", "of_detect", "of_destroy", "of_detect_batch", "of_inspect",
+                     "of_plan_levels", "of_last_error", "of_version"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version(lib):
+    assert ofg.of_version() == 1
+
+
+def test_plan_levels_match_oracle(lib):
+    rng = np.random.default_rng(0)
+    cases = [(1920, 1080, 8, 1.2, 1000), (640, 480, 1, 1.2, 500), (720, 540, 8, 1.2, 1000),
+             (3840, 2160, 8, 1.2, 1000), (97, 61, 5, 1.5, 37)]
+    for _ in range(60):
+        cases.append((int(rng.integers(1, 4000)), int(rng.integers(1, 3000)), int(rng.integers(1, 17)),
+                      float(rng.uniform(1.01, 3.0)), int(rng.integers(0, 8192))))
+    for W, H, L, s, N in cases:
+        ws, hs, q = ofg.of_plan_levels(W, H, L, s, N)
+        ows, ohs, _ = oracle.level_sizes(W, H, L, s)
+        oq = oracle.level_quotas(N, L, s)
+        assert ws == ows.tolist() and hs == ohs.tolist() and q == oq.tolist(), (W, H, L, s, N)
+
+
+def test_plan_levels_rejects_bad_arguments(lib):
+    with pytest.raises(ofg.OfError):
+        ofg.of_plan_levels(0, 10, 3, 1.2, 10)
+    with pytest.raises(ofg.OfError):
+        ofg.of_plan_levels(10, 10, 3, 1.0, 10)
+
+
+def test_keypoint_record_layout():
+    assert ofg.KEYPOINT_DTYPE.itemsize == 64
+    assert ofg.KEYPOINT_DTYPE.fields["key"][1] == 56
+
+
+def test_create_rejects_invalid_params(lib):
+    # Parameter validation happens before any CUDA call.
+    with pytest.raises(ofg.OfError):
+        ofg.of_create(max_w=0, max_h=10)
+    with pytest.raises(ofg.OfError):
+        ofg.of_create(max_w=100, max_h=100, border=10, orient_radius=15)
+    with pytest.raises(ofg.OfError):
+        ofg.of_create(max_w=100, max_h=100, harris_block=5)

@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer outputs (pyramid levels, score maps, cell thresholds, NMS survivors,
+Harris sums and keys, moments, keypoint sets in rank order) must match
+bit-exactly; the Harris response within 1e-6 relative and the angle within
+1e-5 rad.  Inputs are seeded synthetic scenes (synth), sized so the oracle
+finishes in seconds while spanning many tiles and ragged tails.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2506_07164_gb300 as ofg  # noqa: E402
+
+EXACT = ["x_l", "y_l", "level", "fast_score", "A", "B", "C", "m10", "m01", "key"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ofg.build()
+    ofg.load()
+
+
+def compare_keypoints(gpu, ora):
+    assert len(gpu) == len(ora), (len(gpu), len(ora))
+    if len(ora) == 0:
+        return
+    for f in EXACT:
+        np.testing.assert_array_equal(gpu[f], ora[f], err_msg=f)
+    np.testing.assert_array_equal(gpu["x"], ora["x"].astype(np.float32))
+    np.testing.assert_array_equal(gpu["y"], ora["y"].astype(np.float32))
+    np.testing.assert_allclose(gpu["response"].astype(np.float64), ora["response"], rtol=1e-6, atol=0)
+    d = (gpu["angle"].astype(np.float64) - ora["angle"] + math.pi) % (2 * math.pi) - math.pi
+    assert np.abs(d).max() <= 1e-5
+
+
+def oracle_cands(img_level, border, cell, t_hi, t_lo, k=0.04):
+    sm = oracle.score_map(img_level, border)
+    T = oracle.cell_thresh(sm, border, cell, t_hi, t_lo)
+    surv = oracle.nms(sm, border, cell, T)
+    num, den = oracle.k_fraction(k)
+    keys = [oracle.harris_key(*oracle.harris_sums(img_level, x, y), num, den) for x, y in surv]
+    return sm, T, {(int(x), int(y), int(kk)) for (x, y), kk in zip(surv, keys)}
+
+
+def gpu_cands(det, frame, level):
+    raw, dims = det.inspect(ofg.OF_BUF_CAND, frame, level)
+    rec = raw.view(np.dtype([("key", "i8"), ("x", "i4"), ("y", "i4")]))
+    return {(int(r["x"]), int(r["y"]), int(r["key"])) for r in rec}
+
+
+def clipped(sm, t_lo):
+    return np.where(sm >= t_lo, sm, 0).astype(np.uint8)
+
+
+# ------------------------------------------------------------ config 1
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_single_level_640x480(seed):
+    img = synth.scene(640, 480, seed)
+    det = ofg.Detector(640, 480, max_levels=1, max_features=500)
+    kp = det.detect(torch.from_numpy(img).cuda(), levels=1, fast_t=20, n_features=500)
+    ora = oracle.detect(img, levels=1, fast_t=20, n_features=500)
+    compare_keypoints(kp, ora)
+    # Intermediates: score map (clipped at the only threshold), survivors with keys.
+    sm, T, cands = oracle_cands(img, 19, 30, 20, 20)
+    g_sm, _ = det.inspect(ofg.OF_BUF_SCORE)
+    np.testing.assert_array_equal(g_sm.reshape(img.shape), clipped(sm, 20))
+    assert gpu_cands(det, 0, 0) == cands
+    det.close()
+
+
+# ------------------------------------------------------------ config 2
+def test_pyramid_1080p_8_levels_with_cell_fallback():
+    img = synth.scene(1920, 1080, 7, background="pink")
+    det = ofg.Detector(1920, 1080, max_levels=8, max_features=1000, fast_t_lo=7)
+    kp = det.detect(torch.from_numpy(img).cuda(), levels=8, scale=1.2, fast_t=20, n_features=1000)
+    ora = oracle.detect(img, levels=8, scale=1.2, fast_t=20, fast_t_lo=7, n_features=1000)
+    compare_keypoints(kp, ora)
+    for level in range(8):
+        lev = oracle.pyramid_level(img, 8, 1.2, level)
+        g_lev, dims = det.inspect(ofg.OF_BUF_LEVEL, 0, level)
+        np.testing.assert_array_equal(g_lev.reshape(lev.shape), lev, err_msg=f"level {level}")
+        sm, T, cands = oracle_cands(lev, 19, 30, 20, 7)
+        g_sm, _ = det.inspect(ofg.OF_BUF_SCORE, 0, level)
+        np.testing.assert_array_equal(g_sm.reshape(lev.shape), clipped(sm, 7), err_msg=f"score {level}")
+        g_T, dims = det.inspect(ofg.OF_BUF_CELLT, 0, level)
+        np.testing.assert_array_equal(g_T.reshape(T.shape), T, err_msg=f"cells {level}")
+        assert gpu_cands(det, 0, level) == cands, f"candidates {level}"
+    det.close()
+
+
+def test_unclipped_score_map_at_t1():
+    """fast_t = 1 leaves every positive score in the map: s(p) = max(score, 0) everywhere."""
+    det = ofg.Detector(800, 600, max_levels=1, max_features=100)
+    for seed, bg in [(3, "flat"), (4, "pink")]:
+        img = synth.scene(777, 555, seed, background=bg)
+        det.detect(torch.from_numpy(img).cuda(), levels=1, fast_t=1, n_features=100)
+        g_sm, _ = det.inspect(ofg.OF_BUF_SCORE)
+        np.testing.assert_array_equal(g_sm.reshape(img.shape), oracle.score_map(img, 19))
+    det.close()
+
+
+@pytest.mark.parametrize("case", ["a", "b", "c", "d", "e"])
+def test_fig6_pattern_images(case):
+    img, centres = synth.fig6_pattern_image(case)
+    det = ofg.Detector(1024, 1024, max_levels=4, max_features=1000, border=4, orient_radius=4)
+    det.detect(torch.from_numpy(img).cuda(), levels=1, fast_t=1, n_features=10)
+    g_sm, _ = det.inspect(ofg.OF_BUF_SCORE)
+    g_sm = g_sm.reshape(img.shape)
+    np.testing.assert_array_equal(g_sm, oracle.score_map(img, 4))
+    exp = {"a": 40, "b": 40, "c": 40, "d": 0, "e": 0}[case]
+    assert {int(g_sm[y, x]) for x, y in centres} == {exp}
+    # Four-level pyramid of the same image (Fig. 7), whole keypoint sets.
+    kp = det.detect(torch.from_numpy(img).cuda(), levels=4, scale=1.2, fast_t=20, n_features=1000)
+    ora = oracle.detect(img, levels=4, scale=1.2, fast_t=20, n_features=1000, border=4, radius=4)
+    compare_keypoints(kp, ora)
+    det.close()
+
+
+# ------------------------------------------------------ ragged, edges
+@pytest.mark.parametrize("w,h,levels", [(333, 217, 3), (129, 77, 2), (1000, 41, 1), (41, 1000, 4),
+                                        (161, 161, 5), (40, 40, 3), (38, 200, 2), (2, 3, 8)])
+def test_ragged_sizes_and_unaligned_pitch(w, h, levels):
+    det = ofg.Detector(1024, 1024, max_levels=8, max_features=300, fast_t_lo=9)
+    img = synth.scene(w, h, 11 + w, background="pink", n_rect=max(4, w * h // 4000))
+    # Unaligned: an odd pitch and an odd start offset inside a larger buffer.
+    big = torch.zeros((h, w + 7), dtype=torch.uint8, device="cuda")
+    big[:, 3:3 + w] = torch.from_numpy(img).cuda()
+    view = big[:, 3:3 + w]
+    assert view.stride(0) == w + 7
+    kp = det.detect(view, levels=levels, scale=1.2, fast_t=20, n_features=300)
+    ora = oracle.detect(img, levels=levels, scale=1.2, fast_t=20, fast_t_lo=9, n_features=300)
+    compare_keypoints(kp, ora)
+    # The aligned path gives the same.
+    kp2 = det.detect(torch.from_numpy(img).cuda().contiguous(), levels=levels, scale=1.2, fast_t=20,
+                     n_features=300)
+    compare_keypoints(kp2, ora)
+    det.close()
+
+
+@pytest.mark.parametrize("n_features", [0, 1, 7, 8192])
+def test_feature_counts(n_features):
+    img = synth.scene(640, 480, 21, background="pink")
+    det = ofg.Detector(640, 480, max_levels=8, max_features=8192, fast_t_lo=7)
+    kp = det.detect(torch.from_numpy(img).cuda(), levels=8, fast_t=20, n_features=n_features)
+    ora = oracle.detect(img, levels=8, fast_t=20, fast_t_lo=7, n_features=n_features)
+    compare_keypoints(kp, ora)
+    det.close()
+
+
+def test_other_scales_k_and_borders():
+    img = synth.scene(700, 500, 31, background="pink")
+    det = ofg.Detector(700, 500, max_levels=6, max_features=800, min_scale=1.05, border=15,
+                       cell=16, fast_t_lo=5, orient_radius=11)
+    for scale, k, t in [(1.05, 0.04, 20), (1.5, 0.06, 30), (2.0, 0.05, 12), (1.2, 0.0, 20)]:
+        kp = det.detect(torch.from_numpy(img).cuda(), levels=6, scale=scale, fast_t=t, harris_k=k,
+                        n_features=800)
+        ora = oracle.detect(img, levels=6, scale=scale, fast_t=t, fast_t_lo=5, harris_k=k,
+                            n_features=800, border=15, cell=16, radius=11)
+        compare_keypoints(kp, ora)
+    det.close()
+
+
+def test_rebinding_new_pointers():
+    det = ofg.Detector(640, 480, max_levels=3, max_features=400)
+    a = synth.scene(640, 480, 41)
+    b = synth.scene(640, 480, 42)
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    for img, t in [(a, ta), (b, tb), (a, ta), (b, tb.clone())]:
+        kp = det.detect(t, levels=3, fast_t=20, n_features=400)
+        compare_keypoints(kp, oracle.detect(img, levels=3, fast_t=20, n_features=400))
+    det.close()
+
+
+# ------------------------------------------------------------- batch
+def test_batch_mixed_sizes_equal_single_frames_and_oracle():
+    sizes = [(720, 540), (1080, 720), (640, 480), (333, 217), (1080, 720)]
+    imgs = [synth.scene(w, h, 50 + i, background="pink") for i, (w, h) in enumerate(sizes)]
+    det = ofg.Detector(1440, 1080, max_levels=8, max_features=1000, max_batch=8, fast_t_lo=7)
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    det.detect_batch(dev, levels=8, fast_t=20, n_features=1000)
+    torch.cuda.synchronize()
+    res = det.batch_results(len(imgs), 1000)
+    single = ofg.Detector(1440, 1080, max_levels=8, max_features=1000, fast_t_lo=7)
+    for im, d, r in zip(imgs, dev, res):
+        ora = oracle.detect(im, levels=8, fast_t=20, fast_t_lo=7, n_features=1000)
+        compare_keypoints(r, ora)
+        compare_keypoints(single.detect(d, levels=8, fast_t=20, n_features=1000), ora)
+    det.close()
+    single.close()
+
+
+# ------------------------------------------------------------ errors
+def test_invalid_calls_return_errors():
+    det = ofg.Detector(320, 240, max_levels=4, max_features=100)
+    img = torch.zeros((240, 320), dtype=torch.uint8, device="cuda")
+    bad = [dict(levels=0), dict(levels=5), dict(scale=1.1), dict(fast_t=0), dict(fast_t=256),
+           dict(harris_k=0.3), dict(harris_k=0.040001), dict(n_features=101)]
+    for kw in bad:
+        args = dict(levels=2, scale=1.2, fast_t=20, harris_k=0.04, n_features=50)
+        args.update(kw)
+        with pytest.raises(ofg.OfError):
+            ofg.of_detect(det.h, img, 320, 240, 320, args["levels"], args["scale"], args["fast_t"],
+                          args["harris_k"], args["n_features"], det.out)
+    with pytest.raises(ofg.OfError):  # larger than the handle allows
+        ofg.of_detect(det.h, img, 321, 240, 320, 1, 1.2, 20, 0.04, 10, det.out)
+    with pytest.raises(ofg.OfError):  # pitch < w
+        ofg.of_detect(det.h, img, 320, 240, 100, 1, 1.2, 20, 0.04, 10, det.out)
+    # The handle still works afterwards.
+    assert ofg.of_detect(det.h, img, 320, 240, 320, 2, 1.2, 20, 0.04, 50, det.out) == 0
+    det.close()
