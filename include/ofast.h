@@ -151,6 +151,30 @@ int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int6
 #define OF_N_STAGES 5
 int of_time_stages(of_handle* h, void* const* events);
 
+/* Single-level detection that allocates nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running inside a CUDA graph capture, real-time loops
+ * that must not touch the allocator after start-up, and plug-in hosts that
+ * own every device allocation.
+ *   img [device]        uint8 frame, w x h, pitch bytes per row (one level, no pyramid)
+ *   fast_t, fast_t_lo   threshold and per-30x30-cell fallback (0 = none), as of_create/of_detect
+ *   harris_k, n_features as of_detect (n_features <= 8192); border 19, cell 30, radius 15
+ *   out_kpts [device]   room for n_features records (rank order)
+ *   out_count [device]  one int32: keypoints written
+ *   stream              cudaStream_t (NULL = default stream); the call is asynchronous
+ * Intermediate buffers live in one static device array of
+ * OF_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
+ * it until the process exits.  A frame whose buffers do not fit returns
+ * OF_ERR_TOO_LARGE (a 1920x1080 frame fits).  The first call on each device
+ * looks the array's address up with cudaGetSymbolAddress, with that device
+ * current; make that first call before any stream capture.  Calls share the
+ * array: each call clears what must start at zero, and calls whose work
+ * overlaps on the GPU race -- serialise them.  Returns OF_OK or OF_ERR_*. */
+#define OF_NOALLOC_SCRATCH_BYTES (16u << 20)
+int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pitch, int fast_t,
+                            int fast_t_lo, float harris_k, int n_features,
+                            of_keypoint* out_kpts, int32_t* out_count, void* stream);
+
 /* Host-only: the pyramid plan the detector uses for a W x H frame (no GPU
  * needed).  ws, hs [host, levels ints] receive level sizes; quota [host,
  * levels ints] receives the per-level feature quota for n_features.

@@ -21,7 +21,7 @@ import numpy as np
 from .build import LIB, build  # noqa: F401
 
 __all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspect", "of_plan_levels",
-           "of_time_stages", "OF_N_STAGES", "STAGE_NAMES",
+           "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc",
            "of_last_error", "of_version", "OfParams", "OfFrame", "OfKeypoint", "KEYPOINT_DTYPE",
            "OF_BUF_LEVEL", "OF_BUF_SCORE", "OF_BUF_CELLT", "OF_BUF_CAND", "OfError", "load",
            "Detector", "keypoints_to_numpy"]
@@ -94,6 +94,9 @@ def load(path: str | None = None):
     L.of_version.restype = C.c_int
     L.of_time_stages.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
     L.of_time_stages.restype = C.c_int
+    L.of_detect_level_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                          C.c_float, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.of_detect_level_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -174,6 +177,17 @@ def of_time_stages(h: int, events) -> int:
         raise ValueError("need OF_N_STAGES + 1 events")
     arr = (C.c_void_p * len(hs))(*hs)
     return _check(load().of_time_stages(h, arr))
+
+
+def of_detect_level_noalloc(img, w: int, h: int, pitch: int, fast_t: int, fast_t_lo: int,
+                            harris_k: float, n_features: int, out_kpts, out_count, stream=None) -> int:
+    """Single-level detect whose scratch is the library's static device array.
+
+    For callers that cannot allocate device memory (graph capture, real-time
+    loops, hosts that own all allocations).  Asynchronous on ``stream``."""
+    s = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    return _check(load().of_detect_level_noalloc(_ptr(img), w, h, pitch, fast_t, fast_t_lo, harris_k,
+                                                 n_features, _ptr(out_kpts), _ptr(out_count), s))
 
 
 def of_plan_levels(W: int, H: int, levels: int, scale: float, n_features: int):

@@ -609,6 +609,11 @@ int run_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, fl
 
 }  // namespace
 
+namespace ofk {
+// Lets other translation units report through of_last_error().
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace ofk
+
 extern "C" {
 
 int of_version(void) { return OF_VERSION; }
