@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--distinct", type=int, default=16, help="distinct synthetic frames")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frames", type=int, default=0, help="oracle sample size (0: 2 x cores)")
+    ap.add_argument("--skip-plain", action="store_true", help="skip the per-frame path (profiling)")
+    ap.add_argument("--skip-e2e", action="store_true", help="skip the host-buffer path (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -275,7 +277,9 @@ def main():
         smi.wait()
     clocks = summarize_clocks(clock_file)
     plain_steps = max(2, args.steps // 4)
-    ms_p, _ = timed(step_plain, plain_steps, 2)
+    ms_p = float("nan")
+    if not args.skip_plain:
+        ms_p, _ = timed(step_plain, plain_steps, 2)
 
     # End to end through the public API with host buffers.
     host = [torch.from_numpy(frames_np[i % len(frames_np)]).pin_memory() for i in range(B)]
@@ -292,14 +296,16 @@ def main():
         stream.synchronize()
 
     e2e_steps = max(3, args.steps // 2)
-    for _ in range(2):
-        step_e2e()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        step_e2e()
-    barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = float("nan")
+    if not args.skip_e2e:
+        for _ in range(2):
+            step_e2e()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            step_e2e()
+        barrier()
+        e2e_s = time.perf_counter() - t0
 
     # Correctness spot check of the timed configuration: frame 0 vs frame 0 of a single call.
     torch.cuda.synchronize()

@@ -1,15 +1,22 @@
 // FAST-9 segment test with a score (Eq. 1, Sec. 3.1; binary encoding of
-// Alg. 2 / Fig. 3), byte-parallel: one 32-bit register carries the same ring
-// pixel of 4 horizontally adjacent centres.
+// Alg. 2 / Fig. 3), two pixels per 32-bit register in 16-bit lanes.
 //
 // Score.  Eq. 1 calls ring pixel I_i bright when I_i >= I_p + t and dark when
 // I_i <= I_p - t; p is a corner at t when 9 contiguous ring pixels are all
 // bright or all dark.  The largest such t is
 //   s(p) = max( max_j min_{k<9} I_{j+k} - I_p ,  I_p - min_j max_{k<9} I_{j+k} )
 // (the I_p terms leave the min/max), so corner(t) <=> s(p) >= t for t >= 1.
-// Both arc terms are computed once for all 4 pixels with byte-wise min/max:
-// minima of 2, 4, 8 contiguous pixels by doubling, then the 9th pixel.  The
-// map stores s(p) where s(p) >= t_lo (the lowest threshold in use), else 0.
+// The arc terms use the three-input packed min/max of sm_90+ (DPX):
+// minima of 3 contiguous ring pixels, then of 9 = three 3-runs 3 apart, then
+// the maximum over the 16 starts -- 40 instructions per side for 2 pixels,
+// no branches.  The map stores s(p) where s(p) >= t_lo (the lowest threshold
+// in use), else 0.
+//
+// Data movement.  A thread owns 4 adjacent pixels x..x+3 over RPT rows.  Each
+// staged row gives it three 32-bit words (bytes x-4..x+7); one byte permute
+// per pair turns them into six 16-bit-lane words (pixel pairs x-4.., x-2..,
+// x.., x+2.., x+4.., x+6..).  A ring pixel at an even column offset is one of
+// those words; at an odd offset one more permute joins two of them.
 //
 // Per-cell fallback: a cell with any pixel scoring >= t_hi is flagged
 // (shared-memory flags per tile, then one global atomicOr per flagged cell).
@@ -26,33 +33,52 @@ namespace ofk {
     R(7, 1, 3) R(8, 0, 3) R(9, -1, 3) R(10, -2, 2) R(11, -3, 1) R(12, -3, 0) R(13, -3, -1) \
     R(14, -2, -2) R(15, -1, -3)
 
-// s(p) for 4 adjacent centres.  q[i] = ring pixel i of the 4 centres, c = centres.
-__device__ __forceinline__ uint32_t fast_score4(const uint32_t (&q)[16], uint32_t c) {
-    uint32_t lo2[16], hi2[16];
+// The pair (x+o, x+o+1) in 16-bit lanes, o in -4..6, from the six pair words
+// h[j] = (x-4+2j, x-3+2j).
+template <int O>
+__device__ __forceinline__ uint32_t pair_at(const uint32_t (&h)[6]) {
+    constexpr int j = (O + 4) >> 1;
+    if constexpr (((O + 4) & 1) == 0) return h[j];
+    else return __byte_perm(h[j], h[j + 1], 0x5432);  // high lane of h[j], low lane of h[j+1]
+}
+
+// Largest arc minimum and smallest arc maximum over the 16 nine-pixel arcs,
+// for the two pixels in the lanes of q[].
+__device__ __forceinline__ void arc_extrema(const uint32_t (&q)[16], uint32_t& amax, uint32_t& amin) {
+    uint32_t m3[16], M3[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        lo2[i] = __vminu4(q[i], q[(i + 1) & 15]);
-        hi2[i] = __vmaxu4(q[i], q[(i + 1) & 15]);
+        m3[i] = __vimin3_u16x2(q[i], q[(i + 1) & 15], q[(i + 2) & 15]);
+        M3[i] = __vimax3_u16x2(q[i], q[(i + 1) & 15], q[(i + 2) & 15]);
     }
-    uint32_t lo4[16], hi4[16];
+    uint32_t m9[16], M9[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        lo4[i] = __vminu4(lo2[i], lo2[(i + 2) & 15]);
-        hi4[i] = __vmaxu4(hi2[i], hi2[(i + 2) & 15]);
+        m9[i] = __vimin3_u16x2(m3[i], m3[(i + 3) & 15], m3[(i + 6) & 15]);
+        M9[i] = __vimax3_u16x2(M3[i], M3[(i + 3) & 15], M3[(i + 6) & 15]);
     }
-    uint32_t lo8[16], hi8[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        lo8[i] = __vminu4(lo4[i], lo4[(i + 4) & 15]);
-        hi8[i] = __vmaxu4(hi4[i], hi4[(i + 4) & 15]);
-    }
-    uint32_t arc_min_max = 0u, arc_max_min = 0xFFFFFFFFu;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        arc_min_max = __vmaxu4(arc_min_max, __vminu4(lo8[i], q[(i + 8) & 15]));
-        arc_max_min = __vminu4(arc_max_min, __vmaxu4(hi8[i], q[(i + 8) & 15]));
-    }
-    return __vmaxu4(__vsubus4(arc_min_max, c), __vsubus4(c, arc_max_min));
+    const uint32_t a0 = __vimax3_u16x2(m9[0], m9[1], m9[2]), a1 = __vimax3_u16x2(m9[3], m9[4], m9[5]);
+    const uint32_t a2 = __vimax3_u16x2(m9[6], m9[7], m9[8]), a3 = __vimax3_u16x2(m9[9], m9[10], m9[11]);
+    const uint32_t a4 = __vimax3_u16x2(m9[12], m9[13], m9[14]);
+    const uint32_t b0 = __vimin3_u16x2(M9[0], M9[1], M9[2]), b1 = __vimin3_u16x2(M9[3], M9[4], M9[5]);
+    const uint32_t b2 = __vimin3_u16x2(M9[6], M9[7], M9[8]), b3 = __vimin3_u16x2(M9[9], M9[10], M9[11]);
+    const uint32_t b4 = __vimin3_u16x2(M9[12], M9[13], M9[14]);
+    amax = __vimax3_u16x2(__vimax3_u16x2(a0, a1, a2), a3, __vimax3_u16x2(a4, m9[15], 0u));
+    amin = __vimin3_u16x2(__vimin3_u16x2(b0, b1, b2), b3, __vimin3_u16x2(b4, M9[15], 0xFFFFFFFFu));
+}
+
+// s(p) for the two pixels of a pair: lanes of max(amax - c, c - amin, 0).
+__device__ __forceinline__ uint32_t pair_score(const uint32_t (&q)[16], uint32_t c) {
+    uint32_t amax, amin;
+    arc_extrema(q, amax, amin);
+    constexpr uint32_t B = 0x01000100u;  // +256 per lane keeps each difference positive
+    return __vimax3_u16x2(amax + B - c, c + B - amin, B) - B;
+}
+
+// 0xFFFF in each 16-bit lane whose value is >= t (values and t below 2^15).
+__device__ __forceinline__ uint32_t lanes_ge(uint32_t v, uint32_t t) {
+    const uint32_t d = v + (0x8000u - t) * 0x00010001u;
+    return ((d >> 15) & 0x00010001u) * 0xFFFFu;
 }
 
 __global__ void __launch_bounds__(DET_THREADS)
@@ -84,32 +110,42 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
 
     const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int x = X0 + 4 * lane;
-    uint32_t wm[RPT + 6], wc[RPT + 6], wp[RPT + 6];
+    // Six pair words per staged row (RPT + 6 rows).
+    uint32_t hw[RPT + 6][6];
 #pragma unroll
     for (int k = 0; k < RPT + 6; ++k) {
         const uint8_t* row = s + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
-        wm[k] = *reinterpret_cast<const uint32_t*>(row - 4);
-        wc[k] = *reinterpret_cast<const uint32_t*>(row);
-        wp[k] = *reinterpret_cast<const uint32_t*>(row + 4);
+        const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+        const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+        const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
+        hw[k][0] = __byte_perm(wm, 0u, 0x4140);
+        hw[k][1] = __byte_perm(wm, 0u, 0x4342);
+        hw[k][2] = __byte_perm(wc, 0u, 0x4140);
+        hw[k][3] = __byte_perm(wc, 0u, 0x4342);
+        hw[k][4] = __byte_perm(wp, 0u, 0x4140);
+        hw[k][5] = __byte_perm(wp, 0u, 0x4342);
     }
     const uint32_t colmask = range_mask4(x, rx0, rx1);
-    const uint32_t tlo4 = 0x01010101u * (uint32_t)t_lo;
-    const uint32_t thi4 = 0x01010101u * (uint32_t)t_hi;
 
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int y = Y0 + ty * RPT + r;
-        uint32_t q[16];
-#define OF_LOAD_RING(i, dx, dy) q[i] = win4<dx>(wm[r + 3 + (dy)], wc[r + 3 + (dy)], wp[r + 3 + (dy)]);
+        uint32_t q0[16], q1[16];
+#define OF_LOAD_RING(i, dx, dy)                        \
+    q0[i] = pair_at<(dx)>(hw[r + 3 + (dy)]);          \
+    q1[i] = pair_at<(dx) + 2>(hw[r + 3 + (dy)]);
         OF_RING(OF_LOAD_RING)
 #undef OF_LOAD_RING
-        const uint32_t c = wc[r + 3];
-        uint32_t sc = fast_score4(q, c);
+        uint32_t s0 = pair_score(q0, hw[r + 3][2]);
+        uint32_t s1 = pair_score(q1, hw[r + 3][3]);
+        s0 &= lanes_ge(s0, (uint32_t)t_lo);
+        s1 &= lanes_ge(s1, (uint32_t)t_lo);
         const uint32_t m = (y < ry1) ? colmask : 0u;
-        sc &= __vcmpgeu4(sc, tlo4) & m;
+        const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
         if (m != 0u) *reinterpret_cast<uint32_t*>(I.score + (size_t)y * I.spitch + x) = sc;
-        if (cells) {
-            const uint32_t strong = __vcmpgeu4(sc, thi4) & m;
+        if (cells && sc) {
+            const uint32_t strong = __byte_perm(lanes_ge(s0, (uint32_t)t_hi), lanes_ge(s1, (uint32_t)t_hi),
+                                                0x6420) & m;
             if (strong) {
                 const int cyl = (y - border) / cell - cy0;
 #pragma unroll

@@ -5,8 +5,10 @@
 //
 // 1. Stage the score tile (+1 pixel halo) and turn it into S(p): s(p) when p is
 //    a candidate at its cell's threshold, else 0; 0 outside the detect region.
-// 2. NMS, 4 pixels per register: p survives when S(p) > max of its 8
-//    neighbours (byte-wise max of 8 shifted words, one byte-wise compare).
+//    A per-tile table gives, for each staged word and cell row, the bytes that
+//    lie in cells whose threshold is t_hi.
+// 2. NMS, two pixels per register in 16-bit lanes: p survives when S(p) > the
+//    three-input maximum of its 8 neighbours.
 // 3. Survivors go to a shared-memory queue; the image tile (+4 pixel halo) is
 //    staged only when the queue is not empty.
 // 4. Harris (Eqs. 2-4, Alg. 3): one thread per survivor slides down the 9 x 9
@@ -24,6 +26,16 @@
 namespace ofk {
 
 constexpr int QCAP = TILE_W * TILE_H / 4;  // strict maxima are never adjacent
+constexpr int WPR = SROW / 4;               // staged words per row
+constexpr int LCH_MAX = (TILE_H + 2) / 8 + 2;  // cell rows touched by a tile (cell >= 8)
+
+// 0xFF in each byte of v that is below t (t <= 255).
+__device__ __forceinline__ uint32_t bytes_lt(uint32_t v, uint32_t t) {
+    const uint32_t tt = (0x8000u - t) * 0x00010001u;
+    const uint32_t lo = __byte_perm(v, 0u, 0x4140) + tt, hi = __byte_perm(v, 0u, 0x4342) + tt;
+    // bit 15 of a lane set <=> byte >= t
+    return ~__byte_perm((lo >> 15 & 0x00010001u) * 0xFFu, (hi >> 15 & 0x00010001u) * 0xFFu, 0x6420);
+}
 
 __device__ __forceinline__ void harris_sums(const uint8_t* __restrict__ s, int lx, int ly,
                                             int32_t& A, int32_t& B, int32_t& C) {
@@ -66,6 +78,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     __shared__ __align__(16) uint8_t sS[(TILE_H + 2) * SROW];
     __shared__ __align__(16) uint8_t sI[(TILE_H + 8) * SROW];
     __shared__ uint32_t sflag[MAX_CELLS_LOCAL];
+    __shared__ uint32_t fmask[LCH_MAX * WPR];
     __shared__ uint32_t queue[QCAP];
     __shared__ int nq, qbase;
 
@@ -85,6 +98,8 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     const int cy0 = (max(Y0 - 1, ry0) - ry0) / cell;
     const int lcw = (TILE_W + 2) / cell + 2;
     const int lch = (TILE_H + 2) / cell + 2;
+    // Only columns X0-1 .. X0+TILE_W feed the 3x3 test; the rest stay 0.
+    const int lox = max(rx0, X0 - 1), hix = min(rx1, X0 + TILE_W + 1);
     if (threadIdx.x == 0) nq = 0;
     if (cells) {
         for (int i = threadIdx.x; i < lcw * lch; i += blockDim.x) {
@@ -92,14 +107,24 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             sflag[i] = (cx < I.ncx && cy < I.ncy) ? I.cell[cy * I.ncx + cx] : 0u;
         }
         __syncthreads();
+        // fmask[cyl][k]: 0xFF for each byte of staged word k in a flagged cell of cell row cyl.
+        for (int i = threadIdx.x; i < lch * WPR; i += blockDim.x) {
+            const int cyl = i / WPR, k = i - cyl * WPR;
+            uint32_t m = 0u;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int xx = X0 - HALO_X + 4 * k + e;
+                if (xx >= lox && xx < hix && sflag[cyl * lcw + (xx - rx0) / cell - cx0])
+                    m |= 0xFFu << (8 * e);
+            }
+            fmask[i] = m;
+        }
+        __syncthreads();
     }
 
     // 1. S(p) for rows Y0-1 .. Y0+TILE_H, columns X0-16 .. X0+TILE_W+16.
     {
         constexpr int CPR = SROW / 16;
-        const uint32_t thi4 = 0x01010101u * (uint32_t)t_hi;
-        // Only columns X0-1 .. X0+TILE_W feed the 3x3 test; the rest stay 0.
-        const int lox = max(rx0, X0 - 1), hix = min(rx1, X0 + TILE_W + 1);
         const int n = (TILE_H + 2) * CPR;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int r = i / CPR, k = i - r * CPR;
@@ -108,24 +133,12 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             if (iy >= ry0 && iy < ry1 && ix + 16 > lox && ix < hix) {
                 v = __ldg(reinterpret_cast<const uint4*>(I.score + (size_t)iy * I.spitch + ix));
                 uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+                const uint32_t* fm = fmask + ((iy - ry0) / cell - cy0) * WPR + 4 * k;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    uint32_t m = range_mask4(ix + 4 * q, lox, hix);
-                    uint32_t val = wd[q] & m;
-                    if (cells && val) {
-                        // Bytes below t_hi survive only when their cell has no strong pixel.
-                        const uint32_t weak = __vcmpltu4(val, thi4) & __vcmpne4(val, 0u);
-                        if (weak) {
-                            const int cyl = (iy - ry0) / cell - cy0;
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                if ((weak >> (8 * e)) & 1u) {
-                                    const int cxl = (ix + 4 * q + e - rx0) / cell - cx0;
-                                    if (sflag[cyl * lcw + cxl]) val &= ~(0xFFu << (8 * e));
-                                }
-                            }
-                        }
-                    }
+                    uint32_t val = wd[q] & range_mask4(ix + 4 * q, lox, hix);
+                    // Bytes below t_hi survive only when their cell has no strong pixel.
+                    if (cells && val) val &= ~(fm[q] & bytes_lt(val, (uint32_t)t_hi));
                     wd[q] = val;
                 }
                 v = make_uint4(wd[0], wd[1], wd[2], wd[3]);
@@ -135,34 +148,44 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     }
     __syncthreads();
 
-    // 2. Strict 3x3 maxima.
+    // 2. Strict 3x3 maxima, two pixels per register.
     const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
     {
-        uint32_t wm[RPT + 2], wc[RPT + 2], wp[RPT + 2];
+        uint32_t hw[RPT + 2][6];
 #pragma unroll
         for (int k = 0; k < RPT + 2; ++k) {
             const uint8_t* row = sS + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
-            wm[k] = *reinterpret_cast<const uint32_t*>(row - 4);
-            wc[k] = *reinterpret_cast<const uint32_t*>(row);
-            wp[k] = *reinterpret_cast<const uint32_t*>(row + 4);
+            const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+            const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+            const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
+            hw[k][1] = __byte_perm(wm, 0u, 0x4342);  // (x-2, x-1)
+            hw[k][2] = __byte_perm(wc, 0u, 0x4140);  // (x, x+1)
+            hw[k][3] = __byte_perm(wc, 0u, 0x4342);  // (x+2, x+3)
+            hw[k][4] = __byte_perm(wp, 0u, 0x4140);  // (x+4, x+5)
         }
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-            uint32_t nb = win4<-1>(wm[r], wc[r], wp[r]);
-            nb = __vmaxu4(nb, wc[r]);
-            nb = __vmaxu4(nb, win4<1>(wm[r], wc[r], wp[r]));
-            nb = __vmaxu4(nb, win4<-1>(wm[r + 1], wc[r + 1], wp[r + 1]));
-            nb = __vmaxu4(nb, win4<1>(wm[r + 1], wc[r + 1], wp[r + 1]));
-            nb = __vmaxu4(nb, win4<-1>(wm[r + 2], wc[r + 2], wp[r + 2]));
-            nb = __vmaxu4(nb, wc[r + 2]);
-            nb = __vmaxu4(nb, win4<1>(wm[r + 2], wc[r + 2], wp[r + 2]));
-            const uint32_t keep = __vcmpgtu4(wc[r + 1], nb);
-            if (keep) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if ((keep >> (8 * e)) & 1u) {
-                        const int slot = atomicAdd(&nq, 1);
-                        queue[slot] = ((uint32_t)(ty * RPT + r) << 16) | (uint32_t)(4 * lane + e);
+            for (int pr = 0; pr < 2; ++pr) {
+                // Pair (x+2pr, x+2pr+1): neighbours at column offsets -1, 0, +1.
+                const uint32_t* a = hw[r];
+                const uint32_t* c = hw[r + 1];
+                const uint32_t* d = hw[r + 2];
+                const int j = 2 + pr;
+                const uint32_t am = __byte_perm(a[j - 1], a[j], 0x5432), ap = __byte_perm(a[j], a[j + 1], 0x5432);
+                const uint32_t cm = __byte_perm(c[j - 1], c[j], 0x5432), cp = __byte_perm(c[j], c[j + 1], 0x5432);
+                const uint32_t dm = __byte_perm(d[j - 1], d[j], 0x5432), dp = __byte_perm(d[j], d[j + 1], 0x5432);
+                const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(am, a[j], ap), __vimax3_u16x2(cm, cp, dm),
+                                                   __vimax3_u16x2(d[j], dp, dp));
+                // Lane bit 15 set when centre > neighbours (values <= 255).
+                const uint32_t keep = (c[j] + 0x7FFF7FFFu - nb) & 0x80008000u;
+                if (keep) {
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if ((keep >> (16 * e + 15)) & 1u) {
+                            const int slot = atomicAdd(&nq, 1);
+                            queue[slot] = ((uint32_t)(ty * RPT + r) << 16) | (uint32_t)(4 * lane + 2 * pr + e);
+                        }
                     }
                 }
             }
