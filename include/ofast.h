@@ -142,6 +142,18 @@ int of_detect_batch(of_handle* h, const of_frame* frames, int n_frames, int leve
 int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int64_t dst_bytes,
                    int32_t* dims);
 
+/* Wait for the handle's queued work and report device-side failures: returns
+ * OF_ERR_TIMEOUT when a bounded device wait (a tile load that never arrived)
+ * expired since the last check -- the affected calls' out_counts entries are
+ * then OF_ERR_TIMEOUT too -- else OF_OK.  Clears the condition. */
+int of_sync(of_handle* h);
+
+/* Failure-path self test: runs a kernel that waits, with the detector's
+ * bounded wait, on a device flag that nothing sets, for limit_us
+ * microseconds (1..1e7), then reports through of_sync.  Returns
+ * OF_ERR_TIMEOUT when the timeout path works; the handle stays usable. */
+int of_test_timeout(of_handle* h, int64_t limit_us);
+
 /* Stage timing: the next detect call on this handle runs its stages as
  * separate launches and records events[i] (cudaEvent_t, created by the
  * caller with timing enabled) on the handle's stream before stage i and

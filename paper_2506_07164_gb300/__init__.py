@@ -21,7 +21,8 @@ import numpy as np
 from .build import LIB, build  # noqa: F401
 
 __all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspect", "of_plan_levels",
-           "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc",
+           "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc", "of_sync",
+           "of_test_timeout", "OF_ERR_TIMEOUT",
            "of_last_error", "of_version", "OfParams", "OfFrame", "OfKeypoint", "KEYPOINT_DTYPE",
            "OF_BUF_LEVEL", "OF_BUF_SCORE", "OF_BUF_CELLT", "OF_BUF_CAND", "OfError", "load",
            "Detector", "keypoints_to_numpy"]
@@ -97,6 +98,10 @@ def load(path: str | None = None):
     L.of_detect_level_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_float, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     L.of_detect_level_noalloc.restype = C.c_int
+    L.of_sync.argtypes = [C.c_void_p]
+    L.of_sync.restype = C.c_int
+    L.of_test_timeout.argtypes = [C.c_void_p, C.c_int64]
+    L.of_test_timeout.restype = C.c_int
     _lib = L
     return L
 
@@ -188,6 +193,16 @@ def of_detect_level_noalloc(img, w: int, h: int, pitch: int, fast_t: int, fast_t
     s = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
     return _check(load().of_detect_level_noalloc(_ptr(img), w, h, pitch, fast_t, fast_t_lo, harris_k,
                                                  n_features, _ptr(out_kpts), _ptr(out_count), s))
+
+
+def of_sync(h: int) -> int:
+    """Wait for the handle's work; raises OfError(OF_ERR_TIMEOUT) if a device wait expired."""
+    return _check(load().of_sync(h))
+
+
+def of_test_timeout(h: int, limit_us: int) -> int:
+    """Run the bounded-wait failure path on the GPU; returns the raw code (OF_ERR_TIMEOUT expected)."""
+    return int(load().of_test_timeout(h, limit_us))
 
 
 def of_plan_levels(W: int, H: int, levels: int, scale: float, n_features: int):

@@ -20,10 +20,16 @@
 //
 // Per-cell fallback: a cell with any pixel scoring >= t_hi is flagged
 // (shared-memory flags per tile, then one global atomicOr per flagged cell).
+//
+// Persistent launch: a grid of a few blocks per SM walks all tiles of the
+// batch; tiles arrive by TMA (one 160 x 40 box per tile, zero-filled outside
+// the image) into two shared-memory buffers, so the next tile's load overlaps
+// the current tile's arithmetic.
 #include <cuda_runtime.h>
 
 #include "of_internal.h"
 #include "of_tile.cuh"
+#include "of_tma.cuh"
 
 namespace ofk {
 
@@ -81,100 +87,169 @@ __device__ __forceinline__ uint32_t lanes_ge(uint32_t v, uint32_t t) {
     return ((d >> 15) & 0x00010001u) * 0xFFFFu;
 }
 
+// Tile t of the launch: its image and origin.
+struct TileInfo {
+    int32_t img, x0, y0;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
+                                              const int32_t* __restrict__ prefix, int n_list, int t,
+                                              int border) {
+    const int j = find_tile_job(prefix, n_list, t);
+    const int ii = __ldg(list + j);
+    const Img& I = imgs[ii];
+    const int tt = t - __ldg(prefix + j);
+    const int tx = tt % I.tiles_x, ty = tt / I.tiles_x;
+    return TileInfo{ii, I.tile_x0 + tx * TILE_W, border + ty * TILE_H};
+}
+
+constexpr int FAST_BOX = IMG_BOX_ROWS * SROW;           // bytes per TMA box (160 x 40)
+constexpr int FAST_BUF = (FAST_BOX + 127) / 128 * 128;  // buffer stride in shared memory
+
+// Persistent: each block walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// Thread 0 fetches the next tile by TMA into the other buffer while the
+// block scores the current one.
 __global__ void __launch_bounds__(DET_THREADS)
 k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
-       const int32_t* __restrict__ prefix, int n_list, int t_hi, int t_lo, int border, int cell) {
-    __shared__ __align__(16) uint8_t s[(TILE_H + 6) * SROW];
+       const int32_t* __restrict__ prefix, int n_list, int n_tiles, const CUtensorMap* __restrict__ maps,
+       const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell) {
+    __shared__ __align__(128) uint8_t sbuf[2 * FAST_BUF];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ TileInfo tinfo[2];
     __shared__ uint32_t sflag[MAX_CELLS_LOCAL];
 
-    const int b = blockIdx.x;
-    const int j = find_tile_job(prefix, n_list, b);
-    const Img& I = imgs[__ldg(list + j)];
-    const int w = I.w, h = I.h;
-    const int t = b - __ldg(prefix + j);
-    const int tx = t % I.tiles_x, ty_tile = t / I.tiles_x;
-    const int X0 = I.tile_x0 + tx * TILE_W;
-    const int Y0 = border + ty_tile * TILE_H;
+    const int tid = threadIdx.x;
     const bool cells = t_hi != t_lo;
-
-    // Cells overlapping this tile: columns [cx0, ...), rows [cy0, ...).
-    const int rx0 = border, rx1 = w - border, ry1 = h - border;
-    const int cx0 = (max(X0, rx0) - rx0) / cell;
-    const int cy0 = (Y0 - border) / cell;
-    const int lcw = TILE_W / cell + 2;
-    if (cells) {
-        for (int i = threadIdx.x; i < MAX_CELLS_LOCAL; i += blockDim.x) sflag[i] = 0u;
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_barrier_init();
     }
-    stage_tile(s, I.img, w, h, I.pitch, X0 - HALO_X, Y0 - 3, TILE_H + 6);
+    for (int i = tid; i < MAX_CELLS_LOCAL; i += blockDim.x) sflag[i] = 0u;
     __syncthreads();
+    auto issue = [&](int t, int b) {
+        const TileInfo ti = tile_info(imgs, list, prefix, n_list, t, border);
+        tinfo[b] = ti;
+        mbar_arrive_expect_tx(&mbar[b], FAST_BOX);
+        tma_load_2d(sbuf + b * FAST_BUF, maps + ti.img, ti.x0 - HALO_X, ti.y0 - 4, &mbar[b]);
+    };
+    if (tid == 0 && (int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
 
-    const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int x = X0 + 4 * lane;
-    // Six pair words per staged row (RPT + 6 rows).
-    uint32_t hw[RPT + 6][6];
+    const int lane = tid & 31, ty = tid >> 5;
+    for (int it = 0;; ++it) {
+        const int t = blockIdx.x + it * gridDim.x;
+        if (t >= n_tiles) break;
+        const int b = it & 1;
+        if (tid == 0 && t + (int)gridDim.x < n_tiles) {
+            fence_proxy_async_smem();
+            issue(t + gridDim.x, b ^ 1);
+        }
+        const bool ok = mbar_wait(&mbar[b], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(call->status, OF_DEV_TIMEOUT);
+                // Let this block's copies in flight land before its shared memory goes away.
+                mbar_wait(&mbar[b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (t + (int)gridDim.x < n_tiles) mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+            }
+            return;
+        }
+        const TileInfo ti = tinfo[b];
+        const Img& I = imgs[ti.img];
+        const uint8_t* s = sbuf + b * FAST_BUF;
+        const int X0 = ti.x0, Y0 = ti.y0;
+        const int rx0 = border, rx1 = I.w - border, ry1 = I.h - border;
+        const int cx0 = (max(X0, rx0) - rx0) / cell;
+        const int cy0 = (Y0 - border) / cell;
+        const int lcw = TILE_W / cell + 2;
+        const int x = X0 + 4 * lane;
+
+        // Six pair words per staged row: rows y-3 .. y+RPT+2 (staged row 0 is Y0-4).
+        uint32_t hw[RPT + 6][6];
 #pragma unroll
-    for (int k = 0; k < RPT + 6; ++k) {
-        const uint8_t* row = s + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
-        const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
-        const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
-        const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
-        hw[k][0] = __byte_perm(wm, 0u, 0x4140);
-        hw[k][1] = __byte_perm(wm, 0u, 0x4342);
-        hw[k][2] = __byte_perm(wc, 0u, 0x4140);
-        hw[k][3] = __byte_perm(wc, 0u, 0x4342);
-        hw[k][4] = __byte_perm(wp, 0u, 0x4140);
-        hw[k][5] = __byte_perm(wp, 0u, 0x4342);
-    }
-    const uint32_t colmask = range_mask4(x, rx0, rx1);
+        for (int k = 0; k < RPT + 6; ++k) {
+            const uint8_t* row = s + (ty * RPT + k + 1) * SROW + HALO_X + 4 * lane;
+            const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+            const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+            const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
+            hw[k][0] = __byte_perm(wm, 0u, 0x4140);
+            hw[k][1] = __byte_perm(wm, 0u, 0x4342);
+            hw[k][2] = __byte_perm(wc, 0u, 0x4140);
+            hw[k][3] = __byte_perm(wc, 0u, 0x4342);
+            hw[k][4] = __byte_perm(wp, 0u, 0x4140);
+            hw[k][5] = __byte_perm(wp, 0u, 0x4342);
+        }
+        const uint32_t colmask = range_mask4(x, rx0, rx1);
 
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int y = Y0 + ty * RPT + r;
-        uint32_t q0[16], q1[16];
+        for (int r = 0; r < RPT; ++r) {
+            const int y = Y0 + ty * RPT + r;
+            uint32_t q0[16], q1[16];
 #define OF_LOAD_RING(i, dx, dy)                        \
     q0[i] = pair_at<(dx)>(hw[r + 3 + (dy)]);          \
     q1[i] = pair_at<(dx) + 2>(hw[r + 3 + (dy)]);
-        OF_RING(OF_LOAD_RING)
+            OF_RING(OF_LOAD_RING)
 #undef OF_LOAD_RING
-        uint32_t s0 = pair_score(q0, hw[r + 3][2]);
-        uint32_t s1 = pair_score(q1, hw[r + 3][3]);
-        s0 &= lanes_ge(s0, (uint32_t)t_lo);
-        s1 &= lanes_ge(s1, (uint32_t)t_lo);
-        const uint32_t m = (y < ry1) ? colmask : 0u;
-        const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
-        if (m != 0u) *reinterpret_cast<uint32_t*>(I.score + (size_t)y * I.spitch + x) = sc;
-        if (cells && sc) {
-            const uint32_t strong = __byte_perm(lanes_ge(s0, (uint32_t)t_hi), lanes_ge(s1, (uint32_t)t_hi),
-                                                0x6420) & m;
-            if (strong) {
-                const int cyl = (y - border) / cell - cy0;
+            uint32_t s0 = pair_score(q0, hw[r + 3][2]);
+            uint32_t s1 = pair_score(q1, hw[r + 3][3]);
+            s0 &= lanes_ge(s0, (uint32_t)t_lo);
+            s1 &= lanes_ge(s1, (uint32_t)t_lo);
+            const uint32_t m = (y < ry1) ? colmask : 0u;
+            const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
+            if (m != 0u) *reinterpret_cast<uint32_t*>(I.score + (size_t)y * I.spitch + x) = sc;
+            if (cells && sc) {
+                const uint32_t strong =
+                    __byte_perm(lanes_ge(s0, (uint32_t)t_hi), lanes_ge(s1, (uint32_t)t_hi), 0x6420) & m;
+                if (strong) {
+                    const int cyl = (y - border) / cell - cy0;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if ((strong >> (8 * i)) & 1u) {
-                        const int cxl = (x + i - rx0) / cell - cx0;
-                        atomicOr(&sflag[cyl * lcw + cxl], 1u);
+                    for (int i = 0; i < 4; ++i) {
+                        if ((strong >> (8 * i)) & 1u) {
+                            const int cxl = (x + i - rx0) / cell - cx0;
+                            atomicOr(&sflag[cyl * lcw + cxl], 1u);
+                        }
                     }
                 }
             }
         }
-    }
-    if (cells) {
-        __syncthreads();
-        const int lch = TILE_H / cell + 2;
-        for (int i = threadIdx.x; i < lcw * lch; i += blockDim.x) {
-            if (sflag[i]) {
-                const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
-                if (cx < I.ncx && cy < I.ncy) atomicOr(&I.cell[cy * I.ncx + cx], 1u);
+        if (cells) {
+            __syncthreads();
+            const int lch = TILE_H / cell + 2;
+            for (int i = tid; i < lcw * lch; i += blockDim.x) {
+                if (sflag[i]) {
+                    const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
+                    if (cx < I.ncx && cy < I.ncy) atomicOr(&I.cell[cy * I.ncx + cx], 1u);
+                    sflag[i] = 0u;
+                }
             }
         }
+        __syncthreads();  // buffer b is free for the tile after next
     }
 }
 
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
-                 int n_tiles, const Call*, int t_hi, int t_lo, int border, int cell, void* stream) {
+                 int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
+                 int cell, int grid, void* stream) {
     if (n_tiles <= 0) return;
-    k_fast<<<n_tiles, DET_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list,
-                                                               t_hi, t_lo, border, cell);
+    grid = grid < n_tiles ? grid : n_tiles;
+    k_fast<<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles,
+                                                            maps, call, t_hi, t_lo, border, cell);
+}
+
+int fast_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast, DET_THREADS, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+// A block that waits, with the same bounded wait as the tile loads, on a flag
+// nothing sets; exercises the timeout path without any copy in flight.
+__global__ void k_wait_test(const int32_t* flag, int32_t* status, uint64_t limit_ns) {
+    if (threadIdx.x == 0 && !flag_wait(flag, limit_ns)) atomicOr(status, OF_DEV_TIMEOUT);
+}
+
+void launch_wait_test(const int32_t* flag, int32_t* status, uint64_t limit_ns, void* stream) {
+    k_wait_test<<<1, 32, 0, (cudaStream_t)stream>>>(flag, status, limit_ns);
 }
 
 }  // namespace ofk

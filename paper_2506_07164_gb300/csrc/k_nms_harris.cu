@@ -3,31 +3,37 @@
 // Sec. 5.2: the survivors' Harris sums are computed from the same shared
 // memory tile, with no round trip of points through global memory).
 //
-// 1. Stage the score tile (+1 pixel halo) and turn it into S(p): s(p) when p is
-//    a candidate at its cell's threshold, else 0; 0 outside the detect region.
-//    A per-tile table gives, for each staged word and cell row, the bytes that
-//    lie in cells whose threshold is t_hi.
+// Persistent launch; per tile, one thread fetches two TMA boxes into the
+// next buffer pair while the block works on the current one: the score tile
+// (160 x 34, +1 row/col halo) and the image tile (160 x 40, +4 halo).
+// 1. S(p) in place: s(p) when p is a candidate at its cell's threshold, else
+//    0; 0 outside the detect region.  A per-tile table gives, for each staged
+//    word and cell row, the bytes in cells whose threshold is t_hi.
 // 2. NMS, two pixels per register in 16-bit lanes: p survives when S(p) > the
-//    three-input maximum of its 8 neighbours.
-// 3. Survivors go to a shared-memory queue; the image tile (+4 pixel halo) is
-//    staged only when the queue is not empty.
-// 4. Harris (Eqs. 2-4, Alg. 3): one thread per survivor slides down the 9 x 9
+//    three-input maximum of its 8 neighbours.  Survivors go to a queue.
+// 3. Harris (Eqs. 2-4, Alg. 3): one thread per survivor slides down the 9 x 9
 //    footprint keeping three rows of the horizontal Sobel passes (difference
 //    [-1 0 1] and smoothing [1 2 1]) in registers -- the circular buffer of
 //    Alg. 3 -- and combines them vertically into gx, gy, accumulating the
 //    exact int32 sums A = sum gx^2, B = sum gy^2, C = sum gx gy over 7 x 7.
 //    key = kden (AB - C^2) - knum (A+B)^2 (int64, exact for k = knum/kden).
-// 5. One atomicAdd per tile reserves the survivors' slots in the image's list.
+// 4. One atomicAdd per tile reserves the survivors' slots in the image's list.
 #include <cuda_runtime.h>
 
 #include "of_internal.h"
 #include "of_tile.cuh"
+#include "of_tma.cuh"
 
 namespace ofk {
 
-constexpr int QCAP = TILE_W * TILE_H / 4;  // strict maxima are never adjacent
-constexpr int WPR = SROW / 4;               // staged words per row
-constexpr int LCH_MAX = (TILE_H + 2) / 8 + 2;  // cell rows touched by a tile (cell >= 8)
+constexpr int QCAP = TILE_W * TILE_H / 4;        // strict maxima are never adjacent
+constexpr int WPR = SROW / 4;                    // staged words per row
+constexpr int LCH_MAX = (TILE_H + 2) / 8 + 2;    // cell rows touched by a tile (cell >= 8)
+constexpr int S_ROWS = TILE_H + 2;
+constexpr int S_BOX = S_ROWS * SROW;             // 5440
+constexpr int I_BOX = IMG_BOX_ROWS * SROW;       // 6400
+constexpr int S_BUF = (S_BOX + 127) / 128 * 128;
+constexpr int I_BUF = (I_BOX + 127) / 128 * 128;
 
 // 0xFF in each byte of v that is below t (t <= 255).
 __device__ __forceinline__ uint32_t bytes_lt(uint32_t v, uint32_t t) {
@@ -71,161 +77,200 @@ __device__ __forceinline__ void harris_sums(const uint8_t* __restrict__ s, int l
     C = c;
 }
 
+struct NmsTile {
+    int32_t img, x0, y0;
+};
+
 __global__ void __launch_bounds__(DET_THREADS)
 k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
-             const int32_t* __restrict__ prefix, int n_list, const Call* __restrict__ call,
-             int t_hi, int t_lo, int border, int cell) {
-    __shared__ __align__(16) uint8_t sS[(TILE_H + 2) * SROW];
-    __shared__ __align__(16) uint8_t sI[(TILE_H + 8) * SROW];
+             const int32_t* __restrict__ prefix, int n_list, int n_tiles,
+             const CUtensorMap* __restrict__ img_maps, const CUtensorMap* __restrict__ score_maps,
+             const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell) {
+    __shared__ __align__(128) uint8_t ibuf[2 * I_BUF];
+    __shared__ __align__(128) uint8_t sbuf[2 * S_BUF];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ NmsTile tinfo[2];
     __shared__ uint32_t sflag[MAX_CELLS_LOCAL];
     __shared__ uint32_t fmask[LCH_MAX * WPR];
     __shared__ uint32_t queue[QCAP];
     __shared__ int nq, qbase;
 
-    const int b = blockIdx.x;
-    const int j = find_tile_job(prefix, n_list, b);
-    const Img& I = imgs[__ldg(list + j)];
-    const int w = I.w, h = I.h;
-    const int t = b - __ldg(prefix + j);
-    const int tx = t % I.tiles_x, ty_tile = t / I.tiles_x;
-    const int X0 = I.tile_x0 + tx * TILE_W;
-    const int Y0 = border + ty_tile * TILE_H;
-    const int rx0 = border, rx1 = w - border, ry0 = border, ry1 = h - border;
+    const int tid = threadIdx.x;
     const bool cells = t_hi != t_lo;
-
-    // Cells touched by the tile and its 1-pixel halo.
-    const int cx0 = (max(X0 - 1, rx0) - rx0) / cell;
-    const int cy0 = (max(Y0 - 1, ry0) - ry0) / cell;
-    const int lcw = (TILE_W + 2) / cell + 2;
-    const int lch = (TILE_H + 2) / cell + 2;
-    // Only columns X0-1 .. X0+TILE_W feed the 3x3 test; the rest stay 0.
-    const int lox = max(rx0, X0 - 1), hix = min(rx1, X0 + TILE_W + 1);
-    if (threadIdx.x == 0) nq = 0;
-    if (cells) {
-        for (int i = threadIdx.x; i < lcw * lch; i += blockDim.x) {
-            const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
-            sflag[i] = (cx < I.ncx && cy < I.ncy) ? I.cell[cy * I.ncx + cx] : 0u;
-        }
-        __syncthreads();
-        // fmask[cyl][k]: 0xFF for each byte of staged word k in a flagged cell of cell row cyl.
-        for (int i = threadIdx.x; i < lch * WPR; i += blockDim.x) {
-            const int cyl = i / WPR, k = i - cyl * WPR;
-            uint32_t m = 0u;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int xx = X0 - HALO_X + 4 * k + e;
-                if (xx >= lox && xx < hix && sflag[cyl * lcw + (xx - rx0) / cell - cx0])
-                    m |= 0xFFu << (8 * e);
-            }
-            fmask[i] = m;
-        }
-        __syncthreads();
-    }
-
-    // 1. S(p) for rows Y0-1 .. Y0+TILE_H, columns X0-16 .. X0+TILE_W+16.
-    {
-        constexpr int CPR = SROW / 16;
-        const int n = (TILE_H + 2) * CPR;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int r = i / CPR, k = i - r * CPR;
-            const int iy = Y0 - 1 + r, ix = X0 - HALO_X + 16 * k;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (iy >= ry0 && iy < ry1 && ix + 16 > lox && ix < hix) {
-                v = __ldg(reinterpret_cast<const uint4*>(I.score + (size_t)iy * I.spitch + ix));
-                uint32_t wd[4] = {v.x, v.y, v.z, v.w};
-                const uint32_t* fm = fmask + ((iy - ry0) / cell - cy0) * WPR + 4 * k;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t val = wd[q] & range_mask4(ix + 4 * q, lox, hix);
-                    // Bytes below t_hi survive only when their cell has no strong pixel.
-                    if (cells && val) val &= ~(fm[q] & bytes_lt(val, (uint32_t)t_hi));
-                    wd[q] = val;
-                }
-                v = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-            }
-            *reinterpret_cast<uint4*>(sS + r * SROW + 16 * k) = v;
-        }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_barrier_init();
     }
     __syncthreads();
+    auto issue = [&](int t, int b) {
+        const int j = find_tile_job(prefix, n_list, t);
+        const int ii = __ldg(list + j);
+        const Img& I = imgs[ii];
+        const int tt = t - __ldg(prefix + j);
+        const int x0 = I.tile_x0 + (tt % I.tiles_x) * TILE_W, y0 = border + (tt / I.tiles_x) * TILE_H;
+        tinfo[b] = NmsTile{ii, x0, y0};
+        mbar_arrive_expect_tx(&mbar[b], S_BOX + I_BOX);
+        tma_load_2d(sbuf + b * S_BUF, score_maps + ii, x0 - HALO_X, y0 - 1, &mbar[b]);
+        tma_load_2d(ibuf + b * I_BUF, img_maps + ii, x0 - HALO_X, y0 - 4, &mbar[b]);
+    };
+    if (tid == 0 && (int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
 
-    // 2. Strict 3x3 maxima, two pixels per register.
-    const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    {
-        uint32_t hw[RPT + 2][6];
-#pragma unroll
-        for (int k = 0; k < RPT + 2; ++k) {
-            const uint8_t* row = sS + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
-            const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
-            const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
-            const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
-            hw[k][1] = __byte_perm(wm, 0u, 0x4342);  // (x-2, x-1)
-            hw[k][2] = __byte_perm(wc, 0u, 0x4140);  // (x, x+1)
-            hw[k][3] = __byte_perm(wc, 0u, 0x4342);  // (x+2, x+3)
-            hw[k][4] = __byte_perm(wp, 0u, 0x4140);  // (x+4, x+5)
+    const int lane = tid & 31, ty = tid >> 5;
+    const int64_t knum = call->knum, kden = call->kden;
+    for (int it = 0;; ++it) {
+        const int t = blockIdx.x + it * gridDim.x;
+        if (t >= n_tiles) break;
+        const int b = it & 1;
+        if (tid == 0) {
+            nq = 0;
+            if (t + (int)gridDim.x < n_tiles) {
+                fence_proxy_async_smem();
+                issue(t + gridDim.x, b ^ 1);
+            }
         }
+        const bool ok = mbar_wait(&mbar[b], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(call->status, OF_DEV_TIMEOUT);
+                mbar_wait(&mbar[b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (t + (int)gridDim.x < n_tiles)
+                    mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+            }
+            return;
+        }
+        const NmsTile ti = tinfo[b];
+        const Img& I = imgs[ti.img];
+        uint8_t* sS = sbuf + b * S_BUF;
+        const uint8_t* sI = ibuf + b * I_BUF;
+        const int X0 = ti.x0, Y0 = ti.y0;
+        const int rx0 = border, rx1 = I.w - border, ry0 = border, ry1 = I.h - border;
+        // Only columns X0-1 .. X0+TILE_W feed the 3x3 test; the rest become 0.
+        const int lox = max(rx0, X0 - 1), hix = min(rx1, X0 + TILE_W + 1);
+        const int cx0 = (max(X0 - 1, rx0) - rx0) / cell;
+        const int cy0 = (max(Y0 - 1, ry0) - ry0) / cell;
+        const int lcw = (TILE_W + 2) / cell + 2;
+        const int lch = (TILE_H + 2) / cell + 2;
+        if (cells) {
+            for (int i = tid; i < lcw * lch; i += blockDim.x) {
+                const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
+                sflag[i] = (cx < I.ncx && cy < I.ncy) ? I.cell[cy * I.ncx + cx] : 0u;
+            }
+            __syncthreads();
+            // fmask[cyl][k]: 0xFF for each byte of staged word k in a flagged cell of cell row cyl.
+            for (int i = tid; i < lch * WPR; i += blockDim.x) {
+                const int cyl = i / WPR, k = i - cyl * WPR;
+                uint32_t m = 0u;
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
+                for (int e = 0; e < 4; ++e) {
+                    const int xx = X0 - HALO_X + 4 * k + e;
+                    if (xx >= lox && xx < hix && sflag[cyl * lcw + (xx - rx0) / cell - cx0])
+                        m |= 0xFFu << (8 * e);
+                }
+                fmask[i] = m;
+            }
+            __syncthreads();
+        }
+
+        // 1. S(p) in place for rows Y0-1 .. Y0+TILE_H.
+        for (int i = tid; i < S_ROWS * WPR; i += blockDim.x) {
+            const int r = i / WPR, k = i - r * WPR;
+            const int iy = Y0 - 1 + r, ix = X0 - HALO_X + 4 * k;
+            uint32_t* wp = reinterpret_cast<uint32_t*>(sS + r * SROW) + k;
+            uint32_t val = 0u;
+            if (iy >= ry0 && iy < ry1) {
+                val = *wp & range_mask4(ix, lox, hix);
+                // Bytes below t_hi survive only when their cell has no strong pixel.
+                if (cells && val)
+                    val &= ~(fmask[((iy - ry0) / cell - cy0) * WPR + k] & bytes_lt(val, (uint32_t)t_hi));
+            }
+            *wp = val;
+        }
+        __syncthreads();
+
+        // 2. Strict 3x3 maxima, two pixels per register.
+        {
+            uint32_t hw[RPT + 2][6];
 #pragma unroll
-            for (int pr = 0; pr < 2; ++pr) {
-                // Pair (x+2pr, x+2pr+1): neighbours at column offsets -1, 0, +1.
-                const uint32_t* a = hw[r];
-                const uint32_t* c = hw[r + 1];
-                const uint32_t* d = hw[r + 2];
-                const int j = 2 + pr;
-                const uint32_t am = __byte_perm(a[j - 1], a[j], 0x5432), ap = __byte_perm(a[j], a[j + 1], 0x5432);
-                const uint32_t cm = __byte_perm(c[j - 1], c[j], 0x5432), cp = __byte_perm(c[j], c[j + 1], 0x5432);
-                const uint32_t dm = __byte_perm(d[j - 1], d[j], 0x5432), dp = __byte_perm(d[j], d[j + 1], 0x5432);
-                const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(am, a[j], ap), __vimax3_u16x2(cm, cp, dm),
-                                                   __vimax3_u16x2(d[j], dp, dp));
-                // Lane bit 15 set when centre > neighbours (values <= 255).
-                const uint32_t keep = (c[j] + 0x7FFF7FFFu - nb) & 0x80008000u;
-                if (keep) {
+            for (int k = 0; k < RPT + 2; ++k) {
+                const uint8_t* row = sS + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
+                const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+                const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+                const uint32_t wq = *reinterpret_cast<const uint32_t*>(row + 4);
+                hw[k][1] = __byte_perm(wm, 0u, 0x4342);  // (x-2, x-1)
+                hw[k][2] = __byte_perm(wc, 0u, 0x4140);  // (x, x+1)
+                hw[k][3] = __byte_perm(wc, 0u, 0x4342);  // (x+2, x+3)
+                hw[k][4] = __byte_perm(wq, 0u, 0x4140);  // (x+4, x+5)
+            }
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        if ((keep >> (16 * e + 15)) & 1u) {
-                            const int slot = atomicAdd(&nq, 1);
-                            queue[slot] = ((uint32_t)(ty * RPT + r) << 16) | (uint32_t)(4 * lane + 2 * pr + e);
+            for (int r = 0; r < RPT; ++r) {
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    const uint32_t* a = hw[r];
+                    const uint32_t* c = hw[r + 1];
+                    const uint32_t* d = hw[r + 2];
+                    const int j = 2 + pr;
+                    const uint32_t am = __byte_perm(a[j - 1], a[j], 0x5432), ap = __byte_perm(a[j], a[j + 1], 0x5432);
+                    const uint32_t cm = __byte_perm(c[j - 1], c[j], 0x5432), cp = __byte_perm(c[j], c[j + 1], 0x5432);
+                    const uint32_t dm = __byte_perm(d[j - 1], d[j], 0x5432), dp = __byte_perm(d[j], d[j + 1], 0x5432);
+                    const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(am, a[j], ap), __vimax3_u16x2(cm, cp, dm),
+                                                       __vimax3_u16x2(d[j], dp, dp));
+                    // Lane bit 15 set when centre > neighbours (values <= 255).
+                    const uint32_t keep = (c[j] + 0x7FFF7FFFu - nb) & 0x80008000u;
+                    if (keep) {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            if ((keep >> (16 * e + 15)) & 1u) {
+                                const int slot = atomicAdd(&nq, 1);
+                                queue[slot] = ((uint32_t)(ty * RPT + r) << 16) | (uint32_t)(4 * lane + 2 * pr + e);
+                            }
                         }
                     }
                 }
             }
         }
-    }
-    __syncthreads();
-    const int count = nq;
-    if (count == 0) return;
-    if (threadIdx.x == 0) qbase = atomicAdd(&I.ctr[0], count);
-
-    // 3. Image tile for the survivors' 9 x 9 footprints.
-    stage_tile(sI, I.img, w, h, I.pitch, X0 - HALO_X, Y0 - 4, TILE_H + 8);
-    __syncthreads();
-
-    const int base = qbase;
-    const int64_t knum = call->knum, kden = call->kden;
-    for (int i = threadIdx.x; i < count; i += blockDim.x) {
-        const uint32_t e = queue[i];
-        const int lx = (int)(e & 0xFFFFu), ly = (int)(e >> 16);
-        int32_t A, B, C;
-        harris_sums(sI, lx, ly, A, B, C);
-        const int64_t det = (int64_t)A * B - (int64_t)C * C;
-        const int64_t tr = (int64_t)A + B;
-        const int64_t key = kden * det - knum * tr * tr;
-        const int slot = base + i;
-        if (slot < I.cand_cap) {
-            I.ckey[slot] = (uint64_t)key ^ 0x8000000000000000ull;
-            I.cyx[slot] = ((uint32_t)(Y0 + ly) << 16) | (uint32_t)(X0 + lx);
-        } else {
-            I.ctr[2] = 1;  // cannot happen: survivors are an independent set
+        __syncthreads();
+        const int count = nq;
+        if (count > 0) {
+            if (tid == 0) qbase = atomicAdd(&I.ctr[0], count);
+            __syncthreads();
+            const int base = qbase;
+            for (int i = tid; i < count; i += blockDim.x) {
+                const uint32_t e = queue[i];
+                const int lx = (int)(e & 0xFFFFu), ly = (int)(e >> 16);
+                int32_t A, B, C;
+                harris_sums(sI, lx, ly, A, B, C);
+                const int64_t det = (int64_t)A * B - (int64_t)C * C;
+                const int64_t tr = (int64_t)A + B;
+                const int64_t key = kden * det - knum * tr * tr;
+                const int slot = base + i;
+                if (slot < I.cand_cap) {
+                    I.ckey[slot] = (uint64_t)key ^ 0x8000000000000000ull;
+                    I.cyx[slot] = ((uint32_t)(Y0 + ly) << 16) | (uint32_t)(X0 + lx);
+                } else {
+                    I.ctr[2] = 1;  // cannot happen: survivors are an independent set
+                }
+            }
         }
+        fence_proxy_async_smem();  // this thread's buffer accesses before the next TMA into them
+        __syncthreads();
     }
 }
 
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
-                       int n_list, int n_tiles, const Call* call, int t_hi, int t_lo, int border,
-                       int cell, void* stream) {
+                       int n_list, int n_tiles, const CUtensorMap* img_maps, const CUtensorMap* score_maps,
+                       const Call* call, int t_hi, int t_lo, int border, int cell, int grid, void* stream) {
     if (n_tiles <= 0) return;
-    k_nms_harris<<<n_tiles, DET_THREADS, 0, (cudaStream_t)stream>>>(
-        imgs, img_list, tile_prefix, n_list, call, t_hi, t_lo, border, cell);
+    grid = grid < n_tiles ? grid : n_tiles;
+    k_nms_harris<<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(
+        imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell);
+}
+
+int nms_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_harris, DET_THREADS, 0) != cudaSuccess || n < 1)
+        n = 1;
+    return n;
 }
 
 }  // namespace ofk

@@ -35,7 +35,8 @@ k_orient(const Img* __restrict__ imgs, int n_img, const Call* __restrict__ call)
         if (lane == 0) {
             int total = 0;
             for (int l = 0; l < levels; ++l) total += F[l].ctr[1];
-            call->counts[I.frame] = total;
+            // A detect-stage wait that expired leaves partial results: report it instead.
+            call->counts[I.frame] = *call->status ? OF_ERR_TIMEOUT : total;
         }
     }
     if (rank >= I.quota || rank >= I.ctr[1]) return;

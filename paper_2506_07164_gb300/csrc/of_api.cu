@@ -8,12 +8,15 @@
 // pointers only re-uploads that block (from pinned staging memory) before
 // launching the same graph.  The arena is allocated once by of_create for the
 // largest batch the handle accepts; detect calls never allocate device memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -23,6 +26,9 @@
 
 namespace ofk {
 void set_select_smem_limit(int bytes);
+int fast_blocks_per_sm();
+int nms_blocks_per_sm();
+void launch_wait_test(const int32_t* flag, int32_t* status, uint64_t limit_ns, void* stream);
 }
 
 using namespace ofk;
@@ -44,6 +50,39 @@ int fail(int code, const std::string& msg) {
     } while (0)
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mutex;
+
+// The driver's tensor-map encoder, looked up through the runtime (no libcuda link).
+int resolve_encoder() {
+    std::lock_guard<std::mutex> lock(g_encode_mutex);
+    if (g_encode) return OF_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(OF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return OF_OK;
+}
+
+// 2-D uint8 tensor map over a w x h image with `pitch` bytes per row and a
+// box of box_w x box_h bytes; reads outside the image return 0.
+int encode_u8(CUtensorMap* m, const void* base, int w, int h, int pitch, int box_w, int box_h) {
+    std::memset(m, 0, sizeof(*m));
+    if (!base || w < 1 || h < 1) return OF_OK;  // unused map
+    const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides,
+                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(OF_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return OF_OK;
+}
 
 struct FrameKey {
     int w, h, pitch;
@@ -171,6 +210,9 @@ struct Plan {
     Call h_call{};
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_rsp = 0, off_dl = 0, off_dp = 0, off_tab = 0;
+    size_t off_maps = 0;
+    std::vector<CUtensorMap> h_maps;  // [image maps | score maps], n_img each
+    int grid_fast = 0, grid_nms = 0;
     size_t header_bytes = 0;
     uint8_t* stage[2] = {nullptr, nullptr};
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -186,6 +228,7 @@ struct Plan {
     Img* d_img() const { return reinterpret_cast<Img*>(dbuf + off_img); }
     Resize* d_rs() const { return reinterpret_cast<Resize*>(dbuf + off_rs); }
     Call* d_call() const { return reinterpret_cast<Call*>(dbuf + off_call); }
+    const CUtensorMap* d_maps() const { return reinterpret_cast<const CUtensorMap*>(dbuf + off_maps); }
     const int32_t* d_rsp() const { return reinterpret_cast<const int32_t*>(dbuf + off_rsp); }
     const int32_t* d_dl() const { return reinterpret_cast<const int32_t*>(dbuf + off_dl); }
     const int32_t* d_dp() const { return reinterpret_cast<const int32_t*>(dbuf + off_dp); }
@@ -214,7 +257,8 @@ struct of_handle {
     cudaStream_t cap_stream = nullptr;
     uint8_t* arena = nullptr;
     size_t arena_bytes = 0;
-    int32_t* d_counts = nullptr;  // of_detect's per-frame count
+    int32_t* d_counts = nullptr;  // [0] of_detect's count, [4] device status word
+    int n_sms = 0;
     int32_t* h_count = nullptr;   // pinned
     std::vector<Plan*> plans;
     Plan* last = nullptr;
@@ -258,11 +302,13 @@ void enqueue_stages(of_handle* H, Plan* P, int first, int last, cudaStream_t st)
                 break;
             case 1:
                 launch_fast(P->d_img(), P->d_dl(), P->d_dp(), (int)P->det_list.size(),
-                            P->det_tiles, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell, st);
+                            P->det_tiles, P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border,
+                            s.cell, P->grid_fast, st);
                 break;
             case 2:
                 launch_nms_harris(P->d_img(), P->d_dl(), P->d_dp(), (int)P->det_list.size(),
-                                  P->det_tiles, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell, st);
+                                  P->det_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(),
+                                  s.t_hi, s.t_lo, s.border, s.cell, P->grid_nms, st);
                 break;
             case 3:
                 launch_select(P->d_img(), P->n_img, P->d_call(), P->max_quota, st);
@@ -409,6 +455,22 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     C.radius = s.radius;
     C.n_img = P->n_img;
     C.total_slots = P->total_slots;
+    C.status = H->d_counts + 4;
+    P->grid_fast = H->n_sms * fast_blocks_per_sm();
+    P->grid_nms = H->n_sms * nms_blocks_per_sm();
+
+    // Tensor maps: image boxes for FAST and NMS, score boxes for NMS.
+    P->h_maps.assign(2 * P->n_img, CUtensorMap{});
+    for (int i = 0; i < P->n_img; ++i) {
+        const Img& I = P->h_img[i];
+        int rc = encode_u8(&P->h_maps[i], I.img, I.w, I.h, I.pitch, SROW, IMG_BOX_ROWS);
+        if (rc == OF_OK && I.score)
+            rc = encode_u8(&P->h_maps[P->n_img + i], I.score, I.w, I.h, I.spitch, SROW, SCORE_BOX_ROWS);
+        if (rc != OF_OK) {
+            free_plan(P);
+            return rc;
+        }
+    }
 
     // Device descriptor block: [Call | Img[] | Resize[]] (re-uploaded when
     // pointers change) then [resize prefix | detect list | detect prefix | tables].
@@ -418,7 +480,9 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->off_img = off;
     off = align_up(off + sizeof(Img) * P->n_img, 16);
     P->off_rs = off;
-    off = align_up(off + sizeof(Resize) * std::max<size_t>(P->h_rs.size(), 1), 16);
+    off = align_up(off + sizeof(Resize) * std::max<size_t>(P->h_rs.size(), 1), 128);
+    P->off_maps = off;
+    off = align_up(off + sizeof(CUtensorMap) * P->h_maps.size(), 16);
     P->header_bytes = off;
     P->off_rsp = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->rs_prefix.size(), 1), 16);
@@ -445,6 +509,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_call, &C, sizeof(C));
     put(P->off_img, P->h_img.data(), sizeof(Img) * P->h_img.size());
     put(P->off_rs, P->h_rs.data(), sizeof(Resize) * P->h_rs.size());
+    put(P->off_maps, P->h_maps.data(), sizeof(CUtensorMap) * P->h_maps.size());
     put(P->off_rsp, P->rs_prefix.data(), sizeof(int32_t) * P->rs_prefix.size());
     put(P->off_dl, P->det_list.data(), sizeof(int32_t) * P->det_list.size());
     put(P->off_dp, P->det_prefix.data(), sizeof(int32_t) * P->det_prefix.size());
@@ -493,7 +558,10 @@ int bind_plan(of_handle* H, Plan* P, const of_frame* frames, of_keypoint* out, i
     for (int f = 0; f < nf; ++f) {
         if (P->frames[f].copy) continue;
         P->bound_src[f] = frames[f].img;
-        P->h_img[f * nl].img = frames[f].img;
+        Img& I0 = P->h_img[f * nl];
+        I0.img = frames[f].img;
+        const int rc = encode_u8(&P->h_maps[f * nl], I0.img, I0.w, I0.h, I0.pitch, SROW, IMG_BOX_ROWS);
+        if (rc != OF_OK) return rc;
     }
     // Level-1 resize jobs read level 0.
     if (nl > 1) {
@@ -515,6 +583,7 @@ int bind_plan(of_handle* H, Plan* P, const of_frame* frames, of_keypoint* out, i
     std::memcpy(st + P->off_call, &P->h_call, sizeof(Call));
     std::memcpy(st + P->off_img, P->h_img.data(), sizeof(Img) * P->h_img.size());
     std::memcpy(st + P->off_rs, P->h_rs.data(), sizeof(Resize) * P->h_rs.size());
+    std::memcpy(st + P->off_maps, P->h_maps.data(), sizeof(CUtensorMap) * P->h_maps.size());
     OF_CK(cudaMemcpyAsync(P->dbuf, st, P->header_bytes, cudaMemcpyHostToDevice, H->stream));
     OF_CK(cudaEventRecord(P->ev[si], H->stream));
     return OF_OK;
@@ -612,6 +681,12 @@ int run_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, fl
 namespace ofk {
 // Lets other translation units report through of_last_error().
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+int encode_u8_map(CUtensorMap* m, const void* base, int w, int h, int pitch, int box_w, int box_h) {
+    const int rc = resolve_encoder();
+    if (rc != OF_OK) return rc;
+    return encode_u8(m, base, w, h, pitch, box_w, box_h);
+}
 }  // namespace ofk
 
 extern "C" {
@@ -670,9 +745,18 @@ of_handle* of_create(const of_params* pin) {
     H->arena_bytes = L.total;
     e = cudaMalloc(&H->arena, H->arena_bytes);
     if (e != cudaSuccess) return bail(e, "cudaMalloc(arena)");
-    e = cudaMalloc(&H->d_counts, sizeof(int32_t) * 4);
+    e = cudaMalloc(&H->d_counts, sizeof(int32_t) * 8);
     if (e != cudaSuccess) return bail(e, "cudaMalloc(counts)");
-    e = cudaMallocHost(&H->h_count, sizeof(int32_t) * 4);
+    e = cudaMemset(H->d_counts, 0, sizeof(int32_t) * 8);
+    if (e != cudaSuccess) return bail(e, "cudaMemset(counts)");
+    e = cudaMallocHost(&H->h_count, sizeof(int32_t) * 8);
+    if (e != cudaSuccess) return bail(e, "cudaMallocHost");
+    e = cudaDeviceGetAttribute(&H->n_sms, cudaDevAttrMultiProcessorCount, H->device);
+    if (e != cudaSuccess) return bail(e, "cudaDeviceGetAttribute");
+    if (resolve_encoder() != OF_OK) {
+        of_destroy(H);
+        return nullptr;
+    }
     if (e != cudaSuccess) return bail(e, "cudaMallocHost");
     ofk::set_select_smem_limit(ofk::select_smem_bytes(std::max(p.max_features, 1)));
     e = cudaGetLastError();
@@ -717,10 +801,36 @@ int of_detect(of_handle* H, const uint8_t* img, int w, int h_px, int pitch, int 
                              H->d_counts);
     if (rc != OF_OK) return rc;
     DeviceGuard dg(H->device);
-    OF_CK(cudaMemcpyAsync(H->h_count, H->d_counts, sizeof(int32_t), cudaMemcpyDeviceToHost,
+    OF_CK(cudaMemcpyAsync(H->h_count, H->d_counts, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost,
                           H->stream));
     OF_CK(cudaStreamSynchronize(H->stream));
+    if (H->h_count[4] != 0) {
+        OF_CK(cudaMemset(H->d_counts + 4, 0, sizeof(int32_t)));
+        return fail(OF_ERR_TIMEOUT, "a device-side wait expired");
+    }
     return H->h_count[0];
+}
+
+int of_sync(of_handle* H) {
+    if (!H) return fail(OF_ERR_ARG, "null handle");
+    DeviceGuard dg(H->device);
+    OF_CK(cudaMemcpyAsync(H->h_count + 4, H->d_counts + 4, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          H->stream));
+    OF_CK(cudaStreamSynchronize(H->stream));
+    if (H->h_count[4] != 0) {
+        OF_CK(cudaMemset(H->d_counts + 4, 0, sizeof(int32_t)));
+        return fail(OF_ERR_TIMEOUT, "a device-side wait expired");
+    }
+    return OF_OK;
+}
+
+int of_test_timeout(of_handle* H, int64_t limit_us) {
+    if (!H || limit_us < 1 || limit_us > 10000000) return fail(OF_ERR_ARG, "limit_us must be 1..1e7");
+    DeviceGuard dg(H->device);
+    // Waits on a word of the handle's own block that nothing sets.
+    launch_wait_test(H->d_counts + 6, H->d_counts + 4, (uint64_t)limit_us * 1000ull, H->stream);
+    OF_CK(cudaGetLastError());
+    return of_sync(H);
 }
 
 int64_t of_inspect(of_handle* H, int what, int frame, int level, void* dst, int64_t dst_bytes,

@@ -1,6 +1,7 @@
 // Internal descriptors shared by the host runtime and the sm_103a kernels.
 // Not part of the public ABI (include/ofast.h).
 #pragma once
+#include <cuda.h>
 #include <stdint.h>
 
 #include "ofast.h"
@@ -18,6 +19,8 @@ constexpr int RPT = TILE_H / 8;        // rows per thread
 constexpr int HALO_X = 16;             // left/right staging margin (bytes), keeps alignment
 constexpr int SROW = TILE_W + 2 * HALO_X;  // staged row length (bytes)
 constexpr int MAX_CELLS_LOCAL = 128;   // cells overlapping one tile (+halo); needs cell >= 8
+constexpr int IMG_BOX_ROWS = TILE_H + 8;   // image TMA box: rows Y0-4 .. Y0+TILE_H+3, SROW bytes wide
+constexpr int SCORE_BOX_ROWS = TILE_H + 2; // score TMA box: rows Y0-1 .. Y0+TILE_H
 
 // Resize tile: 128 x 16 output pixels, each thread writes 4 consecutive pixels.
 constexpr int RS_TILE_W = 128;
@@ -63,6 +66,7 @@ struct Resize {
 struct Call {
     of_keypoint* out;     // n_frames * n_features records
     int32_t* counts;      // n_frames
+    int32_t* status;      // device status word (OF_DEV_* bits), cleared before each call
     int64_t knum, kden;   // Harris k = knum / kden
     int32_t n_frames, levels, n_features;
     int32_t t_hi, t_lo;   // t_lo == t_hi: no per-cell fallback
@@ -79,11 +83,12 @@ namespace ofk {
 void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
                    void* stream);
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
-                 int n_list, int n_tiles, const Call* call, int t_hi, int t_lo, int border,
-                 int cell, void* stream);
+                 int n_list, int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi,
+                 int t_lo, int border, int cell, int grid, void* stream);
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
-                       int n_list, int n_tiles, const Call* call, int t_hi, int t_lo, int border,
-                       int cell, void* stream);
+                       int n_list, int n_tiles, const CUtensorMap* img_maps,
+                       const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,
+                       int border, int cell, int grid, void* stream);
 void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, void* stream);
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
 void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t* dst,

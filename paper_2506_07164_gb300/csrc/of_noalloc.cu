@@ -34,6 +34,9 @@
 namespace ofk {
 void set_select_smem_limit(int bytes);
 void set_last_error(const std::string& msg);
+int encode_u8_map(CUtensorMap* m, const void* base, int w, int h, int pitch, int box_w, int box_h);
+int fast_blocks_per_sm();
+int nms_blocks_per_sm();
 }
 using namespace ofk;
 
@@ -43,6 +46,7 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[OF_NOALLOC_SCRATCH_BY
 
 constexpr int kMaxDevices = 64;
 uint8_t* g_scratch_addr[kMaxDevices] = {};
+int g_grid_fast[kMaxDevices] = {}, g_grid_nms[kMaxDevices] = {};
 std::mutex g_setup_mutex;
 
 int na_fail(int code, const std::string& msg) {
@@ -52,12 +56,17 @@ int na_fail(int code, const std::string& msg) {
 
 size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Writes the descriptors into the scratch and clears what must start at zero.
-__global__ void k_noalloc_setup(Img img, Call call, Img* d_img, Call* d_call, int32_t* d_list,
+// Writes the descriptors and tensor maps into the scratch and clears what
+// must start at zero.
+__global__ void k_noalloc_setup(Img img, Call call, CUtensorMap img_map, CUtensorMap score_map,
+                                Img* d_img, Call* d_call, CUtensorMap* d_maps, int32_t* d_list,
                                 int32_t* zero, int zero_words, int32_t* out_count) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *d_img = img;
         *d_call = call;
+        d_maps[0] = img_map;
+        d_maps[1] = score_map;
+        asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
         d_list[0] = 0;  // the one image
         d_list[1] = 0;  // its first tile
         if (call.n_features == 0) *out_count = 0;
@@ -66,7 +75,7 @@ __global__ void k_noalloc_setup(Img img, Call call, Img* d_img, Call* d_call, in
         zero[i] = 0;
 }
 
-int device_scratch(uint8_t** out) {
+int device_scratch(uint8_t** out, int* grid_fast, int* grid_nms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(OF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -78,12 +87,18 @@ int device_scratch(uint8_t** out) {
         if (e != cudaSuccess || !p)
             return na_fail(OF_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         set_select_smem_limit(select_smem_bytes(8192));
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        g_grid_fast[dev] = sms * fast_blocks_per_sm();
+        g_grid_nms[dev] = sms * nms_blocks_per_sm();
         e = cudaGetLastError();
         if (e != cudaSuccess)
             return na_fail(OF_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
         g_scratch_addr[dev] = static_cast<uint8_t*>(p);
     }
     *out = g_scratch_addr[dev];
+    *grid_fast = g_grid_fast[dev];
+    *grid_nms = g_grid_nms[dev];
     return OF_OK;
 }
 
@@ -118,10 +133,12 @@ extern "C" int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pit
     off = up(off + sizeof(Img), 256);
     const size_t o_call = off;
     off = up(off + sizeof(Call), 256);
+    const size_t o_maps = off;
+    off = up(off + 2 * sizeof(CUtensorMap), 256);
     const size_t o_list = off;
     off = up(off + 2 * sizeof(int32_t), 256);
-    const size_t o_zero = off;  // counters, then cell flags
-    off = up(off + 4 * sizeof(int32_t) + sizeof(uint32_t) * (size_t)ncx * ncy, 256);
+    const size_t o_zero = off;  // counters (4), status (4), then cell flags
+    off = up(off + 8 * sizeof(int32_t) + sizeof(uint32_t) * (size_t)ncx * ncy, 256);
     const size_t zero_bytes = off - o_zero;
     const size_t o_copy = off;
     if (copy) off = up(off + (size_t)spitch * h, 256);
@@ -141,7 +158,8 @@ extern "C" int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pit
                                              std::to_string((size_t)OF_NOALLOC_SCRATCH_BYTES));
 
     uint8_t* S = nullptr;
-    const int rc = device_scratch(&S);
+    int grid_fast = 0, grid_nms = 0;
+    const int rc = device_scratch(&S, &grid_fast, &grid_nms);
     if (rc != OF_OK) return rc;
 
     Img I;
@@ -158,7 +176,7 @@ extern "C" int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pit
     I.ctr = reinterpret_cast<int32_t*>(S + o_zero);
     I.lscale = 1.0;
     if (det) {
-        I.cell = reinterpret_cast<uint32_t*>(S + o_zero + 4 * sizeof(int32_t));
+        I.cell = reinterpret_cast<uint32_t*>(S + o_zero + 8 * sizeof(int32_t));
         I.score = S + o_score;
         I.ckey = reinterpret_cast<uint64_t*>(S + o_ckey);
         I.cyx = reinterpret_cast<uint32_t*>(S + o_cyx);
@@ -172,6 +190,7 @@ extern "C" int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pit
     std::memset(&Cl, 0, sizeof(Cl));
     Cl.out = out_kpts;
     Cl.counts = out_count;
+    Cl.status = reinterpret_cast<int32_t*>(S + o_zero) + 4;  // a timeout shows up as *out_count < 0
     Cl.knum = knum;
     Cl.kden = kden;
     Cl.n_frames = 1;
@@ -185,11 +204,16 @@ extern "C" int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pit
     Cl.n_img = 1;
     Cl.total_slots = n_features;
 
+    CUtensorMap maps[2];
+    int mrc = encode_u8_map(&maps[0], I.img, w, h, I.pitch, SROW, IMG_BOX_ROWS);
+    if (mrc == OF_OK) mrc = encode_u8_map(&maps[1], det ? I.score : nullptr, w, h, spitch, SROW, SCORE_BOX_ROWS);
+    if (mrc != OF_OK) return mrc;
     Img* d_img = reinterpret_cast<Img*>(S + o_img);
     Call* d_call = reinterpret_cast<Call*>(S + o_call);
+    CUtensorMap* d_maps = reinterpret_cast<CUtensorMap*>(S + o_maps);
     int32_t* d_list = reinterpret_cast<int32_t*>(S + o_list);
     const int zero_words = (int)(zero_bytes / sizeof(int32_t));
-    k_noalloc_setup<<<4, 256, 0, st>>>(I, Cl, d_img, d_call, d_list,
+    k_noalloc_setup<<<4, 256, 0, st>>>(I, Cl, maps[0], maps[1], d_img, d_call, d_maps, d_list,
                                        reinterpret_cast<int32_t*>(S + o_zero), zero_words, out_count);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(OF_ERR_CUDA, std::string("setup kernel: ") + cudaGetErrorString(e));
@@ -198,8 +222,9 @@ extern "C" int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pit
         if (e != cudaSuccess) return na_fail(OF_ERR_CUDA, std::string("copy: ") + cudaGetErrorString(e));
     }
     const int tiles = I.tiles_x * I.tiles_y;
-    launch_fast(d_img, d_list, d_list + 1, 1, tiles, d_call, fast_t, t_lo, border, cell, st);
-    launch_nms_harris(d_img, d_list, d_list + 1, 1, tiles, d_call, fast_t, t_lo, border, cell, st);
+    launch_fast(d_img, d_list, d_list + 1, 1, tiles, d_maps, d_call, fast_t, t_lo, border, cell, grid_fast, st);
+    launch_nms_harris(d_img, d_list, d_list + 1, 1, tiles, d_maps, d_maps + 1, d_call, fast_t, t_lo, border, cell,
+                      grid_nms, st);
     launch_select(d_img, 1, d_call, quota > 0 ? quota : 1, st);
     launch_orient(d_img, 1, d_call, n_features, st);
     e = cudaGetLastError();

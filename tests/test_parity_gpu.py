@@ -219,3 +219,25 @@ def test_invalid_calls_return_errors():
     # The handle still works afterwards.
     assert ofg.of_detect(det.h, img, 320, 240, 320, 2, 1.2, 20, 0.04, 50, det.out) == 0
     det.close()
+
+
+# ------------------------------------------------------- failure path
+def test_device_wait_timeout_is_reported_and_handle_survives():
+    """A bounded device wait on a flag nothing sets expires, is reported as
+    OF_ERR_TIMEOUT through of_sync, and the handle keeps working."""
+    det = ofg.Detector(640, 480, max_levels=2, max_features=300)
+    assert ofg.of_test_timeout(det.h, 20000) == ofg.OF_ERR_TIMEOUT
+    assert ofg.of_sync(det.h) == 0  # the condition was cleared
+    img = synth.scene(640, 480, 77)
+    kp = det.detect(torch.from_numpy(img).cuda(), levels=2, fast_t=20, n_features=300)
+    compare_keypoints(kp, oracle.detect(img, levels=2, fast_t=20, n_features=300))
+    det.close()
+
+
+def test_batch_then_sync_ok():
+    det = ofg.Detector(640, 480, max_levels=3, max_features=200, max_batch=4)
+    imgs = [torch.from_numpy(synth.scene(640, 480, 80 + i)).cuda() for i in range(4)]
+    det.detect_batch(imgs, levels=3, fast_t=20, n_features=200)
+    assert ofg.of_sync(det.h) == 0
+    assert (det.counts[:4].cpu().numpy() > 0).all()
+    det.close()
