@@ -2,10 +2,11 @@
 // an ORB front end, Sec. 1; level sizes "decrease exponentially", Sec. 6.1).
 //
 // One launch resizes level l of every frame in the batch.  Each block owns a
-// 128 x 16 output tile: it stages the tile's source window in shared memory
+// 128 x 64 output tile: it stages the tile's source window in shared memory
 // with aligned 16-byte loads (direct loads when the window is larger than the
 // buffer, i.e. scales above ~2), then each thread writes 4 consecutive output
-// pixels with one 32-bit store.  Source coordinates come from per-axis tables computed on
+// pixels of 4 rows, one 32-bit store per row, with its 4 column weights kept
+// in registers.  Source coordinates come from per-axis tables computed on
 // the host: (i0 << 12) | a, a in [0, 2048] the weight of sample i0 + 1 in
 // units of 1/2048; one rounding at the end:
 //   out = ((2048-ay)((2048-ax)p00 + ax p01) + ay((2048-ax)p10 + ax p11) + 2^21) >> 22.
@@ -25,9 +26,11 @@ __device__ __forceinline__ int find_job(const int32_t* __restrict__ prefix, int 
     return lo;
 }
 
-// Shared-memory source window: up to RS_SW x RS_SH bytes (scale up to ~2).
+// Shared-memory source window: up to RS_SW x RS_SH bytes (enough for scales
+// up to 2 with a 128 x 64 output tile).
 constexpr int RS_SW = 288;
-constexpr int RS_SH = 40;
+constexpr int RS_SH = 136;
+constexpr int RS_RPT = RS_TILE_H / (RS_THREADS / 32);  // output rows per thread
 
 __device__ __forceinline__ int bilerp(int p00, int p01, int p10, int p11, int ax, int ay) {
     const int top = (2048 - ax) * p00 + ax * p01;
@@ -38,26 +41,32 @@ __device__ __forceinline__ int bilerp(int p00, int p01, int p10, int p11, int ax
 __global__ void __launch_bounds__(RS_THREADS)
 k_resize(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix, int n_jobs) {
     __shared__ __align__(16) uint8_t win[RS_SH * RS_SW];
-    __shared__ int32_t xt[RS_TILE_W], yt[RS_TILE_H];
+    __shared__ int32_t yt[RS_TILE_H];
+    __shared__ int32_t sjob, sx0s, sy0s, sbytes, srows;
     const int b = blockIdx.x;
-    const int j = find_job(prefix, n_jobs, b);
-    const Resize J = jobs[j];
+    if (threadIdx.x == 0) sjob = find_job(prefix, n_jobs, b);
+    __syncthreads();
+    const int j = sjob;
+    const Resize& J = jobs[j];
     const int t = b - __ldg(prefix + j);
     const int tx = t % J.tiles_x, ty = t / J.tiles_x;
     const int X0 = tx * RS_TILE_W, Y0 = ty * RS_TILE_H;
     const int nx = min(RS_TILE_W, J.dw - X0), ny = min(RS_TILE_H, J.dh - Y0);
-    for (int i = threadIdx.x; i < RS_TILE_W + RS_TILE_H; i += blockDim.x) {
-        if (i < RS_TILE_W) xt[i] = i < nx ? __ldg(J.xtab + X0 + i) : 0;
-        else yt[i - RS_TILE_W] = (i - RS_TILE_W) < ny ? __ldg(J.ytab + Y0 + i - RS_TILE_W) : 0;
+    const int sw = J.sw, sh = J.sh;
+    for (int i = threadIdx.x; i < RS_TILE_H; i += blockDim.x) yt[i] = i < ny ? __ldg(J.ytab + Y0 + i) : 0;
+    if (threadIdx.x == 0) {
+        // Source window of the tile: columns [sx0, sx1], rows [sy0, sy1].
+        const int sx0 = (__ldg(J.xtab + X0) >> 12) & ~15;
+        const int sx1 = min((__ldg(J.xtab + X0 + nx - 1) >> 12) + 1, sw - 1);
+        const int sy0 = __ldg(J.ytab + Y0) >> 12;
+        const int sy1 = min((__ldg(J.ytab + Y0 + ny - 1) >> 12) + 1, sh - 1);
+        sx0s = sx0;
+        sy0s = sy0;
+        sbytes = ((sx1 - sx0) / 16 + 1) * 16;
+        srows = sy1 - sy0 + 1;
     }
     __syncthreads();
-    // Source window of the tile: columns [sx0, sx1], rows [sy0, sy1].
-    const int sx0 = (xt[0] >> 12) & ~15;
-    const int sx1 = min((xt[nx - 1] >> 12) + 1, J.sw - 1);
-    const int sy0 = yt[0] >> 12;
-    const int sy1 = min((yt[ny - 1] >> 12) + 1, J.sh - 1);
-    const int wbytes = ((sx1 - sx0) / 16 + 1) * 16;
-    const int wrows = sy1 - sy0 + 1;
+    const int sx0 = sx0s, sy0 = sy0s, wbytes = sbytes, wrows = srows;
     const bool staged = wbytes <= RS_SW && wrows <= RS_SH;  // uniform per block
     if (staged) {
         const int cpr = wbytes / 16;
@@ -65,55 +74,63 @@ k_resize(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix, in
             const int r = i / cpr, k = i - r * cpr;
             const int ix = sx0 + 16 * k;
             const uint8_t* p = J.src + (size_t)(sy0 + r) * J.spitch + ix;
-            uint4 v;
-            if (ix + 16 <= J.sw) {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (ix + 16 <= sw) {
                 v = __ldg(reinterpret_cast<const uint4*>(p));  // src and spitch are 16-byte aligned
             } else {
-                uint32_t wd[4] = {0u, 0u, 0u, 0u};
-                for (int q = 0; q < 16 && ix + q < J.sw; ++q) wd[q >> 2] |= (uint32_t)__ldg(p + q) << (8 * (q & 3));
-                v = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                // Ragged end of the row: bytewise, in bounds.
+                uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+                for (int q = 0; q < 16 && ix + q < sw; ++q) {
+                    const uint32_t byte = (uint32_t)__ldg(p + q) << (8 * (q & 3));
+                    if (q < 4) w0 |= byte; else if (q < 8) w1 |= byte; else if (q < 12) w2 |= byte; else w3 |= byte;
+                }
+                v = make_uint4(w0, w1, w2, w3);
             }
             *reinterpret_cast<uint4*>(win + r * RS_SW + 16 * k) = v;
         }
     }
     __syncthreads();
 
-    const int lx = (threadIdx.x & 31) * 4, ly = threadIdx.x >> 5;
-    if (ly >= ny || lx >= nx) return;
-    const int y = Y0 + ly, x = X0 + lx;
-    const int y0 = yt[ly] >> 12, ay = yt[ly] & 4095;
-    const int y1 = min(y0 + 1, J.sh - 1);
+    // Each thread: 4 consecutive columns, rows ly, ly + 16, ...
+    const int lx = (threadIdx.x & 31) * 4, ly0 = threadIdx.x >> 5;
+    if (lx >= nx) return;
     const int n = min(4, nx - lx);
-    uint32_t packed = 0;
-    if (staged) {
-        const uint8_t* r0 = win + (y0 - sy0) * RS_SW - sx0;
-        const uint8_t* r1 = win + (y1 - sy0) * RS_SW - sx0;
+    int x0[4], x1[4], ax[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (i < n) {
-                const int e = xt[lx + i];
-                const int x0 = e >> 12, ax = e & 4095, x1 = min(x0 + 1, J.sw - 1);
-                packed |= (uint32_t)bilerp(r0[x0], r0[x1], r1[x0], r1[x1], ax, ay) << (8 * i);
-            }
-        }
-    } else {
-        const uint8_t* r0 = J.src + (size_t)y0 * J.spitch;
-        const uint8_t* r1 = J.src + (size_t)y1 * J.spitch;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (i < n) {
-                const int e = xt[lx + i];
-                const int x0 = e >> 12, ax = e & 4095, x1 = min(x0 + 1, J.sw - 1);
-                packed |= (uint32_t)bilerp(__ldg(r0 + x0), __ldg(r0 + x1), __ldg(r1 + x0), __ldg(r1 + x1), ax, ay)
-                          << (8 * i);
-            }
-        }
+    for (int i = 0; i < 4; ++i) {
+        const int e = i < n ? __ldg(J.xtab + X0 + lx + i) : __ldg(J.xtab + X0 + lx);
+        x0[i] = e >> 12;
+        ax[i] = e & 4095;
+        x1[i] = min(x0[i] + 1, sw - 1);
     }
-    uint8_t* d = J.dst + (size_t)y * J.dpitch + x;
-    if (n == 4) {
-        *reinterpret_cast<uint32_t*>(d) = packed;  // x % 4 == 0, dpitch % 16 == 0
-    } else {
-        for (int i = 0; i < n; ++i) d[i] = (uint8_t)(packed >> (8 * i));
+#pragma unroll
+    for (int rr = 0; rr < RS_RPT; ++rr) {
+        const int ly = ly0 + rr * (RS_THREADS / 32);
+        if (ly >= ny) break;
+        const int y0 = yt[ly] >> 12, ay = yt[ly] & 4095;
+        const int y1 = min(y0 + 1, sh - 1);
+        uint32_t packed = 0;
+        if (staged) {
+            const uint8_t* r0 = win + (y0 - sy0) * RS_SW - sx0;
+            const uint8_t* r1 = win + (y1 - sy0) * RS_SW - sx0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                packed |= (uint32_t)bilerp(r0[x0[i]], r0[x1[i]], r1[x0[i]], r1[x1[i]], ax[i], ay) << (8 * i);
+        } else {
+            const uint8_t* r0 = J.src + (size_t)y0 * J.spitch;
+            const uint8_t* r1 = J.src + (size_t)y1 * J.spitch;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                packed |= (uint32_t)bilerp(__ldg(r0 + x0[i]), __ldg(r0 + x1[i]), __ldg(r1 + x0[i]),
+                                           __ldg(r1 + x1[i]), ax[i], ay)
+                          << (8 * i);
+        }
+        uint8_t* d = J.dst + (size_t)(Y0 + ly) * J.dpitch + X0 + lx;
+        if (n == 4) {
+            *reinterpret_cast<uint32_t*>(d) = packed;  // X0 + lx is a multiple of 4, dpitch of 16
+        } else {
+            for (int i = 0; i < n; ++i) d[i] = (uint8_t)(packed >> (8 * i));
+        }
     }
 }
 

@@ -22,9 +22,9 @@ constexpr int MAX_CELLS_LOCAL = 128;   // cells overlapping one tile (+halo); ne
 constexpr int IMG_BOX_ROWS = TILE_H + 8;   // image TMA box: rows Y0-4 .. Y0+TILE_H+3, SROW bytes wide
 constexpr int SCORE_BOX_ROWS = TILE_H + 2; // score TMA box: rows Y0-1 .. Y0+TILE_H
 
-// Resize tile: 128 x 16 output pixels, each thread writes 4 consecutive pixels.
+// Resize tile: 128 x 64 output pixels; each thread writes 4 consecutive pixels in 4 rows.
 constexpr int RS_TILE_W = 128;
-constexpr int RS_TILE_H = 16;
+constexpr int RS_TILE_H = 64;
 constexpr int RS_THREADS = 512;
 
 constexpr int SELECT_THREADS = 512;
