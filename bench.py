@@ -231,6 +231,11 @@ def main():
     plain = ofg.Detector(W_, H_, max_levels=LEVELS, max_features=NFEAT, max_batch=1, fast_t_lo=FAST_T_LO,
                          stream=stream)
     frames = [(t, W_, H_, W_) for t in dev_frames]
+    # Autotune the batched plan once (launch configuration per stage), then time it.
+    with torch.cuda.stream(stream):
+        tuning = ofg.of_autotune(batched.h, frames, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, batched.out,
+                                 batched.counts, reps=3).as_dict()
+    torch.cuda.synchronize()
 
     def step_batched(events=None):
         if events is not None:
@@ -372,6 +377,7 @@ def main():
         "batched_vs_plain": round(value / plain_fps, 3),
         "e2e": {"value": round(e2e_fps, 2), "unit": "frames/s", "h2d_bytes_per_step": B * W_ * H_,
                 "d2h_bytes_per_step": B * NFEAT * 64 + 4 * B, "steps": e2e_steps},
+        "autotune": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tuning.items()},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,

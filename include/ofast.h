@@ -67,7 +67,20 @@ typedef struct of_params {
     int32_t harris_block;     /* Harris window side (default 7; only 7 is implemented) */
     int32_t orient_radius;    /* centroid disc radius (default 15; 1..15) */
     void* stream;             /* cudaStream_t to order work on; NULL = the CUDA default stream */
+    int32_t autotune;         /* 1: run of_autotune's search when a new batch shape is first seen */
 } of_params;
+
+/* Launch configuration of one batch shape, as chosen by of_autotune (or the
+ * defaults before tuning). */
+typedef struct of_tuning {
+    int32_t resize_tile_h;        /* pyramid output tile height: 32 or 64 rows */
+    int32_t fast_blocks_per_sm;   /* persistent FAST grid = SMs x this */
+    int32_t nms_blocks_per_sm;    /* persistent NMS + Harris grid = SMs x this */
+    int32_t fast_order;           /* tile walk: 0 round-robin, 1 contiguous chunks */
+    int32_t nms_order;
+    int32_t candidates_tried;     /* configurations timed */
+    float resize_ms, fast_ms, nms_ms;  /* best measured time of each tuned stage (all levels) */
+} of_tuning;
 
 /* One detected keypoint, 64 bytes.  Level-major, rank order within a level
  * (Harris key descending, then y ascending, then x ascending). */
@@ -141,6 +154,18 @@ int of_detect_batch(of_handle* h, const of_frame* frames, int n_frames, int leve
 #define OF_BUF_CAND 3
 int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int64_t dst_bytes,
                    int32_t* dims);
+
+/* Autotuner (batched path): for this batch shape, time each candidate
+ * launch configuration -- pyramid tile height, persistent grid size and tile
+ * order of the FAST and NMS kernels -- with CUDA events on these frames
+ * (reps timed repetitions each, 1..100), keep the fastest per stage for every
+ * later call with the same shape, and run the batch once with it.  Arguments
+ * as of_detect_batch; result [host, may be NULL] receives the choice.
+ * Synchronises the handle's stream.  The paper has no counterpart: its kernels
+ * use fixed launch shapes (Sec. 6). */
+int of_autotune(of_handle* h, const of_frame* frames, int n_frames, int levels, float scale,
+                int fast_t, float harris_k, int n_features, of_keypoint* out_kpts,
+                int32_t* out_counts, int reps, of_tuning* result);
 
 /* Wait for the handle's queued work and report device-side failures: returns
  * OF_ERR_TIMEOUT when a bounded device wait (a tile load that never arrived)

@@ -22,7 +22,7 @@ from .build import LIB, build  # noqa: F401
 
 __all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspect", "of_plan_levels",
            "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc", "of_sync",
-           "of_test_timeout", "OF_ERR_TIMEOUT",
+           "of_test_timeout", "OF_ERR_TIMEOUT", "of_autotune", "OfTuning",
            "of_last_error", "of_version", "OfParams", "OfFrame", "OfKeypoint", "KEYPOINT_DTYPE",
            "OF_BUF_LEVEL", "OF_BUF_SCORE", "OF_BUF_CELLT", "OF_BUF_CAND", "OfError", "load",
            "Detector", "keypoints_to_numpy"]
@@ -41,7 +41,18 @@ class OfParams(C.Structure):
     _fields_ = [("max_w", C.c_int32), ("max_h", C.c_int32), ("max_levels", C.c_int32),
                 ("max_features", C.c_int32), ("max_batch", C.c_int32), ("min_scale", C.c_float),
                 ("fast_t_lo", C.c_int32), ("cell", C.c_int32), ("border", C.c_int32),
-                ("harris_block", C.c_int32), ("orient_radius", C.c_int32), ("stream", C.c_void_p)]
+                ("harris_block", C.c_int32), ("orient_radius", C.c_int32), ("stream", C.c_void_p),
+                ("autotune", C.c_int32)]
+
+
+class OfTuning(C.Structure):
+    _fields_ = [("resize_tile_h", C.c_int32), ("fast_blocks_per_sm", C.c_int32),
+                ("nms_blocks_per_sm", C.c_int32), ("fast_order", C.c_int32), ("nms_order", C.c_int32),
+                ("candidates_tried", C.c_int32), ("resize_ms", C.c_float), ("fast_ms", C.c_float),
+                ("nms_ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class OfKeypoint(C.Structure):
@@ -98,6 +109,9 @@ def load(path: str | None = None):
     L.of_detect_level_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_float, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     L.of_detect_level_noalloc.restype = C.c_int
+    L.of_autotune.argtypes = [C.c_void_p, C.POINTER(OfFrame), C.c_int, C.c_int, C.c_float, C.c_int, C.c_float,
+                              C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(OfTuning)]
+    L.of_autotune.restype = C.c_int
     L.of_sync.argtypes = [C.c_void_p]
     L.of_sync.restype = C.c_int
     L.of_test_timeout.argtypes = [C.c_void_p, C.c_int64]
@@ -195,6 +209,18 @@ def of_detect_level_noalloc(img, w: int, h: int, pitch: int, fast_t: int, fast_t
                                                  n_features, _ptr(out_kpts), _ptr(out_count), s))
 
 
+def of_autotune(h: int, frames, levels: int, scale: float, fast_t: int, harris_k: float, n_features: int,
+                out_kpts, out_counts, reps: int = 3) -> OfTuning:
+    """Tune the launch configuration of this batch shape (see include/ofast.h); returns the choice."""
+    arr = (OfFrame * len(frames))()
+    for i, (img, w, hh, pitch) in enumerate(frames):
+        arr[i] = OfFrame(_ptr(img), w, hh, pitch)
+    t = OfTuning()
+    _check(load().of_autotune(h, arr, len(frames), levels, scale, fast_t, harris_k, n_features, _ptr(out_kpts),
+                              _ptr(out_counts), reps, C.byref(t)))
+    return t
+
+
 def of_sync(h: int) -> int:
     """Wait for the handle's work; raises OfError(OF_ERR_TIMEOUT) if a device wait expired."""
     return _check(load().of_sync(h))
@@ -268,6 +294,11 @@ class Detector:
         frames = [(im, im.shape[1], im.shape[0], im.stride(0)) for im in imgs]
         of_detect_batch(self.h, frames, levels, scale, fast_t, harris_k, n_features, self.out, self.counts)
         return self.out, self.counts
+
+    def autotune(self, imgs, levels=8, scale=1.2, fast_t=20, harris_k=0.04, n_features=1000, reps=3):
+        """Tune this batch shape (a list of 2-D uint8 CUDA tensors); returns an OfTuning."""
+        frames = [(im, im.shape[1], im.shape[0], im.stride(0)) for im in imgs]
+        return of_autotune(self.h, frames, levels, scale, fast_t, harris_k, n_features, self.out, self.counts, reps)
 
     def batch_results(self, n_frames: int, n_features: int):
         """Per-frame numpy keypoints of the last batch (synchronises)."""

@@ -112,7 +112,7 @@ constexpr int FAST_BUF = (FAST_BOX + 127) / 128 * 128;  // buffer stride in shar
 __global__ void __launch_bounds__(DET_THREADS)
 k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
        const int32_t* __restrict__ prefix, int n_list, int n_tiles, const CUtensorMap* __restrict__ maps,
-       const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell) {
+       const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, int order) {
     __shared__ __align__(128) uint8_t sbuf[2 * FAST_BUF];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ TileInfo tinfo[2];
@@ -133,16 +133,18 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         mbar_arrive_expect_tx(&mbar[b], FAST_BOX);
         tma_load_2d(sbuf + b * FAST_BUF, maps + ti.img, ti.x0 - HALO_X, ti.y0 - 4, &mbar[b]);
     };
-    if (tid == 0 && (int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
+    const int g = gridDim.x;
+    if (tid == 0 && tile_of(order, blockIdx.x, g, n_tiles, 0) < n_tiles) issue(tile_of(order, blockIdx.x, g, n_tiles, 0), 0);
 
     const int lane = tid & 31, ty = tid >> 5;
     for (int it = 0;; ++it) {
-        const int t = blockIdx.x + it * gridDim.x;
+        const int t = tile_of(order, blockIdx.x, g, n_tiles, it);
         if (t >= n_tiles) break;
+        const int tn = tile_of(order, blockIdx.x, g, n_tiles, it + 1);
         const int b = it & 1;
-        if (tid == 0 && t + (int)gridDim.x < n_tiles) {
+        if (tid == 0 && tn < n_tiles) {
             fence_proxy_async_smem();
-            issue(t + gridDim.x, b ^ 1);
+            issue(tn, b ^ 1);
         }
         const bool ok = mbar_wait(&mbar[b], (it >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -150,7 +152,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                 atomicOr(call->status, OF_DEV_TIMEOUT);
                 // Let this block's copies in flight land before its shared memory goes away.
                 mbar_wait(&mbar[b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
-                if (t + (int)gridDim.x < n_tiles) mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (tn < n_tiles) mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
             }
             return;
         }
@@ -229,11 +231,11 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
 
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
                  int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
-                 int cell, int grid, void* stream) {
+                 int cell, int grid, int order, void* stream) {
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
     k_fast<<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles,
-                                                            maps, call, t_hi, t_lo, border, cell);
+                                                            maps, call, t_hi, t_lo, border, cell, order);
 }
 
 int fast_blocks_per_sm() {

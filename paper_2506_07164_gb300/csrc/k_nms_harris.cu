@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(DET_THREADS)
 k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
              const int32_t* __restrict__ prefix, int n_list, int n_tiles,
              const CUtensorMap* __restrict__ img_maps, const CUtensorMap* __restrict__ score_maps,
-             const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell) {
+             const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, int order) {
     __shared__ __align__(128) uint8_t ibuf[2 * I_BUF];
     __shared__ __align__(128) uint8_t sbuf[2 * S_BUF];
     __shared__ __align__(8) uint64_t mbar[2];
@@ -114,19 +114,21 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         tma_load_2d(sbuf + b * S_BUF, score_maps + ii, x0 - HALO_X, y0 - 1, &mbar[b]);
         tma_load_2d(ibuf + b * I_BUF, img_maps + ii, x0 - HALO_X, y0 - 4, &mbar[b]);
     };
-    if (tid == 0 && (int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
+    const int g = gridDim.x;
+    if (tid == 0 && tile_of(order, blockIdx.x, g, n_tiles, 0) < n_tiles) issue(tile_of(order, blockIdx.x, g, n_tiles, 0), 0);
 
     const int lane = tid & 31, ty = tid >> 5;
     const int64_t knum = call->knum, kden = call->kden;
     for (int it = 0;; ++it) {
-        const int t = blockIdx.x + it * gridDim.x;
+        const int t = tile_of(order, blockIdx.x, g, n_tiles, it);
         if (t >= n_tiles) break;
+        const int tn = tile_of(order, blockIdx.x, g, n_tiles, it + 1);
         const int b = it & 1;
         if (tid == 0) {
             nq = 0;
-            if (t + (int)gridDim.x < n_tiles) {
+            if (tn < n_tiles) {
                 fence_proxy_async_smem();
-                issue(t + gridDim.x, b ^ 1);
+                issue(tn, b ^ 1);
             }
         }
         const bool ok = mbar_wait(&mbar[b], (it >> 1) & 1);
@@ -134,8 +136,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             if (tid == 0) {
                 atomicOr(call->status, OF_DEV_TIMEOUT);
                 mbar_wait(&mbar[b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
-                if (t + (int)gridDim.x < n_tiles)
-                    mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (tn < n_tiles) mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
             }
             return;
         }
@@ -259,11 +260,12 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
 
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                        int n_list, int n_tiles, const CUtensorMap* img_maps, const CUtensorMap* score_maps,
-                       const Call* call, int t_hi, int t_lo, int border, int cell, int grid, void* stream) {
+                       const Call* call, int t_hi, int t_lo, int border, int cell, int grid, int order,
+                       void* stream) {
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
     k_nms_harris<<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(
-        imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell);
+        imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, order);
 }
 
 int nms_blocks_per_sm() {

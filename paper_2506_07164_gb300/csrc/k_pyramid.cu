@@ -2,10 +2,10 @@
 // an ORB front end, Sec. 1; level sizes "decrease exponentially", Sec. 6.1).
 //
 // One launch resizes level l of every frame in the batch.  Each block owns a
-// 128 x 64 output tile: it stages the tile's source window in shared memory
+// 128 x TH output tile (TH = 32 or 64, chosen by the autotuner): it stages the tile's source window in shared memory
 // with aligned 16-byte loads (direct loads when the window is larger than the
 // buffer, i.e. scales above ~2), then each thread writes 4 consecutive output
-// pixels of 4 rows, one 32-bit store per row, with its 4 column weights kept
+// pixels of TH/16 rows, one 32-bit store per row, with its 4 column weights kept
 // in registers.  Source coordinates come from per-axis tables computed on
 // the host: (i0 << 12) | a, a in [0, 2048] the weight of sample i0 + 1 in
 // units of 1/2048; one rounding at the end:
@@ -30,7 +30,6 @@ __device__ __forceinline__ int find_job(const int32_t* __restrict__ prefix, int 
 // up to 2 with a 128 x 64 output tile).
 constexpr int RS_SW = 288;
 constexpr int RS_SH = 136;
-constexpr int RS_RPT = RS_TILE_H / (RS_THREADS / 32);  // output rows per thread
 
 __device__ __forceinline__ int bilerp(int p00, int p01, int p10, int p11, int ax, int ay) {
     const int top = (2048 - ax) * p00 + ax * p01;
@@ -38,10 +37,12 @@ __device__ __forceinline__ int bilerp(int p00, int p01, int p10, int p11, int ax
     return ((2048 - ay) * top + ay * bot + (1 << 21)) >> 22;
 }
 
+template <int TH>
 __global__ void __launch_bounds__(RS_THREADS)
 k_resize(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix, int n_jobs) {
+    constexpr int RS_RPT = TH / (RS_THREADS / 32);  // output rows per thread
     __shared__ __align__(16) uint8_t win[RS_SH * RS_SW];
-    __shared__ int32_t yt[RS_TILE_H];
+    __shared__ int32_t yt[TH];
     __shared__ int32_t sjob, sx0s, sy0s, sbytes, srows;
     const int b = blockIdx.x;
     if (threadIdx.x == 0) sjob = find_job(prefix, n_jobs, b);
@@ -50,10 +51,10 @@ k_resize(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix, in
     const Resize& J = jobs[j];
     const int t = b - __ldg(prefix + j);
     const int tx = t % J.tiles_x, ty = t / J.tiles_x;
-    const int X0 = tx * RS_TILE_W, Y0 = ty * RS_TILE_H;
-    const int nx = min(RS_TILE_W, J.dw - X0), ny = min(RS_TILE_H, J.dh - Y0);
+    const int X0 = tx * RS_TILE_W, Y0 = ty * TH;
+    const int nx = min(RS_TILE_W, J.dw - X0), ny = min(TH, J.dh - Y0);
     const int sw = J.sw, sh = J.sh;
-    for (int i = threadIdx.x; i < RS_TILE_H; i += blockDim.x) yt[i] = i < ny ? __ldg(J.ytab + Y0 + i) : 0;
+    for (int i = threadIdx.x; i < TH; i += blockDim.x) yt[i] = i < ny ? __ldg(J.ytab + Y0 + i) : 0;
     if (threadIdx.x == 0) {
         // Source window of the tile: columns [sx0, sx1], rows [sy0, sy1].
         const int sx0 = (__ldg(J.xtab + X0) >> 12) & ~15;
@@ -134,10 +135,13 @@ k_resize(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix, in
     }
 }
 
-void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
+void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles, int tile_h,
                    void* stream) {
     if (n_tiles <= 0) return;
-    k_resize<<<n_tiles, RS_THREADS, 0, (cudaStream_t)stream>>>(jobs, tile_prefix, n_jobs);
+    if (tile_h == 32)
+        k_resize<32><<<n_tiles, RS_THREADS, 0, (cudaStream_t)stream>>>(jobs, tile_prefix, n_jobs);
+    else
+        k_resize<64><<<n_tiles, RS_THREADS, 0, (cudaStream_t)stream>>>(jobs, tile_prefix, n_jobs);
 }
 
 }  // namespace ofk

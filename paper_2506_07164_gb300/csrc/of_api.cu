@@ -202,9 +202,9 @@ struct Plan {
     Layout lay;
     std::vector<Img> h_img;
     std::vector<Resize> h_rs;
-    std::vector<int> rs_begin;   // jobs of level l: [rs_begin[l], rs_begin[l+1])
-    std::vector<int> rsp_begin;  // prefix array offset of level l
-    std::vector<int> rs_tiles;   // tiles of level l
+    std::vector<int> rs_begin;      // jobs of level l: [rs_begin[l], rs_begin[l+1])
+    std::vector<int> rsp_begin[2];  // prefix array offset of level l, per resize tile height
+    std::vector<int> rs_tiles[2];   // tiles of level l, per resize tile height
     std::vector<int32_t> rs_prefix, det_list, det_prefix, tables;
     int det_tiles = 0, max_quota = 0, total_slots = 0, n_img = 0;
     Call h_call{};
@@ -212,7 +212,8 @@ struct Plan {
     size_t off_call = 0, off_img = 0, off_rs = 0, off_rsp = 0, off_dl = 0, off_dp = 0, off_tab = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps], n_img each
-    int grid_fast = 0, grid_nms = 0;
+    of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
+    bool tuned = false;
     size_t header_bytes = 0;
     uint8_t* stage[2] = {nullptr, nullptr};
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -295,20 +296,22 @@ void enqueue_stages(of_handle* H, Plan* P, int first, int last, cudaStream_t st)
                 cudaMemsetAsync(H->arena, 0, P->lay.zero_end, st);
                 for (int l = 1; l < nl; ++l) {
                     const int nj = P->rs_begin[l + 1] - P->rs_begin[l];
+                    const int v = P->tun.resize_tile_h == RS_TILE_HS[0] ? 0 : 1;
                     if (nj > 0)
-                        launch_resize(P->d_rs() + P->rs_begin[l], P->d_rsp() + P->rsp_begin[l], nj,
-                                      P->rs_tiles[l], st);
+                        launch_resize(P->d_rs() + P->rs_begin[l], P->d_rsp() + P->rsp_begin[v][l], nj,
+                                      P->rs_tiles[v][l], RS_TILE_HS[v], st);
                 }
                 break;
             case 1:
                 launch_fast(P->d_img(), P->d_dl(), P->d_dp(), (int)P->det_list.size(),
                             P->det_tiles, P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border,
-                            s.cell, P->grid_fast, st);
+                            s.cell, H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
                 break;
             case 2:
                 launch_nms_harris(P->d_img(), P->d_dl(), P->d_dp(), (int)P->det_list.size(),
                                   P->det_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(),
-                                  s.t_hi, s.t_lo, s.border, s.cell, P->grid_nms, st);
+                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm,
+                                  P->tun.nms_order, st);
                 break;
             case 3:
                 launch_select(P->d_img(), P->n_img, P->d_call(), P->max_quota, st);
@@ -328,6 +331,29 @@ cudaError_t capture(of_handle* H, Plan* P, int first, int last, cudaGraph_t* g) 
     const cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(cs, g);
     return e != cudaSuccess ? e : le;
+}
+
+// Capture the launch sequence once as one graph, and once per stage (the
+// per-stage graphs serve calls that time each stage with events).  Replaces
+// earlier instances.
+cudaError_t instantiate_graphs(of_handle* H, Plan* P) {
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    P->exec = nullptr;
+    for (auto& x : P->stage_exec) {
+        if (x) cudaGraphExecDestroy(x);
+        x = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = capture(H, P, 0, kStages, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    for (int st = 0; st < kStages && e == cudaSuccess; ++st) {
+        g = nullptr;
+        e = capture(H, P, st, st + 1, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&P->stage_exec[st], g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    return e;
 }
 
 int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings& s,
@@ -402,12 +428,12 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     };
     std::vector<std::pair<int, int>> tab_idx;  // (xtab, ytab) offsets per job
     P->rs_begin.assign(nl + 1, 0);
-    P->rsp_begin.assign(nl + 1, 0);
-    P->rs_tiles.assign(nl + 1, 0);
+    for (int v = 0; v < 2; ++v) {
+        P->rsp_begin[v].assign(nl + 1, 0);
+        P->rs_tiles[v].assign(nl + 1, 0);
+    }
     for (int l = 1; l < nl; ++l) {
         P->rs_begin[l] = (int)P->h_rs.size();
-        P->rsp_begin[l] = (int)P->rs_prefix.size();
-        int tiles = 0;
         for (int f = 0; f < nf; ++f) {
             const Img& S = P->h_img[f * nl + l - 1];
             const Img& D = P->h_img[f * nl + l];
@@ -423,13 +449,20 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             R.dh = D.h;
             R.dpitch = D.pitch;
             R.tiles_x = (D.w + RS_TILE_W - 1) / RS_TILE_W;
-            R.tiles_y = (D.h + RS_TILE_H - 1) / RS_TILE_H;
+            R.tiles_y = 0;  // depends on the tile height; the prefix arrays carry it
             tab_idx.emplace_back(table(S.w, D.w), table(S.h, D.h));
-            P->rs_prefix.push_back(tiles);
-            tiles += R.tiles_x * R.tiles_y;
             P->h_rs.push_back(R);
         }
-        P->rs_tiles[l] = tiles;
+        // One tile prefix array per resize tile height.
+        for (int v = 0; v < 2; ++v) {
+            P->rsp_begin[v][l] = (int)P->rs_prefix.size();
+            int tiles = 0;
+            for (int i = P->rs_begin[l]; i < (int)P->h_rs.size(); ++i) {
+                P->rs_prefix.push_back(tiles);
+                tiles += P->h_rs[i].tiles_x * ((P->h_rs[i].dh + RS_TILE_HS[v] - 1) / RS_TILE_HS[v]);
+            }
+            P->rs_tiles[v][l] = tiles;
+        }
     }
     P->rs_begin[nl] = (int)P->h_rs.size();
     for (int i = 0; i < P->n_img; ++i) {
@@ -456,8 +489,11 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     C.n_img = P->n_img;
     C.total_slots = P->total_slots;
     C.status = H->d_counts + 4;
-    P->grid_fast = H->n_sms * fast_blocks_per_sm();
-    P->grid_nms = H->n_sms * nms_blocks_per_sm();
+    P->tun.resize_tile_h = RS_TILE_HS[1];
+    P->tun.fast_blocks_per_sm = fast_blocks_per_sm();
+    P->tun.nms_blocks_per_sm = nms_blocks_per_sm();
+    P->tun.fast_order = 0;
+    P->tun.nms_order = 0;
 
     // Tensor maps: image boxes for FAST and NMS, score boxes for NMS.
     P->h_maps.assign(2 * P->n_img, CUtensorMap{});
@@ -524,18 +560,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
         return fail(OF_ERR_CUDA, std::string("plan setup: ") + cudaGetErrorString(e));
     }
 
-    // Capture the launch sequence once as one graph, and once per stage
-    // (the per-stage graphs serve calls that time each stage with events).
-    cudaGraph_t g = nullptr;
-    e = capture(H, P, 0, kStages, &g);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, g, 0);
-    if (g) cudaGraphDestroy(g);
-    for (int st = 0; st < kStages && e == cudaSuccess; ++st) {
-        g = nullptr;
-        e = capture(H, P, st, st + 1, &g);
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&P->stage_exec[st], g, 0);
-        if (g) cudaGraphDestroy(g);
-    }
+    e = instantiate_graphs(H, P);
     if (e != cudaSuccess) {
         free_plan(P);
         return fail(OF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -603,8 +628,11 @@ Plan* find_plan(of_handle* H, const std::vector<FrameKey>& frames, const Setting
     return nullptr;
 }
 
-int run_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, float scale,
-              int fast_t, float harris_k, int n_features, of_keypoint* out, int32_t* counts) {
+// Validate a batch, find or build its plan, stage unaligned frames and bind
+// the call's pointers.  Launches nothing.
+int prepare_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, float scale,
+                  int fast_t, float harris_k, int n_features, of_keypoint* out, int32_t* counts,
+                  Plan** outP) {
     if (!H) return fail(OF_ERR_ARG, "null handle");
     if (!frames || n_frames < 1) return fail(OF_ERR_ARG, "no frames");
     if (n_frames > H->p.max_batch)
@@ -637,7 +665,6 @@ int run_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, fl
         const bool aligned = ((uintptr_t)F.img % 16 == 0) && (F.pitch % 16 == 0);
         keys[i] = FrameKey{F.w, F.h, F.pitch, !aligned};
     }
-    DeviceGuard dg(H->device);
     Plan* P = find_plan(H, keys, s);
     if (!P) {
         if ((int)H->plans.size() >= kMaxPlans) {
@@ -661,6 +688,108 @@ int run_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, fl
     }
     const int rc = bind_plan(H, P, frames, out, counts);
     if (rc != OF_OK) return rc;
+    *outP = P;
+    return OF_OK;
+}
+
+// Time the candidate launch configurations of a bound plan on its own data
+// and keep the fastest per stage:
+//   pyramid  resize output tile 128 x 32 or 128 x 64;
+//   FAST     1 .. max resident blocks per SM, round-robin or contiguous tiles;
+//   NMS      the same choices.
+// Stages are timed one at a time with CUDA events (median-free mean of a few
+// repetitions after a warm-up); select and orientation are not tuned.  The
+// plan's graphs are re-captured with the winners.
+int autotune_plan(of_handle* H, Plan* P, int reps) {
+    cudaStream_t st = H->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    OF_CK(cudaEventCreate(&e0));
+    OF_CK(cudaEventCreate(&e1));
+    int tried = 0;
+    auto timed = [&](auto&& enqueue, float* ms) -> int {
+        enqueue();
+        OF_CK(cudaEventRecord(e0, st));
+        for (int i = 0; i < reps; ++i) enqueue();
+        OF_CK(cudaEventRecord(e1, st));
+        OF_CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        OF_CK(cudaEventElapsedTime(&t, e0, e1));
+        *ms = t / reps;
+        ++tried;
+        return OF_OK;
+    };
+    const size_t ctr_bytes = 4 * sizeof(int32_t) * (size_t)P->n_img;
+    int rc = OF_OK;
+    enqueue_stages(H, P, 0, kStages, st);  // every buffer populated once
+    // Pyramid (idempotent).
+    float best = 1e30f;
+    int best_h = P->tun.resize_tile_h;
+    for (int v = 0; v < 2 && rc == OF_OK; ++v) {
+        P->tun.resize_tile_h = RS_TILE_HS[v];
+        float ms = 0.f;
+        rc = timed([&] { enqueue_stages(H, P, 0, 1, st); }, &ms);
+        if (ms < best) best = ms, best_h = RS_TILE_HS[v];
+    }
+    P->tun.resize_tile_h = best_h;
+    P->tun.resize_ms = best;
+    // FAST (idempotent: rewrites score maps, ORs the same cell flags).
+    best = 1e30f;
+    int bb = P->tun.fast_blocks_per_sm, bo = 0;
+    for (int bp = 1; bp <= fast_blocks_per_sm() && rc == OF_OK; ++bp) {
+        for (int order = 0; order < 2 && rc == OF_OK; ++order) {
+            P->tun.fast_blocks_per_sm = bp;
+            P->tun.fast_order = order;
+            float ms = 0.f;
+            rc = timed([&] { enqueue_stages(H, P, 1, 2, st); }, &ms);
+            if (ms < best) best = ms, bb = bp, bo = order;
+        }
+    }
+    P->tun.fast_blocks_per_sm = bb;
+    P->tun.fast_order = bo;
+    P->tun.fast_ms = best;
+    // NMS + Harris (appends candidates: clear the counters before each run).
+    best = 1e30f;
+    bb = P->tun.nms_blocks_per_sm, bo = 0;
+    for (int bp = 1; bp <= nms_blocks_per_sm() && rc == OF_OK; ++bp) {
+        for (int order = 0; order < 2 && rc == OF_OK; ++order) {
+            P->tun.nms_blocks_per_sm = bp;
+            P->tun.nms_order = order;
+            float ms = 0.f;
+            rc = timed(
+                [&] {
+                    cudaMemsetAsync(H->arena, 0, ctr_bytes, st);
+                    enqueue_stages(H, P, 2, 3, st);
+                },
+                &ms);
+            if (ms < best) best = ms, bb = bp, bo = order;
+        }
+    }
+    P->tun.nms_blocks_per_sm = bb;
+    P->tun.nms_order = bo;
+    P->tun.nms_ms = best;
+    P->tun.candidates_tried = tried;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != OF_OK) return rc;
+    OF_CK(cudaGetLastError());
+    const cudaError_t e = instantiate_graphs(H, P);
+    if (e != cudaSuccess) return fail(OF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    P->tuned = true;
+    return OF_OK;
+}
+
+int run_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, float scale,
+              int fast_t, float harris_k, int n_features, of_keypoint* out, int32_t* counts) {
+    if (!H) return fail(OF_ERR_ARG, "null handle");
+    DeviceGuard dg(H->device);
+    Plan* P = nullptr;
+    int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out,
+                           counts, &P);
+    if (rc != OF_OK) return rc;
+    if (H->p.autotune && !P->tuned) {
+        rc = autotune_plan(H, P, 3);
+        if (rc != OF_OK) return rc;
+    }
     if (n_features == 0) OF_CK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_frames, H->stream));
     if (H->stage_timing) {
         for (int st = 0; st < kStages; ++st) {
@@ -709,6 +838,10 @@ of_handle* of_create(const of_params* pin) {
     if (p.border == 0) p.border = 19;
     if (p.harris_block == 0) p.harris_block = 7;
     if (p.orient_radius == 0) p.orient_radius = 15;
+    if (p.autotune != 0 && p.autotune != 1) {
+        fail(OF_ERR_ARG, "autotune must be 0 or 1");
+        return nullptr;
+    }
     if (p.max_w < 1 || p.max_h < 1 || p.max_w > 65535 || p.max_h > 65535 || p.max_levels < 1 ||
         p.max_levels > 16 || p.max_features < 0 || p.max_features > 8192 || p.max_batch < 1 ||
         !(p.min_scale > 1.0f) || p.fast_t_lo < 0 || p.fast_t_lo > 255 || p.cell < 8 ||
@@ -781,6 +914,25 @@ int of_detect_batch(of_handle* H, const of_frame* frames, int n_frames, int leve
                     int32_t* out_counts) {
     return run_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
                      out_counts);
+}
+
+int of_autotune(of_handle* H, const of_frame* frames, int n_frames, int levels, float scale,
+                int fast_t, float harris_k, int n_features, of_keypoint* out_kpts,
+                int32_t* out_counts, int reps, of_tuning* result) {
+    if (!H) return fail(OF_ERR_ARG, "null handle");
+    if (reps < 1 || reps > 100) return fail(OF_ERR_ARG, "reps must be 1..100");
+    DeviceGuard dg(H->device);
+    Plan* P = nullptr;
+    int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
+                           out_counts, &P);
+    if (rc != OF_OK) return rc;
+    rc = autotune_plan(H, P, reps);
+    if (rc != OF_OK) return rc;
+    if (n_features == 0) OF_CK(cudaMemsetAsync(out_counts, 0, sizeof(int32_t) * n_frames, H->stream));
+    OF_CK(cudaGraphLaunch(P->exec, H->stream));  // leave this call's results in the outputs
+    H->last = P;
+    if (result) *result = P->tun;
+    return OF_OK;
 }
 
 int of_time_stages(of_handle* H, void* const* events) {

@@ -22,9 +22,10 @@ constexpr int MAX_CELLS_LOCAL = 128;   // cells overlapping one tile (+halo); ne
 constexpr int IMG_BOX_ROWS = TILE_H + 8;   // image TMA box: rows Y0-4 .. Y0+TILE_H+3, SROW bytes wide
 constexpr int SCORE_BOX_ROWS = TILE_H + 2; // score TMA box: rows Y0-1 .. Y0+TILE_H
 
-// Resize tile: 128 x 64 output pixels; each thread writes 4 consecutive pixels in 4 rows.
+// Resize tile: 128 x (32 or 64) output pixels; each thread writes 4 consecutive pixels
+// in 2 or 4 rows.  The autotuner picks the height.
 constexpr int RS_TILE_W = 128;
-constexpr int RS_TILE_H = 64;
+constexpr int RS_TILE_HS[2] = {32, 64};
 constexpr int RS_THREADS = 512;
 
 constexpr int SELECT_THREADS = 512;
@@ -75,20 +76,28 @@ struct Call {
     int32_t total_slots;  // sum of quotas
 };
 
+// Order in which a persistent block walks the tiles of a launch:
+// 0 round-robin (t = block + i * grid), 1 contiguous chunks (t = block * per + i).
+__host__ __device__ __forceinline__ int tile_of(int order, int block, int grid, int n_tiles, int i) {
+    if (order == 0) return block + i * grid;
+    const int per = (n_tiles + grid - 1) / grid;
+    return i < per ? block * per + i : n_tiles;
+}
+
 }  // namespace ofk
 
 // Kernel launchers (implemented in the .cu files).  All take device pointers
 // to the plan's descriptor arrays and launch on `stream`.
 namespace ofk {
 void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
-                   void* stream);
+                   int tile_h, void* stream);
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                  int n_list, int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi,
-                 int t_lo, int border, int cell, int grid, void* stream);
+                 int t_lo, int border, int cell, int grid, int order, void* stream);
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                        int n_list, int n_tiles, const CUtensorMap* img_maps,
                        const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,
-                       int border, int cell, int grid, void* stream);
+                       int border, int cell, int grid, int order, void* stream);
 void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, void* stream);
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
 void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t* dst,

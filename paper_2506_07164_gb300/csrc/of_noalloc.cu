@@ -222,9 +222,9 @@ extern "C" int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pit
         if (e != cudaSuccess) return na_fail(OF_ERR_CUDA, std::string("copy: ") + cudaGetErrorString(e));
     }
     const int tiles = I.tiles_x * I.tiles_y;
-    launch_fast(d_img, d_list, d_list + 1, 1, tiles, d_maps, d_call, fast_t, t_lo, border, cell, grid_fast, st);
+    launch_fast(d_img, d_list, d_list + 1, 1, tiles, d_maps, d_call, fast_t, t_lo, border, cell, grid_fast, 0, st);
     launch_nms_harris(d_img, d_list, d_list + 1, 1, tiles, d_maps, d_maps + 1, d_call, fast_t, t_lo, border, cell,
-                      grid_nms, st);
+                      grid_nms, 0, st);
     launch_select(d_img, 1, d_call, quota > 0 ? quota : 1, st);
     launch_orient(d_img, 1, d_call, n_features, st);
     e = cudaGetLastError();

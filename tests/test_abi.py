@@ -35,7 +35,7 @@ def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("of_create", "of_detect", "of_destroy", "of_detect_batch", "of_inspect",
                      "of_plan_levels", "of_last_error", "of_version", "of_sync", "of_test_timeout",
-                     "of_time_stages"):
+                     "of_time_stages", "of_autotune"):
         assert required in names
 
 

@@ -241,3 +241,26 @@ def test_batch_then_sync_ok():
     assert ofg.of_sync(det.h) == 0
     assert (det.counts[:4].cpu().numpy() > 0).all()
     det.close()
+
+
+# ------------------------------------------------------------ autotuner
+def test_autotuner_choice_is_valid_and_results_unchanged():
+    sizes = [(720, 540), (1080, 720), (640, 480)]
+    imgs = [synth.scene(w, h, 60 + i, background="pink") for i, (w, h) in enumerate(sizes)]
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    det = ofg.Detector(1080, 720, max_levels=8, max_features=500, max_batch=4, fast_t_lo=7)
+    tun = det.autotune(dev, levels=8, fast_t=20, n_features=500, reps=2)
+    assert tun.resize_tile_h in (32, 64)
+    assert tun.fast_blocks_per_sm >= 1 and tun.nms_blocks_per_sm >= 1
+    assert tun.fast_order in (0, 1) and tun.nms_order in (0, 1)
+    assert tun.candidates_tried >= 2 + 2 + 2 and tun.fast_ms > 0 and tun.nms_ms > 0
+    torch.cuda.synchronize()
+    first = det.batch_results(len(imgs), 500)  # the tuning call's own outputs
+    det.detect_batch(dev, levels=8, fast_t=20, n_features=500)  # tuned graph
+    torch.cuda.synchronize()
+    tuned = det.batch_results(len(imgs), 500)
+    for im, a, b in zip(imgs, first, tuned):
+        ora = oracle.detect(im, levels=8, fast_t=20, fast_t_lo=7, n_features=500)
+        compare_keypoints(a, ora)
+        compare_keypoints(b, ora)
+    det.close()
