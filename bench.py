@@ -58,6 +58,91 @@ def _oracle_detect(img):
                              harris_k=HARRIS_K, n_features=NFEAT))
 
 
+SERVE_SIZES = [(640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
+
+
+def _gen_sized(args):
+    import synth
+
+    w, h, seed = args
+    return synth.scene(w, h, seed, background="pink")
+
+
+def serving_leg(pool, seconds: float, rate: float, seed: int = 0):
+    """Poisson arrivals at `rate` frames/s of the mixed-size workload, through the
+    continuous-batching server; returns latency percentiles and throughput."""
+    import threading
+
+    import numpy as np
+
+    import paper_2506_07164_gb300 as ofg
+
+    frames = {sz: pool.map(_gen_sized, [(sz[0], sz[1], 500 + 10 * i + k) for k in range(3)])
+              for i, sz in enumerate(SERVE_SIZES)}
+    srv = ofg.of_server_create(max_w=3840, max_h=2160, levels=LEVELS, scale=SCALE, fast_t=FAST_T,
+                               fast_t_lo=FAST_T_LO, harris_k=HARRIS_K, n_features=NFEAT, slots=4,
+                               max_batch=16, memory_budget=12 << 30)
+    rng = np.random.default_rng(seed)
+    done = []
+    submitted = [0]
+    t_end = [None]
+
+    def client():
+        t0 = time.perf_counter()
+        t_next = t0
+        while t_next - t0 < seconds:
+            now = time.perf_counter()
+            if t_next > now:
+                time.sleep(t_next - now)
+            sz = SERVE_SIZES[int(rng.integers(0, len(SERVE_SIZES)))]
+            img = frames[sz][int(rng.integers(0, 3))]
+            if rng.random() < 0.2:  # stereo pair: right view = left shifted by a seeded disparity
+                d = int(rng.integers(4, 24))
+                right = np.empty_like(img)
+                right[:, : img.shape[1] - d] = img[:, d:]
+                right[:, img.shape[1] - d:] = img[:, -1:]
+                ofg.of_server_submit(srv, img, tag=1)
+                ofg.of_server_submit(srv, right, tag=2)
+                submitted[0] += 2
+                t_next += float(rng.exponential(2.0 / rate))
+            else:
+                ofg.of_server_submit(srv, img, tag=0)
+                submitted[0] += 1
+                t_next += float(rng.exponential(1.0 / rate))
+        t_end[0] = time.perf_counter()
+
+    # Warm the plans of each size class (first use captures a graph) before timing.
+    for sz in SERVE_SIZES:
+        for k in range(2):
+            ofg.of_server_submit(srv, frames[sz][0], tag=-1)
+    got = 0
+    while got < 2 * len(SERVE_SIZES):
+        got += len(ofg.of_server_poll(srv, 64, NFEAT, wait_ms=100))
+    th = threading.Thread(target=client)
+    wall0 = time.perf_counter()
+    th.start()
+    while th.is_alive() or len(done) < submitted[0]:
+        for r, _ in ofg.of_server_poll(srv, 256, NFEAT, wait_ms=20):
+            done.append((r.t_submit, r.t_done, r.count, r.batch_frames, r.w * r.h))
+        if not th.is_alive() and time.perf_counter() - wall0 > seconds + 60:
+            break
+    th.join()
+    stats = ofg.of_server_stats(srv)
+    ofg.of_server_destroy(srv)
+    lat = np.array([b - a for a, b, *_ in done]) * 1000.0
+    first = min(a for a, *_ in done)
+    last = max(b for _, b, *_ in done)
+    ok = sum(1 for d in done if d[2] >= 0)
+    return {"offered_rate_fps": round(submitted[0] / seconds, 1), "frames": len(done), "ok": ok,
+            "frames_per_s": round(len(done) / (last - first), 1),
+            "mpix_per_s": round(sum(d[4] for d in done) / (last - first) / 1e6, 1),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mean_ms": round(float(lat.mean()), 3), "mean_batch_frames": round(float(np.mean([d[3] for d in done])), 2),
+            "batches": stats["batches"], "slots": 4, "memory_budget_bytes": 12 << 30,
+            "mix": "uniform over 640x480/1280x720/1920x1080/3840x2160; 20% of arrivals are stereo pairs",
+            "seconds": seconds}
+
+
 def make_frames(n: int, pool=None):
     seeds = list(range(n))
     if pool is not None:
@@ -187,6 +272,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frames", type=int, default=0, help="oracle sample size (0: 2 x cores)")
     ap.add_argument("--skip-plain", action="store_true", help="skip the per-frame path (profiling)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving leg duration (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=500.0, help="Poisson arrival rate, frames/s")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-buffer path (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -355,6 +442,10 @@ def main():
                                       for i, n in enumerate(ofg.STAGE_NAMES)},
                 "algorithmic_bytes_per_frame": dict(zip(ofg.STAGE_NAMES, per_frame))}
 
+    serving = None
+    if args.serve_seconds > 0:
+        serving = serving_leg(pool, args.serve_seconds, args.serve_rate)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n = args.cpu_frames or 2 * min(cores, 16)
@@ -379,6 +470,7 @@ def main():
                 "d2h_bytes_per_step": B * NFEAT * 64 + 4 * B, "steps": e2e_steps},
         "autotune": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tuning.items()},
         "roofline": roofline,
+        "serving": serving,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": kernels_per_step * args.steps,

@@ -68,6 +68,9 @@ typedef struct of_params {
     int32_t orient_radius;    /* centroid disc radius (default 15; 1..15) */
     void* stream;             /* cudaStream_t to order work on; NULL = the CUDA default stream */
     int32_t autotune;         /* 1: run of_autotune's search when a new batch shape is first seen */
+    int64_t arena_bytes;      /* > 0: scratch size in bytes instead of the worst case for max_batch
+                                 frames of max_w x max_h; a batch that needs more is rejected with
+                                 OF_ERR_TOO_LARGE (see of_batch_bytes) */
 } of_params;
 
 /* Launch configuration of one batch shape, as chosen by of_autotune (or the
@@ -211,6 +214,71 @@ int of_time_stages(of_handle* h, void* const* events);
 int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pitch, int fast_t,
                             int fast_t_lo, float harris_k, int n_features,
                             of_keypoint* out_kpts, int32_t* out_count, void* stream);
+
+/* Host-only: scratch bytes a batch of n_frames frames (sizes ws[i] x hs[i])
+ * needs on a handle created with *p (border and cell taken from p, zero
+ * fields defaulted as in of_create), counting unaligned level-0 copies.
+ * Returns the byte count or OF_ERR_ARG. */
+int64_t of_batch_bytes(const of_params* p, const int32_t* ws, const int32_t* hs, int n_frames,
+                       int levels, float scale, int n_features);
+
+/* ------------------------------------------------------------------------
+ * Serving loop with continuous batching.  The paper measures single images
+ * and videos (Sec. 6, Fig. 14); this loop serves streams of mixed-resolution
+ * frames from many clients.
+ *
+ * The server owns `slots` engines, each a handle with its own stream and a
+ * 1/slots share of memory_budget (scratch arena, device input frames,
+ * outputs).  of_server_submit copies a host frame into the queue and returns
+ * at once.  A dispatcher thread admits queued requests into any free slot --
+ * the oldest request and later ones of the same resolution, in arrival
+ * order, while the batch fits the slot's scratch and input bytes and
+ * max_batch -- and launches the batch asynchronously; batches on different
+ * slots overlap on the device, and requests that arrive meanwhile are
+ * admitted as soon as a slot and its memory free up.  Each batch's pyramids
+ * stay resident in its slot until the slot takes its next batch.  Results are
+ * identical to of_detect on each frame alone.  All entry points are
+ * thread-safe. */
+typedef struct of_server of_server;
+
+typedef struct of_server_params {
+    int32_t max_w, max_h;   /* largest frame (required) */
+    int32_t levels;         /* default 8 */
+    float scale;            /* default 1.2 */
+    int32_t fast_t;         /* default 20 */
+    int32_t fast_t_lo;      /* per-cell fallback threshold, 0 = none */
+    float harris_k;         /* default 0.04 */
+    int32_t n_features;     /* per frame, default 1000 */
+    int32_t slots;          /* concurrent batches, default 3 (1..16) */
+    int32_t max_batch;      /* frames per batch, default 8 */
+    int64_t memory_budget;  /* device bytes for all slots (required) */
+    int32_t border, cell, orient_radius;  /* 0 = defaults of of_create */
+} of_server_params;
+
+typedef struct of_server_result {
+    int64_t id, tag;        /* id from of_server_submit, caller's tag */
+    int32_t w, h;
+    int32_t count;          /* keypoints written (>= 0) or a negative OF_ERR_* */
+    int32_t batch_frames;   /* frames in the batch that carried this request */
+    double t_submit, t_launch, t_done;  /* steady-clock seconds */
+} of_server_result;
+
+typedef struct of_server_stats {
+    int64_t submitted, completed, queued, batches, frames_launched, in_flight_batches;
+    int64_t slot_arena_bytes, slot_input_bytes;
+} of_server_stats;
+
+/* NULL on failure (e.g. OF_ERR_TOO_LARGE when a max-size frame does not fit one slot's share). */
+of_server* of_server_create(const of_server_params* p);
+/* Stops the dispatcher after the batches in flight; queued requests are dropped. */
+void of_server_destroy(of_server* s);
+/* img [host] w x h, pitch bytes per row; copied before return.  Returns the request id (>= 0). */
+int64_t of_server_submit(of_server* s, const uint8_t* img, int w, int h, int pitch, int64_t tag);
+/* Moves up to max_results finished requests into results [host]; their keypoints go to
+ * kpts [host, may be NULL] + i * n_features.  Waits up to wait_ms for the first.  Returns the number moved. */
+int of_server_poll(of_server* s, of_server_result* results, of_keypoint* kpts, int max_results,
+                   int wait_ms);
+int of_server_stats_get(of_server* s, of_server_stats* out);
 
 /* Host-only: the pyramid plan the detector uses for a W x H frame (no GPU
  * needed).  ws, hs [host, levels ints] receive level sizes; quota [host,

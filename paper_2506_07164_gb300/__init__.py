@@ -22,7 +22,9 @@ from .build import LIB, build  # noqa: F401
 
 __all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspect", "of_plan_levels",
            "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc", "of_sync",
-           "of_test_timeout", "OF_ERR_TIMEOUT", "of_autotune", "OfTuning",
+           "of_test_timeout", "OF_ERR_TIMEOUT", "of_autotune", "OfTuning", "of_batch_bytes",
+           "of_server_create", "of_server_destroy", "of_server_submit", "of_server_poll", "of_server_stats",
+           "OfServerParams", "OfServerResult",
            "of_last_error", "of_version", "OfParams", "OfFrame", "OfKeypoint", "KEYPOINT_DTYPE",
            "OF_BUF_LEVEL", "OF_BUF_SCORE", "OF_BUF_CELLT", "OF_BUF_CAND", "OfError", "load",
            "Detector", "keypoints_to_numpy"]
@@ -42,7 +44,7 @@ class OfParams(C.Structure):
                 ("max_features", C.c_int32), ("max_batch", C.c_int32), ("min_scale", C.c_float),
                 ("fast_t_lo", C.c_int32), ("cell", C.c_int32), ("border", C.c_int32),
                 ("harris_block", C.c_int32), ("orient_radius", C.c_int32), ("stream", C.c_void_p),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("arena_bytes", C.c_int64)]
 
 
 class OfTuning(C.Structure):
@@ -64,6 +66,29 @@ class OfKeypoint(C.Structure):
 
 class OfFrame(C.Structure):
     _fields_ = [("img", C.c_void_p), ("w", C.c_int32), ("h", C.c_int32), ("pitch", C.c_int32)]
+
+
+class OfServerParams(C.Structure):
+    _fields_ = [("max_w", C.c_int32), ("max_h", C.c_int32), ("levels", C.c_int32), ("scale", C.c_float),
+                ("fast_t", C.c_int32), ("fast_t_lo", C.c_int32), ("harris_k", C.c_float),
+                ("n_features", C.c_int32), ("slots", C.c_int32), ("max_batch", C.c_int32),
+                ("memory_budget", C.c_int64), ("border", C.c_int32), ("cell", C.c_int32),
+                ("orient_radius", C.c_int32)]
+
+
+class OfServerResult(C.Structure):
+    _fields_ = [("id", C.c_int64), ("tag", C.c_int64), ("w", C.c_int32), ("h", C.c_int32),
+                ("count", C.c_int32), ("batch_frames", C.c_int32), ("t_submit", C.c_double),
+                ("t_launch", C.c_double), ("t_done", C.c_double)]
+
+
+class OfServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("queued", C.c_int64),
+                ("batches", C.c_int64), ("frames_launched", C.c_int64), ("in_flight_batches", C.c_int64),
+                ("slot_arena_bytes", C.c_int64), ("slot_input_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 KEYPOINT_DTYPE = np.dtype([("x", "f4"), ("y", "f4"), ("x_l", "i4"), ("y_l", "i4"), ("level", "i4"),
@@ -112,6 +137,19 @@ def load(path: str | None = None):
     L.of_autotune.argtypes = [C.c_void_p, C.POINTER(OfFrame), C.c_int, C.c_int, C.c_float, C.c_int, C.c_float,
                               C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(OfTuning)]
     L.of_autotune.restype = C.c_int
+    L.of_server_create.argtypes = [C.POINTER(OfServerParams)]
+    L.of_server_create.restype = C.c_void_p
+    L.of_server_destroy.argtypes = [C.c_void_p]
+    L.of_server_destroy.restype = None
+    L.of_server_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int64]
+    L.of_server_submit.restype = C.c_int64
+    L.of_server_poll.argtypes = [C.c_void_p, C.POINTER(OfServerResult), C.c_void_p, C.c_int, C.c_int]
+    L.of_server_poll.restype = C.c_int
+    L.of_server_stats_get.argtypes = [C.c_void_p, C.POINTER(OfServerStats)]
+    L.of_server_stats_get.restype = C.c_int
+    L.of_batch_bytes.argtypes = [C.POINTER(OfParams), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int, C.c_int,
+                                 C.c_float, C.c_int]
+    L.of_batch_bytes.restype = C.c_int64
     L.of_sync.argtypes = [C.c_void_p]
     L.of_sync.restype = C.c_int
     L.of_test_timeout.argtypes = [C.c_void_p, C.c_int64]
@@ -219,6 +257,52 @@ def of_autotune(h: int, frames, levels: int, scale: float, fast_t: int, harris_k
     _check(load().of_autotune(h, arr, len(frames), levels, scale, fast_t, harris_k, n_features, _ptr(out_kpts),
                               _ptr(out_counts), reps, C.byref(t)))
     return t
+
+
+def of_batch_bytes(params: OfParams, sizes, levels: int, scale: float, n_features: int) -> int:
+    """Scratch bytes for a batch of frames with the given (w, h) sizes (host-only)."""
+    n = len(sizes)
+    ws = (C.c_int32 * n)(*[w for w, _ in sizes])
+    hs = (C.c_int32 * n)(*[h for _, h in sizes])
+    return _check(int(load().of_batch_bytes(C.byref(params), ws, hs, n, levels, scale, n_features)))
+
+
+def of_server_create(**kw) -> int:
+    p = OfServerParams()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    s = load().of_server_create(C.byref(p))
+    if not s:
+        raise OfError(OF_ERR_ARG, of_last_error())
+    return s
+
+
+def of_server_destroy(s: int) -> None:
+    load().of_server_destroy(s)
+
+
+def of_server_submit(s: int, img: np.ndarray, tag: int = 0) -> int:
+    """img: 2-D uint8 numpy array (rows may be strided)."""
+    assert img.dtype == np.uint8 and img.ndim == 2 and img.strides[1] == 1
+    return _check(int(load().of_server_submit(s, img.ctypes.data, img.shape[1], img.shape[0], img.strides[0], tag)))
+
+
+def of_server_poll(s: int, max_results: int, n_features: int, wait_ms: int = 0):
+    """Returns a list of (OfServerResult, keypoints ndarray)."""
+    res = (OfServerResult * max_results)()
+    kp = np.zeros(max_results * n_features, KEYPOINT_DTYPE)
+    n = _check(load().of_server_poll(s, res, kp.ctypes.data, max_results, wait_ms))
+    out = []
+    for i in range(n):
+        c = res[i].count
+        out.append((res[i], kp[i * n_features: i * n_features + max(c, 0)].copy()))
+    return out
+
+
+def of_server_stats(s: int) -> dict:
+    st = OfServerStats()
+    _check(load().of_server_stats_get(s, C.byref(st)))
+    return st.as_dict()
 
 
 def of_sync(h: int) -> int:

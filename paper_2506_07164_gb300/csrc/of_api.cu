@@ -270,7 +270,7 @@ struct of_handle {
 
 namespace {
 
-constexpr int kMaxPlans = 8;
+constexpr int kMaxPlans = 64;
 
 struct DeviceGuard {
     int prev = -1;
@@ -838,6 +838,10 @@ of_handle* of_create(const of_params* pin) {
     if (p.border == 0) p.border = 19;
     if (p.harris_block == 0) p.harris_block = 7;
     if (p.orient_radius == 0) p.orient_radius = 15;
+    if (p.arena_bytes < 0) {
+        fail(OF_ERR_ARG, "arena_bytes must be >= 0");
+        return nullptr;
+    }
     if (p.autotune != 0 && p.autotune != 1) {
         fail(OF_ERR_ARG, "autotune must be 0 or 1");
         return nullptr;
@@ -873,9 +877,12 @@ of_handle* of_create(const of_params* pin) {
     s.n_features = p.max_features;
     s.border = p.border;
     s.cell = p.cell;
-    std::vector<FrameKey> worst(p.max_batch, FrameKey{p.max_w, p.max_h, (int)align_up(p.max_w, 16), true});
-    const Layout L = make_layout(worst, s, p.max_features);
-    H->arena_bytes = L.total;
+    if (p.arena_bytes > 0) {
+        H->arena_bytes = (size_t)p.arena_bytes;
+    } else {
+        std::vector<FrameKey> worst(p.max_batch, FrameKey{p.max_w, p.max_h, (int)align_up(p.max_w, 16), true});
+        H->arena_bytes = make_layout(worst, s, p.max_features).total;
+    }
     e = cudaMalloc(&H->arena, H->arena_bytes);
     if (e != cudaSuccess) return bail(e, "cudaMalloc(arena)");
     e = cudaMalloc(&H->d_counts, sizeof(int32_t) * 8);
@@ -933,6 +940,25 @@ int of_autotune(of_handle* H, const of_frame* frames, int n_frames, int levels, 
     H->last = P;
     if (result) *result = P->tun;
     return OF_OK;
+}
+
+int64_t of_batch_bytes(const of_params* p, const int32_t* ws, const int32_t* hs, int n_frames,
+                       int levels, float scale, int n_features) {
+    if (!p || !ws || !hs || n_frames < 1 || levels < 1 || levels > 16 || !(scale > 1.0f) || n_features < 0)
+        return fail(OF_ERR_ARG, "bad arguments");
+    Settings s{};
+    s.levels = levels;
+    s.scale = scale;
+    s.n_features = n_features;
+    s.border = p->border ? p->border : 19;
+    s.cell = p->cell ? p->cell : 30;
+    if (s.cell < 8 || s.border < 4) return fail(OF_ERR_ARG, "bad border/cell");
+    std::vector<FrameKey> fr(n_frames);
+    for (int i = 0; i < n_frames; ++i) {
+        if (ws[i] < 1 || hs[i] < 1) return fail(OF_ERR_ARG, "bad frame size");
+        fr[i] = FrameKey{ws[i], hs[i], (int)align_up(ws[i], 16), true};
+    }
+    return (int64_t)make_layout(fr, s, -1).total;
 }
 
 int of_time_stages(of_handle* H, void* const* events) {
