@@ -275,6 +275,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving leg duration (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=500.0, help="Poisson arrival rate, frames/s")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-buffer path (profiling)")
+    ap.add_argument("--skip-learned", action="store_true", help="skip the learned tile-proposal leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -442,6 +443,58 @@ def main():
                                       for i, n in enumerate(ofg.STAGE_NAMES)},
                 "algorithmic_bytes_per_frame": dict(zip(ofg.STAGE_NAMES, per_frame))}
 
+    # Learned tile proposal on the same batch: committed network and threshold.
+    learned_out = None
+    if not args.skip_learned:
+        from paper_2506_07164_gb300 import learned as lrn
+
+        meta = json.load(open(lrn.DEFAULT_META))
+        net = lrn.TileNet(0).load(lrn.DEFAULT_WEIGHTS)
+        thr, dil, mc = meta["threshold"], meta["dilate"], meta["min_confidence"]
+        plain_recs = ofg.keypoints_to_numpy(batched.out[: B * NFEAT * 64]).copy()
+        plain_cnt = batched.counts[:B].cpu().numpy().copy()
+
+        def step_learned():
+            ofg.of_detect_learned(batched.h, frames, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, net.net, thr, mc, dil,
+                                  batched.out, batched.counts, want_stats=False)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step_learned()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step_learned()
+            e1.record(stream)
+            e1.synchronize()
+            ms_l = e0.elapsed_time(e1)
+            st = ofg.of_detect_learned(batched.h, frames, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, net.net, thr, mc,
+                                       dil, batched.out, batched.counts, want_stats=True)
+        torch.cuda.synchronize()
+        lrec = ofg.keypoints_to_numpy(batched.out[: B * NFEAT * 64])
+        lcnt = batched.counts[:B].cpu().numpy()
+        inter = union = tot = same = 0
+        for f in range(B):
+            a = plain_recs[f * NFEAT: f * NFEAT + plain_cnt[f]]
+            b = lrec[f * NFEAT: f * NFEAT + lcnt[f]]
+            A = {(int(l), int(y), int(x)) for l, y, x in zip(a["level"], a["y_l"], a["x_l"])}
+            Bs = {(int(l), int(y), int(x)) for l, y, x in zip(b["level"], b["y_l"], b["x_l"])}
+            inter += len(A & Bs)
+            union += len(A | Bs)
+            tot += len(A)
+            same += int(len(a) == len(b) and np.array_equal(a.view(np.uint8), b.view(np.uint8)))
+        lfps = B * args.steps * world / (ms_l / 1000.0)
+        learned_out = {"value": round(lfps, 2), "unit": "frames/s", "ms_per_step": round(ms_l / args.steps, 4),
+                       "vs_plain_batched": round(lfps / value, 3), "recall": round(inter / max(1, tot), 5),
+                       "jaccard": round(inter / max(1, union), 5), "identical_frames": same, "frames": B,
+                       "proposed_fraction": round(st["proposed"] / max(1, st["tiles"]), 4),
+                       "fallback_images": st["fallback_images"], "threshold": thr, "dilate": dil,
+                       "network": "3x conv3x3 s2 (8/16/16) + GAP + linear, bf16 weights, fp32 accumulate; "
+                                  f"trained on {meta['train_frames']} synthetic 1080p frames "
+                                  f"({meta['train_tiles']} tiles, {meta['steps']} Adam steps)"}
+        net.close()
+
     serving = None
     if args.serve_seconds > 0:
         serving = serving_leg(pool, args.serve_seconds, args.serve_rate)
@@ -470,6 +523,7 @@ def main():
                 "d2h_bytes_per_step": B * NFEAT * 64 + 4 * B, "steps": e2e_steps},
         "autotune": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tuning.items()},
         "roofline": roofline,
+        "learned": learned_out,
         "serving": serving,
         "cpu_baseline": cpu,
         "clocks": clocks,

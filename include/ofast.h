@@ -280,6 +280,64 @@ int of_server_poll(of_server* s, of_server_result* results, of_keypoint* kpts, i
                    int wait_ms);
 int of_server_stats_get(of_server* s, of_server_stats* out);
 
+/* ------------------------------------------------------------------------
+ * Learned tile proposal.  The paper has no counterpart; this is a learned
+ * front end to its exact detector.  A tiny network scores every 32 x 32 tile
+ * of every pyramid level (on the detect-tile grid) from the tile and a
+ * 16-pixel halo: 3 x 3 convolutions with stride 2 and ReLU, 1 -> 8 -> 16 ->
+ * 16 channels, global average pool, linear -> 1 logit; bf16 weights, fp32
+ * accumulation; trained with the library's own forward / backward / Adam
+ * kernels.  The exact path then runs only on proposed tiles. */
+typedef struct of_tcnn of_tcnn;
+
+/* He-uniform initialisation from `seed`, zero biases, Adam state cleared. */
+of_tcnn* of_tcnn_create(uint64_t seed);
+void of_tcnn_destroy(of_tcnn* net);
+int of_tcnn_num_params(void);
+/* Flat fp32 parameters [host, of_tcnn_num_params()]: conv1 w[8][1][3][3], b[8],
+ * conv2 w[16][8][3][3], b[16], conv3 w[16][16][3][3], b[16], head w[16], b.
+ * set: master copy (bf16 compute copy rounded from it; Adam state cleared).
+ * get which: 0 master, 1 the bf16 compute copy, 2 the last gradient. */
+int of_tcnn_set_params(of_tcnn* net, const float* host);
+int of_tcnn_get_params(of_tcnn* net, int which, float* host);
+/* tiles [device]: n x 64 x 64 uint8 patches; logits [device]: n floats. */
+int of_tcnn_forward(of_tcnn* net, const uint8_t* tiles, int n, float* logits, void* stream);
+/* One training step's gradient: weighted BCE with logits over n patches
+ * (labels [device] 0/1 floats, positives weighted by pos_weight), mean over n;
+ * gradients of the bf16 weights replace the previous ones.  loss_out [host,
+ * may be NULL] receives the loss (synchronises the stream). */
+int of_tcnn_loss_grad(of_tcnn* net, const uint8_t* tiles, const float* labels, int n, float pos_weight,
+                      float* loss_out, void* stream);
+/* Adam (bias-corrected, decoupled weight decay) on the master weights. */
+int of_tcnn_adam(of_tcnn* net, float lr, float beta1, float beta2, float eps, float weight_decay,
+                 void* stream);
+/* Checkpoint: "OFTC", version 1, parameter count, step, master weights, Adam
+ * moments, CRC-32.  save with buf NULL returns the size; load verifies all. */
+int64_t of_tcnn_save(of_tcnn* net, uint8_t* buf, int64_t cap);
+int of_tcnn_load(of_tcnn* net, const uint8_t* buf, int64_t n);
+
+/* Detect with tile proposal: the pyramid, then the network on every
+ * proposal tile, then FAST / NMS / Harris / top-N / orientation restricted
+ * to proposed tiles (scores are 0 outside them).  A tile is proposed when
+ * sigmoid(logit) >= threshold, or when a neighbour is and dilate = 1.  An
+ * image (frame, level) whose confidence -- mean |2 sigmoid(logit) - 1| over
+ * its tiles -- is below min_confidence runs on all its tiles (full-frame
+ * fallback).  threshold <= 0 proposes everything (identical to
+ * of_detect_batch).  stats [host, may be NULL] receives {tiles, proposed
+ * tiles, fallback images} and synchronises.  Other arguments as
+ * of_detect_batch. */
+int of_detect_learned(of_handle* h, const of_frame* frames, int n_frames, int levels, float scale,
+                      int fast_t, float harris_k, int n_features, of_tcnn* net, float threshold,
+                      float min_confidence, int dilate, of_keypoint* out_kpts, int32_t* out_counts,
+                      int32_t* stats);
+
+/* Copy the 64 x 64 input patches of every proposal tile of (frame, level) of
+ * the last detect call into dst [device, may be NULL to query], tile-major in
+ * row order of the proposal grid.  grid [host, 2 ints] receives its columns
+ * and rows.  Returns the number of tiles, or a negative OF_ERR_*. */
+int of_extract_tiles(of_handle* h, int frame, int level, uint8_t* dst, int64_t cap_tiles,
+                     int32_t* grid);
+
 /* Host-only: the pyramid plan the detector uses for a W x H frame (no GPU
  * needed).  ws, hs [host, levels ints] receive level sizes; quota [host,
  * levels ints] receives the per-level feature quota for n_features.

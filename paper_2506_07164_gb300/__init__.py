@@ -24,7 +24,9 @@ __all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspec
            "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc", "of_sync",
            "of_test_timeout", "OF_ERR_TIMEOUT", "of_autotune", "OfTuning", "of_batch_bytes",
            "of_server_create", "of_server_destroy", "of_server_submit", "of_server_poll", "of_server_stats",
-           "OfServerParams", "OfServerResult",
+           "OfServerParams", "OfServerResult", "of_tcnn_create", "of_tcnn_destroy", "of_tcnn_num_params",
+           "of_tcnn_set_params", "of_tcnn_get_params", "of_tcnn_forward", "of_tcnn_loss_grad", "of_tcnn_adam",
+           "of_tcnn_save", "of_tcnn_load", "of_detect_learned", "of_extract_tiles",
            "of_last_error", "of_version", "OfParams", "OfFrame", "OfKeypoint", "KEYPOINT_DTYPE",
            "OF_BUF_LEVEL", "OF_BUF_SCORE", "OF_BUF_CELLT", "OF_BUF_CAND", "OfError", "load",
            "Detector", "keypoints_to_numpy"]
@@ -150,6 +152,33 @@ def load(path: str | None = None):
     L.of_batch_bytes.argtypes = [C.POINTER(OfParams), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int, C.c_int,
                                  C.c_float, C.c_int]
     L.of_batch_bytes.restype = C.c_int64
+    L.of_tcnn_create.argtypes = [C.c_uint64]
+    L.of_tcnn_create.restype = C.c_void_p
+    L.of_tcnn_destroy.argtypes = [C.c_void_p]
+    L.of_tcnn_destroy.restype = None
+    L.of_tcnn_num_params.argtypes = []
+    L.of_tcnn_num_params.restype = C.c_int
+    L.of_tcnn_set_params.argtypes = [C.c_void_p, C.c_void_p]
+    L.of_tcnn_set_params.restype = C.c_int
+    L.of_tcnn_get_params.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+    L.of_tcnn_get_params.restype = C.c_int
+    L.of_tcnn_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+    L.of_tcnn_forward.restype = C.c_int
+    L.of_tcnn_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float,
+                                    C.POINTER(C.c_float), C.c_void_p]
+    L.of_tcnn_loss_grad.restype = C.c_int
+    L.of_tcnn_adam.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, C.c_void_p]
+    L.of_tcnn_adam.restype = C.c_int
+    L.of_tcnn_save.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    L.of_tcnn_save.restype = C.c_int64
+    L.of_tcnn_load.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    L.of_tcnn_load.restype = C.c_int
+    L.of_detect_learned.argtypes = [C.c_void_p, C.POINTER(OfFrame), C.c_int, C.c_int, C.c_float, C.c_int,
+                                    C.c_float, C.c_int, C.c_void_p, C.c_float, C.c_float, C.c_int, C.c_void_p,
+                                    C.c_void_p, C.POINTER(C.c_int32)]
+    L.of_detect_learned.restype = C.c_int
+    L.of_extract_tiles.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int32)]
+    L.of_extract_tiles.restype = C.c_int
     L.of_sync.argtypes = [C.c_void_p]
     L.of_sync.restype = C.c_int
     L.of_test_timeout.argtypes = [C.c_void_p, C.c_int64]
@@ -303,6 +332,84 @@ def of_server_stats(s: int) -> dict:
     st = OfServerStats()
     _check(load().of_server_stats_get(s, C.byref(st)))
     return st.as_dict()
+
+
+# ------------------------------------------------------------ tile-proposal network
+def _sp(stream):
+    return None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+
+
+def of_tcnn_create(seed: int = 0) -> int:
+    n = load().of_tcnn_create(seed)
+    if not n:
+        raise OfError(OF_ERR_CUDA, of_last_error())
+    return n
+
+
+def of_tcnn_destroy(net: int) -> None:
+    load().of_tcnn_destroy(net)
+
+
+def of_tcnn_num_params() -> int:
+    return int(load().of_tcnn_num_params())
+
+
+def of_tcnn_set_params(net: int, params: np.ndarray) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == of_tcnn_num_params()
+    _check(load().of_tcnn_set_params(net, p.ctypes.data))
+
+
+def of_tcnn_get_params(net: int, which: int = 0) -> np.ndarray:
+    out = np.zeros(of_tcnn_num_params(), np.float32)
+    _check(load().of_tcnn_get_params(net, which, out.ctypes.data))
+    return out
+
+
+def of_tcnn_forward(net: int, tiles, n: int, logits, stream=None) -> None:
+    _check(load().of_tcnn_forward(net, _ptr(tiles), n, _ptr(logits), _sp(stream)))
+
+
+def of_tcnn_loss_grad(net: int, tiles, labels, n: int, pos_weight: float = 1.0, stream=None) -> float:
+    loss = C.c_float()
+    _check(load().of_tcnn_loss_grad(net, _ptr(tiles), _ptr(labels), n, pos_weight, C.byref(loss), _sp(stream)))
+    return float(loss.value)
+
+
+def of_tcnn_adam(net: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                 weight_decay: float = 0.0, stream=None) -> None:
+    _check(load().of_tcnn_adam(net, lr, beta1, beta2, eps, weight_decay, _sp(stream)))
+
+
+def of_tcnn_save(net: int) -> bytes:
+    n = _check(int(load().of_tcnn_save(net, None, 0)))
+    buf = (C.c_uint8 * n)()
+    _check(int(load().of_tcnn_save(net, buf, n)))
+    return bytes(buf)
+
+
+def of_tcnn_load(net: int, data: bytes) -> None:
+    buf = (C.c_uint8 * len(data)).from_buffer_copy(data)
+    _check(load().of_tcnn_load(net, buf, len(data)))
+
+
+def of_detect_learned(h: int, frames, levels: int, scale: float, fast_t: int, harris_k: float,
+                      n_features: int, net: int, threshold: float, min_confidence: float, dilate: int,
+                      out_kpts, out_counts, want_stats: bool = True):
+    arr = (OfFrame * len(frames))()
+    for i, (img, w, hh, pitch) in enumerate(frames):
+        arr[i] = OfFrame(_ptr(img), w, hh, pitch)
+    st = (C.c_int32 * 3)()
+    _check(load().of_detect_learned(h, arr, len(frames), levels, scale, fast_t, harris_k, n_features, net,
+                                    threshold, min_confidence, dilate, _ptr(out_kpts), _ptr(out_counts),
+                                    st if want_stats else None))
+    return {"tiles": st[0], "proposed": st[1], "fallback_images": st[2]} if want_stats else None
+
+
+def of_extract_tiles(h: int, frame: int, level: int, dst=None, cap_tiles: int = 0):
+    grid = (C.c_int32 * 2)()
+    n = _check(load().of_extract_tiles(h, frame, level, _ptr(dst), cap_tiles, grid))
+    return n, (grid[0], grid[1])
 
 
 def of_sync(h: int) -> int:

@@ -160,6 +160,17 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const Img& I = imgs[ti.img];
         const uint8_t* s = sbuf + b * FAST_BUF;
         const int X0 = ti.x0, Y0 = ti.y0;
+        // Learned path: the 4 proposal tiles of this work tile; skip it when all are off.
+        uint32_t pm = 0xFFFFFFFFu;
+        if (I.pmask) {
+            const int tx = (X0 - I.tile_x0) / TILE_W, tyt = (Y0 - border) / TILE_H;
+            pm = *reinterpret_cast<const uint32_t*>(I.pmask + (size_t)tyt * 4 * I.tiles_x + 4 * tx);
+        }
+        if (pm == 0u) {
+            __syncthreads();
+            continue;
+        }
+        const uint32_t lane_on = ((pm >> (8 * (lane >> 3))) & 0xFFu) ? 0xFFFFFFFFu : 0u;
         const int rx0 = border, rx1 = I.w - border, ry1 = I.h - border;
         const int cx0 = (max(X0, rx0) - rx0) / cell;
         const int cy0 = (Y0 - border) / cell;
@@ -181,7 +192,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             hw[k][4] = __byte_perm(wp, 0u, 0x4140);
             hw[k][5] = __byte_perm(wp, 0u, 0x4342);
         }
-        const uint32_t colmask = range_mask4(x, rx0, rx1);
+        const uint32_t colmask = range_mask4(x, rx0, rx1) & lane_on;
 
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {

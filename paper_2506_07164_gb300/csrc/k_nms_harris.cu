@@ -145,6 +145,15 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         uint8_t* sS = sbuf + b * S_BUF;
         const uint8_t* sI = ibuf + b * I_BUF;
         const int X0 = ti.x0, Y0 = ti.y0;
+        // Learned path: no survivor can lie in a work tile whose proposal tiles are all off.
+        if (I.pmask) {
+            const int tx = (X0 - I.tile_x0) / TILE_W, tyt = (Y0 - border) / TILE_H;
+            if (*reinterpret_cast<const uint32_t*>(I.pmask + (size_t)tyt * 4 * I.tiles_x + 4 * tx) == 0u) {
+                fence_proxy_async_smem();
+                __syncthreads();
+                continue;
+            }
+        }
         const int rx0 = border, rx1 = I.w - border, ry0 = border, ry1 = I.h - border;
         // Only columns X0-1 .. X0+TILE_W feed the 3x3 test; the rest become 0.
         const int lox = max(rx0, X0 - 1), hix = min(rx1, X0 + TILE_W + 1);
@@ -179,7 +188,14 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             const int iy = Y0 - 1 + r, ix = X0 - HALO_X + 4 * k;
             uint32_t* wp = reinterpret_cast<uint32_t*>(sS + r * SROW) + k;
             uint32_t val = 0u;
-            if (iy >= ry0 && iy < ry1) {
+            bool on = iy >= ry0 && iy < ry1;
+            if (on && I.pmask) {
+                // Outside the proposed tiles S is 0 (each staged word lies in one proposal tile).
+                const int px = (ix - I.tile_x0) >> 5, py = (iy - ry0) >> 5;
+                on = ix >= I.tile_x0 && px < 4 * I.tiles_x && py < I.tiles_y &&
+                     I.pmask[(size_t)py * 4 * I.tiles_x + px] != 0;
+            }
+            if (on) {
                 val = *wp & range_mask4(ix, lox, hix);
                 // Bytes below t_hi survive only when their cell has no strong pixel.
                 if (cells && val)

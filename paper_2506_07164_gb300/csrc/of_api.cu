@@ -29,6 +29,12 @@ void set_select_smem_limit(int bytes);
 int fast_blocks_per_sm();
 int nms_blocks_per_sm();
 void launch_wait_test(const int32_t* flag, int32_t* status, uint64_t limit_ns, void* stream);
+int launch_propose(const Img* imgs, const int32_t* list, const int32_t* prefix, int n_list, const float* logits,
+                   uint8_t* pos, uint8_t* mask, float threshold, float min_conf, int dilate, int32_t* stats,
+                   void* stream);
+int launch_extract(const Img* imgs, int img, int border, uint8_t* dst, int n, void* stream);
+int tcnn_forward_tiles(of_tcnn* N, const Img* imgs, const int32_t* list, const int32_t* prefix, int n_list,
+                       int n_tiles, int border, float* logits, void* stream);
 }
 
 using namespace ofk;
@@ -214,6 +220,12 @@ struct Plan {
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps], n_img each
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
     bool tuned = false;
+    // Learned path: proposal tiles per listed image, device buffers
+    // [mask | pos | logits | prefix | stats], allocated on first use.
+    std::vector<int32_t> ptile_prefix;  // det_list.size() + 1 entries
+    uint8_t* lbuf = nullptr;
+    size_t off_mask = 0, off_pos = 0, off_logit = 0, off_pp = 0, off_stats = 0;
+    bool pmask_on = false;
     size_t header_bytes = 0;
     uint8_t* stage[2] = {nullptr, nullptr};
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -245,6 +257,7 @@ void free_plan(Plan* p) {
         if (p->stage[i]) cudaFreeHost(p->stage[i]);
     }
     if (p->dbuf) cudaFree(p->dbuf);
+    if (p->lbuf) cudaFree(p->lbuf);
     delete p;
 }
 
@@ -569,6 +582,60 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     return OF_OK;
 }
 
+// Upload the descriptor header (call constants, images, resize jobs, tensor
+// maps) through the plan's pinned staging ring, ordered on the handle's stream.
+int upload_header(of_handle* H, Plan* P) {
+    const int si = P->stage_i;
+    P->stage_i ^= 1;
+    OF_CK(cudaEventSynchronize(P->ev[si]));
+    uint8_t* st = P->stage[si];
+    std::memcpy(st + P->off_call, &P->h_call, sizeof(Call));
+    std::memcpy(st + P->off_img, P->h_img.data(), sizeof(Img) * P->h_img.size());
+    std::memcpy(st + P->off_rs, P->h_rs.data(), sizeof(Resize) * P->h_rs.size());
+    std::memcpy(st + P->off_maps, P->h_maps.data(), sizeof(CUtensorMap) * P->h_maps.size());
+    OF_CK(cudaMemcpyAsync(P->dbuf, st, P->header_bytes, cudaMemcpyHostToDevice, H->stream));
+    OF_CK(cudaEventRecord(P->ev[si], H->stream));
+    return OF_OK;
+}
+
+// Turn the proposal masks of a plan on (learned path) or off (plain path).
+int set_pmask(of_handle* H, Plan* P, bool on) {
+    if (P->pmask_on == on) return OF_OK;
+    for (size_t j = 0; j < P->det_list.size(); ++j)
+        P->h_img[P->det_list[j]].pmask = on ? P->lbuf + P->off_mask + P->ptile_prefix[j] : nullptr;
+    P->pmask_on = on;
+    return upload_header(H, P);
+}
+
+// Device buffers of the learned path (first use of a plan).
+int ensure_learned(Plan* P) {
+    if (P->lbuf) return OF_OK;
+    const size_t nl = P->det_list.size();
+    P->ptile_prefix.assign(nl + 1, 0);
+    for (size_t j = 0; j < nl; ++j) {
+        const Img& I = P->h_img[P->det_list[j]];
+        P->ptile_prefix[j + 1] = P->ptile_prefix[j] + 4 * I.tiles_x * I.tiles_y;  // multiple of 4
+    }
+    const size_t nt = (size_t)P->ptile_prefix[nl];
+    size_t off = 0;
+    P->off_mask = off;
+    off = align_up(off + std::max<size_t>(nt, 4), 256);
+    P->off_pos = off;
+    off = align_up(off + std::max<size_t>(nt, 4), 256);
+    P->off_logit = off;
+    off = align_up(off + sizeof(float) * std::max<size_t>(nt, 1), 256);
+    P->off_pp = off;
+    off = align_up(off + sizeof(int32_t) * (nl + 1), 256);
+    P->off_stats = off;
+    off += 4 * sizeof(int32_t);
+    cudaError_t e = cudaMalloc(&P->lbuf, off);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->lbuf + P->off_pp, P->ptile_prefix.data(), sizeof(int32_t) * (nl + 1),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(OF_ERR_CUDA, std::string("learned-path buffers: ") + cudaGetErrorString(e));
+    return OF_OK;
+}
+
 // Point the plan at this call's frames and output, re-uploading the
 // descriptor header when anything changed.
 int bind_plan(of_handle* H, Plan* P, const of_frame* frames, of_keypoint* out, int32_t* counts) {
@@ -601,17 +668,7 @@ int bind_plan(of_handle* H, Plan* P, const of_frame* frames, of_keypoint* out, i
     P->bound_out = out;
     P->bound_counts = counts;
     P->bound = true;
-    const int si = P->stage_i;
-    P->stage_i ^= 1;
-    OF_CK(cudaEventSynchronize(P->ev[si]));
-    uint8_t* st = P->stage[si];
-    std::memcpy(st + P->off_call, &P->h_call, sizeof(Call));
-    std::memcpy(st + P->off_img, P->h_img.data(), sizeof(Img) * P->h_img.size());
-    std::memcpy(st + P->off_rs, P->h_rs.data(), sizeof(Resize) * P->h_rs.size());
-    std::memcpy(st + P->off_maps, P->h_maps.data(), sizeof(CUtensorMap) * P->h_maps.size());
-    OF_CK(cudaMemcpyAsync(P->dbuf, st, P->header_bytes, cudaMemcpyHostToDevice, H->stream));
-    OF_CK(cudaEventRecord(P->ev[si], H->stream));
-    return OF_OK;
+    return upload_header(H, P);
 }
 
 Plan* find_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings& s) {
@@ -786,6 +843,8 @@ int run_batch(of_handle* H, const of_frame* frames, int n_frames, int levels, fl
     int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out,
                            counts, &P);
     if (rc != OF_OK) return rc;
+    rc = set_pmask(H, P, false);
+    if (rc != OF_OK) return rc;
     if (H->p.autotune && !P->tuned) {
         rc = autotune_plan(H, P, 3);
         if (rc != OF_OK) return rc;
@@ -959,6 +1018,68 @@ int64_t of_batch_bytes(const of_params* p, const int32_t* ws, const int32_t* hs,
         fr[i] = FrameKey{ws[i], hs[i], (int)align_up(ws[i], 16), true};
     }
     return (int64_t)make_layout(fr, s, -1).total;
+}
+
+int of_detect_learned(of_handle* H, const of_frame* frames, int n_frames, int levels, float scale, int fast_t,
+                      float harris_k, int n_features, of_tcnn* net, float threshold, float min_confidence,
+                      int dilate, of_keypoint* out_kpts, int32_t* out_counts, int32_t* stats) {
+    if (!H) return fail(OF_ERR_ARG, "null handle");
+    if (!net) return fail(OF_ERR_ARG, "null network");
+    if (!(threshold <= 1.0f) || !(min_confidence >= 0.0f && min_confidence <= 1.0f) || (dilate != 0 && dilate != 1))
+        return fail(OF_ERR_ARG, "threshold <= 1, 0 <= min_confidence <= 1, dilate 0/1");
+    DeviceGuard dg(H->device);
+    Plan* P = nullptr;
+    int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
+                           out_counts, &P);
+    if (rc != OF_OK) return rc;
+    rc = ensure_learned(P);
+    if (rc == OF_OK) rc = set_pmask(H, P, true);
+    if (rc != OF_OK) return rc;
+    cudaStream_t st = H->stream;
+    const int n_list = (int)P->det_list.size();
+    const int n_tiles = P->ptile_prefix[n_list];
+    int32_t* d_stats = reinterpret_cast<int32_t*>(P->lbuf + P->off_stats);
+    const int32_t* d_pp = reinterpret_cast<const int32_t*>(P->lbuf + P->off_pp);
+    float* d_logit = reinterpret_cast<float*>(P->lbuf + P->off_logit);
+    OF_CK(cudaMemsetAsync(d_stats, 0, 4 * sizeof(int32_t), st));
+    if (n_features == 0) OF_CK(cudaMemsetAsync(out_counts, 0, sizeof(int32_t) * n_frames, st));
+    OF_CK(cudaGraphLaunch(P->stage_exec[0], st));  // pyramid
+    rc = tcnn_forward_tiles(net, P->d_img(), P->d_dl(), d_pp, n_list, n_tiles, P->s.border, d_logit, st);
+    if (rc == OF_OK)
+        rc = launch_propose(P->d_img(), P->d_dl(), d_pp, n_list, d_logit, P->lbuf + P->off_pos,
+                            P->lbuf + P->off_mask, threshold, min_confidence, dilate, d_stats, st);
+    if (rc != OF_OK) return rc;
+    for (int k = 1; k < kStages; ++k) OF_CK(cudaGraphLaunch(P->stage_exec[k], st));
+    H->last = P;
+    if (stats) {
+        OF_CK(cudaMemcpyAsync(H->h_count + 4, d_stats, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        OF_CK(cudaStreamSynchronize(st));
+        std::memcpy(stats, H->h_count + 4, 3 * sizeof(int32_t));
+    }
+    return OF_OK;
+}
+
+int of_extract_tiles(of_handle* H, int frame, int level, uint8_t* dst, int64_t cap_tiles, int32_t* grid) {
+    if (!H) return fail(OF_ERR_ARG, "null handle");
+    Plan* P = H->last;
+    if (!P) return fail(OF_ERR_ARG, "no detect call to extract from");
+    const int nl = P->s.levels;
+    if (frame < 0 || frame >= (int)P->frames.size() || level < 0 || level >= nl)
+        return fail(OF_ERR_ARG, "frame/level out of range");
+    const int ii = frame * nl + level;
+    const Img& I = P->h_img[ii];
+    const int n = 4 * I.tiles_x * I.tiles_y;
+    if (grid) {
+        grid[0] = 4 * I.tiles_x;
+        grid[1] = I.tiles_y;
+    }
+    if (!dst || n == 0) return n;
+    if (cap_tiles < n) return fail(OF_ERR_ARG, "dst too small");
+    DeviceGuard dg(H->device);
+    const int rc = launch_extract(P->d_img(), ii, P->s.border, dst, n, H->stream);
+    if (rc != OF_OK) return rc;
+    OF_CK(cudaStreamSynchronize(H->stream));
+    return n;
 }
 
 int of_time_stages(of_handle* H, void* const* events) {

@@ -49,6 +49,10 @@ struct Img {
     int32_t tile_x0;           // x origin of tile 0 (multiple of 16)
     int32_t slot0;             // first output slot of this image (sum of earlier quotas)
     double lscale;             // scale^level
+    // Learned path: one byte per 32 x 32 proposal tile on the detect-tile grid
+    // (4 * tiles_x columns, tiles_y rows, tile (px, py) covers x in
+    // [tile_x0 + 32 px, +32), y in [border + 32 py, +32)); 0 = skip.  Null: all on.
+    const uint8_t* pmask;
 };
 
 // One resize job: dst = bilinear(src).  Tables hold (i0 << 12) | a per

@@ -1,0 +1,173 @@
+"""Learned tile proposal on the GPU: kernels against the float64 oracle,
+checkpoints, the all-tiles case against the plain path, and what a trained
+network gains (tiles skipped at high keypoint recall) over no network."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import tcnn as ora
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2506_07164_gb300 as ofg  # noqa: E402
+from paper_2506_07164_gb300 import learned  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ofg.build()
+    ofg.load()
+
+
+def _tiles(n, seed):
+    rng = np.random.default_rng(seed)
+    img = synth.scene(256, 256, seed, n_rect=30, n_checker=5)
+    out = np.zeros((n, 64, 64), np.uint8)
+    for i in range(n):
+        y, x = rng.integers(0, 192, 2)
+        out[i] = img[y:y + 64, x:x + 64]
+    out[0, :16, :] = 0  # a patch at the image edge (zero halo)
+    return out
+
+
+def test_forward_matches_oracle():
+    net = learned.TileNet(3)
+    rng = np.random.default_rng(0)
+    ofg.of_tcnn_set_params(net.net, rng.normal(scale=0.3, size=ofg.of_tcnn_num_params()).astype(np.float32))
+    tiles = _tiles(37, 1)
+    z = net.logits(torch.from_numpy(tiles).cuda()).cpu().numpy()
+    pq = ofg.of_tcnn_get_params(net.net, 1).astype(np.float64)  # the bf16 weights the kernels use
+    zo, _ = ora.forward(tiles, pq)
+    np.testing.assert_allclose(z, zo, rtol=1e-4, atol=1e-4)
+    net.close()
+
+
+def test_gradient_matches_oracle():
+    net = learned.TileNet(4)
+    tiles = _tiles(24, 2)
+    labels = (np.arange(24) % 3 == 0).astype(np.float32)
+    loss = ofg.of_tcnn_loss_grad(net.net, torch.from_numpy(tiles).cuda(), torch.from_numpy(labels).cuda(), 24,
+                                 pos_weight=2.5)
+    g = ofg.of_tcnn_get_params(net.net, 2).astype(np.float64)
+    pq = ofg.of_tcnn_get_params(net.net, 1).astype(np.float64)
+    lo, go = ora.loss_grad(tiles, labels, pq, pos_weight=2.5)
+    assert loss == pytest.approx(lo, rel=1e-5)
+    err = np.linalg.norm(g - go) / np.linalg.norm(go)
+    assert err < 1e-4, err
+    # Every layer's block, not only the largest one.
+    for name, (a, b) in {"W1": (0, 72), "W2": (80, 1232), "W3": (1248, 3552), "wf": (3568, 3584)}.items():
+        e = np.linalg.norm(g[a:b] - go[a:b]) / max(np.linalg.norm(go[a:b]), 1e-30)
+        assert e < 1e-3, (name, e)
+    net.close()
+
+
+def test_adam_matches_oracle():
+    net = learned.TileNet(5)
+    tiles = torch.from_numpy(_tiles(16, 3)).cuda()
+    labels = torch.from_numpy((np.arange(16) % 2).astype(np.float32)).cuda()
+    p0 = ofg.of_tcnn_get_params(net.net, 0).astype(np.float64)
+    m = np.zeros_like(p0)
+    v = np.zeros_like(p0)
+    for step in (1, 2):
+        ofg.of_tcnn_loss_grad(net.net, tiles, labels, 16)
+        g = ofg.of_tcnn_get_params(net.net, 2).astype(np.float64)
+        ofg.of_tcnn_adam(net.net, 1e-2, weight_decay=1e-4)
+        p0, m, v = ora.adam(p0, g, m, v, step, 1e-2, wd=1e-4)
+        np.testing.assert_allclose(ofg.of_tcnn_get_params(net.net, 0), p0, rtol=1e-5, atol=1e-7)
+    net.close()
+
+
+def test_checkpoint_roundtrip_and_crc(tmp_path):
+    net = learned.TileNet(6)
+    tiles = torch.from_numpy(_tiles(8, 4)).cuda()
+    labels = torch.ones(8, device="cuda")
+    ofg.of_tcnn_loss_grad(net.net, tiles, labels, 8)
+    ofg.of_tcnn_adam(net.net, 1e-3)
+    path = tmp_path / "n.oftc"
+    net.save(str(path))
+    other = learned.TileNet(99).load(str(path))
+    for which in (0, 1):
+        np.testing.assert_array_equal(ofg.of_tcnn_get_params(net.net, which), ofg.of_tcnn_get_params(other.net, which))
+    data = bytearray(path.read_bytes())
+    data[100] ^= 1
+    with pytest.raises(ofg.OfError):
+        ofg.of_tcnn_load(other.net, bytes(data))
+    net.close()
+    other.close()
+
+
+def test_all_tiles_proposed_equals_plain():
+    frames = [synth.scene(w, h, 70 + i, background="pink") for i, (w, h) in enumerate([(960, 540), (640, 480)])]
+    det = ofg.Detector(960, 540, max_levels=8, max_features=400, max_batch=2, fast_t_lo=7)
+    net = learned.TileNet(1)
+    dev = [torch.from_numpy(f).cuda() for f in frames]
+    fr = [(t, t.shape[1], t.shape[0], t.stride(0)) for t in dev]
+    det.detect_batch(dev, levels=8, fast_t=20, n_features=400)
+    torch.cuda.synchronize()
+    plain = det.batch_results(2, 400)
+    st = ofg.of_detect_learned(det.h, fr, 8, 1.2, 20, 0.04, 400, net.net, 0.0, 0.0, 0, det.out, det.counts)
+    assert st["proposed"] == st["tiles"] > 0
+    torch.cuda.synchronize()
+    lrn = det.batch_results(2, 400)
+    for a, b in zip(plain, lrn):
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+    # And back to the plain path on the same handle.
+    det.detect_batch(dev, levels=8, fast_t=20, n_features=400)
+    torch.cuda.synchronize()
+    for a, b in zip(plain, det.batch_results(2, 400)):
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+    det.close()
+    net.close()
+
+
+def test_labels_equal_oracle_labels():
+    """Training labels come from the exact CUDA path; they must equal the tiles
+    that hold the oracle's keypoints."""
+    import oracle
+
+    frames = [synth.scene(960, 540, 850 + i, background="pink") for i in range(2)]
+    det = ofg.Detector(960, 540, max_levels=8, max_features=500, max_batch=2, fast_t_lo=7)
+    tiles, labels = learned.label_frames(det, frames, n_features=500)
+    lab = labels.cpu().numpy()
+    exp = []
+    for f in frames:
+        kp = oracle.detect(f, levels=8, fast_t=20, fast_t_lo=7, n_features=500)
+        ws, hs, _ = oracle.level_sizes(f.shape[1], f.shape[0], 8, 1.2)
+        for lvl in range(8):
+            rw, rh = ws[lvl] - 38, hs[lvl] - 38
+            if rw <= 0 or rh <= 0:
+                continue
+            gx = 4 * ((ws[lvl] - 19 - 16 + 127) // 128)
+            gy = (rh + 31) // 32
+            e = np.zeros(gx * gy, np.float32)
+            k = kp[kp["level"] == lvl]
+            e[((k["y_l"] - 19) // 32) * gx + (k["x_l"] - 16) // 32] = 1
+            exp.append(e)
+    np.testing.assert_array_equal(lab, np.concatenate(exp))
+    assert tiles.shape[0] == lab.shape[0]
+    det.close()
+
+
+def test_training_skips_work_at_high_recall():
+    """A short training run: the loss drops, the trained proposal skips tiles
+    while keeping most keypoints, and a random proposal keeping the same
+    fraction of tiles loses far more of them."""
+    train = [synth.scene(960, 540, 800 + i, background="pink") for i in range(8)]
+    held = [synth.scene(960, 540, 900 + i, background="pink") for i in range(2)]
+    det = ofg.Detector(960, 540, max_levels=8, max_features=500, max_batch=8, fast_t_lo=7)
+    tiles, labels = learned.label_frames(det, train, n_features=500)
+    net = learned.TileNet(2)
+    hist = learned.train(net, tiles, labels, steps=400, batch=1024)
+    assert np.mean(hist[-20:]) < 0.8 * np.mean(hist[:5])
+    thr = learned.choose_threshold(net, tiles, labels, 0.995)
+    ev = learned.evaluate(det, net, held, thr, dilate=1, n_features=500)
+    assert ev["proposed_fraction"] < 0.9, ev
+    assert ev["recall"] > 0.9, ev
+    rnd = learned.random_proposal_recall(det, held, ev["proposed_fraction"], n_features=500)
+    assert ev["recall"] > rnd + 0.05, (ev, rnd)
+    det.close()
+    net.close()
