@@ -8,7 +8,8 @@
 // global average pool; linear 16 -> 1 logit.  Weights are stored and used as
 // bf16 (rounded from fp32 master copies that Adam updates); every product is
 // accumulated in fp32.  One block per tile; activations stay in shared
-// memory (forward) and are saved to global memory for the backward pass.
+// memory.  Training uses a plain forward that saves activations to global
+// memory for the backward pass; inference uses a register-blocked forward.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -164,6 +165,154 @@ k_forward(PatchSrc src, int n, const __nv_bfloat16* __restrict__ wq, float* __re
             for (int i = threadIdx.x; i < A2; i += blockDim.x) sv[A1 + i] = a2[i];
             for (int i = threadIdx.x; i < A3; i += blockDim.x) sv[A1 + A2 + i] = a3[i];
             if (threadIdx.x <= C3) sv[A1 + A2 + A3 + threadIdx.x] = red[threadIdx.x];
+        }
+        __syncthreads();
+    }
+}
+
+// Inference forward, register-blocked.  Activations live in zero-padded
+// planes (no bounds tests); weights are transposed to [c][k][o] so one
+// 16-byte broadcast load serves four output channels; a thread accumulates
+// all channels of one output pixel (layers 1, 2) or four channels (layer 3).
+// Same function as k_forward; products are summed over (c, ky, kx) in the
+// same order.
+constexpr int P0 = S0 + 2, P1 = S1 + 2, P2 = S2 + 2;
+constexpr int FAST_SMEM = (P0 * P0 + C1 * P1 * P1 + C2 * P2 * P2 + A3 + NP + 32) * 4;
+
+__global__ void __launch_bounds__(THREADS)
+k_forward_fast(PatchSrc src, int n, const __nv_bfloat16* __restrict__ wq, float* __restrict__ logits, int border) {
+    extern __shared__ __align__(16) float sm[];
+    float* in = sm;                    // P0 x P0
+    float* a1 = in + P0 * P0;          // C1 x P1 x P1
+    float* a2 = a1 + C1 * P1 * P1;     // C2 x P2 x P2
+    float* a3 = a2 + C2 * P2 * P2;     // C3 x 8 x 8
+    float* w = a3 + A3;                // transposed weights + biases + head
+    float* red = w + NP;
+    const int tid = threadIdx.x;
+    // Zero everything once: padding cells are never written afterwards.
+    for (int i = tid; i < (int)(FAST_SMEM / 4); i += blockDim.x) sm[i] = 0.f;
+    __syncthreads();
+    // w1t[k][o], w2t[c][k][o], w3t[c][k][o] at the same offsets as W1, W2, W3.
+    for (int i = tid; i < NP; i += blockDim.x) {
+        float v = __bfloat162float(wq[i]);
+        int dst = i;
+        if (i < B1) {  // W1[o][0][k]
+            const int o = i / 9, k = i % 9;
+            dst = W1 + k * C1 + o;
+        } else if (i >= W2 && i < B2) {
+            const int j = i - W2, o = j / (C1 * 9), c = (j / 9) % C1, k = j % 9;
+            dst = W2 + (c * 9 + k) * C2 + o;
+        } else if (i >= W3 && i < B3) {
+            const int j = i - W3, o = j / (C2 * 9), c = (j / 9) % C2, k = j % 9;
+            dst = W3 + (c * 9 + k) * C3 + o;
+        }
+        w[dst] = v;
+    }
+    __syncthreads();
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        // Input patch into the interior of the padded plane.
+        if (src.tiles) {
+            const uint8_t* p = src.tiles + (size_t)t * S0 * S0;
+            for (int i = tid; i < S0 * S0; i += blockDim.x)
+                in[((i >> 6) + 1) * P0 + (i & 63) + 1] = ((float)p[i] - 128.f) * (1.f / 64.f);
+        } else {
+            int lo = 0, hi = src.n_list - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(src.prefix + mid) <= t) lo = mid; else hi = mid - 1;
+            }
+            const ofk::Img& I = src.imgs[__ldg(src.list + lo)];
+            const int k = t - __ldg(src.prefix + lo);
+            const int ptx = I.tiles_x * 4;
+            const int x0 = I.tile_x0 + 32 * (k % ptx) - 16, y0 = border + 32 * (k / ptx) - 16;
+            for (int i = tid; i < S0 * S0; i += blockDim.x) {
+                const int x = x0 + (i & 63), y = y0 + (i >> 6);
+                const float v = (x >= 0 && x < I.w && y >= 0 && y < I.h) ? (float)I.img[(size_t)y * I.pitch + x] : 0.f;
+                in[((i >> 6) + 1) * P0 + (i & 63) + 1] = (v - 128.f) * (1.f / 64.f);
+            }
+        }
+        __syncthreads();
+        // Layer 1: 32 x 32 pixels, 4 per thread, 8 channels each.
+        for (int px = tid; px < S1 * S1; px += blockDim.x) {
+            const int y = px >> 5, x = px & 31;
+            float acc[C1];
+#pragma unroll
+            for (int o = 0; o < C1; ++o) acc[o] = w[B1 + o];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const float v = in[(2 * y + k / 3) * P0 + 2 * x + k % 3];
+                const float4 wa = *reinterpret_cast<const float4*>(w + W1 + k * C1);
+                const float4 wb = *reinterpret_cast<const float4*>(w + W1 + k * C1 + 4);
+                acc[0] = fmaf(wa.x, v, acc[0]); acc[1] = fmaf(wa.y, v, acc[1]);
+                acc[2] = fmaf(wa.z, v, acc[2]); acc[3] = fmaf(wa.w, v, acc[3]);
+                acc[4] = fmaf(wb.x, v, acc[4]); acc[5] = fmaf(wb.y, v, acc[5]);
+                acc[6] = fmaf(wb.z, v, acc[6]); acc[7] = fmaf(wb.w, v, acc[7]);
+            }
+#pragma unroll
+            for (int o = 0; o < C1; ++o) a1[o * P1 * P1 + (y + 1) * P1 + x + 1] = relu(acc[o]);
+        }
+        __syncthreads();
+        // Layer 2: 16 x 16 pixels, one per thread, 16 channels each.
+        {
+            const int y = tid >> 4, x = tid & 15;
+            float acc[C2];
+#pragma unroll
+            for (int o = 0; o < C2; ++o) acc[o] = w[B2 + o];
+            for (int c = 0; c < C1; ++c) {
+                const float* ic = a1 + c * P1 * P1;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const float v = ic[(2 * y + k / 3) * P1 + 2 * x + k % 3];
+                    const float* wk = w + W2 + (c * 9 + k) * C2;
+#pragma unroll
+                    for (int o4 = 0; o4 < C2; o4 += 4) {
+                        const float4 ww = *reinterpret_cast<const float4*>(wk + o4);
+                        acc[o4] = fmaf(ww.x, v, acc[o4]);
+                        acc[o4 + 1] = fmaf(ww.y, v, acc[o4 + 1]);
+                        acc[o4 + 2] = fmaf(ww.z, v, acc[o4 + 2]);
+                        acc[o4 + 3] = fmaf(ww.w, v, acc[o4 + 3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < C2; ++o) a2[o * P2 * P2 + (y + 1) * P2 + x + 1] = relu(acc[o]);
+        }
+        __syncthreads();
+        // Layer 3: 8 x 8 pixels x 4 channel groups.
+        {
+            const int pxl = tid & 63, g = tid >> 6;
+            const int y = pxl >> 3, x = pxl & 7;
+            float acc[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) acc[o] = w[B3 + 4 * g + o];
+            for (int c = 0; c < C2; ++c) {
+                const float* ic = a2 + c * P2 * P2;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const float v = ic[(2 * y + k / 3) * P2 + 2 * x + k % 3];
+                    const float4 ww = *reinterpret_cast<const float4*>(w + W3 + (c * 9 + k) * C3 + 4 * g);
+                    acc[0] = fmaf(ww.x, v, acc[0]); acc[1] = fmaf(ww.y, v, acc[1]);
+                    acc[2] = fmaf(ww.z, v, acc[2]); acc[3] = fmaf(ww.w, v, acc[3]);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 4; ++o) a3[(4 * g + o) * 64 + pxl] = relu(acc[o]);
+        }
+        __syncthreads();
+        {
+            const int warp = tid >> 5, lane = tid & 31;
+            for (int c = warp; c < C3; c += 8) {
+                float sgap = a3[c * 64 + lane] + a3[c * 64 + 32 + lane];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sgap += __shfl_xor_sync(0xFFFFFFFFu, sgap, o);
+                if (lane == 0) red[c] = sgap * (1.f / 64.f);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float z = w[BF];
+            for (int c = 0; c < C3; ++c) z = fmaf(w[WF + c], red[c], z);
+            logits[t] = z;
         }
         __syncthreads();
     }
@@ -437,8 +586,8 @@ int tcnn_forward_tiles(of_tcnn* N, const Img* imgs, const int32_t* list, const i
                        int n_tiles, int border, float* logits, void* stream) {
     if (n_tiles <= 0) return OF_OK;
     tn::PatchSrc src{nullptr, imgs, list, prefix, n_list};
-    tn::k_forward<<<tn::grid_for(n_tiles), tn::THREADS, tn::SMEM_FWD, (cudaStream_t)stream>>>(src, n_tiles, N->w,
-                                                                                           logits, nullptr, border);
+    tn::k_forward_fast<<<tn::grid_for(n_tiles), tn::THREADS, tn::FAST_SMEM, (cudaStream_t)stream>>>(
+        src, n_tiles, N->w, logits, border);
     return cudaGetLastError() == cudaSuccess ? OF_OK : tn::fail(OF_ERR_CUDA, "tile-net forward launch failed");
 }
 }  // namespace ofk
@@ -450,6 +599,7 @@ of_tcnn* of_tcnn_create(uint64_t seed) {
     if (!attr) {
         cudaFuncSetAttribute(tn::k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, tn::SMEM_FWD);
         cudaFuncSetAttribute(tn::k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, tn::SMEM_BWD);
+        cudaFuncSetAttribute(tn::k_forward_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, tn::FAST_SMEM);
         attr = true;
     }
     of_tcnn* N = new of_tcnn();
@@ -530,8 +680,8 @@ int of_tcnn_forward(of_tcnn* N, const uint8_t* tiles, int n, float* logits, void
     if (!N || !tiles || !logits || n < 0) return tn::fail(OF_ERR_ARG, "bad arguments");
     if (n == 0) return OF_OK;
     tn::PatchSrc src{tiles, nullptr, nullptr, nullptr, 0};
-    tn::k_forward<<<tn::grid_for(n), tn::THREADS, tn::SMEM_FWD, (cudaStream_t)stream>>>(src, n, N->w, logits, nullptr,
-                                                                                     0);
+    tn::k_forward_fast<<<tn::grid_for(n), tn::THREADS, tn::FAST_SMEM, (cudaStream_t)stream>>>(src, n, N->w, logits,
+                                                                                          0);
     return cudaGetLastError() == cudaSuccess ? OF_OK : tn::fail(OF_ERR_CUDA, "tile-net forward launch failed");
 }
 
