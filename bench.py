@@ -335,7 +335,7 @@ def main():
         for f in frames[: args.plain_frames]:
             ofg.of_detect_batch(plain.h, [f], LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, plain.out, plain.counts)
 
-    def timed(fn, steps, warmup, per_step_events=False):
+    def timed(fn, steps, warmup, per_step_events=False, nvtx_name="timed"):
         for _ in range(warmup):
             fn() if not per_step_events else fn(None)
         barrier()
@@ -348,10 +348,12 @@ def main():
                     e.record(stream)
         barrier()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(nvtx_name)
         start.record(stream)
         for k in range(steps):
             fn(evs[k]) if per_step_events else fn()
         end.record(stream)
+        torch.cuda.nvtx.range_pop()
         end.synchronize()
         barrier()
         ms = start.elapsed_time(end)
@@ -365,7 +367,7 @@ def main():
         os.path.join(ROOT, "gpurun_out")) else f"/tmp/ofast_clocks_{os.getpid()}.csv"
     smi = sample_clocks("", clock_file)
     time.sleep(0.3)
-    ms_b, stage_ms = timed(step_batched, args.steps, args.warmup, per_step_events=True)
+    ms_b, stage_ms = timed(step_batched, args.steps, args.warmup, per_step_events=True, nvtx_name="batched_timed")
     if smi is not None:
         smi.terminate()
         smi.wait()
@@ -374,7 +376,7 @@ def main():
     plain_frames = min(args.plain_frames, B)
     ms_p = float("nan")
     if not args.skip_plain:
-        ms_p, _ = timed(step_plain, plain_steps, 2)
+        ms_p, _ = timed(step_plain, plain_steps, 2, nvtx_name="plain_timed")
 
     # End to end through the public API with host buffers.
     host = [torch.from_numpy(frames_np[i % len(frames_np)]).pin_memory() for i in range(B)]
@@ -463,10 +465,12 @@ def main():
                 step_learned()
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("learned_timed")
             e0.record(stream)
             for _ in range(args.steps):
                 step_learned()
             e1.record(stream)
+            torch.cuda.nvtx.range_pop()
             e1.synchronize()
             ms_l = e0.elapsed_time(e1)
             st = ofg.of_detect_learned(batched.h, frames, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, net.net, thr, mc,
