@@ -201,6 +201,38 @@ def summarize_clocks(path: str):
             "samples": len(sm)}
 
 
+# ALU roofline of the FAST score.  The integer ALU pipe (min/max, logic,
+# permutes, shifts) takes 16 lanes per clock in each of the 4 sub-partitions
+# of an SM: 64 lane-ops per clock per SM.  Algorithmic work of the score: per
+# pixel pair, 2 x (16 + 16 + 8) three-input packed min/max operations of the
+# arc network plus 1 for the final score = 81, i.e. 40.5 per pixel of the
+# detect tiles.
+ALU_LANES_PER_SM_CLK = 64
+FAST_OPS_PER_PX = 40.5
+# DRAM bytes of one k_fast launch per frame, from the ncu capture summarised in
+# profiles/k_fast_1080p8.md (64-frame launch, scaled per frame), valid while
+# k_fast.cu has this SHA-1.
+FAST_TRAFFIC = {"sha1": "86b649ca306398cbec374800f8deab9b808dd87a", "bytes_per_frame": (454399232 + 351162624) / 64}
+
+
+def file_sha1(path):
+    import hashlib
+
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def detect_tile_pixels(lw, lh):
+    """Pixels the FAST launch covers per frame: 128 x 32 tiles over each detect region."""
+    tot = 0
+    for w, h in zip(lw, lh):
+        if w - 2 * BORDER <= 0 or h - 2 * BORDER <= 0:
+            continue
+        x0 = BORDER & ~15
+        tot += ((w - BORDER - x0 + 127) // 128) * ((h - 2 * BORDER + 31) // 32) * 128 * 32
+    return tot
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -221,6 +253,21 @@ def stage_bytes(levels_w, levels_h, cand_counts, kept_counts):
     sel = 12 * sum(cand_counts) + 12 * sum(kept_counts)   # read candidates, write kept
     orient = (709 + 81 + 12 + 64) * sum(kept_counts)      # disc + footprint + kept + record
     return [pyr, fast, nmsh, sel, orient]
+
+
+def reduce_max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings (replicas: the slowest rank sets the job time)."""
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replicas_value(frames_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job frames/s: every rank processed frames_per_rank frames within ms_max."""
+    return frames_per_rank * world / (ms_max / 1000.0)
 
 
 def run_reference(args, rank: int, world: int):
@@ -421,29 +468,40 @@ def main():
     per_frame = stage_bytes(lw, lh, cand, kept)
 
     # Max over ranks.
-    vals = torch.tensor([ms_b, ms_p, e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_b, ms_p, e2e_s = vals.tolist()
+    ms_b, ms_p, e2e_s = reduce_max_over_ranks([ms_b, ms_p, e2e_s], dist, device="cuda")
 
-    frames_total = B * args.steps * world
-    value = frames_total / (ms_b / 1000.0)
-    plain_fps = plain_frames * plain_steps * world / (ms_p / 1000.0)
-    e2e_fps = B * e2e_steps * world / e2e_s
+    value = replicas_value(B * args.steps, world, ms_b)
+    plain_fps = replicas_value(plain_frames * plain_steps, world, ms_p)
+    e2e_fps = replicas_value(B * e2e_steps, world, e2e_s * 1000.0)
     mpix = W_ * H_ / 1e6
 
     peak, peak_kind = measured_peaks()
     shares = [m / sum(stage_ms) for m in stage_ms]
     dom = int(np.argmax(stage_ms))
-    achieved = per_frame[dom] * B / (stage_ms[dom] / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "kernel": ofg.STAGE_NAMES[dom], "achieved": round(achieved, 1),
-                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None,
-                "stage_ms_per_step": {n: round(m, 4) for n, m in zip(ofg.STAGE_NAMES, stage_ms)},
-                "stage_share": {n: round(s, 4) for n, s in zip(ofg.STAGE_NAMES, shares)},
-                "stage_frac_of_hbm": {n: round(per_frame[i] * B / (stage_ms[i] / 1000.0) / 1e9 / peak, 4)
-                                      for i, n in enumerate(ofg.STAGE_NAMES)},
-                "algorithmic_bytes_per_frame": dict(zip(ofg.STAGE_NAMES, per_frame))}
+    stage_hbm = {n: round(per_frame[i] * B / (stage_ms[i] / 1000.0) / 1e9 / peak, 4)
+                 for i, n in enumerate(ofg.STAGE_NAMES)}
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = float(clocks.get("sm_max_mhz") or 2070.0)
+    if ofg.STAGE_NAMES[dom] == "fast":
+        # The dominant stage is integer-ALU bound: report it against the ALU pipe.
+        ops = FAST_OPS_PER_PX * detect_tile_pixels(lw, lh) * B
+        achieved = ops / (stage_ms[dom] / 1000.0) / 1e9
+        peak_alu = n_sms * ALU_LANES_PER_SM_CLK * sm_max * 1e6 / 1e9
+        ok = file_sha1(os.path.join(ROOT, "paper_2506_07164_gb300", "csrc", "k_fast.cu")) == FAST_TRAFFIC["sha1"]
+        roofline = {"bound": "alu", "kernel": "k_fast", "achieved": round(achieved, 1), "peak": round(peak_alu, 1),
+                    "peak_kind": f"derived: {n_sms} SMs x {ALU_LANES_PER_SM_CLK} ALU lanes/clk x {sm_max:.0f} MHz",
+                    "unit": "Gop/s", "frac": round(achieved / peak_alu, 4),
+                    "traffic": round(FAST_TRAFFIC["bytes_per_frame"] * B) if ok else None,
+                    "algorithmic_bytes": per_frame[1] * B,
+                    "hbm_frac_of_measured": stage_hbm["fast"], "hbm_peak_gbs": peak}
+    else:
+        achieved = per_frame[dom] * B / (stage_ms[dom] / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "kernel": ofg.STAGE_NAMES[dom], "achieved": round(achieved, 1), "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None}
+    roofline.update({"stage_ms_per_step": {n: round(m, 4) for n, m in zip(ofg.STAGE_NAMES, stage_ms)},
+                     "stage_share": {n: round(x, 4) for n, x in zip(ofg.STAGE_NAMES, shares)},
+                     "stage_frac_of_hbm": stage_hbm,
+                     "algorithmic_bytes_per_frame": dict(zip(ofg.STAGE_NAMES, per_frame))})
 
     # Learned tile proposal on the same batch: committed network and threshold.
     learned_out = None
