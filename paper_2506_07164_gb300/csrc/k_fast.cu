@@ -130,6 +130,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     auto issue = [&](int t, int b) {
         const TileInfo ti = tile_info(imgs, list, prefix, n_list, t, border);
         tinfo[b] = ti;
+        tensormap_acquire(maps + ti.img);
         mbar_arrive_expect_tx(&mbar[b], FAST_BOX);
         tma_load_2d(sbuf + b * FAST_BUF, maps + ti.img, ti.x0 - HALO_X, ti.y0 - 4, &mbar[b]);
     };

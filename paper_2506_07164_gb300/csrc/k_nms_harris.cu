@@ -110,6 +110,8 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int tt = t - __ldg(prefix + j);
         const int x0 = I.tile_x0 + (tt % I.tiles_x) * TILE_W, y0 = border + (tt / I.tiles_x) * TILE_H;
         tinfo[b] = NmsTile{ii, x0, y0};
+        tensormap_acquire(score_maps + ii);
+        tensormap_acquire(img_maps + ii);
         mbar_arrive_expect_tx(&mbar[b], S_BOX + I_BOX);
         tma_load_2d(sbuf + b * S_BUF, score_maps + ii, x0 - HALO_X, y0 - 1, &mbar[b]);
         tma_load_2d(ibuf + b * I_BUF, img_maps + ii, x0 - HALO_X, y0 - 4, &mbar[b]);

@@ -40,6 +40,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+// Tensor maps live in global memory and the host rewrites some of them
+// between launches (a level-0 map follows the caller's frame pointer).  The
+// TMA unit may hold a cached copy of a descriptor, so the issuing thread
+// acquires the map's current contents before each use.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 // 2-D tiled load of the box at (x, y) (x in elements, a multiple of 16 bytes).
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* bar) {

@@ -172,13 +172,26 @@ def test_other_scales_k_and_borders():
 
 
 def test_rebinding_new_pointers():
+    """Same shape, new frame pointers every call: level-0 tensor maps are
+    rewritten in place between launches and must never be read stale."""
     det = ofg.Detector(640, 480, max_levels=3, max_features=400)
     a = synth.scene(640, 480, 41)
     b = synth.scene(640, 480, 42)
+    ra = oracle.detect(a, levels=3, fast_t=20, n_features=400)
+    rb = oracle.detect(b, levels=3, fast_t=20, n_features=400)
     ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
-    for img, t in [(a, ta), (b, tb), (a, ta), (b, tb.clone())]:
-        kp = det.detect(t, levels=3, fast_t=20, n_features=400)
-        compare_keypoints(kp, oracle.detect(img, levels=3, fast_t=20, n_features=400))
+    for k in range(8):
+        img, t, ref = [(a, ta, ra), (b, tb, rb), (b, tb.clone(), rb), (a, ta, ra)][k % 4]
+        compare_keypoints(det.detect(t, levels=3, fast_t=20, n_features=400), ref)
+    det.close()
+    # Batched: swap the frame order between calls.
+    det = ofg.Detector(640, 480, max_levels=3, max_features=400, max_batch=2)
+    for k in range(6):
+        order = [(ta, ra), (tb, rb)] if k % 2 == 0 else [(tb, rb), (ta, ra)]
+        det.detect_batch([t for t, _ in order], levels=3, fast_t=20, n_features=400)
+        torch.cuda.synchronize()
+        for got, (_, ref) in zip(det.batch_results(2, 400), order):
+            compare_keypoints(got, ref)
     det.close()
 
 
