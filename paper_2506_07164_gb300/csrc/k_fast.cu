@@ -109,7 +109,7 @@ constexpr int FAST_BUF = (FAST_BOX + 127) / 128 * 128;  // buffer stride in shar
 // Persistent: each block walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // Thread 0 fetches the next tile by TMA into the other buffer while the
 // block scores the current one.
-__global__ void __launch_bounds__(DET_THREADS)
+__global__ void __launch_bounds__(DET_THREADS, 3)
 k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
        const int32_t* __restrict__ prefix, int n_list, int n_tiles, const CUtensorMap* __restrict__ maps,
        const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, int order) {
