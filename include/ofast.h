@@ -81,6 +81,7 @@ typedef struct of_tuning {
     int32_t nms_blocks_per_sm;    /* persistent NMS + Harris grid = SMs x this */
     int32_t fast_order;           /* tile walk: 0 round-robin, 1 contiguous chunks */
     int32_t nms_order;
+    int32_t resize_tma;           /* 1: persistent TMA resize on the levels whose source box fits */
     int32_t candidates_tried;     /* configurations timed */
     float resize_ms, fast_ms, nms_ms;  /* best measured time of each tuned stage (all levels) */
 } of_tuning;
@@ -159,7 +160,8 @@ int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int6
                    int32_t* dims);
 
 /* Autotuner (batched path): for this batch shape, time each candidate
- * launch configuration -- pyramid tile height, persistent grid size and tile
+ * launch configuration -- pyramid kernel (staged tiles of 32 or 64 rows, or
+ * the persistent TMA kernel), persistent grid size and tile
  * order of the FAST and NMS kernels -- with CUDA events on these frames
  * (reps timed repetitions each, 1..100), keep the fastest per stage for every
  * later call with the same shape, and run the batch once with it.  Arguments
@@ -169,6 +171,17 @@ int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int6
 int of_autotune(of_handle* h, const of_frame* frames, int n_frames, int levels, float scale,
                 int fast_t, float harris_k, int n_features, of_keypoint* out_kpts,
                 int32_t* out_counts, int reps, of_tuning* result);
+
+/* Fix the launch configuration of a batch shape (for instance one saved from
+ * an earlier of_autotune) instead of searching: the shape's plan is built if
+ * needed and its graphs re-captured with *tuning [host].  Fields checked:
+ * resize_tile_h 32 or 64, resize_tma 0 or 1, fast/nms_blocks_per_sm in
+ * 1..the kernel's occupancy, fast/nms_order 0 or 1 (else OF_ERR_ARG); the
+ * remaining fields are ignored.  Launches nothing.  Arguments as
+ * of_detect_batch.  No paper counterpart. */
+int of_set_tuning(of_handle* h, const of_frame* frames, int n_frames, int levels, float scale,
+                  int fast_t, float harris_k, int n_features, of_keypoint* out_kpts,
+                  int32_t* out_counts, const of_tuning* tuning);
 
 /* Wait for the handle's queued work and report device-side failures: returns
  * OF_ERR_TIMEOUT when a bounded device wait (a tile load that never arrived)

@@ -22,7 +22,7 @@ from .build import LIB, build  # noqa: F401
 
 __all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspect", "of_plan_levels",
            "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc", "of_sync",
-           "of_test_timeout", "OF_ERR_TIMEOUT", "of_autotune", "OfTuning", "of_batch_bytes",
+           "of_test_timeout", "OF_ERR_TIMEOUT", "of_autotune", "of_set_tuning", "OfTuning", "of_batch_bytes",
            "of_server_create", "of_server_destroy", "of_server_submit", "of_server_poll", "of_server_stats",
            "OfServerParams", "OfServerResult", "of_tcnn_create", "of_tcnn_destroy", "of_tcnn_num_params",
            "of_tcnn_set_params", "of_tcnn_get_params", "of_tcnn_forward", "of_tcnn_loss_grad", "of_tcnn_adam",
@@ -52,7 +52,7 @@ class OfParams(C.Structure):
 class OfTuning(C.Structure):
     _fields_ = [("resize_tile_h", C.c_int32), ("fast_blocks_per_sm", C.c_int32),
                 ("nms_blocks_per_sm", C.c_int32), ("fast_order", C.c_int32), ("nms_order", C.c_int32),
-                ("candidates_tried", C.c_int32), ("resize_ms", C.c_float), ("fast_ms", C.c_float),
+                ("resize_tma", C.c_int32), ("candidates_tried", C.c_int32), ("resize_ms", C.c_float), ("fast_ms", C.c_float),
                 ("nms_ms", C.c_float)]
 
     def as_dict(self):
@@ -139,6 +139,9 @@ def load(path: str | None = None):
     L.of_autotune.argtypes = [C.c_void_p, C.POINTER(OfFrame), C.c_int, C.c_int, C.c_float, C.c_int, C.c_float,
                               C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(OfTuning)]
     L.of_autotune.restype = C.c_int
+    L.of_set_tuning.argtypes = [C.c_void_p, C.POINTER(OfFrame), C.c_int, C.c_int, C.c_float, C.c_int, C.c_float,
+                                C.c_int, C.c_void_p, C.c_void_p, C.POINTER(OfTuning)]
+    L.of_set_tuning.restype = C.c_int
     L.of_server_create.argtypes = [C.POINTER(OfServerParams)]
     L.of_server_create.restype = C.c_void_p
     L.of_server_destroy.argtypes = [C.c_void_p]
@@ -286,6 +289,16 @@ def of_autotune(h: int, frames, levels: int, scale: float, fast_t: int, harris_k
     _check(load().of_autotune(h, arr, len(frames), levels, scale, fast_t, harris_k, n_features, _ptr(out_kpts),
                               _ptr(out_counts), reps, C.byref(t)))
     return t
+
+
+def of_set_tuning(h: int, frames, levels: int, scale: float, fast_t: int, harris_k: float, n_features: int,
+                  out_kpts, out_counts, tuning: OfTuning) -> None:
+    """Fix the launch configuration of this batch shape (see include/ofast.h)."""
+    arr = (OfFrame * len(frames))()
+    for i, (img, w, hh, pitch) in enumerate(frames):
+        arr[i] = OfFrame(_ptr(img), w, hh, pitch)
+    _check(load().of_set_tuning(h, arr, len(frames), levels, scale, fast_t, harris_k, n_features, _ptr(out_kpts),
+                                _ptr(out_counts), C.byref(tuning)))
 
 
 def of_batch_bytes(params: OfParams, sizes, levels: int, scale: float, n_features: int) -> int:
@@ -490,6 +503,11 @@ class Detector:
         """Tune this batch shape (a list of 2-D uint8 CUDA tensors); returns an OfTuning."""
         frames = [(im, im.shape[1], im.shape[0], im.stride(0)) for im in imgs]
         return of_autotune(self.h, frames, levels, scale, fast_t, harris_k, n_features, self.out, self.counts, reps)
+
+    def set_tuning(self, imgs, tuning: OfTuning, levels=8, scale=1.2, fast_t=20, harris_k=0.04, n_features=1000):
+        """Fix the launch configuration of this batch shape (a list of 2-D uint8 CUDA tensors)."""
+        frames = [(im, im.shape[1], im.shape[0], im.stride(0)) for im in imgs]
+        of_set_tuning(self.h, frames, levels, scale, fast_t, harris_k, n_features, self.out, self.counts, tuning)
 
     def batch_results(self, n_frames: int, n_features: int):
         """Per-frame numpy keypoints of the last batch (synchronises)."""

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "of_internal.h"
+#include "of_tma.cuh"
 
 namespace ofk {
 
@@ -142,6 +143,174 @@ void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, i
         k_resize<32><<<n_tiles, RS_THREADS, 0, (cudaStream_t)stream>>>(jobs, tile_prefix, n_jobs);
     else
         k_resize<64><<<n_tiles, RS_THREADS, 0, (cudaStream_t)stream>>>(jobs, tile_prefix, n_jobs);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent TMA resize, separable and exact.
+//
+// The bilinear value above factors into a horizontal and a vertical step,
+// both exact in unsigned 32-bit arithmetic when every weight is doubled:
+//   h(r, x) = (4096 - 2ax) S[r][x0] + 2ax S[r][x0 + 1]           (< 2^20)
+//   v       = (4096 - 2ay) h(y0, x) + 2ay h(y0 + 1, x) + 2^23    (< 2^32)
+//   out     = v >> 24 = ((sum of the original products) + 2^21) >> 22.
+// h is one __dp2a_lo (two 16 x 8-bit products) on the byte pair picked by one
+// __byte_perm; out is byte 3 of v, so four outputs pack with three byte
+// permutes.  Where a source index is clamped (x0 = w - 1, y0 = h - 1) the
+// tables give that sample's partner weight 0, so the zero fill of the TMA
+// box past the image edge never contributes.
+//
+// Each block walks 128 x 64 output tiles (all frames of one level) and
+// fetches the next tile's source window by TMA into the other buffer while
+// it filters the current one.  Warp w owns output rows 8w .. 8w + 7; each
+// lane owns 4 consecutive output columns and keeps the horizontal values of
+// the two source rows under the current output row in registers, computing
+// each source row once as the warp moves down.
+
+struct RsTile {
+    int32_t job, x0, y0, sx0, sy0;
+};
+
+// Horizontal pass of one staged source row for a lane's 4 columns.
+__device__ __forceinline__ void hrow(const uint8_t* __restrict__ row, int wa, int wb, const uint32_t (&sel)[4],
+                                     const uint32_t (&wgt)[4], uint32_t (&h)[4]) {
+    const uint32_t* rp = reinterpret_cast<const uint32_t*>(row);
+    const uint32_t a0 = rp[wa], a1 = rp[wa + 1], b0 = rp[wb], b1 = rp[wb + 1];
+    h[0] = __dp2a_lo(wgt[0], __byte_perm(a0, a1, sel[0]), 0u);
+    h[1] = __dp2a_lo(wgt[1], __byte_perm(a0, a1, sel[1]), 0u);
+    h[2] = __dp2a_lo(wgt[2], __byte_perm(b0, b1, sel[2]), 0u);
+    h[3] = __dp2a_lo(wgt[3], __byte_perm(b0, b1, sel[3]), 0u);
+}
+
+__global__ void __launch_bounds__(RT_THREADS)
+k_resize_tma(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix, int n_jobs, int n_tiles,
+             const CUtensorMap* __restrict__ maps, const Call* __restrict__ call, int buf_bytes) {
+    extern __shared__ __align__(128) uint8_t rdyn[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ RsTile tinfo[2];
+    // Two buffers of buf_bytes (a multiple of 128) from a 128-byte boundary;
+    // the launch reserves 128 bytes of slack for the rounding.
+    uint8_t* rbuf = rdyn + ((128u - (smem_u32(rdyn) & 127u)) & 127u);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int b) {
+        const int j = find_job(prefix, n_jobs, t);
+        const Resize& J = jobs[j];
+        const int tt = t - __ldg(prefix + j);
+        const int X0 = (tt % J.tiles_x) * RS_TILE_W, Y0 = (tt / J.tiles_x) * RT_TILE_H;
+        const int sx0 = (__ldg(J.xtab + X0) >> 12) & ~15;
+        const int sy0 = __ldg(J.ytab + Y0) >> 12;
+        tinfo[b] = RsTile{j, X0, Y0, sx0, sy0};
+        tensormap_acquire(maps + j);
+        mbar_arrive_expect_tx(&mbar[b], (uint32_t)(J.box_w * J.box_h));
+        tma_load_2d(rbuf + b * buf_bytes, maps + j, sx0, sy0, &mbar[b]);
+    };
+    const int g = gridDim.x;
+    if (tid == 0 && (int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
+
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int it = 0;; ++it) {
+        const int t = blockIdx.x + it * g;
+        if (t >= n_tiles) break;
+        const int tn = t + g;
+        const int b = it & 1;
+        if (tid == 0 && tn < n_tiles) {
+            fence_proxy_async_smem();
+            issue(tn, b ^ 1);
+        }
+        const bool ok = mbar_wait(&mbar[b], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(call->status, OF_DEV_TIMEOUT);
+                mbar_wait(&mbar[b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (tn < n_tiles) mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+            }
+            return;
+        }
+        const RsTile ti = tinfo[b];
+        const Resize& J = jobs[ti.job];
+        const uint8_t* s = rbuf + b * buf_bytes;
+        const int bw = J.box_w;
+        const int nx = min(RS_TILE_W, J.dw - ti.x0), ny = min(RT_TILE_H, J.dh - ti.y0);
+        const int lx = 4 * lane;
+        if (lx < nx) {
+            const int n = min(4, nx - lx);
+            int xo[4];
+            uint32_t wgt[4], sel[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int e = __ldg(J.xtab + ti.x0 + lx + min(i, n - 1));
+                xo[i] = (e >> 12) - ti.sx0;  // byte offset of x0 in the staged row
+                const uint32_t a2 = 2u * (uint32_t)(e & 4095);
+                wgt[i] = (4096u - a2) | (a2 << 16);
+            }
+            // Columns 0-1 read the word pair at wa, columns 2-3 the pair at wb;
+            // consecutive x0 differ by at most 3, so each byte pair lies in its 8 bytes.
+            const int wa = xo[0] >> 2, wb = xo[2] >> 2;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t o = (uint32_t)(xo[i] - 4 * (i < 2 ? wa : wb));
+                sel[i] = o | ((o + 1u) << 4);
+            }
+            uint8_t* d = J.dst + (size_t)ti.y0 * J.dpitch + ti.x0 + lx;
+            uint32_t ha[4], hb[4];
+            int cur = -4;
+            const int ly_end = min(8 * warp + 8, ny);
+            for (int ly = 8 * warp; ly < ly_end; ++ly) {
+                const int e = __ldg(J.ytab + ti.y0 + ly);
+                const int r0 = (e >> 12) - ti.sy0;
+                const uint32_t a2 = 2u * (uint32_t)(e & 4095);
+                if (r0 == cur + 1) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) ha[i] = hb[i];
+                    hrow(s + (r0 + 1) * bw, wa, wb, sel, wgt, hb);
+                } else if (r0 != cur) {
+                    hrow(s + r0 * bw, wa, wb, sel, wgt, ha);
+                    hrow(s + (r0 + 1) * bw, wa, wb, sel, wgt, hb);
+                }
+                cur = r0;
+                uint32_t v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = (4096u - a2) * ha[i] + a2 * hb[i] + (1u << 23);
+                const uint32_t packed =
+                    __byte_perm(__byte_perm(v[0], v[1], 0x0073), __byte_perm(v[2], v[3], 0x0073), 0x5410);
+                uint8_t* dr = d + (size_t)ly * J.dpitch;
+                if (n == 4) {
+                    *reinterpret_cast<uint32_t*>(dr) = packed;  // x0 + lx is a multiple of 4, dpitch of 16
+                } else {
+                    for (int i = 0; i < n; ++i) dr[i] = (uint8_t)(packed >> (8 * i));
+                }
+            }
+        }
+        __syncthreads();  // buffer b is free for the tile after next
+    }
+}
+
+void launch_resize_tma(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
+                       const CUtensorMap* maps, const Call* call, int buf_bytes, int grid, void* stream) {
+    if (n_tiles <= 0) return;
+    grid = grid < n_tiles ? grid : n_tiles;
+    k_resize_tma<<<grid, RT_THREADS, 2 * buf_bytes + 128, (cudaStream_t)stream>>>(jobs, tile_prefix, n_jobs,
+                                                                                   n_tiles, maps, call, buf_bytes);
+}
+
+// The kernel's dynamic shared-memory limit is raised once to the largest
+// size any plan may use (two buffers of RT_MAX_BUF), so graphs captured for
+// different plans never depend on which plan set it last.
+int resize_tma_blocks_per_sm(int buf_bytes) {
+    if (buf_bytes <= 0 || buf_bytes > RT_MAX_BUF) return 0;
+    if (cudaFuncSetAttribute(k_resize_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * RT_MAX_BUF + 128) !=
+        cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_resize_tma, RT_THREADS, 2 * buf_bytes + 128) !=
+        cudaSuccess)
+        return 0;
+    return n;
 }
 
 }  // namespace ofk

@@ -212,12 +212,14 @@ struct Plan {
     std::vector<int> rsp_begin[2];  // prefix array offset of level l, per resize tile height
     std::vector<int> rs_tiles[2];   // tiles of level l, per resize tile height
     std::vector<int32_t> rs_prefix, det_list, det_prefix, tables;
+    std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
+    std::vector<int> rt_bps;        // TMA resize resident blocks per SM of level l
     int det_tiles = 0, max_quota = 0, total_slots = 0, n_img = 0;
     Call h_call{};
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_rsp = 0, off_dl = 0, off_dp = 0, off_tab = 0;
     size_t off_maps = 0;
-    std::vector<CUtensorMap> h_maps;  // [image maps | score maps], n_img each
+    std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
     bool tuned = false;
     // Learned path: proposal tiles per listed image, device buffers
@@ -309,10 +311,17 @@ void enqueue_stages(of_handle* H, Plan* P, int first, int last, cudaStream_t st)
                 cudaMemsetAsync(H->arena, 0, P->lay.zero_end, st);
                 for (int l = 1; l < nl; ++l) {
                     const int nj = P->rs_begin[l + 1] - P->rs_begin[l];
-                    const int v = P->tun.resize_tile_h == RS_TILE_HS[0] ? 0 : 1;
-                    if (nj > 0)
+                    if (nj <= 0) continue;
+                    if (P->tun.resize_tma && P->rt_buf[l] > 0) {
+                        static_assert(RS_TILE_HS[1] == RT_TILE_H, "TMA resize uses the 64-row tile prefix");
+                        launch_resize_tma(P->d_rs() + P->rs_begin[l], P->d_rsp() + P->rsp_begin[1][l], nj,
+                                          P->rs_tiles[1][l], P->d_maps() + 2 * P->n_img + P->rs_begin[l],
+                                          P->d_call(), P->rt_buf[l], H->n_sms * P->rt_bps[l], st);
+                    } else {
+                        const int v = P->tun.resize_tile_h == RS_TILE_HS[0] ? 0 : 1;
                         launch_resize(P->d_rs() + P->rs_begin[l], P->d_rsp() + P->rsp_begin[v][l], nj,
                                       P->rs_tiles[v][l], RS_TILE_HS[v], st);
+                    }
                 }
                 break;
             case 1:
@@ -478,6 +487,44 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
         }
     }
     P->rs_begin[nl] = (int)P->h_rs.size();
+    // Source boxes of the persistent TMA resize; a level uses it when every
+    // job's box fits (<= 256 x 256) and consecutive x0 differ by at most 3.
+    P->rt_buf.assign(nl + 1, 0);
+    P->rt_bps.assign(nl + 1, 0);
+    for (int l = 1; l < nl; ++l) {
+        bool ok = P->rs_begin[l + 1] > P->rs_begin[l];
+        int buf = 0;
+        for (int i = P->rs_begin[l]; i < P->rs_begin[l + 1]; ++i) {
+            Resize& R = P->h_rs[i];
+            const int32_t* xt = P->tables.data() + tab_idx[i].first;
+            const int32_t* yt = P->tables.data() + tab_idx[i].second;
+            int bw = 0, bh = 0, step = 0;
+            for (int X0 = 0; X0 < R.dw; X0 += RS_TILE_W) {
+                const int last = std::min(X0 + RS_TILE_W, R.dw) - 1;
+                bw = std::max(bw, (xt[last] >> 12) + 2 - ((xt[X0] >> 12) & ~15));
+            }
+            for (int Y0 = 0; Y0 < R.dh; Y0 += RT_TILE_H) {
+                const int last = std::min(Y0 + RT_TILE_H, R.dh) - 1;
+                bh = std::max(bh, (yt[last] >> 12) + 2 - (yt[Y0] >> 12));
+            }
+            for (int d = 1; d < R.dw; ++d) step = std::max(step, (xt[d] >> 12) - (xt[d - 1] >> 12));
+            bw = (bw + 15) & ~15;
+            if (bw <= 256 && bh <= 256 && step <= 3) {
+                R.box_w = bw;
+                R.box_h = bh;
+                buf = std::max(buf, (bw * bh + 16 + 127) & ~127);  // +16: a lane's word pair may end past the box
+            } else {
+                ok = false;
+            }
+        }
+        if (ok && buf <= RT_MAX_BUF) {
+            const int bps = resize_tma_blocks_per_sm(buf);
+            if (bps > 0) {
+                P->rt_buf[l] = buf;
+                P->rt_bps[l] = bps;
+            }
+        }
+    }
     for (int i = 0; i < P->n_img; ++i) {
         const Img& I = P->h_img[i];
         if (I.tiles_x > 0) {
@@ -503,18 +550,29 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     C.total_slots = P->total_slots;
     C.status = H->d_counts + 4;
     P->tun.resize_tile_h = RS_TILE_HS[1];
+    P->tun.resize_tma = 1;
     P->tun.fast_blocks_per_sm = fast_blocks_per_sm();
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm();
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
 
-    // Tensor maps: image boxes for FAST and NMS, score boxes for NMS.
-    P->h_maps.assign(2 * P->n_img, CUtensorMap{});
+    // Tensor maps: image boxes for FAST and NMS, score boxes for NMS, then
+    // the source box of each resize job (TMA resize).
+    P->h_maps.assign(2 * P->n_img + P->h_rs.size(), CUtensorMap{});
     for (int i = 0; i < P->n_img; ++i) {
         const Img& I = P->h_img[i];
         int rc = encode_u8(&P->h_maps[i], I.img, I.w, I.h, I.pitch, SROW, IMG_BOX_ROWS);
         if (rc == OF_OK && I.score)
             rc = encode_u8(&P->h_maps[P->n_img + i], I.score, I.w, I.h, I.spitch, SROW, SCORE_BOX_ROWS);
+        if (rc != OF_OK) {
+            free_plan(P);
+            return rc;
+        }
+    }
+    for (size_t i = 0; i < P->h_rs.size(); ++i) {
+        const Resize& R = P->h_rs[i];
+        if (R.box_w == 0) continue;
+        const int rc = encode_u8(&P->h_maps[2 * P->n_img + i], R.src, R.sw, R.sh, R.spitch, R.box_w, R.box_h);
         if (rc != OF_OK) {
             free_plan(P);
             return rc;
@@ -661,6 +719,11 @@ int bind_plan(of_handle* H, Plan* P, const of_frame* frames, of_keypoint* out, i
             Resize& R = P->h_rs[i];
             for (int f = 0; f < nf; ++f)
                 if (R.dst == P->h_img[f * nl + 1].img) R.src = P->h_img[f * nl].img;
+            if (R.box_w > 0) {
+                const int rc = encode_u8(&P->h_maps[2 * P->n_img + i], R.src, R.sw, R.sh, R.spitch, R.box_w,
+                                         R.box_h);
+                if (rc != OF_OK) return rc;
+            }
         }
     }
     P->h_call.out = out;
@@ -779,15 +842,19 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     int rc = OF_OK;
     enqueue_stages(H, P, 0, kStages, st);  // every buffer populated once
     // Pyramid (idempotent).
+    // Candidates: the staged kernel with 32- or 64-row tiles, then the
+    // persistent TMA kernel (on the levels it covers; staged 64 elsewhere).
     float best = 1e30f;
-    int best_h = P->tun.resize_tile_h;
-    for (int v = 0; v < 2 && rc == OF_OK; ++v) {
-        P->tun.resize_tile_h = RS_TILE_HS[v];
+    int best_h = P->tun.resize_tile_h, best_tma = P->tun.resize_tma;
+    for (int c = 0; c < 3 && rc == OF_OK; ++c) {
+        P->tun.resize_tile_h = RS_TILE_HS[c == 0 ? 0 : 1];
+        P->tun.resize_tma = c == 2;
         float ms = 0.f;
         rc = timed([&] { enqueue_stages(H, P, 0, 1, st); }, &ms);
-        if (ms < best) best = ms, best_h = RS_TILE_HS[v];
+        if (ms < best) best = ms, best_h = P->tun.resize_tile_h, best_tma = P->tun.resize_tma;
     }
     P->tun.resize_tile_h = best_h;
+    P->tun.resize_tma = best_tma;
     P->tun.resize_ms = best;
     // FAST (idempotent: rewrites score maps, ORs the same cell flags).
     best = 1e30f;
@@ -998,6 +1065,34 @@ int of_autotune(of_handle* H, const of_frame* frames, int n_frames, int levels, 
     OF_CK(cudaGraphLaunch(P->exec, H->stream));  // leave this call's results in the outputs
     H->last = P;
     if (result) *result = P->tun;
+    return OF_OK;
+}
+
+int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels, float scale, int fast_t,
+                  float harris_k, int n_features, of_keypoint* out_kpts, int32_t* out_counts,
+                  const of_tuning* t) {
+    if (!H) return fail(OF_ERR_ARG, "null handle");
+    if (!t) return fail(OF_ERR_ARG, "null tuning");
+    DeviceGuard dg(H->device);
+    if ((t->resize_tile_h != RS_TILE_HS[0] && t->resize_tile_h != RS_TILE_HS[1]) ||
+        (t->resize_tma != 0 && t->resize_tma != 1) || t->fast_blocks_per_sm < 1 ||
+        t->fast_blocks_per_sm > fast_blocks_per_sm() || t->nms_blocks_per_sm < 1 ||
+        t->nms_blocks_per_sm > nms_blocks_per_sm() || (t->fast_order != 0 && t->fast_order != 1) ||
+        (t->nms_order != 0 && t->nms_order != 1))
+        return fail(OF_ERR_ARG, "tuning field out of range");
+    Plan* P = nullptr;
+    const int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
+                                 out_counts, &P);
+    if (rc != OF_OK) return rc;
+    P->tun.resize_tile_h = t->resize_tile_h;
+    P->tun.resize_tma = t->resize_tma;
+    P->tun.fast_blocks_per_sm = t->fast_blocks_per_sm;
+    P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
+    P->tun.fast_order = t->fast_order;
+    P->tun.nms_order = t->nms_order;
+    const cudaError_t e = instantiate_graphs(H, P);
+    if (e != cudaSuccess) return fail(OF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    P->tuned = true;
     return OF_OK;
 }
 

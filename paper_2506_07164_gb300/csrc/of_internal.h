@@ -65,7 +65,16 @@ struct Resize {
     int32_t sw, sh, spitch;
     int32_t dw, dh, dpitch;
     int32_t tiles_x, tiles_y;
+    // Source box of the persistent TMA kernel (box_w a multiple of 16, both
+    // <= 256): the largest source window of one RS_TILE_W x RT_TILE_H output
+    // tile.  0 when the job is not eligible (scale too large).
+    int32_t box_w, box_h;
 };
+
+// Persistent TMA resize: 128 x 64 output tiles, 8 warps of 8 output rows.
+constexpr int RT_TILE_H = 64;
+constexpr int RT_THREADS = 256;
+constexpr int RT_MAX_BUF = 100 * 1024;  // largest source buffer (two per block)
 
 // Per-call constants.
 struct Call {
@@ -95,6 +104,9 @@ __host__ __device__ __forceinline__ int tile_of(int order, int block, int grid, 
 namespace ofk {
 void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
                    int tile_h, void* stream);
+void launch_resize_tma(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
+                       const CUtensorMap* maps, const Call* call, int buf_bytes, int grid, void* stream);
+int resize_tma_blocks_per_sm(int buf_bytes);  // also raises the kernel's shared-memory limit
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                  int n_list, int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi,
                  int t_lo, int border, int cell, int grid, int order, void* stream);

@@ -82,3 +82,28 @@ def test_create_rejects_invalid_params(lib):
         ofg.of_create(max_w=100, max_h=100, border=10, orient_radius=15)
     with pytest.raises(ofg.OfError):
         ofg.of_create(max_w=100, max_h=100, harris_block=5)
+
+
+def _header_struct_fields(name):
+    text = open(os.path.join(ROOT, "include", "ofast.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), text, flags=re.S).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"^(?:const\s+)?[A-Za-z_]\w*\s*\**\s*(.*)$", decl, flags=re.S)
+        for part in m.group(1).split(","):
+            fields.append(part.strip().lstrip("*").strip())
+    return fields
+
+
+@pytest.mark.parametrize("c_name,py_name", [
+    ("of_params", "OfParams"), ("of_tuning", "OfTuning"), ("of_keypoint", "OfKeypoint"), ("of_frame", "OfFrame"),
+    ("of_server_params", "OfServerParams"), ("of_server_result", "OfServerResult"),
+    ("of_server_stats", "OfServerStats")])
+def test_binding_structs_mirror_the_header(c_name, py_name):
+    """The ctypes mirrors list the header's fields in the header's order."""
+    py = [f[0] for f in getattr(ofg, py_name)._fields_]
+    assert py == _header_struct_fields(c_name), c_name

@@ -277,3 +277,40 @@ def test_autotuner_choice_is_valid_and_results_unchanged():
         compare_keypoints(a, ora)
         compare_keypoints(b, ora)
     det.close()
+
+
+# ------------------------------------------------------------ pyramid kernels
+@pytest.mark.parametrize("scale", [1.05, 1.2, 1.5, 1.8, 2.0, 3.0])
+def test_every_resize_kernel_matches_oracle_levels(scale):
+    """Each pyramid kernel -- staged tiles of 32 or 64 rows, and the persistent
+    TMA kernel (scales up to ~1.85; above that its levels use the staged
+    kernel) -- gives the oracle's levels on ragged sizes, every level."""
+    sizes = [(1283, 723), (640, 480), (333, 197)]
+    imgs = [synth.scene(w, h, 400 + i, background="pink") for i, (w, h) in enumerate(sizes)]
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    levels = 6
+    det = ofg.Detector(1283, 723, max_levels=levels, max_features=300, max_batch=3, min_scale=1.05, fast_t_lo=7)
+    ora = [[oracle.pyramid_level(im, levels, scale, lv) for lv in range(levels)] for im in imgs]
+    for tile_h, tma in [(32, 0), (64, 0), (64, 1)]:
+        tun = ofg.OfTuning(resize_tile_h=tile_h, resize_tma=tma, fast_blocks_per_sm=1, nms_blocks_per_sm=1)
+        det.set_tuning(dev, tun, levels=levels, scale=scale, fast_t=20, n_features=300)
+        det.detect_batch(dev, levels=levels, scale=scale, fast_t=20, n_features=300)
+        torch.cuda.synchronize()
+        for f in range(len(imgs)):
+            for lv in range(1, levels):
+                g, _ = det.inspect(ofg.OF_BUF_LEVEL, f, lv)
+                np.testing.assert_array_equal(g.reshape(ora[f][lv].shape), ora[f][lv],
+                                              err_msg=f"tile_h {tile_h} tma {tma} frame {f} level {lv}")
+    det.close()
+
+
+def test_set_tuning_rejects_out_of_range_fields():
+    img = torch.from_numpy(synth.scene(320, 240, 3)).cuda()
+    det = ofg.Detector(320, 240, max_levels=2, max_features=50)
+    good = dict(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=1, nms_blocks_per_sm=1)
+    for bad in (dict(resize_tile_h=48), dict(resize_tma=2), dict(fast_blocks_per_sm=0),
+                dict(nms_blocks_per_sm=1000), dict(fast_order=2)):
+        with pytest.raises(ofg.OfError):
+            det.set_tuning([img], ofg.OfTuning(**{**good, **bad}), levels=2, n_features=50)
+    det.set_tuning([img], ofg.OfTuning(**good), levels=2, n_features=50)
+    det.close()
