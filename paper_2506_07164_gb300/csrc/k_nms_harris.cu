@@ -92,6 +92,8 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     __shared__ NmsTile tinfo[2];
     __shared__ uint32_t sflag[MAX_CELLS_LOCAL];
     __shared__ uint32_t fmask[LCH_MAX * WPR];
+    __shared__ int32_t rcell[S_ROWS];   // staged row -> its cell row's offset in fmask
+    __shared__ int32_t ccell[SROW];     // staged column -> local cell column, -1 outside lox..hix
     __shared__ uint32_t queue[QCAP];
     __shared__ int nq, qbase;
 
@@ -164,9 +166,18 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int lcw = (TILE_W + 2) / cell + 2;
         const int lch = (TILE_H + 2) / cell + 2;
         if (cells) {
+            // Cell flags of the tile, and the cell of each staged row and
+            // column (the only divisions by the cell size per tile).
             for (int i = tid; i < lcw * lch; i += blockDim.x) {
                 const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
                 sflag[i] = (cx < I.ncx && cy < I.ncy) ? I.cell[cy * I.ncx + cx] : 0u;
+            }
+            if (tid < S_ROWS) {
+                const int iy = Y0 - 1 + tid;
+                rcell[tid] = (iy >= ry0 && iy < ry1) ? ((iy - ry0) / cell - cy0) * WPR : 0;
+            } else if (tid < S_ROWS + SROW) {
+                const int c = tid - S_ROWS, xx = X0 - HALO_X + c;
+                ccell[c] = (xx >= lox && xx < hix) ? (xx - rx0) / cell - cx0 : -1;
             }
             __syncthreads();
             // fmask[cyl][k]: 0xFF for each byte of staged word k in a flagged cell of cell row cyl.
@@ -175,9 +186,8 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                 uint32_t m = 0u;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int xx = X0 - HALO_X + 4 * k + e;
-                    if (xx >= lox && xx < hix && sflag[cyl * lcw + (xx - rx0) / cell - cx0])
-                        m |= 0xFFu << (8 * e);
+                    const int cc = ccell[4 * k + e];
+                    if (cc >= 0 && sflag[cyl * lcw + cc]) m |= 0xFFu << (8 * e);
                 }
                 fmask[i] = m;
             }
@@ -200,8 +210,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             if (on) {
                 val = *wp & range_mask4(ix, lox, hix);
                 // Bytes below t_hi survive only when their cell has no strong pixel.
-                if (cells && val)
-                    val &= ~(fmask[((iy - ry0) / cell - cy0) * WPR + k] & bytes_lt(val, (uint32_t)t_hi));
+                if (cells && val) val &= ~(fmask[rcell[r] + k] & bytes_lt(val, (uint32_t)t_hi));
             }
             *wp = val;
         }
