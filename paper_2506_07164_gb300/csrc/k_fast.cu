@@ -48,35 +48,35 @@ __device__ __forceinline__ uint32_t pair_at(const uint32_t (&h)[6]) {
     else return __byte_perm(h[j], h[j + 1], 0x5432);  // high lane of h[j], low lane of h[j+1]
 }
 
-// Largest arc minimum and smallest arc maximum over the 16 nine-pixel arcs,
-// for the two pixels in the lanes of q[].
-__device__ __forceinline__ void arc_extrema(const uint32_t (&q)[16], uint32_t& amax, uint32_t& amin) {
-    uint32_t m3[16], M3[16];
+// One side of the score for the two pixels in the lanes of q[]: MIN = true
+// gives the largest arc minimum max_j min_{k<9} q[j+k], MIN = false the
+// smallest arc maximum.  Minima of 3 contiguous ring pixels, then of three
+// 3-runs 3 apart (9 pixels), then the extremum over the 16 starts.
+template <bool MIN>
+__device__ __forceinline__ uint32_t arc_side(const uint32_t (&q)[16]) {
+    auto f = [](uint32_t a, uint32_t b, uint32_t c) {
+        if constexpr (MIN) return __vimin3_u16x2(a, b, c);
+        else return __vimax3_u16x2(a, b, c);
+    };
+    auto g = [](uint32_t a, uint32_t b, uint32_t c) {
+        if constexpr (MIN) return __vimax3_u16x2(a, b, c);
+        else return __vimin3_u16x2(a, b, c);
+    };
+    uint32_t m3[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        m3[i] = __vimin3_u16x2(q[i], q[(i + 1) & 15], q[(i + 2) & 15]);
-        M3[i] = __vimax3_u16x2(q[i], q[(i + 1) & 15], q[(i + 2) & 15]);
-    }
-    uint32_t m9[16], M9[16];
+    for (int i = 0; i < 16; ++i) m3[i] = f(q[i], q[(i + 1) & 15], q[(i + 2) & 15]);
+    uint32_t m9[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        m9[i] = __vimin3_u16x2(m3[i], m3[(i + 3) & 15], m3[(i + 6) & 15]);
-        M9[i] = __vimax3_u16x2(M3[i], M3[(i + 3) & 15], M3[(i + 6) & 15]);
-    }
-    const uint32_t a0 = __vimax3_u16x2(m9[0], m9[1], m9[2]), a1 = __vimax3_u16x2(m9[3], m9[4], m9[5]);
-    const uint32_t a2 = __vimax3_u16x2(m9[6], m9[7], m9[8]), a3 = __vimax3_u16x2(m9[9], m9[10], m9[11]);
-    const uint32_t a4 = __vimax3_u16x2(m9[12], m9[13], m9[14]);
-    const uint32_t b0 = __vimin3_u16x2(M9[0], M9[1], M9[2]), b1 = __vimin3_u16x2(M9[3], M9[4], M9[5]);
-    const uint32_t b2 = __vimin3_u16x2(M9[6], M9[7], M9[8]), b3 = __vimin3_u16x2(M9[9], M9[10], M9[11]);
-    const uint32_t b4 = __vimin3_u16x2(M9[12], M9[13], M9[14]);
-    amax = __vimax3_u16x2(__vimax3_u16x2(a0, a1, a2), a3, __vimax3_u16x2(a4, m9[15], 0u));
-    amin = __vimin3_u16x2(__vimin3_u16x2(b0, b1, b2), b3, __vimin3_u16x2(b4, M9[15], 0xFFFFFFFFu));
+    for (int i = 0; i < 16; ++i) m9[i] = f(m3[i], m3[(i + 3) & 15], m3[(i + 6) & 15]);
+    const uint32_t a0 = g(m9[0], m9[1], m9[2]), a1 = g(m9[3], m9[4], m9[5]), a2 = g(m9[6], m9[7], m9[8]);
+    const uint32_t a3 = g(m9[9], m9[10], m9[11]), a4 = g(m9[12], m9[13], m9[14]);
+    return g(g(a0, a1, a2), a3, g(a4, m9[15], m9[15]));
 }
 
 // s(p) for the two pixels of a pair: lanes of max(amax - c, c - amin, 0).
 __device__ __forceinline__ uint32_t pair_score(const uint32_t (&q)[16], uint32_t c) {
-    uint32_t amax, amin;
-    arc_extrema(q, amax, amin);
+    const uint32_t amax = arc_side<true>(q);
+    const uint32_t amin = arc_side<false>(q);
     constexpr uint32_t B = 0x01000100u;  // +256 per lane keeps each difference positive
     return __vimax3_u16x2(amax + B - c, c + B - amin, B) - B;
 }
@@ -85,6 +85,18 @@ __device__ __forceinline__ uint32_t pair_score(const uint32_t (&q)[16], uint32_t
 __device__ __forceinline__ uint32_t lanes_ge(uint32_t v, uint32_t t) {
     const uint32_t d = v + (0x8000u - t) * 0x00010001u;
     return ((d >> 15) & 0x00010001u) * 0xFFFFu;
+}
+
+// Score of pixel pair E (pixels x+2E, x+2E+1) of an output row, clipped
+// below t_lo, from the pair words of staged rows y-3 .. y+3 (hw[0..6]).
+template <int E>
+__device__ __forceinline__ uint32_t ring_pair_score(const uint32_t (*hw)[6], uint32_t t_lo) {
+    uint32_t q[16];
+#define OF_LOAD_RING(i, dx, dy) q[i] = pair_at<(dx) + 2 * E>(hw[3 + (dy)]);
+    OF_RING(OF_LOAD_RING)
+#undef OF_LOAD_RING
+    const uint32_t se = pair_score(q, hw[3][2 + E]);
+    return se & lanes_ge(se, t_lo);
 }
 
 // Tile t of the launch: its image and origin.
@@ -178,10 +190,10 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int lcw = TILE_W / cell + 2;
         const int x = X0 + 4 * lane;
 
-        // Six pair words per staged row: rows y-3 .. y+RPT+2 (staged row 0 is Y0-4).
+        // Six pair words per staged row: rows y-3 .. y+RPT+2 (staged row 0 is
+        // Y0-4), each loaded just before the first output row that needs it.
         uint32_t hw[RPT + 6][6];
-#pragma unroll
-        for (int k = 0; k < RPT + 6; ++k) {
+        auto load_row = [&](int k) {
             const uint8_t* row = s + (ty * RPT + k + 1) * SROW + HALO_X + 4 * lane;
             const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
             const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
@@ -192,22 +204,18 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             hw[k][3] = __byte_perm(wc, 0u, 0x4342);
             hw[k][4] = __byte_perm(wp, 0u, 0x4140);
             hw[k][5] = __byte_perm(wp, 0u, 0x4342);
-        }
+        };
+#pragma unroll
+        for (int k = 0; k < 7; ++k) load_row(k);
         const uint32_t colmask = range_mask4(x, rx0, rx1) & lane_on;
 
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             const int y = Y0 + ty * RPT + r;
-            uint32_t q0[16], q1[16];
-#define OF_LOAD_RING(i, dx, dy)                        \
-    q0[i] = pair_at<(dx)>(hw[r + 3 + (dy)]);          \
-    q1[i] = pair_at<(dx) + 2>(hw[r + 3 + (dy)]);
-            OF_RING(OF_LOAD_RING)
-#undef OF_LOAD_RING
-            uint32_t s0 = pair_score(q0, hw[r + 3][2]);
-            uint32_t s1 = pair_score(q1, hw[r + 3][3]);
-            s0 &= lanes_ge(s0, (uint32_t)t_lo);
-            s1 &= lanes_ge(s1, (uint32_t)t_lo);
+            if (r > 0) load_row(r + 6);
+            // Pixel pairs (x, x+1) and (x+2, x+3), one after the other.
+            const uint32_t s0 = ring_pair_score<0>(hw + r, (uint32_t)t_lo);
+            const uint32_t s1 = ring_pair_score<1>(hw + r, (uint32_t)t_lo);
             const uint32_t m = (y < ry1) ? colmask : 0u;
             const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
             if (m != 0u) *reinterpret_cast<uint32_t*>(I.score + (size_t)y * I.spitch + x) = sc;
