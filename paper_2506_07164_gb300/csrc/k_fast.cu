@@ -208,6 +208,14 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
 #pragma unroll
         for (int k = 0; k < 7; ++k) load_row(k);
         const uint32_t colmask = range_mask4(x, rx0, rx1) & lane_on;
+        // Cells of this thread's 4 x RPT pixels (cell >= 8 > RPT, 4): at most
+        // two cell columns (the bytes in mask_a lie in the first) and two cell
+        // rows (the second from row y_next on); no division per pixel.
+        const int ca = (max(x, rx0) - rx0) / cell;
+        const uint32_t mask_a = range_mask4(x, 0, rx0 + (ca + 1) * cell);
+        const int cr = (Y0 + ty * RPT - border) / cell;
+        const int y_next = border + (cr + 1) * cell;
+        const int fbase = (cr - cy0) * lcw + (ca - cx0);
 
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
@@ -223,14 +231,9 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                 const uint32_t strong =
                     __byte_perm(lanes_ge(s0, (uint32_t)t_hi), lanes_ge(s1, (uint32_t)t_hi), 0x6420) & m;
                 if (strong) {
-                    const int cyl = (y - border) / cell - cy0;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if ((strong >> (8 * i)) & 1u) {
-                            const int cxl = (x + i - rx0) / cell - cx0;
-                            atomicOr(&sflag[cyl * lcw + cxl], 1u);
-                        }
-                    }
+                    const int f = fbase + (y >= y_next ? lcw : 0);
+                    if (strong & mask_a) atomicOr(&sflag[f], 1u);
+                    if (strong & ~mask_a) atomicOr(&sflag[f + 1], 1u);
                 }
             }
         }
