@@ -7,10 +7,11 @@
 // next buffer pair while the block works on the current one: the score tile
 // (160 x 34, +1 row/col halo) and the image tile (160 x 40, +4 halo).
 // 1. S(p) in place: s(p) when p is a candidate at its cell's threshold, else
-//    0; 0 outside the detect region.  A per-tile table gives, for each staged
-//    word and cell row, the bytes in cells whose threshold is t_hi.
+//    0; 0 outside the detect region.  Each thread keeps one staged word
+//    column, whose in-region bytes lie in at most two cells.
 // 2. NMS, two pixels per register in 16-bit lanes: p survives when S(p) > the
-//    three-input maximum of its 8 neighbours.  Survivors go to a queue.
+//    three-input maximum of its 8 neighbours.  Survivors go to a queue (one
+//    shared atomic per warp).
 // 3. Harris (Eqs. 2-4, Alg. 3): one thread per survivor slides down the 9 x 9
 //    footprint keeping three rows of the horizontal Sobel passes (difference
 //    [-1 0 1] and smoothing [1 2 1]) in registers -- the circular buffer of
@@ -27,12 +28,13 @@
 namespace ofk {
 
 constexpr int QCAP = TILE_W * TILE_H / 4;        // strict maxima are never adjacent
-constexpr int WPR = SROW / 4;                    // staged words per row
-constexpr int LCH_MAX = (TILE_H + 2) / 8 + 2;    // cell rows touched by a tile (cell >= 8)
 constexpr int S_ROWS = TILE_H + 2;
 constexpr int S_BOX = S_ROWS * SROW;             // 5440
 constexpr int I_BOX = IMG_BOX_ROWS * SROW;       // 6400
 constexpr int S_BUF = (S_BOX + 127) / 128 * 128;
+constexpr int S_W0 = HALO_X / 4 - 1;             // first staged word the 3x3 test reads (X0-4)
+constexpr int S_WORDS = TILE_W / 4 + 2;          // words X0-4 .. X0+TILE_W+3
+constexpr int S_GROUPS = DET_THREADS / S_WORDS;  // row groups of the S(p) pass
 constexpr int I_BUF = (I_BOX + 127) / 128 * 128;
 
 // 0xFF in each byte of v that is below t (t <= 255).
@@ -91,9 +93,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ NmsTile tinfo[2];
     __shared__ uint32_t sflag[MAX_CELLS_LOCAL];
-    __shared__ uint32_t fmask[LCH_MAX * WPR];
-    __shared__ int32_t rcell[S_ROWS];   // staged row -> its cell row's offset in fmask
-    __shared__ int32_t ccell[SROW];     // staged column -> local cell column, -1 outside lox..hix
+    __shared__ int32_t rcell[S_ROWS];   // staged row -> (local cell row) * lcw
     __shared__ uint32_t queue[QCAP];
     __shared__ int nq, qbase;
 
@@ -166,58 +166,68 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int lcw = (TILE_W + 2) / cell + 2;
         const int lch = (TILE_H + 2) / cell + 2;
         if (cells) {
-            // Cell flags of the tile, and the cell of each staged row and
-            // column (the only divisions by the cell size per tile).
+            // Cell flags of the tile, and the cell row of each staged row.
             for (int i = tid; i < lcw * lch; i += blockDim.x) {
                 const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
                 sflag[i] = (cx < I.ncx && cy < I.ncy) ? I.cell[cy * I.ncx + cx] : 0u;
             }
             if (tid < S_ROWS) {
                 const int iy = Y0 - 1 + tid;
-                rcell[tid] = (iy >= ry0 && iy < ry1) ? ((iy - ry0) / cell - cy0) * WPR : 0;
-            } else if (tid < S_ROWS + SROW) {
-                const int c = tid - S_ROWS, xx = X0 - HALO_X + c;
-                ccell[c] = (xx >= lox && xx < hix) ? (xx - rx0) / cell - cx0 : -1;
-            }
-            __syncthreads();
-            // fmask[cyl][k]: 0xFF for each byte of staged word k in a flagged cell of cell row cyl.
-            for (int i = tid; i < lch * WPR; i += blockDim.x) {
-                const int cyl = i / WPR, k = i - cyl * WPR;
-                uint32_t m = 0u;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int cc = ccell[4 * k + e];
-                    if (cc >= 0 && sflag[cyl * lcw + cc]) m |= 0xFFu << (8 * e);
-                }
-                fmask[i] = m;
+                rcell[tid] = (iy >= ry0 && iy < ry1) ? ((iy - ry0) / cell - cy0) * lcw : 0;
             }
             __syncthreads();
         }
 
-        // 1. S(p) in place for rows Y0-1 .. Y0+TILE_H.
-        for (int i = tid; i < S_ROWS * WPR; i += blockDim.x) {
-            const int r = i / WPR, k = i - r * WPR;
-            const int iy = Y0 - 1 + r, ix = X0 - HALO_X + 4 * k;
-            uint32_t* wp = reinterpret_cast<uint32_t*>(sS + r * SROW) + k;
-            uint32_t val = 0u;
-            bool on = iy >= ry0 && iy < ry1;
-            if (on && I.pmask) {
-                // Outside the proposed tiles S is 0 (each staged word lies in one proposal tile).
-                const int px = (ix - I.tile_x0) >> 5, py = (iy - ry0) >> 5;
-                on = ix >= I.tile_x0 && px < 4 * I.tiles_x && py < I.tiles_y &&
-                     I.pmask[(size_t)py * 4 * I.tiles_x + px] != 0;
+        // 1. S(p) in place for rows Y0-1 .. Y0+TILE_H, on the staged words the
+        //    3x3 test reads (X0-4 .. X0+TILE_W+3).  A thread keeps one word
+        //    column: its in-region byte mask and the (at most two) cells of its
+        //    bytes are fixed for the tile.
+        if (tid < S_WORDS * S_GROUPS) {
+            const int k = S_W0 + tid % S_WORDS, rg = tid / S_WORDS;
+            const int ix = X0 - HALO_X + 4 * k;
+            const uint32_t cmask = range_mask4(ix, lox, hix);
+            int fa = 0, fb = 0;
+            uint32_t ma = 0u, mb = 0u;
+            if (cells && cmask) {
+                const int ca = (max(ix, lox) - rx0) / cell, cb = (min(ix + 3, hix - 1) - rx0) / cell;
+                ma = cmask & range_mask4(ix, 0, rx0 + (ca + 1) * cell);
+                mb = cmask & ~ma;
+                fa = ca - cx0;
+                fb = cb - cx0;
             }
-            if (on) {
-                val = *wp & range_mask4(ix, lox, hix);
-                // Bytes below t_hi survive only when their cell has no strong pixel.
-                if (cells && val) val &= ~(fmask[rcell[r] + k] & bytes_lt(val, (uint32_t)t_hi));
+            int px = 0;
+            bool col_on = cmask != 0u;
+            if (I.pmask) {
+                px = (ix - I.tile_x0) >> 5;
+                col_on = col_on && ix >= I.tile_x0 && px < 4 * I.tiles_x;
             }
-            *wp = val;
+            for (int r = rg; r < S_ROWS; r += S_GROUPS) {
+                const int iy = Y0 - 1 + r;
+                uint32_t* wp = reinterpret_cast<uint32_t*>(sS + r * SROW) + k;
+                uint32_t val = 0u;
+                bool on = col_on && iy >= ry0 && iy < ry1;
+                if (on && I.pmask) {
+                    // Outside the proposed tiles S is 0 (each staged word lies in one proposal tile).
+                    const int py = (iy - ry0) >> 5;
+                    on = py < I.tiles_y && I.pmask[(size_t)py * 4 * I.tiles_x + px] != 0;
+                }
+                if (on) {
+                    val = *wp & cmask;
+                    // Bytes below t_hi survive only when their cell has no strong pixel.
+                    if (cells && val) {
+                        const int rc = rcell[r];
+                        const uint32_t fm = (sflag[rc + fa] ? ma : 0u) | (sflag[rc + fb] ? mb : 0u);
+                        val &= ~(fm & bytes_lt(val, (uint32_t)t_hi));
+                    }
+                }
+                *wp = val;
+            }
         }
         __syncthreads();
 
         // 2. Strict 3x3 maxima, two pixels per register.
         {
+            uint32_t smask = 0u;  // survivor bits: (2 * row + pair) * 2 + lane
             uint32_t hw[RPT + 2][6];
 #pragma unroll
             for (int k = 0; k < RPT + 2; ++k) {
@@ -245,16 +255,27 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                                                        __vimax3_u16x2(d[j], dp, dp));
                     // Lane bit 15 set when centre > neighbours (values <= 255).
                     const uint32_t keep = (c[j] + 0x7FFF7FFFu - nb) & 0x80008000u;
-                    if (keep) {
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            if ((keep >> (16 * e + 15)) & 1u) {
-                                const int slot = atomicAdd(&nq, 1);
-                                queue[slot] = ((uint32_t)(ty * RPT + r) << 16) | (uint32_t)(4 * lane + 2 * pr + e);
-                            }
-                        }
-                    }
+                    const int bit = 2 * (2 * r + pr);
+                    smask |= ((keep >> 15) & 1u) << bit | (keep >> 31) << (bit + 1);
                 }
+            }
+            // Queue the survivors: a warp scan of the per-thread counts and one
+            // shared atomic per warp.
+            const int mine = __popc(smask);
+            int incl = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            int wbase = 0;
+            if (lane == 31 && incl) wbase = atomicAdd(&nq, incl);
+            int slot = __shfl_sync(0xFFFFFFFFu, wbase, 31) + incl - mine;
+            while (smask) {
+                const int bit = __ffs(smask) - 1;
+                smask &= smask - 1u;
+                queue[slot++] = ((uint32_t)(ty * RPT + (bit >> 2)) << 16) |
+                                (uint32_t)(4 * lane + 2 * ((bit >> 1) & 1) + (bit & 1));
             }
         }
         __syncthreads();
