@@ -83,7 +83,7 @@ struct NmsTile {
     int32_t img, x0, y0;
 };
 
-__global__ void __launch_bounds__(DET_THREADS)
+__global__ void __launch_bounds__(DET_THREADS, 5)
 k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
              const int32_t* __restrict__ prefix, int n_list, int n_tiles,
              const CUtensorMap* __restrict__ img_maps, const CUtensorMap* __restrict__ score_maps,
