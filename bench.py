@@ -143,6 +143,71 @@ def serving_leg(pool, seconds: float, rate: float, seed: int = 0):
             "seconds": seconds}
 
 
+# The paper's variant pipelines (Table 2; Figs. 8-9 order them by runtime, slowest first).
+ABLATION_PIPELINES = [("Baseline_ORB", 0, 0), ("Binary_ORB", 1, 0), ("SM_ORB", 3, 0), ("Sep_ORB", 3, 1),
+                      ("Para-Sep_ORB", 3, 2), ("Semi-Sep_ORB", 3, 3)]
+ABLATION_FAST = [("Baseline(FAST)", 0), ("BinaryFAST", 1), ("SMFAST", 2), ("SM-BinaryFAST", 3)]
+ABLATION_SIZES = [(720, 540), (1080, 720), (1440, 1080), (1920, 1080)]
+
+
+def ablation_leg(pool, det, stream, reps: int = 20):
+    """Time each paper variant (FAST + Harris of every FAST point at t = 20, no NMS) on one synthetic scene of
+    each of the paper's image sizes, on 1 and 4 pyramid layers (the detector's own levels)."""
+    import torch
+
+    import paper_2506_07164_gb300 as ofg
+
+    imgs = pool.map(_gen_sized, [(w, h, 7000 + i) for i, (w, h) in enumerate(ABLATION_SIZES)])
+    out = {"unit": "ms per image (CUDA events, mean of %d calls after 3 warm-ups)" % reps, "fast_t": FAST_T,
+           "border": 19, "sizes": {}}
+    holds = []
+    for (w, h), img in zip(ABLATION_SIZES, imgs):
+        dev0 = torch.from_numpy(img).cuda()
+        det.detect_batch([dev0], levels=4, scale=SCALE, fast_t=FAST_T, n_features=NFEAT)
+        torch.cuda.synchronize()
+        levels = []
+        for lv in range(4):
+            a, dims = det.inspect(ofg.OF_BUF_LEVEL, 0, lv)
+            lw, lh = int(dims[0]), int(dims[1])
+            levels.append((torch.from_numpy(a.reshape(lh, lw).copy()).cuda(), lw, lh))
+        cap = w * h
+        pts = torch.empty(cap * 32, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+        def call(fv, hv, n_layers):
+            for t_img, lw, lh in levels[:n_layers]:
+                ofg.of_variant_detect(fv, hv, t_img, lw, lh, lw, FAST_T, 19, HARRIS_K, pts, cnt, cap, stream)
+
+        def time_it(fv, hv, n_layers):
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    call(fv, hv, n_layers)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    call(fv, hv, n_layers)
+                e1.record(stream)
+                e1.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        entry = {}
+        for n_layers in (1, 4):
+            pipes = {name: round(time_it(fv, hv, n_layers), 4) for name, fv, hv in ABLATION_PIPELINES}
+            fast = {name: round(time_it(fv, -1, n_layers), 4) for name, fv in ABLATION_FAST}
+            call(3, -1, 1)
+            torch.cuda.synchronize()
+            times = [pipes[name] for name, _, _ in ABLATION_PIPELINES]
+            order = all(a >= b for a, b in zip(times, times[1:]))
+            holds.append(order)
+            entry[f"layers{n_layers}"] = {"pipelines": pipes, "fast_only": fast,
+                                          "paper_order_holds": order}
+        entry["fast_points_layer0"] = int(cnt.item())
+        out["sizes"][f"{w}x{h}"] = entry
+    out["paper_order"] = " > ".join(name for name, _, _ in ABLATION_PIPELINES) + " (runtime, paper Figs. 8-9)"
+    out["paper_order_holds_everywhere"] = all(holds)
+    return out
+
+
 def make_frames(n: int, pool=None):
     seeds = list(range(n))
     if pool is not None:
@@ -323,6 +388,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=500.0, help="Poisson arrival rate, frames/s")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-buffer path (profiling)")
     ap.add_argument("--skip-learned", action="store_true", help="skip the learned tile-proposal leg")
+    ap.add_argument("--skip-ablation", action="store_true", help="skip the paper-variant ablation leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -557,6 +623,10 @@ def main():
                                   f"({meta['train_tiles']} tiles, {meta['steps']} Adam steps)"}
         net.close()
 
+    ablation = None
+    if not args.skip_ablation and rank == 0:
+        ablation = ablation_leg(pool, batched, stream)
+
     serving = None
     if args.serve_seconds > 0:
         serving = serving_leg(pool, args.serve_seconds, args.serve_rate)
@@ -586,6 +656,7 @@ def main():
         "autotune": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tuning.items()},
         "roofline": roofline,
         "learned": learned_out,
+        "ablation": ablation,
         "serving": serving,
         "cpu_baseline": cpu,
         "clocks": clocks,

@@ -351,6 +351,45 @@ int of_detect_learned(of_handle* h, const of_frame* frames, int n_frames, int le
 int of_extract_tiles(of_handle* h, int frame, int level, uint8_t* dst, int64_t cap_tiles,
                      int32_t* grid);
 
+/* ---- The paper's ablation variants (Table 2, Sec. 6.2) ------------------
+ * For measuring whether the paper's ordering of its FAST and Harris variants
+ * holds on GB300; not the detector's path.  One level, FAST points at
+ * threshold fast_t (Eq. 1) in the region border <= x < w - border (same for
+ * y), border >= 4, and for a Harris variant the exact Sobel sums over the
+ * 7 x 7 window (Eqs. 2-4) and key = kden (AB - C^2) - knum (A+B)^2 with
+ * harris_k = knum / kden as of_detect.  No NMS, no ranking.
+ *   fast_variant    OF_VAR_FAST_*: baseline (branchy run-length test, global
+ *                   loads), binary (Alg. 2 bit windows, global), sm, sm_binary
+ *                   (the same on a shared-memory tile)
+ *   harris_variant  OF_VAR_HARRIS_*: none, baseline (2-D Sobel, second launch,
+ *                   global loads; any FAST variant), sep, para_sep, semi_sep
+ *                   (fused after sm_binary FAST in one kernel, as the paper
+ *                   pairs them; fast_variant must be OF_VAR_FAST_SM_BINARY)
+ *   img [device]    uint8 image, w x h, pitch bytes per row
+ *   out_points [device] room for capacity records, in no particular order;
+ *                   points past capacity are counted but not written
+ *   out_count [device]  one int32, set to the number of points
+ *   stream          cudaStream_t (NULL = default stream); asynchronous
+ * Returns OF_OK or OF_ERR_ARG.  Allocates nothing. */
+typedef struct of_var_point {
+    int32_t x, y;
+    int32_t A, B, C;      /* exact window sums (0 without a Harris variant) */
+    int32_t reserved;
+    int64_t key;          /* exact Harris key (0 without a Harris variant) */
+} of_var_point;
+#define OF_VAR_FAST_BASELINE 0
+#define OF_VAR_FAST_BINARY 1
+#define OF_VAR_FAST_SM 2
+#define OF_VAR_FAST_SM_BINARY 3
+#define OF_VAR_HARRIS_NONE (-1)
+#define OF_VAR_HARRIS_BASELINE 0
+#define OF_VAR_HARRIS_SEP 1
+#define OF_VAR_HARRIS_PARA_SEP 2
+#define OF_VAR_HARRIS_SEMI_SEP 3
+int of_variant_detect(int fast_variant, int harris_variant, const uint8_t* img, int w, int h, int pitch,
+                      int fast_t, int border, float harris_k, of_var_point* out_points, int32_t* out_count,
+                      int64_t capacity, void* stream);
+
 /* Host-only: the pyramid plan the detector uses for a W x H frame (no GPU
  * needed).  ws, hs [host, levels ints] receive level sizes; quota [host,
  * levels ints] receives the per-level feature quota for n_features.

@@ -22,7 +22,8 @@ from .build import LIB, build  # noqa: F401
 
 __all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspect", "of_plan_levels",
            "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc", "of_sync",
-           "of_test_timeout", "OF_ERR_TIMEOUT", "of_autotune", "of_set_tuning", "OfTuning", "of_batch_bytes",
+           "of_test_timeout", "OF_ERR_TIMEOUT", "of_autotune", "of_variant_detect", "OfVarPoint",
+           "VAR_POINT_DTYPE", "of_set_tuning", "OfTuning", "of_batch_bytes",
            "of_server_create", "of_server_destroy", "of_server_submit", "of_server_poll", "of_server_stats",
            "OfServerParams", "OfServerResult", "of_tcnn_create", "of_tcnn_destroy", "of_tcnn_num_params",
            "of_tcnn_set_params", "of_tcnn_get_params", "of_tcnn_forward", "of_tcnn_loss_grad", "of_tcnn_adam",
@@ -93,6 +94,18 @@ class OfServerStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class OfVarPoint(C.Structure):
+    _fields_ = [("x", C.c_int32), ("y", C.c_int32), ("A", C.c_int32), ("B", C.c_int32), ("C", C.c_int32),
+                ("reserved", C.c_int32), ("key", C.c_int64)]
+
+
+VAR_POINT_DTYPE = np.dtype([("x", "i4"), ("y", "i4"), ("A", "i4"), ("B", "i4"), ("C", "i4"), ("reserved", "i4"),
+                            ("key", "i8")])
+assert VAR_POINT_DTYPE.itemsize == C.sizeof(OfVarPoint) == 32
+OF_VAR_FAST_BASELINE, OF_VAR_FAST_BINARY, OF_VAR_FAST_SM, OF_VAR_FAST_SM_BINARY = 0, 1, 2, 3
+OF_VAR_HARRIS_NONE, OF_VAR_HARRIS_BASELINE, OF_VAR_HARRIS_SEP, OF_VAR_HARRIS_PARA_SEP, OF_VAR_HARRIS_SEMI_SEP = \
+    -1, 0, 1, 2, 3
+
 KEYPOINT_DTYPE = np.dtype([("x", "f4"), ("y", "f4"), ("x_l", "i4"), ("y_l", "i4"), ("level", "i4"),
                            ("fast_score", "i4"), ("response", "f4"), ("angle", "f4"), ("A", "i4"),
                            ("B", "i4"), ("C", "i4"), ("m10", "i4"), ("m01", "i4"),
@@ -136,6 +149,9 @@ def load(path: str | None = None):
     L.of_detect_level_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_float, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     L.of_detect_level_noalloc.restype = C.c_int
+    L.of_variant_detect.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.c_float, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+    L.of_variant_detect.restype = C.c_int
     L.of_autotune.argtypes = [C.c_void_p, C.POINTER(OfFrame), C.c_int, C.c_int, C.c_float, C.c_int, C.c_float,
                               C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(OfTuning)]
     L.of_autotune.restype = C.c_int
@@ -277,6 +293,14 @@ def of_detect_level_noalloc(img, w: int, h: int, pitch: int, fast_t: int, fast_t
     s = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
     return _check(load().of_detect_level_noalloc(_ptr(img), w, h, pitch, fast_t, fast_t_lo, harris_k,
                                                  n_features, _ptr(out_kpts), _ptr(out_count), s))
+
+
+def of_variant_detect(fast_variant: int, harris_variant: int, img, w: int, h: int, pitch: int, fast_t: int,
+                      border: int, harris_k: float, out_points, out_count, capacity: int, stream=None) -> None:
+    """One of the paper's ablation variants (Table 2) on one level (see include/ofast.h). Asynchronous."""
+    s = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    _check(load().of_variant_detect(fast_variant, harris_variant, _ptr(img), w, h, pitch, fast_t, border, harris_k,
+                                    _ptr(out_points), _ptr(out_count), capacity, s))
 
 
 def of_autotune(h: int, frames, levels: int, scale: float, fast_t: int, harris_k: float, n_features: int,

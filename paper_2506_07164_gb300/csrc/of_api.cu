@@ -1096,6 +1096,32 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     return OF_OK;
 }
 
+int of_variant_detect(int fast_variant, int harris_variant, const uint8_t* img, int w, int h, int pitch, int fast_t,
+                      int border, float harris_k, of_var_point* out_points, int32_t* out_count, int64_t capacity,
+                      void* stream) {
+    if (fast_variant < OF_VAR_FAST_BASELINE || fast_variant > OF_VAR_FAST_SM_BINARY)
+        return fail(OF_ERR_ARG, "fast_variant out of range");
+    if (harris_variant < OF_VAR_HARRIS_NONE || harris_variant > OF_VAR_HARRIS_SEMI_SEP)
+        return fail(OF_ERR_ARG, "harris_variant out of range");
+    if (harris_variant > OF_VAR_HARRIS_BASELINE && fast_variant != OF_VAR_FAST_SM_BINARY)
+        return fail(OF_ERR_ARG, "sep / para_sep / semi_sep Harris run fused after sm_binary FAST");
+    if (!img || !out_count || (capacity > 0 && !out_points) || capacity < 0 || capacity > INT32_MAX)
+        return fail(OF_ERR_ARG, "null pointer or bad capacity");
+    if (w < 1 || h < 1 || pitch < w || fast_t < 1 || fast_t > 255 || border < 4)
+        return fail(OF_ERR_ARG, "bad image size, pitch, threshold or border");
+    int64_t knum = 0, kden = 1;
+    if (!ofh::k_fraction(harris_k, &knum, &kden)) return fail(OF_ERR_ARG, "harris_k not representable");
+    int dev = 0, n_sms = 0;
+    OF_CK(cudaGetDevice(&dev));
+    OF_CK(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
+    const cudaStream_t st = (cudaStream_t)stream;
+    OF_CK(cudaMemsetAsync(out_count, 0, sizeof(int32_t), st));
+    launch_variant(fast_variant, harris_variant, img, w, h, pitch, fast_t, border, knum, kden, out_points, out_count,
+                   (int)capacity, n_sms, stream);
+    OF_CK(cudaGetLastError());
+    return OF_OK;
+}
+
 int64_t of_batch_bytes(const of_params* p, const int32_t* ws, const int32_t* hs, int n_frames,
                        int levels, float scale, int n_features) {
     if (!p || !ws || !hs || n_frames < 1 || levels < 1 || levels > 16 || !(scale > 1.0f) || n_features < 0)

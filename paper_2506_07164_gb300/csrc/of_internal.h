@@ -120,4 +120,7 @@ void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t*
                           void* stream);
 void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream);
 int select_smem_bytes(int max_quota);
+// Paper ablation variants (k_ablation.cu); returns the number of launches.
+int launch_variant(int fast_v, int harris_v, const uint8_t* img, int w, int h, int pitch, int t, int border,
+                   int64_t knum, int64_t kden, of_var_point* out, int32_t* count, int cap, int n_sms, void* stream);
 }  // namespace ofk

@@ -102,8 +102,18 @@ def _header_struct_fields(name):
 @pytest.mark.parametrize("c_name,py_name", [
     ("of_params", "OfParams"), ("of_tuning", "OfTuning"), ("of_keypoint", "OfKeypoint"), ("of_frame", "OfFrame"),
     ("of_server_params", "OfServerParams"), ("of_server_result", "OfServerResult"),
-    ("of_server_stats", "OfServerStats")])
+    ("of_server_stats", "OfServerStats"), ("of_var_point", "OfVarPoint")])
 def test_binding_structs_mirror_the_header(c_name, py_name):
     """The ctypes mirrors list the header's fields in the header's order."""
     py = [f[0] for f in getattr(ofg, py_name)._fields_]
     assert py == _header_struct_fields(c_name), c_name
+
+
+def test_variant_detect_validates_before_any_device_work(lib):
+    """Bad variant choices are rejected on the host (no GPU needed)."""
+    for fv, hv in [(4, -1), (-1, -1), (0, 4), (0, -2), (ofg.OF_VAR_FAST_BASELINE, ofg.OF_VAR_HARRIS_SEP),
+                   (ofg.OF_VAR_FAST_SM, ofg.OF_VAR_HARRIS_SEMI_SEP)]:
+        with pytest.raises(ofg.OfError):
+            ofg.of_variant_detect(fv, hv, 16, 64, 64, 64, 20, 19, 0.04, 16, 16, 10)
+    with pytest.raises(ofg.OfError):  # border < 4
+        ofg.of_variant_detect(0, -1, 16, 64, 64, 64, 20, 3, 0.04, 16, 16, 10)
