@@ -277,7 +277,7 @@ FAST_OPS_PER_PX = 40.5
 # DRAM bytes of one k_fast launch per frame, from the ncu capture summarised in
 # profiles/k_fast_1080p8.md (64-frame launch, scaled per frame), valid while
 # k_fast.cu has this SHA-1.
-FAST_TRAFFIC = {"sha1": "86b649ca306398cbec374800f8deab9b808dd87a", "bytes_per_frame": (454399232 + 351162624) / 64}
+FAST_TRAFFIC = {"sha1": "9ab4f7341de30c46531da6be77f481ffef9e2268", "bytes_per_frame": (476473600 + 354774528) / 64}
 
 
 def file_sha1(path):
