@@ -480,11 +480,16 @@ def main():
         os.path.join(ROOT, "gpurun_out")) else f"/tmp/ofast_clocks_{os.getpid()}.csv"
     smi = sample_clocks("", clock_file)
     time.sleep(0.3)
-    ms_b, stage_ms = timed(step_batched, args.steps, args.warmup, per_step_events=True, nvtx_name="batched_timed")
+    ms_b, _ = timed(step_batched, args.steps, args.warmup, nvtx_name="batched_timed")
     if smi is not None:
         smi.terminate()
         smi.wait()
     clocks = summarize_clocks(clock_file)
+    # Stage times: the same kernels run stage by stage (the per-stage graphs of
+    # of_time_stages, one launch per stage over the whole batch), with events
+    # between the stages; the timed graph above may run two frame groups on
+    # two branches whose stages overlap.
+    ms_stages, stage_ms = timed(step_batched, args.steps, 1, per_step_events=True, nvtx_name="stages_timed")
     plain_steps = max(2, args.steps // 4)
     plain_frames = min(args.plain_frames, B)
     ms_p = float("nan")
@@ -637,7 +642,7 @@ def main():
         cpu = cpu_baseline(pool, min(cores, 16), frames_np, n)
     pool.close()
 
-    kernels_per_step = (LEVELS - 1) + 4
+    kernels_per_step = ((LEVELS - 1) + 4) * int(tuning.get("stream_groups", 1))
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_b / args.steps, 4),
@@ -647,6 +652,7 @@ def main():
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {B} frames x {W_ * H_ / 1e6:.2f} MB per step"},
         "mpix_per_s": round(value * mpix, 1),
+        "staged_ms_per_step": round(ms_stages / args.steps, 4),
         "plain": {"value": round(plain_fps, 2), "unit": "frames/s", "mpix_per_s": round(plain_fps * mpix, 1),
                   "steps": plain_steps, "frames_per_step": plain_frames,
                   "launch": "one of_detect_batch call (one graph) per frame"},

@@ -16,11 +16,12 @@
 namespace ofk {
 
 __global__ void __launch_bounds__(ORIENT_WARPS * 32)
-k_orient(const Img* __restrict__ imgs, int n_img, const Call* __restrict__ call) {
-    const int slot = blockIdx.x * ORIENT_WARPS + (threadIdx.x >> 5);
+k_orient(const Img* __restrict__ imgs, int img_begin, int n_img, int slot_begin, int slot_end,
+         const Call* __restrict__ call) {
+    const int slot = slot_begin + blockIdx.x * ORIENT_WARPS + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (slot >= call->total_slots) return;
-    int lo = 0, hi = n_img - 1;
+    if (slot >= slot_end) return;
+    int lo = img_begin, hi = img_begin + n_img - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (imgs[mid].slot0 <= slot) lo = mid; else hi = mid - 1;
@@ -115,10 +116,16 @@ k_orient(const Img* __restrict__ imgs, int n_img, const Call* __restrict__ call)
     }
 }
 
+void launch_orient_range(const Img* imgs, int img_begin, int n_img, int slot_begin, int slot_end, const Call* call,
+                         void* stream) {
+    if (slot_end <= slot_begin || n_img <= 0) return;
+    const int blocks = (slot_end - slot_begin + ORIENT_WARPS - 1) / ORIENT_WARPS;
+    k_orient<<<blocks, ORIENT_WARPS * 32, 0, (cudaStream_t)stream>>>(imgs, img_begin, n_img, slot_begin, slot_end,
+                                                                       call);
+}
+
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream) {
-    if (total_slots <= 0) return;
-    const int blocks = (total_slots + ORIENT_WARPS - 1) / ORIENT_WARPS;
-    k_orient<<<blocks, ORIENT_WARPS * 32, 0, (cudaStream_t)stream>>>(imgs, n_img, call);
+    launch_orient_range(imgs, 0, n_img, 0, total_slots, call, stream);
 }
 
 // ---------------------------------------------------------------- inspect

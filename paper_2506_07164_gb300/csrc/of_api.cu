@@ -209,15 +209,27 @@ struct Plan {
     std::vector<Img> h_img;
     std::vector<Resize> h_rs;
     std::vector<int> rs_begin;      // jobs of level l: [rs_begin[l], rs_begin[l+1])
-    std::vector<int> rsp_begin[2];  // prefix array offset of level l, per resize tile height
-    std::vector<int> rs_tiles[2];   // tiles of level l, per resize tile height
-    std::vector<int32_t> rs_prefix, det_list, det_prefix, tables;
+    std::vector<int32_t> det_list, det_prefix, tables;
+    std::vector<int> rs_frame;      // frame of each resize job
+    // Launch ranges of one group of frames: groups[k] splits the batch into k
+    // groups (k = 1: everything; k = 2: the forked graph).  Tile prefixes of a
+    // group are rebased to 0 and stored in gp_det / gp_rs.
+    struct Group {
+        int img_begin = 0, n_img = 0;
+        int dl_begin = 0, n_list = 0, det_tiles = 0, dp_off = 0;
+        int slot_begin = 0, slot_end = 0;
+        std::vector<int> rs_job, rs_n;              // per level: first resize job, jobs
+        std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
+    };
+    std::vector<Group> groups[3];
+    std::vector<int32_t> gp_det, gp_rs;
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
     std::vector<int> rt_bps;        // TMA resize resident blocks per SM of level l
     int det_tiles = 0, max_quota = 0, total_slots = 0, n_img = 0;
     Call h_call{};
     uint8_t* dbuf = nullptr;
-    size_t off_call = 0, off_img = 0, off_rs = 0, off_rsp = 0, off_dl = 0, off_dp = 0, off_tab = 0;
+    size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0;
+    size_t off_gdp = 0, off_grs = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -244,9 +256,9 @@ struct Plan {
     Resize* d_rs() const { return reinterpret_cast<Resize*>(dbuf + off_rs); }
     Call* d_call() const { return reinterpret_cast<Call*>(dbuf + off_call); }
     const CUtensorMap* d_maps() const { return reinterpret_cast<const CUtensorMap*>(dbuf + off_maps); }
-    const int32_t* d_rsp() const { return reinterpret_cast<const int32_t*>(dbuf + off_rsp); }
     const int32_t* d_dl() const { return reinterpret_cast<const int32_t*>(dbuf + off_dl); }
-    const int32_t* d_dp() const { return reinterpret_cast<const int32_t*>(dbuf + off_dp); }
+    const int32_t* d_gdp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gdp); }
+    const int32_t* d_grs() const { return reinterpret_cast<const int32_t*>(dbuf + off_grs); }
 };
 
 void free_plan(Plan* p) {
@@ -271,6 +283,8 @@ struct of_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;  // second branch of a forked capture
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     uint8_t* arena = nullptr;
     size_t arena_bytes = 0;
     int32_t* d_counts = nullptr;  // [0] of_detect's count, [4] device status word
@@ -298,66 +312,94 @@ struct DeviceGuard {
     }
 };
 
-// Enqueue stages [first, last) of a plan on `st`:
+// Enqueue stage `stage` of one frame group of a plan on `st` (stage 0 here is
+// the resize chain only; the clearing memset is enqueued once per call):
+//   0 resize levels 1..L-1 (pyramid)   1 FAST score + cell flags
+//   2 NMS + Harris keys                3 top-N per level
+//   4 orientation + output records
+void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage, cudaStream_t st) {
+    const Settings& s = P->s;
+    const int nl = s.levels;
+    switch (stage) {
+        case 0:
+            for (int l = 1; l < nl; ++l) {
+                const int nj = G.rs_n[l];
+                if (nj <= 0) continue;
+                if (P->tun.resize_tma && P->rt_buf[l] > 0) {
+                    static_assert(RS_TILE_HS[1] == RT_TILE_H, "TMA resize uses the 64-row tile prefix");
+                    launch_resize_tma(P->d_rs() + G.rs_job[l], P->d_grs() + G.rsp_off[1][l], nj, G.rs_tiles[1][l],
+                                      P->d_maps() + 2 * P->n_img + G.rs_job[l], P->d_call(), P->rt_buf[l],
+                                      H->n_sms * P->rt_bps[l], st);
+                } else {
+                    const int v = P->tun.resize_tile_h == RS_TILE_HS[0] ? 0 : 1;
+                    launch_resize(P->d_rs() + G.rs_job[l], P->d_grs() + G.rsp_off[v][l], nj, G.rs_tiles[v][l],
+                                  RS_TILE_HS[v], st);
+                }
+            }
+            break;
+        case 1:
+            launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
+                        P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                        H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+            break;
+        case 2:
+            launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
+                              P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                              H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st);
+            break;
+        case 3:
+            launch_select(P->d_img() + G.img_begin, G.n_img, P->d_call(), P->max_quota, st);
+            break;
+        case 4:
+            launch_orient_range(P->d_img(), G.img_begin, G.n_img, G.slot_begin, G.slot_end, P->d_call(), st);
+            break;
+    }
+}
+
+// Enqueue stages [first, last) of a plan on `st`, one launch per stage over
+// the whole batch:
 //   0 clear counters and cell flags, resize levels 1..L-1 (pyramid)
 //   1 FAST score + cell flags      2 NMS + Harris keys
 //   3 top-N per level              4 orientation + output records
 void enqueue_stages(of_handle* H, Plan* P, int first, int last, cudaStream_t st) {
-    const Settings& s = P->s;
-    const int nl = s.levels;
     for (int stage = first; stage < last; ++stage) {
-        switch (stage) {
-            case 0:
-                cudaMemsetAsync(H->arena, 0, P->lay.zero_end, st);
-                for (int l = 1; l < nl; ++l) {
-                    const int nj = P->rs_begin[l + 1] - P->rs_begin[l];
-                    if (nj <= 0) continue;
-                    if (P->tun.resize_tma && P->rt_buf[l] > 0) {
-                        static_assert(RS_TILE_HS[1] == RT_TILE_H, "TMA resize uses the 64-row tile prefix");
-                        launch_resize_tma(P->d_rs() + P->rs_begin[l], P->d_rsp() + P->rsp_begin[1][l], nj,
-                                          P->rs_tiles[1][l], P->d_maps() + 2 * P->n_img + P->rs_begin[l],
-                                          P->d_call(), P->rt_buf[l], H->n_sms * P->rt_bps[l], st);
-                    } else {
-                        const int v = P->tun.resize_tile_h == RS_TILE_HS[0] ? 0 : 1;
-                        launch_resize(P->d_rs() + P->rs_begin[l], P->d_rsp() + P->rsp_begin[v][l], nj,
-                                      P->rs_tiles[v][l], RS_TILE_HS[v], st);
-                    }
-                }
-                break;
-            case 1:
-                launch_fast(P->d_img(), P->d_dl(), P->d_dp(), (int)P->det_list.size(),
-                            P->det_tiles, P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border,
-                            s.cell, H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
-                break;
-            case 2:
-                launch_nms_harris(P->d_img(), P->d_dl(), P->d_dp(), (int)P->det_list.size(),
-                                  P->det_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(),
-                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm,
-                                  P->tun.nms_order, st);
-                break;
-            case 3:
-                launch_select(P->d_img(), P->n_img, P->d_call(), P->max_quota, st);
-                break;
-            case 4:
-                launch_orient(P->d_img(), P->n_img, P->d_call(), P->total_slots, st);
-                break;
-        }
+        if (stage == 0) cudaMemsetAsync(H->arena, 0, P->lay.zero_end, st);
+        enqueue_group_stage(H, P, P->groups[1][0], stage, st);
     }
 }
 
-cudaError_t capture(of_handle* H, Plan* P, int first, int last, cudaGraph_t* g) {
+// The whole call with the frames split into two groups whose stage chains run
+// on two branches (cs and the handle's second capture stream), forked after
+// the clearing memset and joined at the end: one group's latency-bound
+// stages overlap the other's ALU-bound ones.  Only inside a stream capture.
+void enqueue_forked(of_handle* H, Plan* P, cudaStream_t cs) {
+    cudaMemsetAsync(H->arena, 0, P->lay.zero_end, cs);
+    cudaEventRecord(H->fork_ev, cs);
+    cudaStreamWaitEvent(H->cap_stream2, H->fork_ev, 0);
+    const std::vector<Plan::Group>& gs = P->groups[2];
+    for (int stage = 0; stage < kStages; ++stage) {
+        enqueue_group_stage(H, P, gs[0], stage, cs);
+        enqueue_group_stage(H, P, gs[1], stage, H->cap_stream2);
+    }
+    cudaEventRecord(H->join_ev, H->cap_stream2);
+    cudaStreamWaitEvent(cs, H->join_ev, 0);
+}
+
+cudaError_t capture(of_handle* H, Plan* P, int first, int last, cudaGraph_t* g, bool forked = false) {
     cudaStream_t cs = H->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    enqueue_stages(H, P, first, last, cs);
+    if (forked) enqueue_forked(H, P, cs);
+    else enqueue_stages(H, P, first, last, cs);
     const cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(cs, g);
     return e != cudaSuccess ? e : le;
 }
 
-// Capture the launch sequence once as one graph, and once per stage (the
-// per-stage graphs serve calls that time each stage with events).  Replaces
-// earlier instances.
+// Capture the launch sequence once as one graph (forked into two frame
+// groups when the tuning says so), and once per stage over the whole batch
+// (the per-stage graphs serve calls that time each stage with events).
+// Replaces earlier instances.
 cudaError_t instantiate_graphs(of_handle* H, Plan* P) {
     if (P->exec) cudaGraphExecDestroy(P->exec);
     P->exec = nullptr;
@@ -366,7 +408,8 @@ cudaError_t instantiate_graphs(of_handle* H, Plan* P) {
         x = nullptr;
     }
     cudaGraph_t g = nullptr;
-    cudaError_t e = capture(H, P, 0, kStages, &g);
+    const bool forked = P->tun.stream_groups == 2 && P->groups[2].size() == 2;
+    cudaError_t e = capture(H, P, 0, kStages, &g, forked);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, g, 0);
     if (g) cudaGraphDestroy(g);
     for (int st = 0; st < kStages && e == cudaSuccess; ++st) {
@@ -450,10 +493,6 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     };
     std::vector<std::pair<int, int>> tab_idx;  // (xtab, ytab) offsets per job
     P->rs_begin.assign(nl + 1, 0);
-    for (int v = 0; v < 2; ++v) {
-        P->rsp_begin[v].assign(nl + 1, 0);
-        P->rs_tiles[v].assign(nl + 1, 0);
-    }
     for (int l = 1; l < nl; ++l) {
         P->rs_begin[l] = (int)P->h_rs.size();
         for (int f = 0; f < nf; ++f) {
@@ -471,19 +510,10 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             R.dh = D.h;
             R.dpitch = D.pitch;
             R.tiles_x = (D.w + RS_TILE_W - 1) / RS_TILE_W;
-            R.tiles_y = 0;  // depends on the tile height; the prefix arrays carry it
+            R.tiles_y = 0;  // depends on the tile height; the groups' prefix arrays carry it
             tab_idx.emplace_back(table(S.w, D.w), table(S.h, D.h));
             P->h_rs.push_back(R);
-        }
-        // One tile prefix array per resize tile height.
-        for (int v = 0; v < 2; ++v) {
-            P->rsp_begin[v][l] = (int)P->rs_prefix.size();
-            int tiles = 0;
-            for (int i = P->rs_begin[l]; i < (int)P->h_rs.size(); ++i) {
-                P->rs_prefix.push_back(tiles);
-                tiles += P->h_rs[i].tiles_x * ((P->h_rs[i].dh + RS_TILE_HS[v] - 1) / RS_TILE_HS[v]);
-            }
-            P->rs_tiles[v][l] = tiles;
+            P->rs_frame.push_back(f);
         }
     }
     P->rs_begin[nl] = (int)P->h_rs.size();
@@ -534,6 +564,54 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
         }
     }
 
+    // Launch ranges per frame group (k = 1, and k = 2 when there are >= 2 frames).
+    for (int k = 1; k <= 2; ++k) {
+        if (k == 2 && nf < 2) break;
+        for (int g = 0; g < k; ++g) {
+            Plan::Group G;
+            const int f0 = nf * g / k, f1 = nf * (g + 1) / k;
+            G.img_begin = f0 * nl;
+            G.n_img = (f1 - f0) * nl;
+            const int nd = (int)P->det_list.size();
+            int j0 = 0, j1 = 0;
+            while (j0 < nd && P->det_list[j0] < G.img_begin) ++j0;
+            j1 = j0;
+            while (j1 < nd && P->det_list[j1] < G.img_begin + G.n_img) ++j1;
+            G.dl_begin = j0;
+            G.n_list = j1 - j0;
+            G.dp_off = (int)P->gp_det.size();
+            const int t0 = j0 < nd ? P->det_prefix[j0] : P->det_tiles;
+            for (int j = j0; j < j1; ++j) P->gp_det.push_back(P->det_prefix[j] - t0);
+            G.det_tiles = (j1 < nd ? P->det_prefix[j1] : P->det_tiles) - t0;
+            G.slot_begin = P->h_img[G.img_begin].slot0;
+            G.slot_end = f1 < nf ? P->h_img[f1 * nl].slot0 : P->total_slots;
+            G.rs_job.assign(nl + 1, 0);
+            G.rs_n.assign(nl + 1, 0);
+            for (int v = 0; v < 2; ++v) {
+                G.rsp_off[v].assign(nl + 1, 0);
+                G.rs_tiles[v].assign(nl + 1, 0);
+            }
+            for (int l = 1; l < nl; ++l) {
+                int b = P->rs_begin[l];
+                while (b < P->rs_begin[l + 1] && P->rs_frame[b] < f0) ++b;
+                int e = b;
+                while (e < P->rs_begin[l + 1] && P->rs_frame[e] < f1) ++e;
+                G.rs_job[l] = b;
+                G.rs_n[l] = e - b;
+                for (int v = 0; v < 2; ++v) {
+                    G.rsp_off[v][l] = (int)P->gp_rs.size();
+                    int tiles = 0;
+                    for (int i = b; i < e; ++i) {
+                        P->gp_rs.push_back(tiles);
+                        tiles += P->h_rs[i].tiles_x * ((P->h_rs[i].dh + RS_TILE_HS[v] - 1) / RS_TILE_HS[v]);
+                    }
+                    G.rs_tiles[v][l] = tiles;
+                }
+            }
+            P->groups[k].push_back(G);
+        }
+    }
+
     Call& C = P->h_call;
     std::memset(&C, 0, sizeof(C));
     C.knum = s.knum;
@@ -551,6 +629,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     C.status = H->d_counts + 4;
     P->tun.resize_tile_h = RS_TILE_HS[1];
     P->tun.resize_tma = 1;
+    P->tun.stream_groups = 1;
     P->tun.fast_blocks_per_sm = fast_blocks_per_sm();
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm();
     P->tun.fast_order = 0;
@@ -580,7 +659,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     }
 
     // Device descriptor block: [Call | Img[] | Resize[]] (re-uploaded when
-    // pointers change) then [resize prefix | detect list | detect prefix | tables].
+    // pointers change) then [detect list | tables | group tile prefixes
+    // (detect, resize)].
     size_t off = 0;
     P->off_call = off;
     off = align_up(off + sizeof(Call), 16);
@@ -591,14 +671,14 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->off_maps = off;
     off = align_up(off + sizeof(CUtensorMap) * P->h_maps.size(), 16);
     P->header_bytes = off;
-    P->off_rsp = off;
-    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->rs_prefix.size(), 1), 16);
     P->off_dl = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->det_list.size(), 1), 16);
-    P->off_dp = off;
-    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->det_prefix.size(), 1), 16);
     P->off_tab = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->tables.size(), 1), 16);
+    P->off_gdp = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_det.size(), 1), 16);
+    P->off_grs = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_rs.size(), 1), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -617,10 +697,10 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_img, P->h_img.data(), sizeof(Img) * P->h_img.size());
     put(P->off_rs, P->h_rs.data(), sizeof(Resize) * P->h_rs.size());
     put(P->off_maps, P->h_maps.data(), sizeof(CUtensorMap) * P->h_maps.size());
-    put(P->off_rsp, P->rs_prefix.data(), sizeof(int32_t) * P->rs_prefix.size());
     put(P->off_dl, P->det_list.data(), sizeof(int32_t) * P->det_list.size());
-    put(P->off_dp, P->det_prefix.data(), sizeof(int32_t) * P->det_prefix.size());
     put(P->off_tab, P->tables.data(), sizeof(int32_t) * P->tables.size());
+    put(P->off_gdp, P->gp_det.data(), sizeof(int32_t) * P->gp_det.size());
+    put(P->off_grs, P->gp_rs.data(), sizeof(int32_t) * P->gp_rs.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);
@@ -891,6 +971,24 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     P->tun.nms_blocks_per_sm = bb;
     P->tun.nms_order = bo;
     P->tun.nms_ms = best;
+    // Whole-call graph with the chosen stages: one group, or two frame groups
+    // on forked branches.
+    int best_g = 1;
+    if (rc == OF_OK && P->groups[2].size() == 2) {
+        float bg = 1e30f;
+        for (int k = 1; k <= 2 && rc == OF_OK; ++k) {
+            P->tun.stream_groups = k;
+            const cudaError_t ge = instantiate_graphs(H, P);
+            if (ge != cudaSuccess) {
+                rc = fail(OF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ge));
+                break;
+            }
+            float ms = 0.f;
+            rc = timed([&] { cudaGraphLaunch(P->exec, st); }, &ms);
+            if (ms < bg) bg = ms, best_g = k;
+        }
+    }
+    P->tun.stream_groups = best_g;
     P->tun.candidates_tried = tried;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -995,7 +1093,11 @@ of_handle* of_create(const of_params* pin) {
     if (e != cudaSuccess) return bail(e, "cudaGetDevice");
     H->stream = (cudaStream_t)p.stream;  // NULL: the CUDA default stream
     e = cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap_stream2, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(e, "cudaStreamCreate");
+    e = cudaEventCreateWithFlags(&H->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H->join_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(e, "cudaEventCreate");
     // Scratch for the largest batch: max_batch frames of max_w x max_h.
     Settings s{};
     s.levels = p.max_levels;
@@ -1038,6 +1140,9 @@ void of_destroy(of_handle* H) {
     if (H->d_counts) cudaFree(H->d_counts);
     if (H->h_count) cudaFreeHost(H->h_count);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+    if (H->cap_stream2) cudaStreamDestroy(H->cap_stream2);
+    if (H->fork_ev) cudaEventDestroy(H->fork_ev);
+    if (H->join_ev) cudaEventDestroy(H->join_ev);
     if (H->own_stream && H->stream) cudaStreamDestroy(H->stream);
     delete H;
 }
@@ -1078,7 +1183,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         (t->resize_tma != 0 && t->resize_tma != 1) || t->fast_blocks_per_sm < 1 ||
         t->fast_blocks_per_sm > fast_blocks_per_sm() || t->nms_blocks_per_sm < 1 ||
         t->nms_blocks_per_sm > nms_blocks_per_sm() || (t->fast_order != 0 && t->fast_order != 1) ||
-        (t->nms_order != 0 && t->nms_order != 1))
+        (t->nms_order != 0 && t->nms_order != 1) || (t->stream_groups != 1 && t->stream_groups != 2))
         return fail(OF_ERR_ARG, "tuning field out of range");
     Plan* P = nullptr;
     const int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
@@ -1090,6 +1195,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
     P->tun.fast_order = t->fast_order;
     P->tun.nms_order = t->nms_order;
+    P->tun.stream_groups = P->groups[2].size() == 2 ? t->stream_groups : 1;
     const cudaError_t e = instantiate_graphs(H, P);
     if (e != cudaSuccess) return fail(OF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     P->tuned = true;

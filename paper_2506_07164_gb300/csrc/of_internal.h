@@ -116,6 +116,9 @@ void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* 
                        int border, int cell, int grid, int order, void* stream);
 void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, void* stream);
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
+// Slots [slot_begin, slot_end) of images [img_begin, img_begin + n_img) (one frame group).
+void launch_orient_range(const Img* imgs, int img_begin, int n_img, int slot_begin, int slot_end, const Call* call,
+                         void* stream);
 void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t* dst,
                           void* stream);
 void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream);
