@@ -82,7 +82,7 @@ typedef struct of_tuning {
     int32_t fast_order;           /* tile walk: 0 round-robin, 1 contiguous chunks */
     int32_t nms_order;
     int32_t resize_tma;           /* 1: persistent TMA resize on the levels whose source box fits */
-    int32_t stream_groups;        /* 2: the frames run as two groups on two forked graph branches */
+    int32_t stream_groups;        /* k > 1: the frames run as k groups on k forked graph branches (1..8) */
     int32_t candidates_tried;     /* configurations timed */
     float resize_ms, fast_ms, nms_ms;  /* best measured time of each tuned stage (all levels) */
 } of_tuning;
@@ -163,8 +163,8 @@ int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int6
 /* Autotuner (batched path): for this batch shape, time each candidate
  * launch configuration -- pyramid kernel (staged tiles of 32 or 64 rows, or
  * the persistent TMA kernel), persistent grid size and tile order of the FAST
- * and NMS kernels, and whether the frames run as one group or as two groups
- * on two forked graph branches -- with CUDA events on these frames (reps
+ * and NMS kernels, and whether the frames run as one group or as 2..8 groups
+ * on forked graph branches -- with CUDA events on these frames (reps
  * timed repetitions each, 1..100), keep the fastest for every later call with
  * the same shape, and run the batch once with it.  Arguments
  * as of_detect_batch; result [host, may be NULL] receives the choice.
@@ -178,8 +178,8 @@ int of_autotune(of_handle* h, const of_frame* frames, int n_frames, int levels, 
  * an earlier of_autotune) instead of searching: the shape's plan is built if
  * needed and its graphs re-captured with *tuning [host].  Fields checked:
  * resize_tile_h 32 or 64, resize_tma 0 or 1, fast/nms_blocks_per_sm in
- * 1..the kernel's occupancy, fast/nms_order 0 or 1, stream_groups 1 or 2 (a
- * one-frame batch always runs as one group) (else OF_ERR_ARG); the
+ * 1..the kernel's occupancy, fast/nms_order 0 or 1, stream_groups 1..8
+ * (capped at the number of frames) (else OF_ERR_ARG); the
  * remaining fields are ignored.  Launches nothing.  Arguments as
  * of_detect_batch.  No paper counterpart. */
 int of_set_tuning(of_handle* h, const of_frame* frames, int n_frames, int levels, float scale,

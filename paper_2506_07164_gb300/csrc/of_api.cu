@@ -126,6 +126,7 @@ struct Layout {
 
 constexpr size_t kAlign = 256;
 constexpr int kStages = 5;
+constexpr int kMaxGroups = 8;  // frame groups of a forked batched graph
 
 // Lay out one batch.  `quota_each` overrides the per-level quotas (capacity sizing).
 Layout make_layout(const std::vector<FrameKey>& frames, const Settings& s, int quota_each) {
@@ -212,8 +213,8 @@ struct Plan {
     std::vector<int32_t> det_list, det_prefix, tables;
     std::vector<int> rs_frame;      // frame of each resize job
     // Launch ranges of one group of frames: groups[k] splits the batch into k
-    // groups (k = 1: everything; k = 2: the forked graph).  Tile prefixes of a
-    // group are rebased to 0 and stored in gp_det / gp_rs.
+    // groups (k = 1: everything; k > 1: the forked graph's branches).  Tile
+    // prefixes of a group are rebased to 0 and stored in gp_det / gp_rs.
     struct Group {
         int img_begin = 0, n_img = 0;
         int dl_begin = 0, n_list = 0, det_tiles = 0, dp_off = 0;
@@ -221,7 +222,7 @@ struct Plan {
         std::vector<int> rs_job, rs_n;              // per level: first resize job, jobs
         std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
     };
-    std::vector<Group> groups[3];
+    std::vector<Group> groups[kMaxGroups + 1];
     std::vector<int32_t> gp_det, gp_rs;
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
     std::vector<int> rt_bps;        // TMA resize resident blocks per SM of level l
@@ -283,8 +284,9 @@ struct of_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
-    cudaStream_t cap_stream2 = nullptr;  // second branch of a forked capture
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaStream_t cap_branch[kMaxGroups - 1] = {};  // further branches of a forked capture
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kMaxGroups - 1] = {};
     uint8_t* arena = nullptr;
     size_t arena_bytes = 0;
     int32_t* d_counts = nullptr;  // [0] of_detect's count, [4] device status word
@@ -368,28 +370,28 @@ void enqueue_stages(of_handle* H, Plan* P, int first, int last, cudaStream_t st)
     }
 }
 
-// The whole call with the frames split into two groups whose stage chains run
-// on two branches (cs and the handle's second capture stream), forked after
+// The whole call with the frames split into k groups whose stage chains run
+// on k branches (cs and the handle's further capture streams), forked after
 // the clearing memset and joined at the end: one group's latency-bound
-// stages overlap the other's ALU-bound ones.  Only inside a stream capture.
-void enqueue_forked(of_handle* H, Plan* P, cudaStream_t cs) {
+// stages overlap another's ALU-bound ones.  Only inside a stream capture.
+void enqueue_forked(of_handle* H, Plan* P, int k, cudaStream_t cs) {
     cudaMemsetAsync(H->arena, 0, P->lay.zero_end, cs);
     cudaEventRecord(H->fork_ev, cs);
-    cudaStreamWaitEvent(H->cap_stream2, H->fork_ev, 0);
-    const std::vector<Plan::Group>& gs = P->groups[2];
-    for (int stage = 0; stage < kStages; ++stage) {
-        enqueue_group_stage(H, P, gs[0], stage, cs);
-        enqueue_group_stage(H, P, gs[1], stage, H->cap_stream2);
+    for (int g = 1; g < k; ++g) cudaStreamWaitEvent(H->cap_branch[g - 1], H->fork_ev, 0);
+    const std::vector<Plan::Group>& gs = P->groups[k];
+    for (int stage = 0; stage < kStages; ++stage)
+        for (int g = 0; g < k; ++g) enqueue_group_stage(H, P, gs[g], stage, g == 0 ? cs : H->cap_branch[g - 1]);
+    for (int g = 1; g < k; ++g) {
+        cudaEventRecord(H->join_ev[g - 1], H->cap_branch[g - 1]);
+        cudaStreamWaitEvent(cs, H->join_ev[g - 1], 0);
     }
-    cudaEventRecord(H->join_ev, H->cap_stream2);
-    cudaStreamWaitEvent(cs, H->join_ev, 0);
 }
 
-cudaError_t capture(of_handle* H, Plan* P, int first, int last, cudaGraph_t* g, bool forked = false) {
+cudaError_t capture(of_handle* H, Plan* P, int first, int last, cudaGraph_t* g, int forked = 1) {
     cudaStream_t cs = H->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    if (forked) enqueue_forked(H, P, cs);
+    if (forked > 1) enqueue_forked(H, P, forked, cs);
     else enqueue_stages(H, P, first, last, cs);
     const cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(cs, g);
@@ -408,8 +410,8 @@ cudaError_t instantiate_graphs(of_handle* H, Plan* P) {
         x = nullptr;
     }
     cudaGraph_t g = nullptr;
-    const bool forked = P->tun.stream_groups == 2 && P->groups[2].size() == 2;
-    cudaError_t e = capture(H, P, 0, kStages, &g, forked);
+    const int k = P->tun.stream_groups;
+    cudaError_t e = capture(H, P, 0, kStages, &g, (k > 1 && (int)P->groups[k].size() == k) ? k : 1);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, g, 0);
     if (g) cudaGraphDestroy(g);
     for (int st = 0; st < kStages && e == cudaSuccess; ++st) {
@@ -564,9 +566,9 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
         }
     }
 
-    // Launch ranges per frame group (k = 1, and k = 2 when there are >= 2 frames).
-    for (int k = 1; k <= 2; ++k) {
-        if (k == 2 && nf < 2) break;
+    // Launch ranges per frame group (k = 1 .. min(kMaxGroups, frames)).
+    for (int k = 1; k <= kMaxGroups; ++k) {
+        if (k > nf) break;
         for (int g = 0; g < k; ++g) {
             Plan::Group G;
             const int f0 = nf * g / k, f1 = nf * (g + 1) / k;
@@ -971,12 +973,12 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     P->tun.nms_blocks_per_sm = bb;
     P->tun.nms_order = bo;
     P->tun.nms_ms = best;
-    // Whole-call graph with the chosen stages: one group, or two frame groups
-    // on forked branches.
+    // Whole-call graph with the chosen stages: one group, or 2..kMaxGroups
+    // frame groups on forked branches.
     int best_g = 1;
-    if (rc == OF_OK && P->groups[2].size() == 2) {
+    {
         float bg = 1e30f;
-        for (int k = 1; k <= 2 && rc == OF_OK; ++k) {
+        for (int k = 1; k <= kMaxGroups && k <= (int)P->frames.size() && rc == OF_OK; ++k) {
             P->tun.stream_groups = k;
             const cudaError_t ge = instantiate_graphs(H, P);
             if (ge != cudaSuccess) {
@@ -1093,10 +1095,12 @@ of_handle* of_create(const of_params* pin) {
     if (e != cudaSuccess) return bail(e, "cudaGetDevice");
     H->stream = (cudaStream_t)p.stream;  // NULL: the CUDA default stream
     e = cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap_stream2, cudaStreamNonBlocking);
+    for (int g = 0; g < kMaxGroups - 1 && e == cudaSuccess; ++g)
+        e = cudaStreamCreateWithFlags(&H->cap_branch[g], cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(e, "cudaStreamCreate");
     e = cudaEventCreateWithFlags(&H->fork_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H->join_ev, cudaEventDisableTiming);
+    for (int g = 0; g < kMaxGroups - 1 && e == cudaSuccess; ++g)
+        e = cudaEventCreateWithFlags(&H->join_ev[g], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(e, "cudaEventCreate");
     // Scratch for the largest batch: max_batch frames of max_w x max_h.
     Settings s{};
@@ -1140,9 +1144,11 @@ void of_destroy(of_handle* H) {
     if (H->d_counts) cudaFree(H->d_counts);
     if (H->h_count) cudaFreeHost(H->h_count);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
-    if (H->cap_stream2) cudaStreamDestroy(H->cap_stream2);
+    for (int g = 0; g < kMaxGroups - 1; ++g) {
+        if (H->cap_branch[g]) cudaStreamDestroy(H->cap_branch[g]);
+        if (H->join_ev[g]) cudaEventDestroy(H->join_ev[g]);
+    }
     if (H->fork_ev) cudaEventDestroy(H->fork_ev);
-    if (H->join_ev) cudaEventDestroy(H->join_ev);
     if (H->own_stream && H->stream) cudaStreamDestroy(H->stream);
     delete H;
 }
@@ -1183,7 +1189,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         (t->resize_tma != 0 && t->resize_tma != 1) || t->fast_blocks_per_sm < 1 ||
         t->fast_blocks_per_sm > fast_blocks_per_sm() || t->nms_blocks_per_sm < 1 ||
         t->nms_blocks_per_sm > nms_blocks_per_sm() || (t->fast_order != 0 && t->fast_order != 1) ||
-        (t->nms_order != 0 && t->nms_order != 1) || (t->stream_groups != 1 && t->stream_groups != 2))
+        (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups)
         return fail(OF_ERR_ARG, "tuning field out of range");
     Plan* P = nullptr;
     const int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
@@ -1195,7 +1201,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
     P->tun.fast_order = t->fast_order;
     P->tun.nms_order = t->nms_order;
-    P->tun.stream_groups = P->groups[2].size() == 2 ? t->stream_groups : 1;
+    P->tun.stream_groups = std::min(t->stream_groups, (int)P->frames.size());
     const cudaError_t e = instantiate_graphs(H, P);
     if (e != cudaSuccess) return fail(OF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     P->tuned = true;

@@ -263,7 +263,7 @@ def test_autotuner_choice_is_valid_and_results_unchanged():
     dev = [torch.from_numpy(im).cuda() for im in imgs]
     det = ofg.Detector(1080, 720, max_levels=8, max_features=500, max_batch=4, fast_t_lo=7)
     tun = det.autotune(dev, levels=8, fast_t=20, n_features=500, reps=2)
-    assert tun.resize_tile_h in (32, 64) and tun.resize_tma in (0, 1) and tun.stream_groups in (1, 2)
+    assert tun.resize_tile_h in (32, 64) and tun.resize_tma in (0, 1) and 1 <= tun.stream_groups <= 3
     assert tun.fast_blocks_per_sm >= 1 and tun.nms_blocks_per_sm >= 1
     assert tun.fast_order in (0, 1) and tun.nms_order in (0, 1)
     assert tun.candidates_tried >= 2 + 2 + 2 and tun.fast_ms > 0 and tun.nms_ms > 0
@@ -310,22 +310,22 @@ def test_set_tuning_rejects_out_of_range_fields():
     det = ofg.Detector(320, 240, max_levels=2, max_features=50)
     good = dict(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=1, nms_blocks_per_sm=1, stream_groups=1)
     for bad in (dict(resize_tile_h=48), dict(resize_tma=2), dict(fast_blocks_per_sm=0),
-                dict(nms_blocks_per_sm=1000), dict(fast_order=2), dict(stream_groups=3)):
+                dict(nms_blocks_per_sm=1000), dict(fast_order=2), dict(stream_groups=9), dict(stream_groups=0)):
         with pytest.raises(ofg.OfError):
             det.set_tuning([img], ofg.OfTuning(**{**good, **bad}), levels=2, n_features=50)
     det.set_tuning([img], ofg.OfTuning(**good), levels=2, n_features=50)
     det.close()
 
 
-def test_two_frame_groups_equal_one_group_and_oracle():
-    """The forked graph (frames in two groups on two branches) gives the same
+def test_frame_groups_equal_one_group_and_oracle():
+    """The forked graph (frames in 2..5 groups on as many branches) gives the same
     records as the one-group graph and the oracle, also after new pointers."""
     sizes = [(1280, 720), (640, 480), (960, 540), (333, 197), (720, 540)]
     imgs = [synth.scene(w, h, 500 + i, background="pink") for i, (w, h) in enumerate(sizes)]
     dev = [torch.from_numpy(im).cuda() for im in imgs]
     det = ofg.Detector(1280, 720, max_levels=6, max_features=400, max_batch=5, fast_t_lo=7)
     got = {}
-    for groups in (1, 2):
+    for groups in (1, 2, 3, 5):
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
                            stream_groups=groups)
         det.set_tuning(dev, tun, levels=6, fast_t=20, n_features=400)
@@ -338,7 +338,8 @@ def test_two_frame_groups_equal_one_group_and_oracle():
         torch.cuda.synchronize()
         for a, b in zip(got[groups], det.batch_results(len(imgs), 400)):
             assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
-    for im, a, b in zip(imgs, got[1], got[2]):
-        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
-        compare_keypoints(b, oracle.detect(im, levels=6, fast_t=20, fast_t_lo=7, n_features=400))
+    for i, im in enumerate(imgs):
+        for k in (2, 3, 5):
+            assert np.array_equal(got[1][i].view(np.uint8), got[k][i].view(np.uint8)), (i, k)
+        compare_keypoints(got[5][i], oracle.detect(im, levels=6, fast_t=20, fast_t_lo=7, n_features=400))
     det.close()
