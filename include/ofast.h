@@ -144,9 +144,11 @@ int of_detect_batch(of_handle* h, const of_frame* frames, int n_frames, int leve
 /* Copy an intermediate buffer of the most recent detect call into `dst`, for
  * inspection and parity checks.  what:
  *   OF_BUF_LEVEL  pyramid level image, w x h bytes, packed rows (pitch = w)
- *   OF_BUF_SCORE  FAST score map, w x h bytes: s(p) where s(p) >= the lowest
- *                 threshold in use (fast_t_lo if enabled, else fast_t), else 0;
- *                 0 outside the detect region
+ *   OF_BUF_SCORE  FAST score map, w x h bytes, 0 outside the detect region.
+ *                 Cells of 8..30 pixels: the candidate score S(p) = s(p) where
+ *                 s(p) >= the threshold of p's cell, else 0 (what NMS keys on);
+ *                 other cell sizes: s(p) where s(p) >= the lowest threshold in
+ *                 use (fast_t_lo if enabled, else fast_t), else 0
  *   OF_BUF_CELLT  per-cell threshold, ncx x ncy bytes (fast_t or fast_t_lo)
  *   OF_BUF_CAND   NMS survivors, count x 16 bytes {int64 key; int32 x; int32 y},
  *                 in no particular order

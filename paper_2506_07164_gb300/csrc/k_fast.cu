@@ -87,16 +87,35 @@ __device__ __forceinline__ uint32_t lanes_ge(uint32_t v, uint32_t t) {
     return ((d >> 15) & 0x00010001u) * 0xFFFFu;
 }
 
-// Score of pixel pair E (pixels x+2E, x+2E+1) of an output row, clipped
-// below t_lo, from the pair words of staged rows y-3 .. y+3 (hw[0..6]).
+// Score of pixel pair E (pixels x+2E, x+2E+1) of an output row from the pair
+// words of staged rows y-3 .. y+3 (hw[0..6]).
 template <int E>
-__device__ __forceinline__ uint32_t ring_pair_score(const uint32_t (*hw)[6], uint32_t t_lo) {
+__device__ __forceinline__ uint32_t ring_pair_raw(const uint32_t (*hw)[6]) {
     uint32_t q[16];
 #define OF_LOAD_RING(i, dx, dy) q[i] = pair_at<(dx) + 2 * E>(hw[3 + (dy)]);
     OF_RING(OF_LOAD_RING)
 #undef OF_LOAD_RING
-    const uint32_t se = pair_score(q, hw[3][2 + E]);
+    return pair_score(q, hw[3][2 + E]);
+}
+
+// The same, clipped below t_lo.
+template <int E>
+__device__ __forceinline__ uint32_t ring_pair_score(const uint32_t (*hw)[6], uint32_t t_lo) {
+    const uint32_t se = ring_pair_raw<E>(hw);
     return se & lanes_ge(se, t_lo);
+}
+
+// Store the bytes of v selected by mask (0xFF per byte) at d: one word store
+// when all four are selected, else byte stores (the other bytes may belong
+// to a tile another block writes at the same time).
+__device__ __forceinline__ void store_bytes(uint8_t* d, uint32_t v, uint32_t mask) {
+    if (mask == 0xFFFFFFFFu) {
+        *reinterpret_cast<uint32_t*>(d) = v;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if ((mask >> (8 * i)) & 1u) d[i] = (uint8_t)(v >> (8 * i));
+    }
 }
 
 // Tile t of the launch: its image and origin.
@@ -264,6 +283,219 @@ void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_p
 int fast_blocks_per_sm() {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast, DET_THREADS, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// Cell tiles: FAST with the per-cell threshold applied in the same kernel.
+//
+// A tile is CPT whole cells of one cell row (CPT = floor(124 / cell); 4 x 30 =
+// 120 x 30 pixels for 30-pixel cells), so the tile sees every pixel of its
+// cells: it scores them, ORs each cell's "a pixel scores >= t_hi" flag in
+// shared memory, and after one barrier writes the candidate score
+// S(p) = s(p) if s(p) >= T(cell(p)) else 0 -- what NMS keys on -- and the
+// cell flags.  Nothing is accumulated across tiles, so NMS needs no cell
+// bookkeeping.  Lanes own 4-aligned 4-pixel groups (the first and last
+// groups straddle the tile edge and store only their in-tile bytes); warp w
+// owns rows 5w .. 5w+4 of the tile (ceil(cell / 5) warps).  The TMA box is
+// the 160 x 40 image box at x = (group origin - 4) rounded down to 16 bytes,
+// starting 3 rows above the tile.
+
+constexpr int CT_RPT = 5;
+constexpr int CT_MAX_WARPS = (CT_MAX_CELL + CT_RPT - 1) / CT_RPT;  // 6: rows up to 5*5+10 = 35 of the box
+static_assert((CT_MAX_WARPS - 1) * CT_RPT + 10 < IMG_BOX_ROWS, "ring rows of the last warp stay in the box");
+
+struct CellTile {
+    int32_t img, x_lo, y0, box_x;
+};
+
+__global__ void __launch_bounds__(32 * CT_MAX_WARPS, 4)
+k_fast_cells(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ prefix,
+             int n_list, int n_tiles, const CUtensorMap* __restrict__ maps, const Call* __restrict__ call,
+             int t_hi, int t_lo, int border, int cell, int cpt, int order) {
+    __shared__ __align__(128) uint8_t sbuf[2 * FAST_BUF];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ CellTile tinfo[2];
+    __shared__ uint32_t cflag[2];
+    __shared__ int any_on[2];
+
+    const int tid = threadIdx.x;
+    const bool cells = t_hi != t_lo;
+    const int tw = cpt * cell;  // tile width in pixels
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_barrier_init();
+        cflag[0] = cflag[1] = 0u;
+    }
+    __syncthreads();
+    auto issue = [&](int t, int b) {
+        const int j = find_tile_job(prefix, n_list, t);
+        const int ii = __ldg(list + j);
+        const Img& I = imgs[ii];
+        const int tt = t - __ldg(prefix + j);
+        const int ftx = tt % I.ftiles_x, fty = tt / I.ftiles_x;
+        const int x_lo = border + ftx * tw, y0 = border + fty * cell;
+        const int box_x = ((x_lo & ~3) - 4) & ~15;
+        // Learned path: does any proposal tile under this work tile hold a proposed pixel?
+        int on = 1;
+        if (I.pmask) {
+            on = 0;
+            const int x_hi = min(x_lo + tw, I.w - border) - 1, y_hi = min(y0 + cell, I.h - border) - 1;
+            for (int py = (y0 - border) >> 5; py <= (y_hi - border) >> 5 && !on; ++py)
+                for (int px = (x_lo - I.tile_x0) >> 5; px <= (x_hi - I.tile_x0) >> 5 && !on; ++px)
+                    on = I.pmask[(size_t)py * 4 * I.tiles_x + px] != 0;
+        }
+        tinfo[b] = CellTile{ii, x_lo, y0, box_x};
+        any_on[b] = on;
+        tensormap_acquire(maps + ii);
+        mbar_arrive_expect_tx(&mbar[b], FAST_BOX);
+        tma_load_2d(sbuf + b * FAST_BUF, maps + ii, box_x, y0 - 3, &mbar[b]);
+    };
+    const int g = gridDim.x;
+    if (tid == 0 && tile_of(order, blockIdx.x, g, n_tiles, 0) < n_tiles)
+        issue(tile_of(order, blockIdx.x, g, n_tiles, 0), 0);
+
+    const int lane = tid & 31, ty = tid >> 5;
+    for (int it = 0;; ++it) {
+        const int t = tile_of(order, blockIdx.x, g, n_tiles, it);
+        if (t >= n_tiles) break;
+        const int tn = tile_of(order, blockIdx.x, g, n_tiles, it + 1);
+        const int b = it & 1;
+        if (tid == 0) {
+            cflag[b ^ 1] = 0u;  // last read before the previous tile's final barrier
+            if (tn < n_tiles) {
+                fence_proxy_async_smem();
+                issue(tn, b ^ 1);
+            }
+        }
+        const bool ok = mbar_wait(&mbar[b], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(call->status, OF_DEV_TIMEOUT);
+                mbar_wait(&mbar[b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (tn < n_tiles) mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+            }
+            return;
+        }
+        const CellTile ti = tinfo[b];
+        const Img& I = imgs[ti.img];
+        const uint8_t* s = sbuf + b * FAST_BUF;
+        const int rx1 = I.w - border, ry1 = I.h - border;
+        const int x_hi = min(ti.x_lo + tw, rx1), y1 = min(ti.y0 + cell, ry1);
+        const int gx0 = ti.x_lo & ~3;
+        const int x = gx0 + 4 * lane;
+        const int row0 = ti.y0 + ty * CT_RPT;
+        const uint32_t colmask = range_mask4(x, ti.x_lo, x_hi);
+        if (!any_on[b]) {
+            // No proposed pixel: S is 0 over the tile.
+#pragma unroll
+            for (int r = 0; r < CT_RPT; ++r) {
+                const int y = row0 + r;
+                if (y < y1 && colmask) store_bytes(I.score + (size_t)y * I.spitch + x, 0u, colmask);
+            }
+            if (tid < cpt) {
+                const int cx = (ti.x_lo - border) / cell + tid, cy = (ti.y0 - border) / cell;
+                if (cx < I.ncx) I.cell[cy * I.ncx + cx] = 0u;
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // Six pair words per staged row (staged row 0 is y0 - 3), loaded just in time.
+        uint32_t hw[CT_RPT + 6][6];
+        const int xoff = gx0 - ti.box_x + 4 * lane;  // >= 4, multiple of 4
+        auto load_row = [&](int k) {
+            const uint8_t* row = s + (ty * CT_RPT + k) * SROW + xoff;
+            const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+            const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+            const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
+            hw[k][0] = __byte_perm(wm, 0u, 0x4140);
+            hw[k][1] = __byte_perm(wm, 0u, 0x4342);
+            hw[k][2] = __byte_perm(wc, 0u, 0x4140);
+            hw[k][3] = __byte_perm(wc, 0u, 0x4342);
+            hw[k][4] = __byte_perm(wp, 0u, 0x4140);
+            hw[k][5] = __byte_perm(wp, 0u, 0x4342);
+        };
+        const bool warp_rows = row0 < y1;  // warp-uniform
+        uint32_t sv[CT_RPT][2];
+        uint32_t u0 = 0u, u1 = 0u;  // running maxima of the in-tile scores (16-bit lanes)
+        if (warp_rows) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) load_row(k);
+#pragma unroll
+            for (int r = 0; r < CT_RPT; ++r) {
+                if (r > 0) load_row(r + 6);
+                const int y = row0 + r;
+                uint32_t s0 = ring_pair_raw<0>(hw + r);
+                uint32_t s1 = ring_pair_raw<1>(hw + r);
+                uint32_t m = (y < y1) ? colmask : 0u;
+                if (I.pmask && m) {
+                    const int px = (x - I.tile_x0) >> 5, py = (y - border) >> 5;
+                    if (I.pmask[(size_t)py * 4 * I.tiles_x + px] == 0) m = 0u;
+                }
+                const uint32_t m0 = __byte_perm(m, 0u, 0x4140), m1 = __byte_perm(m, 0u, 0x4342);
+                s0 &= m0;
+                s1 &= m1;
+                sv[r][0] = s0;
+                sv[r][1] = s1;
+                u0 = __vimax3_u16x2(u0, s0, s0);
+                u1 = __vimax3_u16x2(u1, s1, s1);
+            }
+        }
+        // Cells of this lane's bytes: ca for the bytes in mask_a, ca + 1 for the rest.
+        const int ca = (max(x, ti.x_lo) - ti.x_lo) / cell;
+        const uint32_t mask_a = colmask & range_mask4(x, 0, ti.x_lo + (ca + 1) * cell);
+        const uint32_t mask_b = colmask & ~mask_a;
+        if (cells) {
+            const uint32_t su = __byte_perm(lanes_ge(u0, (uint32_t)t_hi), lanes_ge(u1, (uint32_t)t_hi), 0x6420);
+            uint32_t bits = ((su & mask_a) ? 1u << ca : 0u) | ((su & mask_b) ? 2u << ca : 0u);
+            bits = __reduce_or_sync(0xFFFFFFFFu, bits);
+            if (lane == 0 && bits) atomicOr(&cflag[b], bits);
+        }
+        __syncthreads();
+        const uint32_t flags = cflag[b];
+        if (tid < cpt) {
+            const int cx = (ti.x_lo - border) / cell + tid, cy = (ti.y0 - border) / cell;
+            if (cx < I.ncx) I.cell[cy * I.ncx + cx] = (flags >> tid) & 1u;
+        }
+        if (warp_rows) {
+            // Per-byte threshold T(cell) as lanes_ge constants for the two pairs.
+            const bool fa = (flags >> ca) & 1u, fb = (flags >> (ca + 1)) & 1u;
+            uint32_t kk[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const bool flagged = ((mask_a >> (8 * i)) & 1u) ? fa : fb;
+                kk[i] = 0x8000u - (uint32_t)(flagged ? t_hi : t_lo);
+            }
+            const uint32_t K0 = kk[0] | (kk[1] << 16), K1 = kk[2] | (kk[3] << 16);
+#pragma unroll
+            for (int r = 0; r < CT_RPT; ++r) {
+                const int y = row0 + r;
+                if (y >= y1 || colmask == 0u) continue;
+                const uint32_t s0 = sv[r][0] & ((((sv[r][0] + K0) >> 15) & 0x00010001u) * 0xFFFFu);
+                const uint32_t s1 = sv[r][1] & ((((sv[r][1] + K1) >> 15) & 0x00010001u) * 0xFFFFu);
+                store_bytes(I.score + (size_t)y * I.spitch + x, __byte_perm(s0, s1, 0x6420), colmask);
+            }
+        }
+        __syncthreads();  // buffer b and cflag[b] are free for the tile after next
+    }
+}
+
+void launch_fast_cells(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
+                       int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
+                       int cell, int grid, int order, void* stream) {
+    if (n_tiles <= 0) return;
+    grid = grid < n_tiles ? grid : n_tiles;
+    const int nw = (cell + CT_RPT - 1) / CT_RPT, cpt = CT_MAX_W / cell;
+    k_fast_cells<<<grid, 32 * nw, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps,
+                                                              call, t_hi, t_lo, border, cell, cpt, order);
+}
+
+int fast_cells_blocks_per_sm(int cell) {
+    const int nw = (cell + CT_RPT - 1) / CT_RPT;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_cells, 32 * nw, 0) != cudaSuccess || n < 1) n = 1;
     return n;
 }
 

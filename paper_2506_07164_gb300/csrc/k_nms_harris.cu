@@ -83,6 +83,10 @@ struct NmsTile {
     int32_t img, x0, y0;
 };
 
+// FINAL: the score maps already hold S(p) inside the detect region (the
+// cell-tile FAST kernel applied the cell thresholds); the kernel then skips the
+// cell bookkeeping and the candidate pass and masks the region in registers.
+template <bool FINAL>
 __global__ void __launch_bounds__(DET_THREADS, 5)
 k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
              const int32_t* __restrict__ prefix, int n_list, int n_tiles,
@@ -165,7 +169,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int cy0 = (max(Y0 - 1, ry0) - ry0) / cell;
         const int lcw = (TILE_W + 2) / cell + 2;
         const int lch = (TILE_H + 2) / cell + 2;
-        if (cells) {
+        if (cells && !FINAL) {
             // Cell flags of the tile, and the cell row of each staged row.
             for (int i = tid; i < lcw * lch; i += blockDim.x) {
                 const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
@@ -182,7 +186,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         //    3x3 test reads (X0-4 .. X0+TILE_W+3).  A thread keeps one word
         //    column: its in-region byte mask and the (at most two) cells of its
         //    bytes are fixed for the tile.
-        if (tid < S_WORDS * S_GROUPS) {
+        if (!FINAL && tid < S_WORDS * S_GROUPS) {
             const int k = S_W0 + tid % S_WORDS, rg = tid / S_WORDS;
             const int ix = X0 - HALO_X + 4 * k;
             const uint32_t cmask = range_mask4(ix, lox, hix);
@@ -223,18 +227,33 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                 *wp = val;
             }
         }
-        __syncthreads();
+        if (!FINAL) __syncthreads();
 
         // 2. Strict 3x3 maxima, two pixels per register.
         {
             uint32_t smask = 0u;  // survivor bits: (2 * row + pair) * 2 + lane
             uint32_t hw[RPT + 2][6];
+            // FINAL: the in-region bytes of the three words this thread reads.
+            uint32_t cm_m = 0xFFFFFFFFu, cm_c = 0xFFFFFFFFu, cm_q = 0xFFFFFFFFu;
+            if (FINAL) {
+                const int xc = X0 + 4 * lane;
+                cm_m = range_mask4(xc - 4, lox, hix);
+                cm_c = range_mask4(xc, lox, hix);
+                cm_q = range_mask4(xc + 4, lox, hix);
+            }
 #pragma unroll
             for (int k = 0; k < RPT + 2; ++k) {
                 const uint8_t* row = sS + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
-                const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
-                const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
-                const uint32_t wq = *reinterpret_cast<const uint32_t*>(row + 4);
+                uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+                uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+                uint32_t wq = *reinterpret_cast<const uint32_t*>(row + 4);
+                if (FINAL) {
+                    const int iy = Y0 - 1 + ty * RPT + k;
+                    const uint32_t rm = (iy >= ry0 && iy < ry1) ? 0xFFFFFFFFu : 0u;
+                    wm &= cm_m & rm;
+                    wc &= cm_c & rm;
+                    wq &= cm_q & rm;
+                }
                 hw[k][1] = __byte_perm(wm, 0u, 0x4342);  // (x-2, x-1)
                 hw[k][2] = __byte_perm(wc, 0u, 0x4140);  // (x, x+1)
                 hw[k][3] = __byte_perm(wc, 0u, 0x4342);  // (x+2, x+3)
@@ -309,16 +328,21 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                        int n_list, int n_tiles, const CUtensorMap* img_maps, const CUtensorMap* score_maps,
                        const Call* call, int t_hi, int t_lo, int border, int cell, int grid, int order,
-                       void* stream) {
+                       void* stream, bool final_scores) {
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
-    k_nms_harris<<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(
-        imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, order);
+    if (final_scores)
+        k_nms_harris<true><<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(
+            imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, order);
+    else
+        k_nms_harris<false><<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(
+            imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, order);
 }
 
 int nms_blocks_per_sm() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_harris, DET_THREADS, 0) != cudaSuccess || n < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_harris<false>, DET_THREADS, 0) != cudaSuccess ||
+        n < 1)
         n = 1;
     return n;
 }

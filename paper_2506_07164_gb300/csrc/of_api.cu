@@ -218,19 +218,21 @@ struct Plan {
     struct Group {
         int img_begin = 0, n_img = 0;
         int dl_begin = 0, n_list = 0, det_tiles = 0, dp_off = 0;
+        int fast_tiles = 0, fp_off = 0;             // cell-tile FAST: tiles and prefix offset in gp_fast
         int slot_begin = 0, slot_end = 0;
         std::vector<int> rs_job, rs_n;              // per level: first resize job, jobs
         std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
     };
     std::vector<Group> groups[kMaxGroups + 1];
-    std::vector<int32_t> gp_det, gp_rs;
+    std::vector<int32_t> gp_det, gp_rs, gp_fast;
+    bool cell_tiles = false;     // FAST on whole-cell tiles writes final candidate scores
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
     std::vector<int> rt_bps;        // TMA resize resident blocks per SM of level l
     int det_tiles = 0, max_quota = 0, total_slots = 0, n_img = 0;
     Call h_call{};
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0;
-    size_t off_gdp = 0, off_grs = 0;
+    size_t off_gdp = 0, off_grs = 0, off_gfp = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -260,7 +262,13 @@ struct Plan {
     const int32_t* d_dl() const { return reinterpret_cast<const int32_t*>(dbuf + off_dl); }
     const int32_t* d_gdp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gdp); }
     const int32_t* d_grs() const { return reinterpret_cast<const int32_t*>(dbuf + off_grs); }
+    const int32_t* d_gfp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfp); }
 };
+
+// Resident blocks per SM of the plan's FAST kernel.
+int plan_fast_bps(const Plan* P) {
+    return P->cell_tiles ? fast_cells_blocks_per_sm(P->s.cell) : fast_blocks_per_sm();
+}
 
 void free_plan(Plan* p) {
     if (!p) return;
@@ -340,14 +348,19 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
             }
             break;
         case 1:
-            launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
-                        P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                        H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+            if (P->cell_tiles)
+                launch_fast_cells(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfp() + G.fp_off, G.n_list, G.fast_tiles,
+                                  P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                                  H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+            else
+                launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
+                            P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
             break;
         case 2:
             launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                               P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                              H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st);
+                              H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, P->cell_tiles);
             break;
         case 3:
             launch_select(P->d_img() + G.img_begin, G.n_img, P->d_call(), P->max_quota, st);
@@ -438,6 +451,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     const int nl = s.levels;
     const int nf = (int)frames.size();
     P->n_img = nf * nl;
+    // Cell tiles: FAST applies the per-cell threshold itself (cells of 8..30 pixels).
+    P->cell_tiles = s.cell >= CT_MIN_CELL && s.cell <= CT_MAX_CELL;
     uint8_t* A = H->arena;
 
     // Image descriptors.
@@ -471,6 +486,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
                 I.tiles_x = L.tiles_x;
                 I.tiles_y = L.tiles_y;
                 I.tile_x0 = L.tile_x0;
+                if (P->cell_tiles) I.ftiles_x = (I.ncx + CT_MAX_W / s.cell - 1) / (CT_MAX_W / s.cell);
             } else {
                 I.quota = 0;  // an empty level keeps nothing; its share is not redistributed
             }
@@ -585,6 +601,12 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             const int t0 = j0 < nd ? P->det_prefix[j0] : P->det_tiles;
             for (int j = j0; j < j1; ++j) P->gp_det.push_back(P->det_prefix[j] - t0);
             G.det_tiles = (j1 < nd ? P->det_prefix[j1] : P->det_tiles) - t0;
+            G.fp_off = (int)P->gp_fast.size();
+            for (int j = j0; j < j1; ++j) {
+                const Img& I = P->h_img[P->det_list[j]];
+                P->gp_fast.push_back(G.fast_tiles);
+                G.fast_tiles += I.ftiles_x * I.ncy;
+            }
             G.slot_begin = P->h_img[G.img_begin].slot0;
             G.slot_end = f1 < nf ? P->h_img[f1 * nl].slot0 : P->total_slots;
             G.rs_job.assign(nl + 1, 0);
@@ -632,7 +654,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.resize_tile_h = RS_TILE_HS[1];
     P->tun.resize_tma = 1;
     P->tun.stream_groups = 1;
-    P->tun.fast_blocks_per_sm = fast_blocks_per_sm();
+    P->tun.fast_blocks_per_sm = plan_fast_bps(P);
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm();
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
@@ -681,6 +703,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_det.size(), 1), 16);
     P->off_grs = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_rs.size(), 1), 16);
+    P->off_gfp = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_fast.size(), 1), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -703,6 +727,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_tab, P->tables.data(), sizeof(int32_t) * P->tables.size());
     put(P->off_gdp, P->gp_det.data(), sizeof(int32_t) * P->gp_det.size());
     put(P->off_grs, P->gp_rs.data(), sizeof(int32_t) * P->gp_rs.size());
+    put(P->off_gfp, P->gp_fast.data(), sizeof(int32_t) * P->gp_fast.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);
@@ -941,7 +966,7 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     // FAST (idempotent: rewrites score maps, ORs the same cell flags).
     best = 1e30f;
     int bb = P->tun.fast_blocks_per_sm, bo = 0;
-    for (int bp = 1; bp <= fast_blocks_per_sm() && rc == OF_OK; ++bp) {
+    for (int bp = 1; bp <= plan_fast_bps(P) && rc == OF_OK; ++bp) {
         for (int order = 0; order < 2 && rc == OF_OK; ++order) {
             P->tun.fast_blocks_per_sm = bp;
             P->tun.fast_order = order;
@@ -1187,7 +1212,8 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     DeviceGuard dg(H->device);
     if ((t->resize_tile_h != RS_TILE_HS[0] && t->resize_tile_h != RS_TILE_HS[1]) ||
         (t->resize_tma != 0 && t->resize_tma != 1) || t->fast_blocks_per_sm < 1 ||
-        t->fast_blocks_per_sm > fast_blocks_per_sm() || t->nms_blocks_per_sm < 1 ||
+        t->fast_blocks_per_sm > std::max(fast_blocks_per_sm(), fast_cells_blocks_per_sm(CT_MAX_CELL)) ||
+        t->nms_blocks_per_sm < 1 ||
         t->nms_blocks_per_sm > nms_blocks_per_sm() || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups)
         return fail(OF_ERR_ARG, "tuning field out of range");
@@ -1197,7 +1223,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     if (rc != OF_OK) return rc;
     P->tun.resize_tile_h = t->resize_tile_h;
     P->tun.resize_tma = t->resize_tma;
-    P->tun.fast_blocks_per_sm = t->fast_blocks_per_sm;
+    P->tun.fast_blocks_per_sm = std::min(t->fast_blocks_per_sm, plan_fast_bps(P));
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
     P->tun.fast_order = t->fast_order;
     P->tun.nms_order = t->nms_order;

@@ -22,6 +22,14 @@ constexpr int MAX_CELLS_LOCAL = 128;   // cells overlapping one tile (+halo); ne
 constexpr int IMG_BOX_ROWS = TILE_H + 8;   // image TMA box: rows Y0-4 .. Y0+TILE_H+3, SROW bytes wide
 constexpr int SCORE_BOX_ROWS = TILE_H + 2; // score TMA box: rows Y0-1 .. Y0+TILE_H
 
+// Cell tiles of the FAST kernel that applies the per-cell threshold itself:
+// floor(CT_MAX_W / cell) whole cells wide, one cell row high; used for cells
+// of CT_MIN_CELL .. CT_MAX_CELL pixels (5 rows per warp, 6 warps at most, so
+// every warp's 11 staged rows lie in the 40-row image box).
+constexpr int CT_MAX_W = 124;
+constexpr int CT_MIN_CELL = 8;
+constexpr int CT_MAX_CELL = 30;
+
 // Resize tile: 128 x (32 or 64) output pixels; each thread writes 4 consecutive pixels
 // in 2 or 4 rows.  The autotuner picks the height.
 constexpr int RS_TILE_W = 128;
@@ -47,6 +55,7 @@ struct Img {
     int32_t frame, level;
     int32_t tiles_x, tiles_y;  // detect-stage tiling (0 when the detect region is empty)
     int32_t tile_x0;           // x origin of tile 0 (multiple of 16)
+    int32_t ftiles_x;          // cell tiles per row of the cell-tile FAST kernel (0: not used)
     int32_t slot0;             // first output slot of this image (sum of earlier quotas)
     double lscale;             // scale^level
     // Learned path: one byte per 32 x 32 proposal tile on the detect-tile grid
@@ -110,10 +119,15 @@ int resize_tma_blocks_per_sm(int buf_bytes);  // also raises the kernel's shared
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                  int n_list, int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi,
                  int t_lo, int border, int cell, int grid, int order, void* stream);
+void launch_fast_cells(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
+                       int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
+                       int cell, int grid, int order, void* stream);
+int fast_cells_blocks_per_sm(int cell);
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                        int n_list, int n_tiles, const CUtensorMap* img_maps,
                        const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,
-                       int border, int cell, int grid, int order, void* stream);
+                       int border, int cell, int grid, int order, void* stream,
+                       bool final_scores = false);
 void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, void* stream);
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
 // Slots [slot_begin, slot_end) of images [img_begin, img_begin + n_img) (one frame group).

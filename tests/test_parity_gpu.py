@@ -63,6 +63,15 @@ def clipped(sm, t_lo):
     return np.where(sm >= t_lo, sm, 0).astype(np.uint8)
 
 
+def candidate_scores(sm, T, border, cell):
+    """S(p) = s(p) where s(p) >= the threshold of p's cell, else 0 (detect region only)."""
+    h, w = sm.shape
+    tp = np.full(sm.shape, 256, np.int32)
+    ys, xs = np.mgrid[border:h - border, border:w - border]
+    tp[border:h - border, border:w - border] = T[(ys - border) // cell, (xs - border) // cell]
+    return np.where(sm.astype(np.int32) >= tp, sm, 0).astype(np.uint8)
+
+
 # ------------------------------------------------------------ config 1
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_single_level_640x480(seed):
@@ -92,7 +101,8 @@ def test_pyramid_1080p_8_levels_with_cell_fallback():
         np.testing.assert_array_equal(g_lev.reshape(lev.shape), lev, err_msg=f"level {level}")
         sm, T, cands = oracle_cands(lev, 19, 30, 20, 7)
         g_sm, _ = det.inspect(ofg.OF_BUF_SCORE, 0, level)
-        np.testing.assert_array_equal(g_sm.reshape(lev.shape), clipped(sm, 7), err_msg=f"score {level}")
+        np.testing.assert_array_equal(g_sm.reshape(lev.shape), candidate_scores(sm, T, 19, 30),
+                                      err_msg=f"score {level}")
         g_T, dims = det.inspect(ofg.OF_BUF_CELLT, 0, level)
         np.testing.assert_array_equal(g_T.reshape(T.shape), T, err_msg=f"cells {level}")
         assert gpu_cands(det, 0, level) == cands, f"candidates {level}"
@@ -342,4 +352,26 @@ def test_frame_groups_equal_one_group_and_oracle():
         for k in (2, 3, 5):
             assert np.array_equal(got[1][i].view(np.uint8), got[k][i].view(np.uint8)), (i, k)
         compare_keypoints(got[5][i], oracle.detect(im, levels=6, fast_t=20, fast_t_lo=7, n_features=400))
+    det.close()
+
+
+@pytest.mark.parametrize("cell", [8, 13, 30, 31, 40])
+def test_cell_sizes_both_fast_paths(cell):
+    """Cells of 8..30 pixels run the cell-tile FAST kernel (final candidate
+    scores), larger cells the general one with cell flags accumulated across
+    tiles; both give the oracle's cell thresholds, survivors and keypoints."""
+    img = synth.scene(900, 700, 90 + cell, background="pink")
+    det = ofg.Detector(900, 700, max_levels=3, max_features=600, fast_t_lo=6, cell=cell)
+    kp = det.detect(torch.from_numpy(img).cuda(), levels=3, scale=1.2, fast_t=22, n_features=600)
+    compare_keypoints(kp, oracle.detect(img, levels=3, scale=1.2, fast_t=22, fast_t_lo=6, n_features=600,
+                                        cell=cell))
+    for level in range(3):
+        lev = oracle.pyramid_level(img, 3, 1.2, level)
+        sm, T, cands = oracle_cands(lev, 19, cell, 22, 6)
+        g_T, _ = det.inspect(ofg.OF_BUF_CELLT, 0, level)
+        np.testing.assert_array_equal(g_T.reshape(T.shape), T, err_msg=f"cells {level}")
+        g_sm, _ = det.inspect(ofg.OF_BUF_SCORE, 0, level)
+        want = candidate_scores(sm, T, 19, cell) if cell <= 30 else clipped(sm, 6)
+        np.testing.assert_array_equal(g_sm.reshape(lev.shape), want, err_msg=f"score {level}")
+        assert gpu_cands(det, 0, level) == cands, f"candidates {level}"
     det.close()
