@@ -83,6 +83,8 @@ typedef struct of_tuning {
     int32_t nms_order;
     int32_t resize_tma;           /* 1: persistent TMA resize on the levels whose source box fits */
     int32_t stream_groups;        /* k > 1: the frames run as k groups on k forked graph branches (1..8) */
+    int32_t fast_cell_tiles;      /* 1: FAST on whole-cell tiles applies the cell threshold itself (cells of
+                                     8..30 pixels); 0: general FAST, then a threshold pass */
     int32_t candidates_tried;     /* configurations timed */
     float resize_ms, fast_ms, nms_ms;  /* best measured time of each tuned stage (all levels) */
 } of_tuning;
@@ -144,11 +146,10 @@ int of_detect_batch(of_handle* h, const of_frame* frames, int n_frames, int leve
 /* Copy an intermediate buffer of the most recent detect call into `dst`, for
  * inspection and parity checks.  what:
  *   OF_BUF_LEVEL  pyramid level image, w x h bytes, packed rows (pitch = w)
- *   OF_BUF_SCORE  FAST score map, w x h bytes, 0 outside the detect region.
- *                 Cells of 8..30 pixels: the candidate score S(p) = s(p) where
- *                 s(p) >= the threshold of p's cell, else 0 (what NMS keys on);
- *                 other cell sizes: s(p) where s(p) >= the lowest threshold in
- *                 use (fast_t_lo if enabled, else fast_t), else 0
+ *   OF_BUF_SCORE  candidate score map, w x h bytes: S(p) = s(p) where s(p)
+ *                 >= the threshold of p's cell (fast_t, or fast_t_lo in a cell
+ *                 with no pixel scoring >= fast_t), else 0; 0 outside the
+ *                 detect region -- what NMS keys on
  *   OF_BUF_CELLT  per-cell threshold, ncx x ncy bytes (fast_t or fast_t_lo)
  *   OF_BUF_CAND   NMS survivors, count x 16 bytes {int64 key; int32 x; int32 y},
  *                 in no particular order
@@ -165,7 +166,8 @@ int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int6
 /* Autotuner (batched path): for this batch shape, time each candidate
  * launch configuration -- pyramid kernel (staged tiles of 32 or 64 rows, or
  * the persistent TMA kernel), persistent grid size and tile order of the FAST
- * and NMS kernels, and whether the frames run as one group or as 2..8 groups
+ * and NMS kernels, the FAST form (cell-tile kernel or general kernel +
+ * threshold pass), and whether the frames run as one group or as 2..8 groups
  * on forked graph branches -- with CUDA events on these frames (reps
  * timed repetitions each, 1..100), keep the fastest for every later call with
  * the same shape, and run the batch once with it.  Arguments
@@ -181,7 +183,8 @@ int of_autotune(of_handle* h, const of_frame* frames, int n_frames, int levels, 
  * needed and its graphs re-captured with *tuning [host].  Fields checked:
  * resize_tile_h 32 or 64, resize_tma 0 or 1, fast/nms_blocks_per_sm in
  * 1..the kernel's occupancy, fast/nms_order 0 or 1, stream_groups 1..8
- * (capped at the number of frames) (else OF_ERR_ARG); the
+ * (capped at the number of frames), fast_cell_tiles 0 or 1 (ignored for
+ * cells outside 8..30 pixels) (else OF_ERR_ARG); the
  * remaining fields are ignored.  Launches nothing.  Arguments as
  * of_detect_batch.  No paper counterpart. */
 int of_set_tuning(of_handle* h, const of_frame* frames, int n_frames, int levels, float scale,

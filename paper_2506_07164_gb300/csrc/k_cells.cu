@@ -1,0 +1,120 @@
+// Per-cell threshold applied to FAST score maps in place.
+//
+// After the general FAST kernel the maps hold s(p) where s(p) >= t_lo, and
+// each cell (anchored at the border) has a flag "some pixel scores >= t_hi".
+// This pass turns them into the candidate scores NMS keys on,
+// S(p) = s(p) if s(p) >= T(cell(p)) else 0 with T = t_hi in flagged cells:
+// in a flagged cell the bytes below t_hi are cleared.  On the learned path it
+// also clears the scores outside the proposed 32 x 32 tiles.
+//
+// One block per band of cell rows (one cell high) of one image: the block
+// writes, for up to 4096 columns at a time, a byte 0xFF where the column's
+// cell in this band is flagged (all rows of a band share their cells' flags),
+// then its warps stream the band's rows in 16-byte chunks against that mask,
+// four chunks in flight per lane, writing a chunk back only when it changes.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "of_internal.h"
+#include "of_tile.cuh"
+
+namespace ofk {
+
+// 0xFF in each byte of v that is below t (t <= 255).
+__device__ __forceinline__ uint32_t bytes_below(uint32_t v, uint32_t t) {
+    const uint32_t tt = (0x8000u - t) * 0x00010001u;
+    const uint32_t lo = __byte_perm(v, 0u, 0x4140) + tt, hi = __byte_perm(v, 0u, 0x4342) + tt;
+    return ~__byte_perm((lo >> 15 & 0x00010001u) * 0xFFu, (hi >> 15 & 0x00010001u) * 0xFFu, 0x6420);
+}
+
+constexpr int CA_THREADS = 256;
+constexpr int CA_SEG = 256;  // 16-byte chunks per column-mask segment (4096 columns)
+
+__device__ __forceinline__ uint32_t apply_word(uint32_t v, uint32_t fm, uint32_t t_hi) {
+    return v & ~(fm & bytes_below(v, t_hi));
+}
+
+__global__ void __launch_bounds__(CA_THREADS)
+k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ band_prefix,
+             int n_list, int n_bands, int t_hi, int t_lo, int border, int cell) {
+    __shared__ __align__(16) uint8_t colmask[16 * CA_SEG];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool cells = t_hi != t_lo;
+    for (int band = blockIdx.x; band < n_bands; band += gridDim.x) {
+        const int j = find_tile_job(band_prefix, n_list, band);
+        const Img& I = imgs[__ldg(list + j)];
+        if (!cells && !I.pmask) continue;  // block-uniform
+        const int cy = band - __ldg(band_prefix + j);
+        const int rx1 = I.w - border, ry1 = I.h - border;
+        const int xb0 = border & ~15;  // first chunk column
+        const int n_chunks = (rx1 - xb0 + 15) >> 4;
+        const uint32_t* crow = I.cell + (size_t)cy * I.ncx;
+        const int y0 = border + cy * cell, y1 = min(y0 + cell, ry1);
+        for (int s0 = 0; s0 < n_chunks; s0 += CA_SEG) {
+            const int s1 = min(s0 + CA_SEG, n_chunks);
+            __syncthreads();  // earlier readers of colmask are done
+            // Column mask of the segment: 0xFF where the column is in the region and its cell is flagged.
+            for (int c = s0 + tid; c < s1; c += CA_THREADS) {
+                const int x = xb0 + 16 * c;
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t m = 0u;
+                    if (cells) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int xx = x + 4 * q + i;
+                            if (xx >= border && xx < rx1 && crow[(xx - border) / cell]) m |= 0xFFu << (8 * i);
+                        }
+                    }
+                    w[q] = m;
+                }
+                *reinterpret_cast<uint4*>(colmask + 16 * (c - s0)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+            __syncthreads();
+            for (int y = y0 + warp; y < y1; y += CA_THREADS / 32) {
+                uint8_t* srow = I.score + (size_t)y * I.spitch;
+                const int py = (y - border) >> 5;
+                for (int c0 = s0; c0 < s1; c0 += 128) {
+                    uint4 v[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int c = c0 + lane + 32 * k;
+                        if (c < s1) v[k] = *reinterpret_cast<const uint4*>(srow + xb0 + 16 * c);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int c = c0 + lane + 32 * k;
+                        if (c >= s1) continue;
+                        const int x = xb0 + 16 * c;
+                        uint4 nv;
+                        if (I.pmask && I.pmask[(size_t)py * 4 * I.tiles_x + ((x - I.tile_x0) >> 5)] == 0) {
+                            // Outside the proposed tiles the region's bytes become 0.
+                            nv.x = v[k].x & ~range_mask4(x, border, rx1);
+                            nv.y = v[k].y & ~range_mask4(x + 4, border, rx1);
+                            nv.z = v[k].z & ~range_mask4(x + 8, border, rx1);
+                            nv.w = v[k].w & ~range_mask4(x + 12, border, rx1);
+                        } else {
+                            const uint4 fm = *reinterpret_cast<const uint4*>(colmask + 16 * (c - s0));
+                            nv.x = apply_word(v[k].x, fm.x, (uint32_t)t_hi);
+                            nv.y = apply_word(v[k].y, fm.y, (uint32_t)t_hi);
+                            nv.z = apply_word(v[k].z, fm.z, (uint32_t)t_hi);
+                            nv.w = apply_word(v[k].w, fm.w, (uint32_t)t_hi);
+                        }
+                        if (nv.x != v[k].x || nv.y != v[k].y || nv.z != v[k].z || nv.w != v[k].w)
+                            *reinterpret_cast<uint4*>(srow + x) = nv;
+                    }
+                }
+            }
+        }
+    }
+}
+
+void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
+                       int t_hi, int t_lo, int border, int cell, int grid, void* stream) {
+    if (n_bands <= 0) return;
+    k_cell_apply<<<grid < n_bands ? grid : n_bands, CA_THREADS, 0, (cudaStream_t)stream>>>(
+        imgs, img_list, band_prefix, n_list, n_bands, t_hi, t_lo, border, cell);
+}
+
+}  // namespace ofk

@@ -219,20 +219,21 @@ struct Plan {
         int img_begin = 0, n_img = 0;
         int dl_begin = 0, n_list = 0, det_tiles = 0, dp_off = 0;
         int fast_tiles = 0, fp_off = 0;             // cell-tile FAST: tiles and prefix offset in gp_fast
+        int n_bands = 0, rp_off = 0;                // threshold pass: cell rows and prefix offset in gp_rows
         int slot_begin = 0, slot_end = 0;
         std::vector<int> rs_job, rs_n;              // per level: first resize job, jobs
         std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
     };
     std::vector<Group> groups[kMaxGroups + 1];
-    std::vector<int32_t> gp_det, gp_rs, gp_fast;
-    bool cell_tiles = false;     // FAST on whole-cell tiles writes final candidate scores
+    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows;
+    bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
     std::vector<int> rt_bps;        // TMA resize resident blocks per SM of level l
     int det_tiles = 0, max_quota = 0, total_slots = 0, n_img = 0;
     Call h_call{};
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0;
-    size_t off_gdp = 0, off_grs = 0, off_gfp = 0;
+    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -263,11 +264,12 @@ struct Plan {
     const int32_t* d_gdp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gdp); }
     const int32_t* d_grs() const { return reinterpret_cast<const int32_t*>(dbuf + off_grs); }
     const int32_t* d_gfp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfp); }
+    const int32_t* d_grp() const { return reinterpret_cast<const int32_t*>(dbuf + off_grp); }
 };
 
 // Resident blocks per SM of the plan's FAST kernel.
 int plan_fast_bps(const Plan* P) {
-    return P->cell_tiles ? fast_cells_blocks_per_sm(P->s.cell) : fast_blocks_per_sm();
+    return (P->cell_tiles && P->tun.fast_cell_tiles) ? fast_cells_blocks_per_sm(P->s.cell) : fast_blocks_per_sm();
 }
 
 void free_plan(Plan* p) {
@@ -348,19 +350,24 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
             }
             break;
         case 1:
-            if (P->cell_tiles)
+            // Final candidate scores S(p): the cell-tile kernel, or the general
+            // kernel followed by the threshold pass.
+            if (P->cell_tiles && P->tun.fast_cell_tiles) {
                 launch_fast_cells(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfp() + G.fp_off, G.n_list, G.fast_tiles,
                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                                   H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
-            else
+            } else {
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                             H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+                launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list, G.n_bands,
+                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st);
+            }
             break;
         case 2:
             launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                               P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                              H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, P->cell_tiles);
+                              H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, true);
             break;
         case 3:
             launch_select(P->d_img() + G.img_begin, G.n_img, P->d_call(), P->max_quota, st);
@@ -602,10 +609,13 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             for (int j = j0; j < j1; ++j) P->gp_det.push_back(P->det_prefix[j] - t0);
             G.det_tiles = (j1 < nd ? P->det_prefix[j1] : P->det_tiles) - t0;
             G.fp_off = (int)P->gp_fast.size();
+            G.rp_off = (int)P->gp_rows.size();
             for (int j = j0; j < j1; ++j) {
                 const Img& I = P->h_img[P->det_list[j]];
                 P->gp_fast.push_back(G.fast_tiles);
                 G.fast_tiles += I.ftiles_x * I.ncy;
+                P->gp_rows.push_back(G.n_bands);
+                G.n_bands += I.ncy;
             }
             G.slot_begin = P->h_img[G.img_begin].slot0;
             G.slot_end = f1 < nf ? P->h_img[f1 * nl].slot0 : P->total_slots;
@@ -654,6 +664,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.resize_tile_h = RS_TILE_HS[1];
     P->tun.resize_tma = 1;
     P->tun.stream_groups = 1;
+    P->tun.fast_cell_tiles = P->cell_tiles ? 1 : 0;
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm();
     P->tun.fast_order = 0;
@@ -705,6 +716,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_rs.size(), 1), 16);
     P->off_gfp = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_fast.size(), 1), 16);
+    P->off_grp = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_rows.size(), 1), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -728,6 +741,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_gdp, P->gp_det.data(), sizeof(int32_t) * P->gp_det.size());
     put(P->off_grs, P->gp_rs.data(), sizeof(int32_t) * P->gp_rs.size());
     put(P->off_gfp, P->gp_fast.data(), sizeof(int32_t) * P->gp_fast.size());
+    put(P->off_grp, P->gp_rows.data(), sizeof(int32_t) * P->gp_rows.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);
@@ -963,18 +977,24 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     P->tun.resize_tile_h = best_h;
     P->tun.resize_tma = best_tma;
     P->tun.resize_ms = best;
-    // FAST (idempotent: rewrites score maps, ORs the same cell flags).
+    // FAST (idempotent: rewrites score maps, sets the same cell flags): the
+    // general kernel + threshold pass, and the cell-tile kernel where the cell
+    // size allows it.
     best = 1e30f;
-    int bb = P->tun.fast_blocks_per_sm, bo = 0;
-    for (int bp = 1; bp <= plan_fast_bps(P) && rc == OF_OK; ++bp) {
-        for (int order = 0; order < 2 && rc == OF_OK; ++order) {
-            P->tun.fast_blocks_per_sm = bp;
-            P->tun.fast_order = order;
-            float ms = 0.f;
-            rc = timed([&] { enqueue_stages(H, P, 1, 2, st); }, &ms);
-            if (ms < best) best = ms, bb = bp, bo = order;
+    int bb = P->tun.fast_blocks_per_sm, bo = 0, bv = P->tun.fast_cell_tiles;
+    for (int v = 0; v <= (P->cell_tiles ? 1 : 0) && rc == OF_OK; ++v) {
+        P->tun.fast_cell_tiles = v;
+        for (int bp = 1; bp <= plan_fast_bps(P) && rc == OF_OK; ++bp) {
+            for (int order = 0; order < 2 && rc == OF_OK; ++order) {
+                P->tun.fast_blocks_per_sm = bp;
+                P->tun.fast_order = order;
+                float ms = 0.f;
+                rc = timed([&] { enqueue_stages(H, P, 1, 2, st); }, &ms);
+                if (ms < best) best = ms, bb = bp, bo = order, bv = v;
+            }
         }
     }
+    P->tun.fast_cell_tiles = bv;
     P->tun.fast_blocks_per_sm = bb;
     P->tun.fast_order = bo;
     P->tun.fast_ms = best;
@@ -1215,7 +1235,8 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         t->fast_blocks_per_sm > std::max(fast_blocks_per_sm(), fast_cells_blocks_per_sm(CT_MAX_CELL)) ||
         t->nms_blocks_per_sm < 1 ||
         t->nms_blocks_per_sm > nms_blocks_per_sm() || (t->fast_order != 0 && t->fast_order != 1) ||
-        (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups)
+        (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
+        (t->fast_cell_tiles != 0 && t->fast_cell_tiles != 1))
         return fail(OF_ERR_ARG, "tuning field out of range");
     Plan* P = nullptr;
     const int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
@@ -1223,6 +1244,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     if (rc != OF_OK) return rc;
     P->tun.resize_tile_h = t->resize_tile_h;
     P->tun.resize_tma = t->resize_tma;
+    P->tun.fast_cell_tiles = P->cell_tiles ? t->fast_cell_tiles : 0;
     P->tun.fast_blocks_per_sm = std::min(t->fast_blocks_per_sm, plan_fast_bps(P));
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
     P->tun.fast_order = t->fast_order;

@@ -123,6 +123,8 @@ void launch_fast_cells(const Img* imgs, const int32_t* img_list, const int32_t* 
                        int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
                        int cell, int grid, int order, void* stream);
 int fast_cells_blocks_per_sm(int cell);
+void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
+                       int t_hi, int t_lo, int border, int cell, int grid, void* stream);
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                        int n_list, int n_tiles, const CUtensorMap* img_maps,
                        const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,

@@ -320,7 +320,7 @@ def test_set_tuning_rejects_out_of_range_fields():
     det = ofg.Detector(320, 240, max_levels=2, max_features=50)
     good = dict(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=1, nms_blocks_per_sm=1, stream_groups=1)
     for bad in (dict(resize_tile_h=48), dict(resize_tma=2), dict(fast_blocks_per_sm=0),
-                dict(nms_blocks_per_sm=1000), dict(fast_order=2), dict(stream_groups=9), dict(stream_groups=0)):
+                dict(nms_blocks_per_sm=1000), dict(fast_order=2), dict(stream_groups=9), dict(stream_groups=0), dict(fast_cell_tiles=2)):
         with pytest.raises(ofg.OfError):
             det.set_tuning([img], ofg.OfTuning(**{**good, **bad}), levels=2, n_features=50)
     det.set_tuning([img], ofg.OfTuning(**good), levels=2, n_features=50)
@@ -356,22 +356,28 @@ def test_frame_groups_equal_one_group_and_oracle():
 
 
 @pytest.mark.parametrize("cell", [8, 13, 30, 31, 40])
-def test_cell_sizes_both_fast_paths(cell):
-    """Cells of 8..30 pixels run the cell-tile FAST kernel (final candidate
-    scores), larger cells the general one with cell flags accumulated across
-    tiles; both give the oracle's cell thresholds, survivors and keypoints."""
+def test_cell_sizes_both_fast_forms(cell):
+    """Both FAST forms -- the cell-tile kernel (cells of 8..30 pixels) and the
+    general kernel followed by the threshold pass -- give the oracle's cell
+    thresholds, candidate scores, survivors and keypoints."""
     img = synth.scene(900, 700, 90 + cell, background="pink")
+    dev = torch.from_numpy(img).cuda()
     det = ofg.Detector(900, 700, max_levels=3, max_features=600, fast_t_lo=6, cell=cell)
-    kp = det.detect(torch.from_numpy(img).cuda(), levels=3, scale=1.2, fast_t=22, n_features=600)
-    compare_keypoints(kp, oracle.detect(img, levels=3, scale=1.2, fast_t=22, fast_t_lo=6, n_features=600,
-                                        cell=cell))
-    for level in range(3):
-        lev = oracle.pyramid_level(img, 3, 1.2, level)
-        sm, T, cands = oracle_cands(lev, 19, cell, 22, 6)
-        g_T, _ = det.inspect(ofg.OF_BUF_CELLT, 0, level)
-        np.testing.assert_array_equal(g_T.reshape(T.shape), T, err_msg=f"cells {level}")
-        g_sm, _ = det.inspect(ofg.OF_BUF_SCORE, 0, level)
-        want = candidate_scores(sm, T, 19, cell) if cell <= 30 else clipped(sm, 6)
-        np.testing.assert_array_equal(g_sm.reshape(lev.shape), want, err_msg=f"score {level}")
-        assert gpu_cands(det, 0, level) == cands, f"candidates {level}"
+    ora = oracle.detect(img, levels=3, scale=1.2, fast_t=22, fast_t_lo=6, n_features=600, cell=cell)
+    for form in (0, 1):
+        tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
+                           stream_groups=1, fast_cell_tiles=form)
+        det.set_tuning([dev], tun, levels=3, scale=1.2, fast_t=22, n_features=600)
+        det.detect_batch([dev], levels=3, scale=1.2, fast_t=22, n_features=600)
+        torch.cuda.synchronize()
+        compare_keypoints(det.batch_results(1, 600)[0], ora)
+        for level in range(3):
+            lev = oracle.pyramid_level(img, 3, 1.2, level)
+            sm, T, cands = oracle_cands(lev, 19, cell, 22, 6)
+            g_T, _ = det.inspect(ofg.OF_BUF_CELLT, 0, level)
+            np.testing.assert_array_equal(g_T.reshape(T.shape), T, err_msg=f"form {form} cells {level}")
+            g_sm, _ = det.inspect(ofg.OF_BUF_SCORE, 0, level)
+            np.testing.assert_array_equal(g_sm.reshape(lev.shape), candidate_scores(sm, T, 19, cell),
+                                          err_msg=f"form {form} score {level}")
+            assert gpu_cands(det, 0, level) == cands, f"form {form} candidates {level}"
     det.close()
