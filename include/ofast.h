@@ -86,7 +86,8 @@ typedef struct of_tuning {
     int32_t fast_cell_tiles;      /* 1: FAST on whole-cell tiles applies the cell threshold itself (cells of
                                      8..30 pixels); 0: general FAST, then a threshold pass */
     int32_t candidates_tried;     /* configurations timed */
-    float resize_ms, fast_ms, nms_ms;  /* best measured time of each tuned stage (all levels) */
+    float resize_ms, fast_ms, nms_ms;  /* best measured time of each tuned stage (all levels);
+                                          fast_ms covers FAST + NMS (the FAST forms differ in both) */
 } of_tuning;
 
 /* One detected keypoint, 64 bytes.  Level-major, rank order within a level
@@ -207,7 +208,8 @@ int of_test_timeout(of_handle* h, int64_t limit_us);
  * separate launches and records events[i] (cudaEvent_t, created by the
  * caller with timing enabled) on the handle's stream before stage i and
  * events[5] after the last one:
- *   0 pyramid (clear + resize)  1 FAST score  2 NMS + Harris  3 top-N  4 orientation.
+ *   0 pyramid (clear + resize)  1 FAST score  2 cell thresholds (when FAST
+ *   did not apply them) + NMS + Harris  3 top-N  4 orientation.
  * Results are identical to an untimed call.  Returns OF_OK or OF_ERR_ARG. */
 #define OF_N_STAGES 5
 int of_time_stages(of_handle* h, void* const* events);

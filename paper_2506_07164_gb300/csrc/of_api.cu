@@ -327,8 +327,8 @@ struct DeviceGuard {
 // Enqueue stage `stage` of one frame group of a plan on `st` (stage 0 here is
 // the resize chain only; the clearing memset is enqueued once per call):
 //   0 resize levels 1..L-1 (pyramid)   1 FAST score + cell flags
-//   2 NMS + Harris keys                3 top-N per level
-//   4 orientation + output records
+//   2 (threshold pass,) NMS + Harris keys
+//   3 top-N per level                  4 orientation + output records
 void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage, cudaStream_t st) {
     const Settings& s = P->s;
     const int nl = s.levels;
@@ -350,21 +350,21 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
             }
             break;
         case 1:
-            // Final candidate scores S(p): the cell-tile kernel, or the general
-            // kernel followed by the threshold pass.
-            if (P->cell_tiles && P->tun.fast_cell_tiles) {
+            // The cell-tile kernel writes final candidate scores S(p); the
+            // general kernel's maps get the threshold pass at the start of stage 2.
+            if (P->cell_tiles && P->tun.fast_cell_tiles)
                 launch_fast_cells(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfp() + G.fp_off, G.n_list, G.fast_tiles,
                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                                   H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
-            } else {
+            else
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                             H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
-                launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list, G.n_bands,
-                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st);
-            }
             break;
         case 2:
+            if (!(P->cell_tiles && P->tun.fast_cell_tiles))
+                launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list, G.n_bands,
+                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st);
             launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                               P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                               H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, true);
@@ -978,8 +978,8 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     P->tun.resize_tma = best_tma;
     P->tun.resize_ms = best;
     // FAST (idempotent: rewrites score maps, sets the same cell flags): the
-    // general kernel + threshold pass, and the cell-tile kernel where the cell
-    // size allows it.
+    // general kernel (+ threshold pass, stage 2), and the cell-tile kernel
+    // where the cell size allows it; fast_ms below is FAST + NMS.
     best = 1e30f;
     int bb = P->tun.fast_blocks_per_sm, bo = 0, bv = P->tun.fast_cell_tiles;
     for (int v = 0; v <= (P->cell_tiles ? 1 : 0) && rc == OF_OK; ++v) {
@@ -988,8 +988,15 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
             for (int order = 0; order < 2 && rc == OF_OK; ++order) {
                 P->tun.fast_blocks_per_sm = bp;
                 P->tun.fast_order = order;
+                // FAST and NMS together (NMS appends candidates: clear the
+                // counters): the general form's threshold pass runs in stage 2.
                 float ms = 0.f;
-                rc = timed([&] { enqueue_stages(H, P, 1, 2, st); }, &ms);
+                rc = timed(
+                    [&] {
+                        cudaMemsetAsync(H->arena, 0, ctr_bytes, st);
+                        enqueue_stages(H, P, 1, 3, st);
+                    },
+                    &ms);
                 if (ms < best) best = ms, bb = bp, bo = order, bv = v;
             }
         }
