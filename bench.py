@@ -281,7 +281,7 @@ FAST_OPS_PER_PX = 40.5
 # DRAM bytes of one k_fast launch per frame, from the ncu capture summarised in
 # profiles/k_fast_1080p8.md (64-frame launch, scaled per frame), valid while
 # k_fast.cu has this SHA-1.
-FAST_TRAFFIC = {"sha1": "9ab4f7341de30c46531da6be77f481ffef9e2268", "bytes_per_frame": (476473600 + 354774528) / 64}
+FAST_TRAFFIC = {"sha1": "1faadb9ee769f98fe19a01b810ada9531e29d7ae", "bytes_per_frame": (468449024 + 355659776) / 64}
 
 
 def file_sha1(path):
@@ -291,15 +291,9 @@ def file_sha1(path):
         return hashlib.sha1(f.read()).hexdigest()
 
 
-def detect_tile_pixels(lw, lh):
-    """Pixels the FAST launch covers per frame: 128 x 32 tiles over each detect region."""
-    tot = 0
-    for w, h in zip(lw, lh):
-        if w - 2 * BORDER <= 0 or h - 2 * BORDER <= 0:
-            continue
-        x0 = BORDER & ~15
-        tot += ((w - BORDER - x0 + 127) // 128) * ((h - 2 * BORDER + 31) // 32) * 128 * 32
-    return tot
+def detect_region_pixels(lw, lh):
+    """Pixels whose FAST score the method needs per frame: the detect regions of all levels."""
+    return sum(max(0, w - 2 * BORDER) * max(0, h - 2 * BORDER) for w, h in zip(lw, lh))
 
 
 def measured_peaks():
@@ -586,11 +580,13 @@ def main():
     sm_max = float(clocks.get("sm_max_mhz") or 2070.0)
     if ofg.STAGE_NAMES[dom] == "fast":
         # The dominant stage is integer-ALU bound: report it against the ALU pipe.
-        ops = FAST_OPS_PER_PX * detect_tile_pixels(lw, lh) * B
+        ops = FAST_OPS_PER_PX * detect_region_pixels(lw, lh) * B
         achieved = ops / (stage_ms[dom] / 1000.0) / 1e9
         peak_alu = n_sms * ALU_LANES_PER_SM_CLK * sm_max * 1e6 / 1e9
-        ok = file_sha1(os.path.join(ROOT, "paper_2506_07164_gb300", "csrc", "k_fast.cu")) == FAST_TRAFFIC["sha1"]
-        roofline = {"bound": "alu", "kernel": "k_fast", "achieved": round(achieved, 1), "peak": round(peak_alu, 1),
+        kname = "k_fast_cells" if tuning.get("fast_cell_tiles") else "k_fast"
+        ok = kname == "k_fast" and file_sha1(
+            os.path.join(ROOT, "paper_2506_07164_gb300", "csrc", "k_fast.cu")) == FAST_TRAFFIC["sha1"]
+        roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 1), "peak": round(peak_alu, 1),
                     "peak_kind": f"derived: {n_sms} SMs x {ALU_LANES_PER_SM_CLK} ALU lanes/clk x {sm_max:.0f} MHz",
                     "unit": "Gop/s", "frac": round(achieved / peak_alu, 4),
                     "traffic": round(FAST_TRAFFIC["bytes_per_frame"] * B) if ok else None,
