@@ -1,17 +1,21 @@
 // Per-cell threshold applied to FAST score maps in place.
 //
-// After the general FAST kernel the maps hold s(p) where s(p) >= t_lo, and
-// each cell (anchored at the border) has a flag "some pixel scores >= t_hi".
-// This pass turns them into the candidate scores NMS keys on,
+// After the general FAST kernel the maps hold s(p) where s(p) >= t_lo.  Each
+// cell (anchored at the border) is flagged when some pixel scores >= t_hi --
+// by FAST itself, or here (FLAGS) from the maps, band by band.  This pass
+// turns the maps into the candidate scores NMS keys on,
 // S(p) = s(p) if s(p) >= T(cell(p)) else 0 with T = t_hi in flagged cells:
 // in a flagged cell the bytes below t_hi are cleared.  On the learned path it
 // also clears the scores outside the proposed 32 x 32 tiles.
 //
-// One block per band of cell rows (one cell high) of one image: the block
-// writes, for up to 4096 columns at a time, a byte 0xFF where the column's
-// cell in this band is flagged (all rows of a band share their cells' flags),
-// then its warps stream the band's rows in 16-byte chunks against that mask,
-// four chunks in flight per lane, writing a chunk back only when it changes.
+// One block per band of cell rows (one cell high) of one image.  With FLAGS
+// the block first ORs, per lane and 16-byte chunk, the bytes >= t_hi over the
+// band's rows, maps them to cells in shared memory and stores the band's
+// flags.  Then it writes, for up to 4096 columns at a time, a byte 0xFF where
+// the column's cell in this band is flagged (all rows of a band share their
+// cells' flags), and its warps stream the band's rows in 16-byte chunks
+// against that mask, four chunks in flight per lane, writing a chunk back
+// only when it changes (the second read of a band mostly hits L1/L2).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,12 +38,18 @@ __device__ __forceinline__ uint32_t apply_word(uint32_t v, uint32_t fm, uint32_t
     return v & ~(fm & bytes_below(v, t_hi));
 }
 
+// 0xFF in each byte of v that is >= t.
+__device__ __forceinline__ uint32_t bytes_at_least(uint32_t v, uint32_t t) { return ~bytes_below(v, t); }
+
+template <bool FLAGS>
 __global__ void __launch_bounds__(CA_THREADS)
 k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ band_prefix,
              int n_list, int n_bands, int t_hi, int t_lo, int border, int cell) {
     __shared__ __align__(16) uint8_t colmask[16 * CA_SEG];
+    __shared__ uint32_t bflag[FLAGS ? CA_MAX_CELLS : 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool cells = t_hi != t_lo;
+    const uint32_t magic = 0xFFFFFFFFu / (uint32_t)cell + 1u;  // n / cell == umulhi(n, magic) for n < 2^16
     for (int band = blockIdx.x; band < n_bands; band += gridDim.x) {
         const int j = find_tile_job(band_prefix, n_list, band);
         const Img& I = imgs[__ldg(list + j)];
@@ -48,8 +58,58 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
         const int rx1 = I.w - border, ry1 = I.h - border;
         const int xb0 = border & ~15;  // first chunk column
         const int n_chunks = (rx1 - xb0 + 15) >> 4;
-        const uint32_t* crow = I.cell + (size_t)cy * I.ncx;
+        uint32_t* crow = I.cell + (size_t)cy * I.ncx;
         const int y0 = border + cy * cell, y1 = min(y0 + cell, ry1);
+        const uint32_t* fl = crow;
+        if (FLAGS && cells) {
+            __syncthreads();  // the previous band's readers are done with bflag and colmask
+            for (int i = tid; i < I.ncx; i += CA_THREADS) bflag[i] = 0u;
+            __syncthreads();
+            for (int c0 = 0; c0 < n_chunks; c0 += 128) {
+                uint4 acc[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[k] = make_uint4(0u, 0u, 0u, 0u);
+                for (int y = y0 + warp; y < y1; y += CA_THREADS / 32) {
+                    const uint8_t* srow = I.score + (size_t)y * I.spitch;
+                    const int py = (y - border) >> 5;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int c = c0 + lane + 32 * k;
+                        if (c >= n_chunks) continue;
+                        const int x = xb0 + 16 * c;
+                        // Scores outside proposed tiles are stale: they do not count.
+                        if (I.pmask && I.pmask[(size_t)py * 4 * I.tiles_x + ((x - I.tile_x0) >> 5)] == 0) continue;
+                        const uint4 v = *reinterpret_cast<const uint4*>(srow + x);
+                        acc[k].x |= bytes_at_least(v.x, (uint32_t)t_hi);
+                        acc[k].y |= bytes_at_least(v.y, (uint32_t)t_hi);
+                        acc[k].z |= bytes_at_least(v.z, (uint32_t)t_hi);
+                        acc[k].w |= bytes_at_least(v.w, (uint32_t)t_hi);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int c = c0 + lane + 32 * k;
+                    if (c >= n_chunks) continue;
+                    const int x = xb0 + 16 * c;
+                    const uint32_t wd[4] = {acc[k].x, acc[k].y, acc[k].z, acc[k].w};
+                    int last = -1;  // last cell flagged by this chunk (adjacent bytes share cells)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int xx = x + i;
+                        if (((wd[i >> 2] >> (8 * (i & 3))) & 1u) && xx >= border && xx < rx1) {
+                            const int cx = (int)__umulhi((uint32_t)(xx - border), magic);
+                            if (cx != last) {
+                                atomicOr(&bflag[cx], 1u);
+                                last = cx;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i < I.ncx; i += CA_THREADS) crow[i] = bflag[i];
+            fl = bflag;
+        }
         for (int s0 = 0; s0 < n_chunks; s0 += CA_SEG) {
             const int s1 = min(s0 + CA_SEG, n_chunks);
             __syncthreads();  // earlier readers of colmask are done
@@ -64,7 +124,8 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int xx = x + 4 * q + i;
-                            if (xx >= border && xx < rx1 && crow[(xx - border) / cell]) m |= 0xFFu << (8 * i);
+                            if (xx >= border && xx < rx1 && fl[(int)__umulhi((uint32_t)(xx - border), magic)])
+                                m |= 0xFFu << (8 * i);
                         }
                     }
                     w[q] = m;
@@ -111,10 +172,15 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
 }
 
 void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
-                       int t_hi, int t_lo, int border, int cell, int grid, void* stream) {
+                       int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags) {
     if (n_bands <= 0) return;
-    k_cell_apply<<<grid < n_bands ? grid : n_bands, CA_THREADS, 0, (cudaStream_t)stream>>>(
-        imgs, img_list, band_prefix, n_list, n_bands, t_hi, t_lo, border, cell);
+    grid = grid < n_bands ? grid : n_bands;
+    if (flags)
+        k_cell_apply<true><<<grid, CA_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, band_prefix, n_list,
+                                                                           n_bands, t_hi, t_lo, border, cell);
+    else
+        k_cell_apply<false><<<grid, CA_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, band_prefix, n_list,
+                                                                            n_bands, t_hi, t_lo, border, cell);
 }
 
 }  // namespace ofk

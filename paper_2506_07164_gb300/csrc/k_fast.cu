@@ -139,7 +139,9 @@ constexpr int FAST_BUF = (FAST_BOX + 127) / 128 * 128;  // buffer stride in shar
 
 // Persistent: each block walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // Thread 0 fetches the next tile by TMA into the other buffer while the
-// block scores the current one.
+// block scores the current one.  FLAGS: also set the per-cell "a pixel
+// scores >= t_hi" flags (else the threshold pass computes them).
+template <bool FLAGS>
 __global__ void __launch_bounds__(DET_THREADS, 3)
 k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
        const int32_t* __restrict__ prefix, int n_list, int n_tiles, const CUtensorMap* __restrict__ maps,
@@ -150,7 +152,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     __shared__ uint32_t sflag[MAX_CELLS_LOCAL];
 
     const int tid = threadIdx.x;
-    const bool cells = t_hi != t_lo;
+    const bool cells = FLAGS && t_hi != t_lo;
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
@@ -273,16 +275,21 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
 
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
                  int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
-                 int cell, int grid, int order, void* stream) {
+                 int cell, int grid, int order, void* stream, bool flags) {
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
-    k_fast<<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles,
-                                                            maps, call, t_hi, t_lo, border, cell, order);
+    if (flags)
+        k_fast<true><<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles,
+                                                                      maps, call, t_hi, t_lo, border, cell, order);
+    else
+        k_fast<false><<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles,
+                                                                       maps, call, t_hi, t_lo, border, cell, order);
 }
 
 int fast_blocks_per_sm() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast, DET_THREADS, 0) != cudaSuccess || n < 1) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<true>, DET_THREADS, 0) != cudaSuccess || n < 1)
+        n = 1;
     return n;
 }
 

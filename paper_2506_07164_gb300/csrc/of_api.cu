@@ -227,6 +227,7 @@ struct Plan {
     std::vector<Group> groups[kMaxGroups + 1];
     std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows;
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
+    bool apply_flags = false;    // the threshold pass sets the cell flags (the general FAST kernel does not)
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
     std::vector<int> rt_bps;        // TMA resize resident blocks per SM of level l
     int det_tiles = 0, max_quota = 0, total_slots = 0, n_img = 0;
@@ -359,12 +360,12 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
             else
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, !P->apply_flags);
             break;
         case 2:
             if (!(P->cell_tiles && P->tun.fast_cell_tiles))
                 launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list, G.n_bands,
-                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st);
+                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st, P->apply_flags);
             launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                               P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                               H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, true);
@@ -460,6 +461,10 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->n_img = nf * nl;
     // Cell tiles: FAST applies the per-cell threshold itself (cells of 8..30 pixels).
     P->cell_tiles = s.cell >= CT_MIN_CELL && s.cell <= CT_MAX_CELL;
+    // The threshold pass flags the cells itself when a band's cells fit its shared array.
+    P->apply_flags = true;
+    for (const auto& L : P->lay.img)
+        if (L.ncx > CA_MAX_CELLS) P->apply_flags = false;
     uint8_t* A = H->arena;
 
     // Image descriptors.
