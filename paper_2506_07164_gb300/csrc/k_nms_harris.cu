@@ -27,15 +27,11 @@
 
 namespace ofk {
 
-constexpr int QCAP = TILE_W * TILE_H / 4;        // strict maxima are never adjacent
-constexpr int S_ROWS = TILE_H + 2;
-constexpr int S_BOX = S_ROWS * SROW;             // 5440
+constexpr int S_BOX = SCORE_BOX_ROWS * SROW;     // 5440
 constexpr int I_BOX = IMG_BOX_ROWS * SROW;       // 6400
-constexpr int S_BUF = (S_BOX + 127) / 128 * 128;
 constexpr int S_W0 = HALO_X / 4 - 1;             // first staged word the 3x3 test reads (X0-4)
 constexpr int S_WORDS = TILE_W / 4 + 2;          // words X0-4 .. X0+TILE_W+3
 constexpr int S_GROUPS = DET_THREADS / S_WORDS;  // row groups of the S(p) pass
-constexpr int I_BUF = (I_BOX + 127) / 128 * 128;
 
 // 0xFF in each byte of v that is below t (t <= 255).
 __device__ __forceinline__ uint32_t bytes_lt(uint32_t v, uint32_t t) {
@@ -83,22 +79,49 @@ struct NmsTile {
     int32_t img, x0, y0;
 };
 
+// Geometry of TH-row NMS tiles: the score box (34 rows) and the image box (40
+// rows) are loaded as many times as the tile's rows need, stacked in shared
+// memory on 128-byte boundaries (a 64-row tile takes two of each): score box k
+// lands at staged row 32k (its first two rows repeat the previous box's last
+// two, same bytes), image box k at staged row 40k.
+template <int TH>
+struct NmsGeom {
+    static constexpr int RPT_N = TH / 8;                                    // rows per thread
+    static constexpr int S_ROWS_N = TH + 2;                                 // score rows Y0-1 .. Y0+TH
+    static constexpr int S_STEP = 32;                                       // staged rows between score boxes
+    static constexpr int S_LOADS = (S_ROWS_N - SCORE_BOX_ROWS + S_STEP - 1) / S_STEP + 1;
+    static constexpr int I_LOADS = (TH + 8 + IMG_BOX_ROWS - 1) / IMG_BOX_ROWS;  // image rows Y0-4 .. Y0+TH+3
+    static constexpr int S_BUF_N = (((S_LOADS - 1) * S_STEP + SCORE_BOX_ROWS) * SROW + 127) / 128 * 128;
+    static constexpr int I_BUF_N = (I_LOADS * I_BOX + 127) / 128 * 128;
+    static constexpr int QCAP_N = TILE_W * TH / 4;                          // strict maxima are never adjacent
+    static constexpr int DYN_BYTES = 2 * I_BUF_N + 2 * S_BUF_N + 4 * QCAP_N + 128;  // + alignment slack
+    static_assert((S_STEP * SROW) % 128 == 0 && I_BOX % 128 == 0, "TMA destinations on 128-byte boundaries");
+};
+
 // FINAL: the score maps already hold S(p) inside the detect region (the
 // cell-tile FAST kernel applied the cell thresholds); the kernel then skips the
 // cell bookkeeping and the candidate pass and masks the region in registers.
-template <bool FINAL>
-__global__ void __launch_bounds__(DET_THREADS, 5)
+// TH: tile rows (32; or 64 with FINAL -- fewer barriers per pixel and ~2x the
+// survivors per Harris phase).  Buffers live in dynamic shared memory
+// (NmsGeom<TH>::DYN_BYTES, from a 128-byte boundary).
+template <bool FINAL, int TH>
+__global__ void __launch_bounds__(DET_THREADS, TH == 32 ? 5 : 4)
 k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
              const int32_t* __restrict__ prefix, int n_list, int n_tiles,
              const CUtensorMap* __restrict__ img_maps, const CUtensorMap* __restrict__ score_maps,
              const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, int order) {
-    __shared__ __align__(128) uint8_t ibuf[2 * I_BUF];
-    __shared__ __align__(128) uint8_t sbuf[2 * S_BUF];
+    using G = NmsGeom<TH>;
+    static_assert(FINAL || TH == TILE_H, "the cell bookkeeping path uses 32-row tiles");
+    constexpr int RPT = G::RPT_N, S_ROWS = G::S_ROWS_N, S_BUF = G::S_BUF_N, I_BUF = G::I_BUF_N;
+    extern __shared__ __align__(128) uint8_t nms_dyn_raw[];
+    uint8_t* nms_dyn = nms_dyn_raw + ((128u - (smem_u32(nms_dyn_raw) & 127u)) & 127u);
+    uint8_t* ibuf = nms_dyn;
+    uint8_t* sbuf = nms_dyn + 2 * I_BUF;
+    uint32_t* queue = reinterpret_cast<uint32_t*>(nms_dyn + 2 * I_BUF + 2 * S_BUF);
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ NmsTile tinfo[2];
-    __shared__ uint32_t sflag[MAX_CELLS_LOCAL];
-    __shared__ int32_t rcell[S_ROWS];   // staged row -> (local cell row) * lcw
-    __shared__ uint32_t queue[QCAP];
+    __shared__ uint32_t sflag[FINAL ? 1 : MAX_CELLS_LOCAL];
+    __shared__ int32_t rcell[FINAL ? 1 : S_ROWS];   // staged row -> (local cell row) * lcw
     __shared__ int nq, qbase;
 
     const int tid = threadIdx.x;
@@ -114,13 +137,19 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int ii = __ldg(list + j);
         const Img& I = imgs[ii];
         const int tt = t - __ldg(prefix + j);
-        const int x0 = I.tile_x0 + (tt % I.tiles_x) * TILE_W, y0 = border + (tt / I.tiles_x) * TILE_H;
+        const int x0 = I.tile_x0 + (tt % I.tiles_x) * TILE_W, y0 = border + (tt / I.tiles_x) * TH;
         tinfo[b] = NmsTile{ii, x0, y0};
         tensormap_acquire(score_maps + ii);
         tensormap_acquire(img_maps + ii);
-        mbar_arrive_expect_tx(&mbar[b], S_BOX + I_BOX);
-        tma_load_2d(sbuf + b * S_BUF, score_maps + ii, x0 - HALO_X, y0 - 1, &mbar[b]);
-        tma_load_2d(ibuf + b * I_BUF, img_maps + ii, x0 - HALO_X, y0 - 4, &mbar[b]);
+        mbar_arrive_expect_tx(&mbar[b], G::S_LOADS * S_BOX + G::I_LOADS * I_BOX);
+#pragma unroll
+        for (int k = 0; k < G::S_LOADS; ++k)
+            tma_load_2d(sbuf + b * S_BUF + k * G::S_STEP * SROW, score_maps + ii, x0 - HALO_X,
+                        y0 - 1 + k * G::S_STEP, &mbar[b]);
+#pragma unroll
+        for (int k = 0; k < G::I_LOADS; ++k)
+            tma_load_2d(ibuf + b * I_BUF + k * I_BOX, img_maps + ii, x0 - HALO_X, y0 - 4 + k * IMG_BOX_ROWS,
+                        &mbar[b]);
     };
     const int g = gridDim.x;
     if (tid == 0 && tile_of(order, blockIdx.x, g, n_tiles, 0) < n_tiles) issue(tile_of(order, blockIdx.x, g, n_tiles, 0), 0);
@@ -156,7 +185,10 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         // Learned path: no survivor can lie in a work tile whose proposal tiles are all off.
         if (I.pmask) {
             const int tx = (X0 - I.tile_x0) / TILE_W, tyt = (Y0 - border) / TILE_H;
-            if (*reinterpret_cast<const uint32_t*>(I.pmask + (size_t)tyt * 4 * I.tiles_x + 4 * tx) == 0u) {
+            uint32_t on = 0u;
+            for (int k = 0; k < TH / TILE_H && tyt + k < I.tiles_y; ++k)
+                on |= *reinterpret_cast<const uint32_t*>(I.pmask + (size_t)(tyt + k) * 4 * I.tiles_x + 4 * tx);
+            if (on == 0u) {
                 fence_proxy_async_smem();
                 __syncthreads();
                 continue;
@@ -168,7 +200,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int cx0 = (max(X0 - 1, rx0) - rx0) / cell;
         const int cy0 = (max(Y0 - 1, ry0) - ry0) / cell;
         const int lcw = (TILE_W + 2) / cell + 2;
-        const int lch = (TILE_H + 2) / cell + 2;
+        const int lch = (TH + 2) / cell + 2;
         if (cells && !FINAL) {
             // Cell flags of the tile, and the cell row of each staged row.
             for (int i = tid; i < lcw * lch; i += blockDim.x) {
@@ -325,26 +357,50 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     }
 }
 
+template <bool FINAL, int TH>
+void launch_nms_t(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list, int n_tiles,
+                  const CUtensorMap* img_maps, const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,
+                  int border, int cell, int grid, int order, void* stream) {
+    k_nms_harris<FINAL, TH><<<grid, DET_THREADS, NmsGeom<TH>::DYN_BYTES, (cudaStream_t)stream>>>(
+        imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, order);
+}
+
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                        int n_list, int n_tiles, const CUtensorMap* img_maps, const CUtensorMap* score_maps,
                        const Call* call, int t_hi, int t_lo, int border, int cell, int grid, int order,
-                       void* stream, bool final_scores) {
+                       void* stream, bool final_scores, int tile_h) {
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
-    if (final_scores)
-        k_nms_harris<true><<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(
-            imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, order);
+    if (!final_scores)
+        launch_nms_t<false, 32>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
+                                border, cell, grid, order, stream);
+    else if (tile_h == 64)
+        launch_nms_t<true, 64>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
+                               border, cell, grid, order, stream);
     else
-        k_nms_harris<false><<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(
-            imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, order);
+        launch_nms_t<true, 32>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
+                               border, cell, grid, order, stream);
 }
 
-int nms_blocks_per_sm() {
+// Resident blocks per SM of the NMS kernel with TH-row tiles (final scores;
+// the 32-row general variant has the same occupancy).  Raises the dynamic
+// shared-memory limit where the buffers need it.
+int nms_blocks_per_sm(int tile_h) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_harris<false>, DET_THREADS, 0) != cudaSuccess ||
-        n < 1)
-        n = 1;
-    return n;
+    cudaError_t e;
+    if (tile_h == 64) {
+        e = cudaFuncSetAttribute(k_nms_harris<true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 NmsGeom<64>::DYN_BYTES);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_harris<true, 64>, DET_THREADS,
+                                                              NmsGeom<64>::DYN_BYTES);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_harris<false, 32>, DET_THREADS,
+                                                          NmsGeom<32>::DYN_BYTES);
+    }
+    return (e != cudaSuccess || n < 1) ? 1 : n;
 }
+
+int nms_blocks_per_sm() { return nms_blocks_per_sm(32); }
 
 }  // namespace ofk

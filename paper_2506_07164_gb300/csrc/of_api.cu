@@ -219,13 +219,14 @@ struct Plan {
         int img_begin = 0, n_img = 0;
         int dl_begin = 0, n_list = 0, det_tiles = 0, dp_off = 0;
         int fast_tiles = 0, fp_off = 0;             // cell-tile FAST: tiles and prefix offset in gp_fast
+        int nms64_tiles = 0, np_off = 0;            // NMS with 64-row tiles: tiles and prefix offset in gp_nms64
         int n_bands = 0, rp_off = 0;                // threshold pass: cell rows and prefix offset in gp_rows
         int slot_begin = 0, slot_end = 0;
         std::vector<int> rs_job, rs_n;              // per level: first resize job, jobs
         std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
     };
     std::vector<Group> groups[kMaxGroups + 1];
-    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows;
+    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64;
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
     bool apply_flags = false;    // the threshold pass sets the cell flags (the general FAST kernel does not)
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
@@ -234,7 +235,7 @@ struct Plan {
     Call h_call{};
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0;
-    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0;
+    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -266,6 +267,7 @@ struct Plan {
     const int32_t* d_grs() const { return reinterpret_cast<const int32_t*>(dbuf + off_grs); }
     const int32_t* d_gfp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfp); }
     const int32_t* d_grp() const { return reinterpret_cast<const int32_t*>(dbuf + off_grp); }
+    const int32_t* d_gnp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gnp); }
 };
 
 // Resident blocks per SM of the plan's FAST kernel.
@@ -366,9 +368,16 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
             if (!(P->cell_tiles && P->tun.fast_cell_tiles))
                 launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list, G.n_bands,
                                   s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st, P->apply_flags);
-            launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
-                              P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                              H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, true);
+            if (P->tun.nms_tile_h == 64)
+                launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list,
+                                  G.nms64_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
+                                  s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, true,
+                                  64);
+            else
+                launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list,
+                                  G.det_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
+                                  s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, true,
+                                  32);
             break;
         case 3:
             launch_select(P->d_img() + G.img_begin, G.n_img, P->d_call(), P->max_quota, st);
@@ -615,8 +624,11 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             G.det_tiles = (j1 < nd ? P->det_prefix[j1] : P->det_tiles) - t0;
             G.fp_off = (int)P->gp_fast.size();
             G.rp_off = (int)P->gp_rows.size();
+            G.np_off = (int)P->gp_nms64.size();
             for (int j = j0; j < j1; ++j) {
                 const Img& I = P->h_img[P->det_list[j]];
+                P->gp_nms64.push_back(G.nms64_tiles);
+                G.nms64_tiles += I.tiles_x * ((I.h - 2 * s.border + 63) / 64);
                 P->gp_fast.push_back(G.fast_tiles);
                 G.fast_tiles += I.ftiles_x * I.ncy;
                 P->gp_rows.push_back(G.n_bands);
@@ -671,7 +683,9 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.stream_groups = 1;
     P->tun.fast_cell_tiles = P->cell_tiles ? 1 : 0;
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
-    P->tun.nms_blocks_per_sm = nms_blocks_per_sm();
+    P->tun.nms_tile_h = 32;
+    P->tun.nms_blocks_per_sm = nms_blocks_per_sm(32);
+    nms_blocks_per_sm(64);  // raises the 64-row kernel's shared-memory limit before any capture
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
 
@@ -723,6 +737,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_fast.size(), 1), 16);
     P->off_grp = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_rows.size(), 1), 16);
+    P->off_gnp = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_nms64.size(), 1), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -747,6 +763,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_grs, P->gp_rs.data(), sizeof(int32_t) * P->gp_rs.size());
     put(P->off_gfp, P->gp_fast.data(), sizeof(int32_t) * P->gp_fast.size());
     put(P->off_grp, P->gp_rows.data(), sizeof(int32_t) * P->gp_rows.size());
+    put(P->off_gnp, P->gp_nms64.data(), sizeof(int32_t) * P->gp_nms64.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);
@@ -1010,11 +1027,15 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     P->tun.fast_blocks_per_sm = bb;
     P->tun.fast_order = bo;
     P->tun.fast_ms = best;
-    // NMS + Harris (appends candidates: clear the counters before each run).
+    // NMS + Harris (appends candidates: clear the counters before each run),
+    // 32- or 64-row tiles.
     best = 1e30f;
     bb = P->tun.nms_blocks_per_sm, bo = 0;
-    for (int bp = 1; bp <= nms_blocks_per_sm() && rc == OF_OK; ++bp) {
+    int bth = P->tun.nms_tile_h;
+    for (int th = 32; th <= 64 && rc == OF_OK; th += 32)
+    for (int bp = 1; bp <= nms_blocks_per_sm(th) && rc == OF_OK; ++bp) {
         for (int order = 0; order < 2 && rc == OF_OK; ++order) {
+            P->tun.nms_tile_h = th;
             P->tun.nms_blocks_per_sm = bp;
             P->tun.nms_order = order;
             float ms = 0.f;
@@ -1024,9 +1045,10 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
                     enqueue_stages(H, P, 2, 3, st);
                 },
                 &ms);
-            if (ms < best) best = ms, bb = bp, bo = order;
+            if (ms < best) best = ms, bb = bp, bo = order, bth = th;
         }
     }
+    P->tun.nms_tile_h = bth;
     P->tun.nms_blocks_per_sm = bb;
     P->tun.nms_order = bo;
     P->tun.nms_ms = best;
@@ -1246,7 +1268,8 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         (t->resize_tma != 0 && t->resize_tma != 1) || t->fast_blocks_per_sm < 1 ||
         t->fast_blocks_per_sm > std::max(fast_blocks_per_sm(), fast_cells_blocks_per_sm(CT_MAX_CELL)) ||
         t->nms_blocks_per_sm < 1 ||
-        t->nms_blocks_per_sm > nms_blocks_per_sm() || (t->fast_order != 0 && t->fast_order != 1) ||
+        (t->nms_tile_h != 32 && t->nms_tile_h != 64) ||
+        t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h == 64 ? 64 : 32) || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
         (t->fast_cell_tiles != 0 && t->fast_cell_tiles != 1))
         return fail(OF_ERR_ARG, "tuning field out of range");
@@ -1259,6 +1282,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     P->tun.fast_cell_tiles = P->cell_tiles ? t->fast_cell_tiles : 0;
     P->tun.fast_blocks_per_sm = std::min(t->fast_blocks_per_sm, plan_fast_bps(P));
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
+    P->tun.nms_tile_h = t->nms_tile_h;
     P->tun.fast_order = t->fast_order;
     P->tun.nms_order = t->nms_order;
     P->tun.stream_groups = std::min(t->stream_groups, (int)P->frames.size());

@@ -130,7 +130,8 @@ void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* 
                        int n_list, int n_tiles, const CUtensorMap* img_maps,
                        const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,
                        int border, int cell, int grid, int order, void* stream,
-                       bool final_scores = false);
+                       bool final_scores = false, int tile_h = 32);
+int nms_blocks_per_sm(int tile_h);
 void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, void* stream);
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
 // Slots [slot_begin, slot_end) of images [img_begin, img_begin + n_img) (one frame group).
