@@ -145,7 +145,7 @@ def serving_leg(pool, seconds: float, rate: float, seed: int = 0):
 
 
 TUNING_FIELDS = ("resize_tile_h", "fast_blocks_per_sm", "nms_blocks_per_sm", "fast_order", "nms_order", "resize_tma",
-                 "stream_groups", "fast_cell_tiles", "nms_tile_h")
+                 "stream_groups", "fast_cell_tiles", "nms_tile_h", "fast_tile_h")
 
 # The paper's variant pipelines (Table 2; Figs. 8-9 order them by runtime, slowest first).
 ABLATION_PIPELINES = [("Baseline_ORB", 0, 0), ("Binary_ORB", 1, 0), ("SM_ORB", 3, 0), ("Sep_ORB", 3, 1),

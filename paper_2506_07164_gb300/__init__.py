@@ -54,6 +54,7 @@ class OfTuning(C.Structure):
     _fields_ = [("resize_tile_h", C.c_int32), ("fast_blocks_per_sm", C.c_int32),
                 ("nms_blocks_per_sm", C.c_int32), ("fast_order", C.c_int32), ("nms_order", C.c_int32),
                 ("resize_tma", C.c_int32), ("stream_groups", C.c_int32), ("fast_cell_tiles", C.c_int32), ("nms_tile_h", C.c_int32),
+                ("fast_tile_h", C.c_int32),
                 ("candidates_tried", C.c_int32), ("resize_ms", C.c_float), ("fast_ms", C.c_float),
                 ("nms_ms", C.c_float)]
 

@@ -125,13 +125,13 @@ struct TileInfo {
 
 __device__ __forceinline__ TileInfo tile_info(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                                               const int32_t* __restrict__ prefix, int n_list, int t,
-                                              int border) {
+                                              int border, int tile_h) {
     const int j = find_tile_job(prefix, n_list, t);
     const int ii = __ldg(list + j);
     const Img& I = imgs[ii];
     const int tt = t - __ldg(prefix + j);
     const int tx = tt % I.tiles_x, ty = tt / I.tiles_x;
-    return TileInfo{ii, I.tile_x0 + tx * TILE_W, border + ty * TILE_H};
+    return TileInfo{ii, I.tile_x0 + tx * TILE_W, border + ty * tile_h};
 }
 
 constexpr int FAST_BOX = IMG_BOX_ROWS * SROW;           // bytes per TMA box (160 x 40)
@@ -140,13 +140,19 @@ constexpr int FAST_BUF = (FAST_BOX + 127) / 128 * 128;  // buffer stride in shar
 // Persistent: each block walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // Thread 0 fetches the next tile by TMA into the other buffer while the
 // block scores the current one.  FLAGS: also set the per-cell "a pixel
-// scores >= t_hi" flags (else the threshold pass computes them).
-template <bool FLAGS>
-__global__ void __launch_bounds__(DET_THREADS, 3)
+// scores >= t_hi" flags (else the threshold pass computes them).  TH: tile
+// rows, 32 or (without FLAGS) 64 -- a 64-row tile stacks two image boxes and
+// halves the barriers per pixel and the staged rows per output row.
+template <bool FLAGS, int TH>
+__global__ void __launch_bounds__(DET_THREADS, TH == 32 ? 3 : 2)
 k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
        const int32_t* __restrict__ prefix, int n_list, int n_tiles, const CUtensorMap* __restrict__ maps,
        const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, int order) {
-    __shared__ __align__(128) uint8_t sbuf[2 * FAST_BUF];
+    static_assert(!FLAGS || TH == TILE_H, "the cell-flag variant uses 32-row tiles");
+    constexpr int RPT = TH / 8;                                    // rows per thread
+    constexpr int LOADS = (TH + 8 + IMG_BOX_ROWS - 1) / IMG_BOX_ROWS;  // image boxes per tile
+    constexpr int BUF = LOADS * FAST_BUF;
+    __shared__ __align__(128) uint8_t sbuf[2 * BUF];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ TileInfo tinfo[2];
     __shared__ uint32_t sflag[MAX_CELLS_LOCAL];
@@ -161,11 +167,14 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     for (int i = tid; i < MAX_CELLS_LOCAL; i += blockDim.x) sflag[i] = 0u;
     __syncthreads();
     auto issue = [&](int t, int b) {
-        const TileInfo ti = tile_info(imgs, list, prefix, n_list, t, border);
+        const TileInfo ti = tile_info(imgs, list, prefix, n_list, t, border, TH);
         tinfo[b] = ti;
         tensormap_acquire(maps + ti.img);
-        mbar_arrive_expect_tx(&mbar[b], FAST_BOX);
-        tma_load_2d(sbuf + b * FAST_BUF, maps + ti.img, ti.x0 - HALO_X, ti.y0 - 4, &mbar[b]);
+        mbar_arrive_expect_tx(&mbar[b], LOADS * FAST_BOX);
+#pragma unroll
+        for (int k = 0; k < LOADS; ++k)
+            tma_load_2d(sbuf + b * BUF + k * FAST_BOX, maps + ti.img, ti.x0 - HALO_X, ti.y0 - 4 + k * IMG_BOX_ROWS,
+                        &mbar[b]);
     };
     const int g = gridDim.x;
     if (tid == 0 && tile_of(order, blockIdx.x, g, n_tiles, 0) < n_tiles) issue(tile_of(order, blockIdx.x, g, n_tiles, 0), 0);
@@ -192,15 +201,21 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         }
         const TileInfo ti = tinfo[b];
         const Img& I = imgs[ti.img];
-        const uint8_t* s = sbuf + b * FAST_BUF;
+        const uint8_t* s = sbuf + b * BUF;
         const int X0 = ti.x0, Y0 = ti.y0;
-        // Learned path: the 4 proposal tiles of this work tile; skip it when all are off.
-        uint32_t pm = 0xFFFFFFFFu;
+        // Learned path: the 4 proposal tiles of each 32-row band of this work
+        // tile; skip the tile when all are off.  A warp's rows lie in one band.
+        uint32_t pm = 0xFFFFFFFFu, pm_any = 0xFFFFFFFFu;
         if (I.pmask) {
             const int tx = (X0 - I.tile_x0) / TILE_W, tyt = (Y0 - border) / TILE_H;
-            pm = *reinterpret_cast<const uint32_t*>(I.pmask + (size_t)tyt * 4 * I.tiles_x + 4 * tx);
+            const int band = tyt + (ty * RPT) / TILE_H;
+            pm = band < I.tiles_y ? *reinterpret_cast<const uint32_t*>(I.pmask + (size_t)band * 4 * I.tiles_x + 4 * tx)
+                                  : 0u;
+            pm_any = 0u;
+            for (int k = 0; k < TH / TILE_H && tyt + k < I.tiles_y; ++k)
+                pm_any |= *reinterpret_cast<const uint32_t*>(I.pmask + (size_t)(tyt + k) * 4 * I.tiles_x + 4 * tx);
         }
-        if (pm == 0u) {
+        if (pm_any == 0u) {
             __syncthreads();
             continue;
         }
@@ -260,7 +275,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         }
         if (cells) {
             __syncthreads();
-            const int lch = TILE_H / cell + 2;
+            const int lch = TH / cell + 2;
             for (int i = tid; i < lcw * lch; i += blockDim.x) {
                 if (sflag[i]) {
                     const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
@@ -275,22 +290,35 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
 
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
                  int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
-                 int cell, int grid, int order, void* stream, bool flags) {
+                 int cell, int grid, int order, void* stream, bool flags, int tile_h) {
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
+    const cudaStream_t st = (cudaStream_t)stream;
     if (flags)
-        k_fast<true><<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles,
-                                                                      maps, call, t_hi, t_lo, border, cell, order);
+        k_fast<true, 32><<<grid, DET_THREADS, 0, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps, call, t_hi,
+                                                        t_lo, border, cell, order);
+    else if (tile_h == 64)
+        k_fast<false, 64><<<grid, DET_THREADS, 0, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps, call,
+                                                         t_hi, t_lo, border, cell, order);
     else
-        k_fast<false><<<grid, DET_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles,
-                                                                       maps, call, t_hi, t_lo, border, cell, order);
+        k_fast<false, 32><<<grid, DET_THREADS, 0, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps, call,
+                                                         t_hi, t_lo, border, cell, order);
 }
 
 int fast_blocks_per_sm() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<true>, DET_THREADS, 0) != cudaSuccess || n < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<true, 32>, DET_THREADS, 0) != cudaSuccess || n < 1)
         n = 1;
     return n;
+}
+
+// Resident blocks per SM of the flag-free kernel with tile_h-row tiles.
+int fast_blocks_per_sm(int tile_h) {
+    int n = 0;
+    const cudaError_t e = tile_h == 64
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<false, 64>, DET_THREADS, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<false, 32>, DET_THREADS, 0);
+    return (e != cudaSuccess || n < 1) ? 1 : n;
 }
 
 // ---------------------------------------------------------------------------

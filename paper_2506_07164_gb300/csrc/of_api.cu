@@ -272,7 +272,8 @@ struct Plan {
 
 // Resident blocks per SM of the plan's FAST kernel.
 int plan_fast_bps(const Plan* P) {
-    return (P->cell_tiles && P->tun.fast_cell_tiles) ? fast_cells_blocks_per_sm(P->s.cell) : fast_blocks_per_sm();
+    if (P->cell_tiles && P->tun.fast_cell_tiles) return fast_cells_blocks_per_sm(P->s.cell);
+    return P->apply_flags ? fast_blocks_per_sm(P->tun.fast_tile_h) : fast_blocks_per_sm();
 }
 
 void free_plan(Plan* p) {
@@ -359,10 +360,14 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                 launch_fast_cells(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfp() + G.fp_off, G.n_list, G.fast_tiles,
                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                                   H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+            else if (P->apply_flags && P->tun.fast_tile_h == 64)
+                launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list, G.nms64_tiles,
+                            P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, false, 64);
             else
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, !P->apply_flags);
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, !P->apply_flags, 32);
             break;
         case 2:
             if (!(P->cell_tiles && P->tun.fast_cell_tiles))
@@ -682,6 +687,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.resize_tma = 1;
     P->tun.stream_groups = 1;
     P->tun.fast_cell_tiles = P->cell_tiles ? 1 : 0;
+    P->tun.fast_tile_h = 32;
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
     P->tun.nms_tile_h = 32;
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm(32);
@@ -1003,9 +1009,13 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     // general kernel (+ threshold pass, stage 2), and the cell-tile kernel
     // where the cell size allows it; fast_ms below is FAST + NMS.
     best = 1e30f;
-    int bb = P->tun.fast_blocks_per_sm, bo = 0, bv = P->tun.fast_cell_tiles;
-    for (int v = 0; v <= (P->cell_tiles ? 1 : 0) && rc == OF_OK; ++v) {
+    int bb = P->tun.fast_blocks_per_sm, bo = 0, bv = P->tun.fast_cell_tiles, bt = P->tun.fast_tile_h;
+    // Forms: 0 = general kernel (32- or 64-row tiles when the pass sets the flags), 1 = cell tiles.
+    for (int cand = 0; cand < 3 && rc == OF_OK; ++cand) {
+        const int v = cand == 2 ? 1 : 0, th = cand == 1 ? 64 : 32;
+        if ((v == 1 && !P->cell_tiles) || (th == 64 && !P->apply_flags)) continue;
         P->tun.fast_cell_tiles = v;
+        P->tun.fast_tile_h = th;
         for (int bp = 1; bp <= plan_fast_bps(P) && rc == OF_OK; ++bp) {
             for (int order = 0; order < 2 && rc == OF_OK; ++order) {
                 P->tun.fast_blocks_per_sm = bp;
@@ -1019,11 +1029,12 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
                         enqueue_stages(H, P, 1, 3, st);
                     },
                     &ms);
-                if (ms < best) best = ms, bb = bp, bo = order, bv = v;
+                if (ms < best) best = ms, bb = bp, bo = order, bv = v, bt = th;
             }
         }
     }
     P->tun.fast_cell_tiles = bv;
+    P->tun.fast_tile_h = bt;
     P->tun.fast_blocks_per_sm = bb;
     P->tun.fast_order = bo;
     P->tun.fast_ms = best;
@@ -1268,7 +1279,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         (t->resize_tma != 0 && t->resize_tma != 1) || t->fast_blocks_per_sm < 1 ||
         t->fast_blocks_per_sm > std::max(fast_blocks_per_sm(), fast_cells_blocks_per_sm(CT_MAX_CELL)) ||
         t->nms_blocks_per_sm < 1 ||
-        (t->nms_tile_h != 32 && t->nms_tile_h != 64) ||
+        (t->nms_tile_h != 32 && t->nms_tile_h != 64) || (t->fast_tile_h != 32 && t->fast_tile_h != 64) ||
         t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h == 64 ? 64 : 32) || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
         (t->fast_cell_tiles != 0 && t->fast_cell_tiles != 1))
@@ -1280,6 +1291,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     P->tun.resize_tile_h = t->resize_tile_h;
     P->tun.resize_tma = t->resize_tma;
     P->tun.fast_cell_tiles = P->cell_tiles ? t->fast_cell_tiles : 0;
+    P->tun.fast_tile_h = P->apply_flags ? t->fast_tile_h : 32;
     P->tun.fast_blocks_per_sm = std::min(t->fast_blocks_per_sm, plan_fast_bps(P));
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
     P->tun.nms_tile_h = t->nms_tile_h;

@@ -118,11 +118,13 @@ void launch_resize_tma(const Resize* jobs, const int32_t* tile_prefix, int n_job
 int resize_tma_blocks_per_sm(int buf_bytes);  // also raises the kernel's shared-memory limit
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                  int n_list, int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi,
-                 int t_lo, int border, int cell, int grid, int order, void* stream, bool flags = true);
+                 int t_lo, int border, int cell, int grid, int order, void* stream, bool flags = true,
+                 int tile_h = 32);
 void launch_fast_cells(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
                        int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
                        int cell, int grid, int order, void* stream);
 int fast_cells_blocks_per_sm(int cell);
+int fast_blocks_per_sm(int tile_h);  // the flag-free general kernel
 void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
                        int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags);
 constexpr int CA_MAX_CELLS = 1024;  // cells per band row the threshold pass can flag itself

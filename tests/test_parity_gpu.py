@@ -303,7 +303,7 @@ def test_every_resize_kernel_matches_oracle_levels(scale):
     ora = [[oracle.pyramid_level(im, levels, scale, lv) for lv in range(levels)] for im in imgs]
     for tile_h, tma in [(32, 0), (64, 0), (64, 1)]:
         tun = ofg.OfTuning(resize_tile_h=tile_h, resize_tma=tma, fast_blocks_per_sm=1, nms_blocks_per_sm=1,
-                           stream_groups=1, nms_tile_h=32)
+                           stream_groups=1, nms_tile_h=32, fast_tile_h=32)
         det.set_tuning(dev, tun, levels=levels, scale=scale, fast_t=20, n_features=300)
         det.detect_batch(dev, levels=levels, scale=scale, fast_t=20, n_features=300)
         torch.cuda.synchronize()
@@ -319,10 +319,10 @@ def test_set_tuning_rejects_out_of_range_fields():
     img = torch.from_numpy(synth.scene(320, 240, 3)).cuda()
     det = ofg.Detector(320, 240, max_levels=2, max_features=50)
     good = dict(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=1, nms_blocks_per_sm=1, stream_groups=1,
-                nms_tile_h=32)
+                nms_tile_h=32, fast_tile_h=32)
     for bad in (dict(resize_tile_h=48), dict(resize_tma=2), dict(fast_blocks_per_sm=0),
                 dict(nms_blocks_per_sm=1000), dict(fast_order=2), dict(stream_groups=9), dict(stream_groups=0), dict(fast_cell_tiles=2),
-                dict(nms_tile_h=48)):
+                dict(nms_tile_h=48), dict(fast_tile_h=16)):
         with pytest.raises(ofg.OfError):
             det.set_tuning([img], ofg.OfTuning(**{**good, **bad}), levels=2, n_features=50)
     det.set_tuning([img], ofg.OfTuning(**good), levels=2, n_features=50)
@@ -339,7 +339,8 @@ def test_frame_groups_equal_one_group_and_oracle():
     got = {}
     for groups in (1, 2, 3, 5):
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
-                           stream_groups=groups, nms_tile_h=64 if groups % 2 else 32)
+                           stream_groups=groups, nms_tile_h=64 if groups % 2 else 32,
+                           fast_tile_h=32 if groups % 2 else 64)
         det.set_tuning(dev, tun, levels=6, fast_t=20, n_features=400)
         det.detect_batch(dev, levels=6, fast_t=20, n_features=400)
         torch.cuda.synchronize()
@@ -360,15 +361,16 @@ def test_frame_groups_equal_one_group_and_oracle():
 @pytest.mark.parametrize("cell", [8, 13, 30, 31, 40])
 def test_cell_sizes_both_fast_forms(cell):
     """Both FAST forms -- the cell-tile kernel (cells of 8..30 pixels) and the
-    general kernel followed by the threshold pass -- and both NMS tile heights
-    give the oracle's cell thresholds, candidate scores, survivors and keypoints."""
+    general kernel followed by the threshold pass -- and both FAST and NMS
+    tile heights give the oracle's cell thresholds, candidate scores, survivors
+    and keypoints."""
     img = synth.scene(900, 700, 90 + cell, background="pink")
     dev = torch.from_numpy(img).cuda()
     det = ofg.Detector(900, 700, max_levels=3, max_features=600, fast_t_lo=6, cell=cell)
     ora = oracle.detect(img, levels=3, scale=1.2, fast_t=22, fast_t_lo=6, n_features=600, cell=cell)
-    for form, nms_h in ((0, 32), (1, 64), (0, 64)):
+    for form, nms_h, fast_h in ((0, 32, 32), (1, 64, 32), (0, 64, 64)):
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
-                           stream_groups=1, fast_cell_tiles=form, nms_tile_h=nms_h)
+                           stream_groups=1, fast_cell_tiles=form, nms_tile_h=nms_h, fast_tile_h=fast_h)
         det.set_tuning([dev], tun, levels=3, scale=1.2, fast_t=22, n_features=600)
         det.detect_batch([dev], levels=3, scale=1.2, fast_t=22, n_features=600)
         torch.cuda.synchronize()
