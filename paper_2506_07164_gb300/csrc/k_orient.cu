@@ -76,11 +76,19 @@ k_orient(const Img* __restrict__ imgs, int img_begin, int n_img, int slot_begin,
     const int u = lane - 15;
     int m10 = 0, m01 = 0;
     if (u >= -R && u <= R) {
-        for (int v = -R; v <= R; ++v) {
-            if (u * u + v * v <= R * R) {
-                const int iv = __ldg(img + (size_t)(y + v) * pitch + (x + u));
-                m10 += u * iv;
-                m01 += v * iv;
+        // Rows in groups of 8 so that each lane has 8 loads in flight.
+        const uint8_t* col = img + (size_t)y * pitch + (x + u);
+        for (int v0 = -R; v0 <= R; v0 += 8) {
+            int iv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int v = v0 + k;
+                iv[k] = (v <= R && u * u + v * v <= R * R) ? __ldg(col + (ptrdiff_t)v * pitch) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                m10 += u * iv[k];
+                m01 += (v0 + k) * iv[k];
             }
         }
     }

@@ -137,6 +137,35 @@ def test_fig6_pattern_images(case):
     det.close()
 
 
+@pytest.mark.parametrize("n_features", [1, 16, 64, 300])
+def test_top_n_with_many_equal_keys(n_features):
+    """A tiled image repeats every candidate's key hundreds of times, so the
+    bin of the n-th best key holds more candidates than the sort buffer: the
+    exact radix select decides, and ties fall back to (y, x)."""
+    patch = synth.scene(24, 20, 9)
+    img = np.ascontiguousarray(np.tile(patch, (24, 20))[:480, :480])
+    det = ofg.Detector(480, 480, max_levels=1, max_features=300)
+    kp = det.detect(torch.from_numpy(img).cuda(), levels=1, fast_t=20, n_features=n_features)
+    ora = oracle.detect(img, levels=1, fast_t=20, n_features=n_features)
+    assert len(ora) == n_features and (ora["key"] == ora["key"][0]).sum() == n_features
+    compare_keypoints(kp, ora)
+    det.close()
+
+
+@pytest.mark.parametrize("n_features", [3000, 3400, 3600, 8192])
+def test_top_n_boundary_among_negative_keys(n_features):
+    """At t = 1 most survivors are edge points with negative Harris keys; a
+    large quota puts the n-th best key among them (8192 keeps every survivor)."""
+    img = synth.scene(320, 240, 6, background="pink")
+    det = ofg.Detector(320, 240, max_levels=1, max_features=8192)
+    kp = det.detect(torch.from_numpy(img).cuda(), levels=1, fast_t=1, n_features=n_features)
+    ora = oracle.detect(img, levels=1, fast_t=1, n_features=n_features)
+    if n_features < 8192:
+        assert len(ora) == n_features and ora["key"][-1] < 0
+    compare_keypoints(kp, ora)
+    det.close()
+
+
 # ------------------------------------------------------ ragged, edges
 @pytest.mark.parametrize("w,h,levels", [(333, 217, 3), (129, 77, 2), (1000, 41, 1), (41, 1000, 4),
                                         (161, 161, 5), (40, 40, 3), (38, 200, 2), (2, 3, 8)])
