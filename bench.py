@@ -281,7 +281,7 @@ FAST_OPS_PER_PX = 40.5
 # DRAM bytes of one k_fast launch per frame, from the ncu capture summarised in
 # profiles/k_fast_1080p8.md (64-frame launch, scaled per frame), valid while
 # k_fast.cu has this SHA-1.
-FAST_TRAFFIC = {"sha1": "531301a03ce26e040964a2dd5cc79e48a3400568", "bytes_per_frame": (468686848 + 349728256) / 64}
+FAST_TRAFFIC = {"sha1": "d74caf98bce626ef2ccaf18b8858e6c218d9f852", "bytes_per_frame": (488090624 + 349121024) / 64}
 
 
 def file_sha1(path):
