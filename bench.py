@@ -12,6 +12,8 @@ Reported:
   value        batched path, frames/s (inputs resident in HBM, one
                of_detect_batch call per step, B frames)
   plain        per-frame path (one of_detect_batch call per frame), frames/s
+  mixed        64 frames of uneven sizes (720x540 .. 1920x1080, 8 levels each)
+               in one batched call vs one call per frame, frames/s
   e2e          batched path with host buffers: pinned H2D of the frames and
                D2H of keypoints + counts inside the timed region (double
                buffered: the next step's upload overlaps this step's detection)
@@ -60,6 +62,16 @@ def _oracle_detect(img):
 
 
 SERVE_SIZES = [(640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
+# The uneven-size batch: 64 frames drawn uniformly from these sizes, 8 levels each (~512 images).
+MIXED_SIZES = [(720, 540), (1080, 720), (1440, 1080), (1920, 1080)]
+MIXED_FRAMES = 64
+
+
+def mixed_frames(pool, n: int, seed: int = 3):
+    import numpy as np
+
+    picks = np.random.default_rng(seed).integers(0, len(MIXED_SIZES), n)
+    return pool.map(_gen_sized, [(MIXED_SIZES[k][0], MIXED_SIZES[k][1], 5000 + i) for i, k in enumerate(picks)])
 
 
 def _gen_sized(args):
@@ -387,6 +399,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-buffer path (profiling)")
     ap.add_argument("--skip-learned", action="store_true", help="skip the learned tile-proposal leg")
     ap.add_argument("--skip-ablation", action="store_true", help="skip the paper-variant ablation leg")
+    ap.add_argument("--skip-mixed", action="store_true", help="skip the uneven-size batch leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -494,6 +507,40 @@ def main():
     if not args.skip_plain:
         ms_p, _ = timed(step_plain, plain_steps, 2, nvtx_name="plain_timed")
 
+    # Uneven sizes: one batched call over 64 frames of four sizes (its own
+    # autotuned plan) against one call per frame on the same frames.
+    mixed = None
+    ms_m = ms_mp = float("nan")
+    if not args.skip_mixed:
+        mdev = [torch.from_numpy(a).cuda() for a in mixed_frames(pool, MIXED_FRAMES)]
+        mframes = [(t, t.shape[1], t.shape[0], t.shape[1]) for t in mdev]
+        mdet = ofg.Detector(W_, H_, max_levels=LEVELS, max_features=NFEAT, max_batch=MIXED_FRAMES,
+                            fast_t_lo=FAST_T_LO, stream=stream)
+        with torch.cuda.stream(stream):
+            mtun = ofg.of_autotune(mdet.h, mframes, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, mdet.out,
+                                   mdet.counts, reps=3).as_dict()
+
+        def step_mixed():
+            ofg.of_detect_batch(mdet.h, mframes, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, mdet.out, mdet.counts)
+
+        def step_mixed_plain():
+            for f in mframes:
+                ofg.of_detect_batch(plain.h, [f], LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, plain.out, plain.counts)
+
+        ms_m, _ = timed(step_mixed, args.steps, args.warmup, nvtx_name="mixed_timed")
+        ms_mp, _ = timed(step_mixed_plain, plain_steps, 2, nvtx_name="mixed_plain_timed")
+        # The per-frame path's last call is the batch's last frame: same records.
+        last = MIXED_FRAMES - 1
+        nb, npl = int(mdet.counts[last].item()), int(plain.counts[0].item())
+        same = nb == npl and torch.equal(mdet.out[last * NFEAT * 64:(last * NFEAT + nb) * 64],
+                                         plain.out[: npl * 64])
+        mpx_m = sum(w * h for (_, w, h, _) in mframes) / 1e6
+        mixed = {"frames_per_step": MIXED_FRAMES, "sizes": [f"{w}x{h}" for w, h in MIXED_SIZES],
+                 "base_mpix_per_step": round(mpx_m, 2), "steps": args.steps, "plain_steps": plain_steps,
+                 "last_frame_identical_to_per_frame": bool(same),
+                 "autotune": {k: mtun[k] for k in TUNING_FIELDS}}
+        mdet.close()
+
     # End to end through the public API with host buffers: every step copies
     # its B frames from one pinned host batch to the device (one copy), detects
     # and copies the keypoint records and counts back.  Two device input sets,
@@ -564,11 +611,18 @@ def main():
     per_frame = stage_bytes(lw, lh, cand, kept)
 
     # Max over ranks.
-    ms_b, ms_p, e2e_s = reduce_max_over_ranks([ms_b, ms_p, e2e_s], dist, device="cuda")
+    ms_b, ms_p, e2e_s, ms_m, ms_mp = reduce_max_over_ranks([ms_b, ms_p, e2e_s, ms_m, ms_mp], dist, device="cuda")
 
     value = replicas_value(B * args.steps, world, ms_b)
     plain_fps = replicas_value(plain_frames * plain_steps, world, ms_p)
     e2e_fps = replicas_value(B * e2e_steps, world, e2e_s * 1000.0)
+    if mixed is not None:
+        m_fps = replicas_value(MIXED_FRAMES * args.steps, world, ms_m)
+        mp_fps = replicas_value(MIXED_FRAMES * plain_steps, world, ms_mp)
+        per_frame_mpix = mixed["base_mpix_per_step"] / MIXED_FRAMES
+        mixed.update({"value": round(m_fps, 2), "unit": "frames/s", "mpix_per_s": round(m_fps * per_frame_mpix, 1),
+                      "plain": round(mp_fps, 2), "plain_mpix_per_s": round(mp_fps * per_frame_mpix, 1),
+                      "batched_vs_plain": round(m_fps / mp_fps, 3)})
     mpix = W_ * H_ / 1e6
 
     peak, peak_kind = measured_peaks()
@@ -690,6 +744,7 @@ def main():
                               "step k's detection"},
         "autotune": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tuning.items()},
         "roofline": roofline,
+        "mixed": mixed,
         "learned": learned_out,
         "ablation": ablation,
         "serving": serving,

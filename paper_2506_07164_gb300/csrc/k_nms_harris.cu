@@ -18,7 +18,8 @@
 //    Alg. 3 -- and combines them vertically into gx, gy, accumulating the
 //    exact int32 sums A = sum gx^2, B = sum gy^2, C = sum gx gy over 7 x 7.
 //    key = kden (AB - C^2) - knum (A+B)^2 (int64, exact for k = knum/kden).
-// 4. One atomicAdd per tile reserves the survivors' slots in the image's list.
+// 4. One atomicAdd per warp of the Harris phase reserves its survivors' slots
+//    in the image's list.
 #include <cuda_runtime.h>
 
 #include "of_internal.h"
@@ -122,7 +123,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     __shared__ NmsTile tinfo[2];
     __shared__ uint32_t sflag[FINAL ? 1 : MAX_CELLS_LOCAL];
     __shared__ int32_t rcell[FINAL ? 1 : S_ROWS];   // staged row -> (local cell row) * lcw
-    __shared__ int nq, qbase;
+    __shared__ int nq;
 
     const int tid = threadIdx.x;
     const bool cells = t_hi != t_lo;
@@ -331,19 +332,25 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         }
         __syncthreads();
         const int count = nq;
-        if (count > 0) {
-            if (tid == 0) qbase = atomicAdd(&I.ctr[0], count);
-            __syncthreads();
-            const int base = qbase;
-            for (int i = tid; i < count; i += blockDim.x) {
-                const uint32_t e = queue[i];
+        for (int i0 = 0; i0 < count; i0 += DET_THREADS) {  // block-uniform
+            const int i = i0 + tid;
+            // Each warp reserves its entries' slots in the image's list; the
+            // atomic's latency hides behind the Harris sums.
+            const int n_w = min(max(count - (i0 + 32 * ty), 0), 32);
+            int wb = 0;
+            if (lane == 0 && n_w > 0) wb = atomicAdd(&I.ctr[0], n_w);
+            int32_t A = 0, B = 0, C = 0;
+            uint32_t e = 0u;
+            if (i < count) {
+                e = queue[i];
+                harris_sums(sI, (int)(e & 0xFFFFu), (int)(e >> 16), A, B, C);
+            }
+            const int slot = __shfl_sync(0xFFFFFFFFu, wb, 0) + lane;
+            if (i < count) {
                 const int lx = (int)(e & 0xFFFFu), ly = (int)(e >> 16);
-                int32_t A, B, C;
-                harris_sums(sI, lx, ly, A, B, C);
                 const int64_t det = (int64_t)A * B - (int64_t)C * C;
                 const int64_t tr = (int64_t)A + B;
                 const int64_t key = kden * det - knum * tr * tr;
-                const int slot = base + i;
                 if (slot < I.cand_cap) {
                     I.ckey[slot] = (uint64_t)key ^ 0x8000000000000000ull;
                     I.cyx[slot] = ((uint32_t)(Y0 + ly) << 16) | (uint32_t)(X0 + lx);
