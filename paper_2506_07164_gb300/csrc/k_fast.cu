@@ -324,45 +324,51 @@ int fast_blocks_per_sm(int tile_h) {
 // ---------------------------------------------------------------------------
 // Cell tiles: FAST with the per-cell threshold applied in the same kernel.
 //
-// A tile is CPT whole cells of one cell row (CPT = floor(124 / cell); 4 x 30 =
-// 120 x 30 pixels for 30-pixel cells), so the tile sees every pixel of its
-// cells: it scores them, ORs each cell's "a pixel scores >= t_hi" flag in
-// shared memory, and after one barrier writes the candidate score
+// A tile is cpt = floor(124 / cell) whole cells wide and cr = ct_cell_rows
+// whole cell rows high (4 x 2 cells = 120 x 60 pixels for 30-pixel cells),
+// so it sees every pixel of its cells: it scores them, ORs each cell's "a
+// pixel scores >= t_hi" flag in shared memory, and writes the candidate score
 // S(p) = s(p) if s(p) >= T(cell(p)) else 0 -- what NMS keys on -- and the
-// cell flags.  Nothing is accumulated across tiles, so NMS needs no cell
-// bookkeeping.  Lanes own 4-aligned 4-pixel groups (the first and last
-// groups straddle the tile edge and store only their in-tile bytes); warp w
-// owns rows 5w .. 5w+4 of the tile (ceil(cell / 5) warps).  The TMA box is
-// the 160 x 40 image box at x = (group origin - 4) rounded down to 16 bytes,
-// starting 3 rows above the tile.
-
-constexpr int CT_RPT = 5;
-constexpr int CT_MAX_WARPS = (CT_MAX_CELL + CT_RPT - 1) / CT_RPT;  // 6: rows up to 5*5+10 = 35 of the box
-static_assert((CT_MAX_WARPS - 1) * CT_RPT + 10 < IMG_BOX_ROWS, "ring rows of the last warp stay in the box");
+// cell flags.  Nothing is accumulated across tiles, so no threshold pass runs
+// between FAST and NMS.  A tile's writes wait for its flags: they happen in
+// the next iteration, right after the one barrier that ends each tile, from
+// the scores the threads keep in registers; the flags rotate through three
+// shared-memory slots (ORed in iteration i, read in i + 1, cleared in i + 2).
+// Lanes own 4-aligned 4-pixel groups (the first and last groups straddle
+// the tile edge and store only their in-tile bytes); warp w owns rows
+// 5 (w mod nw) .. +4 of cell row w / nw (nw = ct_warps(cell) warps per cell
+// row).  The TMA boxes are 160 x 40 image boxes at x = (group origin - 4)
+// rounded down to 16 bytes, starting 3 rows above the tile, stacked.
 
 struct CellTile {
     int32_t img, x_lo, y0, box_x;
 };
 
-__global__ void __launch_bounds__(32 * CT_MAX_WARPS, 4)
+constexpr int CT_BUF = 2 * FAST_BUF;  // two stacked image boxes
+
+__global__ void __launch_bounds__(32 * CT_MAX_WARPS, 2)
 k_fast_cells(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ prefix,
              int n_list, int n_tiles, const CUtensorMap* __restrict__ maps, const Call* __restrict__ call,
              int t_hi, int t_lo, int border, int cell, int cpt, int order) {
-    __shared__ __align__(128) uint8_t sbuf[2 * FAST_BUF];
+    __shared__ __align__(128) uint8_t sbuf[2 * CT_BUF];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ CellTile tinfo[2];
-    __shared__ uint32_t cflag[2];
+    __shared__ uint32_t cflag[3][CT_MAX_CR];
     __shared__ int any_on[2];
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const bool cells = t_hi != t_lo;
-    const int tw = cpt * cell;  // tile width in pixels
+    const int nw = ct_warps(cell), cr = ct_cell_rows(cell);
+    const int wcr = w / nw, wr = w % nw;  // this warp's cell row in the tile, and its 5-row group there
+    const int tw = cpt * cell, th = cr * cell;
+    const int srow0 = wcr * cell + CT_RPT * wr;  // the warp's first staged row (staged row 0 = tile row -3)
+    const int loads = ((cr - 1) * cell + CT_RPT * nw + 6 + IMG_BOX_ROWS - 1) / IMG_BOX_ROWS;  // 1 or 2
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         fence_barrier_init();
-        cflag[0] = cflag[1] = 0u;
     }
+    for (int i = tid; i < 3 * CT_MAX_CR; i += blockDim.x) (&cflag[0][0])[i] = 0u;
     __syncthreads();
     auto issue = [&](int t, int b) {
         const int j = find_tile_job(prefix, n_list, t);
@@ -370,13 +376,13 @@ k_fast_cells(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
         const Img& I = imgs[ii];
         const int tt = t - __ldg(prefix + j);
         const int ftx = tt % I.ftiles_x, fty = tt / I.ftiles_x;
-        const int x_lo = border + ftx * tw, y0 = border + fty * cell;
+        const int x_lo = border + ftx * tw, y0 = border + fty * th;
         const int box_x = ((x_lo & ~3) - 4) & ~15;
         // Learned path: does any proposal tile under this work tile hold a proposed pixel?
         int on = 1;
         if (I.pmask) {
             on = 0;
-            const int x_hi = min(x_lo + tw, I.w - border) - 1, y_hi = min(y0 + cell, I.h - border) - 1;
+            const int x_hi = min(x_lo + tw, I.w - border) - 1, y_hi = min(y0 + th, I.h - border) - 1;
             for (int py = (y0 - border) >> 5; py <= (y_hi - border) >> 5 && !on; ++py)
                 for (int px = (x_lo - I.tile_x0) >> 5; px <= (x_hi - I.tile_x0) >> 5 && !on; ++px)
                     on = I.pmask[(size_t)py * 4 * I.tiles_x + px] != 0;
@@ -384,78 +390,112 @@ k_fast_cells(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
         tinfo[b] = CellTile{ii, x_lo, y0, box_x};
         any_on[b] = on;
         tensormap_acquire(maps + ii);
-        mbar_arrive_expect_tx(&mbar[b], FAST_BOX);
-        tma_load_2d(sbuf + b * FAST_BUF, maps + ii, box_x, y0 - 3, &mbar[b]);
+        mbar_arrive_expect_tx(&mbar[b], loads * FAST_BOX);
+        for (int k = 0; k < loads; ++k)
+            tma_load_2d(sbuf + b * CT_BUF + k * FAST_BOX, maps + ii, box_x, y0 - 3 + k * IMG_BOX_ROWS, &mbar[b]);
     };
     const int g = gridDim.x;
     if (tid == 0 && tile_of(order, blockIdx.x, g, n_tiles, 0) < n_tiles)
         issue(tile_of(order, blockIdx.x, g, n_tiles, 0), 0);
 
-    const int lane = tid & 31, ty = tid >> 5;
+    uint32_t sv[CT_RPT][2];  // this thread's scores of the previous tile (16-bit lanes)
+    CellTile prev{-1, 0, 0, 0};
     for (int it = 0;; ++it) {
         const int t = tile_of(order, blockIdx.x, g, n_tiles, it);
-        if (t >= n_tiles) break;
-        const int tn = tile_of(order, blockIdx.x, g, n_tiles, it + 1);
+        const bool have = t < n_tiles;  // block-uniform
         const int b = it & 1;
         if (tid == 0) {
-            cflag[b ^ 1] = 0u;  // last read before the previous tile's final barrier
-            if (tn < n_tiles) {
+#pragma unroll
+            for (int i = 0; i < CT_MAX_CR; ++i) cflag[(it + 1) % 3][i] = 0u;  // slot of tile it - 2, read in it - 1
+            const int tn = tile_of(order, blockIdx.x, g, n_tiles, it + 1);
+            if (have && tn < n_tiles) {
                 fence_proxy_async_smem();
                 issue(tn, b ^ 1);
             }
         }
-        const bool ok = mbar_wait(&mbar[b], (it >> 1) & 1);
+        const bool ok = have ? mbar_wait(&mbar[b], (it >> 1) & 1) : true;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicOr(call->status, OF_DEV_TIMEOUT);
+                // Let this block's copies in flight land before its shared memory goes away.
                 mbar_wait(&mbar[b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
-                if (tn < n_tiles) mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (tile_of(order, blockIdx.x, g, n_tiles, it + 1) < n_tiles)
+                    mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
             }
             return;
         }
+
+        // The previous tile: its flags are complete (the barrier that ended its
+        // iteration); write its cell flags and S(p) from the kept scores.
+        if (prev.img >= 0) {
+            const Img& I = imgs[prev.img];
+            const int rx1 = I.w - border, ry1 = I.h - border;
+            const int x_hi = min(prev.x_lo + tw, rx1);
+            const int x = (prev.x_lo & ~3) + 4 * lane;
+            const int row0 = prev.y0 + srow0;
+            const int y1 = min(prev.y0 + (wcr + 1) * cell, ry1);
+            const uint32_t* fl = cflag[(it - 1) % 3];
+            if (tid < cpt * cr) {
+                const int cx = (prev.x_lo - border) / cell + tid % cpt, cy = (prev.y0 - border) / cell + tid / cpt;
+                if (cx < I.ncx && cy < I.ncy) I.cell[cy * I.ncx + cx] = (fl[tid / cpt] >> (tid % cpt)) & 1u;
+            }
+            const uint32_t colmask = range_mask4(x, prev.x_lo, x_hi);
+            if (row0 < y1 && colmask != 0u) {
+                // Cells of this lane's bytes: ca for the bytes in mask_a, ca + 1 for the rest.
+                const int ca = (max(x, prev.x_lo) - prev.x_lo) / cell;
+                const uint32_t mask_a = colmask & range_mask4(x, 0, prev.x_lo + (ca + 1) * cell);
+                const uint32_t flags = fl[wcr];
+                const bool fa = (flags >> ca) & 1u, fb = (flags >> (ca + 1)) & 1u;
+                uint32_t kk[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool flagged = ((mask_a >> (8 * i)) & 1u) ? fa : fb;
+                    kk[i] = 0x8000u - (uint32_t)(flagged ? t_hi : t_lo);
+                }
+                const uint32_t K0 = kk[0] | (kk[1] << 16), K1 = kk[2] | (kk[3] << 16);
+#pragma unroll
+                for (int r = 0; r < CT_RPT; ++r) {
+                    const int y = row0 + r;
+                    if (y >= y1) break;
+                    const uint32_t s0 = sv[r][0] & ((((sv[r][0] + K0) >> 15) & 0x00010001u) * 0xFFFFu);
+                    const uint32_t s1 = sv[r][1] & ((((sv[r][1] + K1) >> 15) & 0x00010001u) * 0xFFFFu);
+                    store_bytes(I.score + (size_t)y * I.spitch + x, __byte_perm(s0, s1, 0x6420), colmask);
+                }
+            }
+        }
+        if (!have) break;
+
+        // This tile: scores into sv, each cell's strong flag into slot it % 3.
         const CellTile ti = tinfo[b];
+        prev = ti;
         const Img& I = imgs[ti.img];
-        const uint8_t* s = sbuf + b * FAST_BUF;
+        const uint8_t* s = sbuf + b * CT_BUF;
         const int rx1 = I.w - border, ry1 = I.h - border;
-        const int x_hi = min(ti.x_lo + tw, rx1), y1 = min(ti.y0 + cell, ry1);
+        const int x_hi = min(ti.x_lo + tw, rx1);
         const int gx0 = ti.x_lo & ~3;
         const int x = gx0 + 4 * lane;
-        const int row0 = ti.y0 + ty * CT_RPT;
+        const int row0 = ti.y0 + srow0;
+        const int y1 = min(ti.y0 + (wcr + 1) * cell, ry1);
         const uint32_t colmask = range_mask4(x, ti.x_lo, x_hi);
-        if (!any_on[b]) {
-            // No proposed pixel: S is 0 over the tile.
 #pragma unroll
-            for (int r = 0; r < CT_RPT; ++r) {
-                const int y = row0 + r;
-                if (y < y1 && colmask) store_bytes(I.score + (size_t)y * I.spitch + x, 0u, colmask);
-            }
-            if (tid < cpt) {
-                const int cx = (ti.x_lo - border) / cell + tid, cy = (ti.y0 - border) / cell;
-                if (cx < I.ncx) I.cell[cy * I.ncx + cx] = 0u;
-            }
-            __syncthreads();
-            continue;
-        }
-
-        // Six pair words per staged row (staged row 0 is y0 - 3), loaded just in time.
-        uint32_t hw[CT_RPT + 6][6];
-        const int xoff = gx0 - ti.box_x + 4 * lane;  // >= 4, multiple of 4
-        auto load_row = [&](int k) {
-            const uint8_t* row = s + (ty * CT_RPT + k) * SROW + xoff;
-            const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
-            const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
-            const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
-            hw[k][0] = __byte_perm(wm, 0u, 0x4140);
-            hw[k][1] = __byte_perm(wm, 0u, 0x4342);
-            hw[k][2] = __byte_perm(wc, 0u, 0x4140);
-            hw[k][3] = __byte_perm(wc, 0u, 0x4342);
-            hw[k][4] = __byte_perm(wp, 0u, 0x4140);
-            hw[k][5] = __byte_perm(wp, 0u, 0x4342);
-        };
-        const bool warp_rows = row0 < y1;  // warp-uniform
-        uint32_t sv[CT_RPT][2];
-        uint32_t u0 = 0u, u1 = 0u;  // running maxima of the in-tile scores (16-bit lanes)
-        if (warp_rows) {
+        for (int r = 0; r < CT_RPT; ++r) sv[r][0] = sv[r][1] = 0u;
+        if (any_on[b] && row0 < y1) {  // warp-uniform
+            // Six pair words per staged row, loaded just in time.
+            uint32_t hw[CT_RPT + 6][6];
+            const int xoff = gx0 - ti.box_x + 4 * lane;  // >= 4, multiple of 4
+            auto load_row = [&](int k) {
+                const uint8_t* row = s + (srow0 + k) * SROW + xoff;
+                const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+                const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+                const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
+                hw[k][0] = __byte_perm(wm, 0u, 0x4140);
+                hw[k][1] = __byte_perm(wm, 0u, 0x4342);
+                hw[k][2] = __byte_perm(wc, 0u, 0x4140);
+                hw[k][3] = __byte_perm(wc, 0u, 0x4342);
+                hw[k][4] = __byte_perm(wp, 0u, 0x4140);
+                hw[k][5] = __byte_perm(wp, 0u, 0x4342);
+            };
+            uint32_t u0 = 0u, u1 = 0u;  // running maxima of the in-tile scores (16-bit lanes)
 #pragma unroll
             for (int k = 0; k < 7; ++k) load_row(k);
 #pragma unroll
@@ -477,43 +517,17 @@ k_fast_cells(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                 u0 = __vimax3_u16x2(u0, s0, s0);
                 u1 = __vimax3_u16x2(u1, s1, s1);
             }
-        }
-        // Cells of this lane's bytes: ca for the bytes in mask_a, ca + 1 for the rest.
-        const int ca = (max(x, ti.x_lo) - ti.x_lo) / cell;
-        const uint32_t mask_a = colmask & range_mask4(x, 0, ti.x_lo + (ca + 1) * cell);
-        const uint32_t mask_b = colmask & ~mask_a;
-        if (cells) {
-            const uint32_t su = __byte_perm(lanes_ge(u0, (uint32_t)t_hi), lanes_ge(u1, (uint32_t)t_hi), 0x6420);
-            uint32_t bits = ((su & mask_a) ? 1u << ca : 0u) | ((su & mask_b) ? 2u << ca : 0u);
-            bits = __reduce_or_sync(0xFFFFFFFFu, bits);
-            if (lane == 0 && bits) atomicOr(&cflag[b], bits);
-        }
-        __syncthreads();
-        const uint32_t flags = cflag[b];
-        if (tid < cpt) {
-            const int cx = (ti.x_lo - border) / cell + tid, cy = (ti.y0 - border) / cell;
-            if (cx < I.ncx) I.cell[cy * I.ncx + cx] = (flags >> tid) & 1u;
-        }
-        if (warp_rows) {
-            // Per-byte threshold T(cell) as lanes_ge constants for the two pairs.
-            const bool fa = (flags >> ca) & 1u, fb = (flags >> (ca + 1)) & 1u;
-            uint32_t kk[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const bool flagged = ((mask_a >> (8 * i)) & 1u) ? fa : fb;
-                kk[i] = 0x8000u - (uint32_t)(flagged ? t_hi : t_lo);
-            }
-            const uint32_t K0 = kk[0] | (kk[1] << 16), K1 = kk[2] | (kk[3] << 16);
-#pragma unroll
-            for (int r = 0; r < CT_RPT; ++r) {
-                const int y = row0 + r;
-                if (y >= y1 || colmask == 0u) continue;
-                const uint32_t s0 = sv[r][0] & ((((sv[r][0] + K0) >> 15) & 0x00010001u) * 0xFFFFu);
-                const uint32_t s1 = sv[r][1] & ((((sv[r][1] + K1) >> 15) & 0x00010001u) * 0xFFFFu);
-                store_bytes(I.score + (size_t)y * I.spitch + x, __byte_perm(s0, s1, 0x6420), colmask);
+            if (cells) {
+                const int ca = (max(x, ti.x_lo) - ti.x_lo) / cell;
+                const uint32_t mask_a = colmask & range_mask4(x, 0, ti.x_lo + (ca + 1) * cell);
+                const uint32_t mask_b = colmask & ~mask_a;
+                const uint32_t su = __byte_perm(lanes_ge(u0, (uint32_t)t_hi), lanes_ge(u1, (uint32_t)t_hi), 0x6420);
+                uint32_t bits = ((su & mask_a) ? 1u << ca : 0u) | ((su & mask_b) ? 2u << ca : 0u);
+                bits = __reduce_or_sync(0xFFFFFFFFu, bits);
+                if (lane == 0 && bits) atomicOr(&cflag[it % 3][wcr], bits);
             }
         }
-        __syncthreads();  // buffer b and cflag[b] are free for the tile after next
+        __syncthreads();  // this tile's flags are complete; buffer b is free for the tile after next
     }
 }
 
@@ -522,15 +536,15 @@ void launch_fast_cells(const Img* imgs, const int32_t* img_list, const int32_t* 
                        int cell, int grid, int order, void* stream) {
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
-    const int nw = (cell + CT_RPT - 1) / CT_RPT, cpt = CT_MAX_W / cell;
-    k_fast_cells<<<grid, 32 * nw, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps,
+    const int threads = 32 * ct_warps(cell) * ct_cell_rows(cell), cpt = CT_MAX_W / cell;
+    k_fast_cells<<<grid, threads, 0, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps,
                                                               call, t_hi, t_lo, border, cell, cpt, order);
 }
 
 int fast_cells_blocks_per_sm(int cell) {
-    const int nw = (cell + CT_RPT - 1) / CT_RPT;
+    const int threads = 32 * ct_warps(cell) * ct_cell_rows(cell);
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_cells, 32 * nw, 0) != cudaSuccess || n < 1) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_cells, threads, 0) != cudaSuccess || n < 1) n = 1;
     return n;
 }
 

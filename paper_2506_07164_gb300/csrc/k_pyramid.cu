@@ -256,12 +256,18 @@ k_resize_tma(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix
                 const uint32_t o = (uint32_t)(xo[i] - 4 * (i < 2 ? wa : wb));
                 sel[i] = o | ((o + 1u) << 4);
             }
-            uint8_t* d = J.dst + (size_t)ti.y0 * J.dpitch + ti.x0 + lx;
+            // The job's fields, read once (the stores below could alias them).
+            const int dpitch = J.dpitch;
+            const int32_t* ytab = J.ytab + ti.y0;
+            uint8_t* d = J.dst + (size_t)ti.y0 * dpitch + ti.x0 + lx;
             uint32_t ha[4], hb[4];
             int cur = -4;
             const int ly_end = min(8 * warp + 8, ny);
-            for (int ly = 8 * warp; ly < ly_end; ++ly) {
-                const int e = __ldg(J.ytab + ti.y0 + ly);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {  // unrolled: the row-table loads are issued together
+                const int ly = 8 * warp + k;
+                if (ly >= ly_end) break;
+                const int e = __ldg(ytab + ly);
                 const int r0 = (e >> 12) - ti.sy0;
                 const uint32_t a2 = 2u * (uint32_t)(e & 4095);
                 if (r0 == cur + 1) {
@@ -278,7 +284,7 @@ k_resize_tma(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix
                 for (int i = 0; i < 4; ++i) v[i] = (4096u - a2) * ha[i] + a2 * hb[i] + (1u << 23);
                 const uint32_t packed =
                     __byte_perm(__byte_perm(v[0], v[1], 0x0073), __byte_perm(v[2], v[3], 0x0073), 0x5410);
-                uint8_t* dr = d + (size_t)ly * J.dpitch;
+                uint8_t* dr = d + (size_t)ly * dpitch;
                 if (n == 4) {
                     *reinterpret_cast<uint32_t*>(dr) = packed;  // x0 + lx is a multiple of 4, dpitch of 16
                 } else {

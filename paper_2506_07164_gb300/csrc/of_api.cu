@@ -635,7 +635,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
                 P->gp_nms64.push_back(G.nms64_tiles);
                 G.nms64_tiles += I.tiles_x * ((I.h - 2 * s.border + 63) / 64);
                 P->gp_fast.push_back(G.fast_tiles);
-                G.fast_tiles += I.ftiles_x * I.ncy;
+                G.fast_tiles += P->cell_tiles ? I.ftiles_x * ((I.ncy + ct_cell_rows(s.cell) - 1) / ct_cell_rows(s.cell)) : 0;
                 P->gp_rows.push_back(G.n_bands);
                 G.n_bands += I.ncy;
             }

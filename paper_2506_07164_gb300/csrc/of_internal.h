@@ -23,12 +23,24 @@ constexpr int IMG_BOX_ROWS = TILE_H + 8;   // image TMA box: rows Y0-4 .. Y0+TIL
 constexpr int SCORE_BOX_ROWS = TILE_H + 2; // score TMA box: rows Y0-1 .. Y0+TILE_H
 
 // Cell tiles of the FAST kernel that applies the per-cell threshold itself:
-// floor(CT_MAX_W / cell) whole cells wide, one cell row high; used for cells
-// of CT_MIN_CELL .. CT_MAX_CELL pixels (5 rows per warp, 6 warps at most, so
-// every warp's 11 staged rows lie in the 40-row image box).
+// floor(CT_MAX_W / cell) whole cells wide and ct_cell_rows(cell) cell rows
+// high (at most CT_MAX_TILE_ROWS rows); used for cells of CT_MIN_CELL ..
+// CT_MAX_CELL pixels.  A warp scores CT_RPT rows of one cell row, so a cell
+// row takes ct_warps(cell) warps; a tile's staged rows fit two stacked
+// 40-row image boxes.
 constexpr int CT_MAX_W = 124;
 constexpr int CT_MIN_CELL = 8;
 constexpr int CT_MAX_CELL = 30;
+constexpr int CT_RPT = 5;             // rows per warp
+constexpr int CT_MAX_WARPS = 12;      // warps per block
+constexpr int CT_MAX_TILE_ROWS = 64;  // rows per tile
+constexpr int CT_MAX_CR = 8;          // cell rows per tile
+__host__ __device__ constexpr int ct_warps(int cell) { return (cell + CT_RPT - 1) / CT_RPT; }
+__host__ __device__ constexpr int ct_cell_rows(int cell) {
+    return CT_MAX_TILE_ROWS / cell < CT_MAX_WARPS / ct_warps(cell) ? CT_MAX_TILE_ROWS / cell
+                                                                   : CT_MAX_WARPS / ct_warps(cell);
+}
+static_assert(ct_cell_rows(CT_MIN_CELL) <= CT_MAX_CR && ct_cell_rows(CT_MAX_CELL) >= 1, "cell rows per tile");
 
 // Resize tile: 128 x (32 or 64) output pixels; each thread writes 4 consecutive pixels
 // in 2 or 4 rows.  The autotuner picks the height.
