@@ -293,7 +293,7 @@ FAST_OPS_PER_PX = 40.5
 # DRAM bytes of one k_fast launch per frame, from the ncu capture summarised in
 # profiles/k_fast_1080p8.md (64-frame launch, scaled per frame), valid while
 # k_fast.cu has this SHA-1.
-FAST_TRAFFIC = {"sha1": "d74caf98bce626ef2ccaf18b8858e6c218d9f852", "bytes_per_frame": (488090624 + 349121024) / 64}
+FAST_TRAFFIC = {"sha1": "17a8a449b7bf8b8c5fb01826c0c52c383e1d996c", "bytes_per_frame": (488078848 + 348993280) / 64}
 
 
 def file_sha1(path):

@@ -244,6 +244,9 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
 #pragma unroll
         for (int k = 0; k < 7; ++k) load_row(k);
         const uint32_t colmask = range_mask4(x, rx0, rx1) & lane_on;
+        // The score map's address, read once (the stores below could alias the image's fields).
+        uint8_t* const sdst = I.score + x;
+        const size_t spitch = (size_t)I.spitch;
         // Cells of this thread's 4 x RPT pixels (cell >= 8 > RPT, 4): at most
         // two cell columns (the bytes in mask_a lie in the first) and two cell
         // rows (the second from row y_next on); no division per pixel.
@@ -262,7 +265,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             const uint32_t s1 = ring_pair_score<1>(hw + r, (uint32_t)t_lo);
             const uint32_t m = (y < ry1) ? colmask : 0u;
             const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
-            if (m != 0u) *reinterpret_cast<uint32_t*>(I.score + (size_t)y * I.spitch + x) = sc;
+            if (m != 0u) *reinterpret_cast<uint32_t*>(sdst + (size_t)y * spitch) = sc;
             if (cells && sc) {
                 const uint32_t strong =
                     __byte_perm(lanes_ge(s0, (uint32_t)t_hi), lanes_ge(s1, (uint32_t)t_hi), 0x6420) & m;

@@ -689,9 +689,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.fast_cell_tiles = P->cell_tiles ? 1 : 0;
     P->tun.fast_tile_h = 32;
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
-    P->tun.nms_tile_h = 32;
-    P->tun.nms_blocks_per_sm = nms_blocks_per_sm(32);
-    nms_blocks_per_sm(64);  // raises the 64-row kernel's shared-memory limit before any capture
+    P->tun.nms_tile_h = 64;
+    P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64);  // also raises its shared-memory limit before any capture
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
 
