@@ -487,8 +487,10 @@ def main():
                         for i in range(ofg.OF_N_STAGES)]
         return ms, stage_ms
 
-    clock_file = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/ofast_clocks_{os.getpid()}.csv"
+    # Clock samples go to $OFAST_CLOCKS_DIR when that directory exists (to keep them), else to /tmp.
+    clock_dir = os.environ.get("OFAST_CLOCKS_DIR", "")
+    clock_file = (os.path.join(clock_dir, f"clocks_rank{rank}.csv") if clock_dir and os.path.isdir(clock_dir)
+                  else f"/tmp/ofast_clocks_{os.getpid()}.csv")
     smi = sample_clocks("", clock_file)
     time.sleep(0.3)
     ms_b, _ = timed(step_batched, args.steps, args.warmup, nvtx_name="batched_timed")

@@ -60,7 +60,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::mutex g_encode_mutex;
 
-// The driver's tensor-map encoder, looked up through the runtime (no libcuda link).
+// The CUDA driver API's tensor-map encoder, looked up through the runtime (no libcuda link).
 int resolve_encoder() {
     std::lock_guard<std::mutex> lock(g_encode_mutex);
     if (g_encode) return OF_OK;
