@@ -42,22 +42,39 @@ __device__ __forceinline__ uint32_t bytes_lt(uint32_t v, uint32_t t) {
     return ~__byte_perm((lo >> 15 & 0x00010001u) * 0xFFu, (hi >> 15 & 0x00010001u) * 0xFFu, 0x6420);
 }
 
+// Unsigned bytes of a times signed bytes of b, summed, plus c.
+__device__ __forceinline__ int dp4a_us(uint32_t a, uint32_t b, int c) {
+    int d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+constexpr uint32_t W_DIFF = 0x000100FFu;  // byte weights (-1, 0, 1, 0): p[u+2] - p[u]
+constexpr uint32_t W_SMOOTH = 0x00010201u;  // byte weights (1, 2, 1, 0): p[u] + 2 p[u+1] + p[u+2]
+
 __device__ __forceinline__ void harris_sums(const uint8_t* __restrict__ s, int lx, int ly,
                                             int32_t& A, int32_t& B, int32_t& C) {
-    // s: image tile, row 0 = tile row -4, column HALO_X = tile column 0.
+    // s: image tile, row 0 = tile row -4, column HALO_X = tile column 0.  A
+    // window row is bytes lx-4 .. lx+4: three aligned words, realigned by two
+    // funnel shifts; the seven 4-byte windows give both horizontal passes as
+    // byte dot products.
+    const int start = HALO_X + lx - 4;
+    const int w0 = start >> 2, sh = 8 * (start & 3);
     int hd[3][7], hsm[3][7];
     int a = 0, bb = 0, c = 0;
 #pragma unroll
     for (int v = -4; v <= 4; ++v) {
-        const uint8_t* row = s + (ly + 4 + v) * SROW + HALO_X + lx - 4;
-        int p[9];
-#pragma unroll
-        for (int u = 0; u < 9; ++u) p[u] = row[u];
+        const uint32_t* rp = reinterpret_cast<const uint32_t*>(s + (ly + 4 + v) * SROW) + w0;
+        const uint32_t x0 = rp[0], x1 = rp[1], x2 = rp[2];
+        const uint32_t r0 = __funnelshift_r(x0, x1, sh), r1 = __funnelshift_r(x1, x2, sh), r2 = x2 >> sh;
+        const uint32_t win[7] = {r0, __byte_perm(r0, r1, 0x4321), __byte_perm(r0, r1, 0x5432),
+                                 __byte_perm(r0, r1, 0x6543), r1, __byte_perm(r1, r2, 0x4321),
+                                 __byte_perm(r1, r2, 0x5432)};
         const int slot = (v + 4) % 3;
 #pragma unroll
         for (int u = 0; u < 7; ++u) {
-            hd[slot][u] = p[u + 2] - p[u];
-            hsm[slot][u] = p[u] + 2 * p[u + 1] + p[u + 2];
+            hd[slot][u] = dp4a_us(win[u], W_DIFF, 0);
+            hsm[slot][u] = (int)__dp4a(win[u], W_SMOOTH, 0u);
         }
         if (v >= -2) {
             const int s0 = (v + 2) % 3, s1 = (v + 3) % 3;  // rows v-2, v-1
