@@ -241,8 +241,10 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             hw[k][4] = __byte_perm(wp, 0u, 0x4140);
             hw[k][5] = __byte_perm(wp, 0u, 0x4342);
         };
-#pragma unroll
-        for (int k = 0; k < 7; ++k) load_row(k);
+        // Rows of this warp inside the detect region (warp-uniform): a warp
+        // below the region's last row (the last tile row of a level) goes
+        // straight to the tile barrier, leaving its issue slots to others.
+        const int nrows = min(RPT, ry1 - (Y0 + ty * RPT));
         const uint32_t colmask = range_mask4(x, rx0, rx1) & lane_on;
         // The score map's address, read once (the stores below could alias the image's fields).
         uint8_t* const sdst = I.score + x;
@@ -256,23 +258,28 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int y_next = border + (cr + 1) * cell;
         const int fbase = (cr - cy0) * lcw + (ca - cx0);
 
+        if (nrows > 0) {
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const int y = Y0 + ty * RPT + r;
-            if (r > 0) load_row(r + 6);
-            // Pixel pairs (x, x+1) and (x+2, x+3), one after the other.
-            const uint32_t s0 = ring_pair_score<0>(hw + r, (uint32_t)t_lo);
-            const uint32_t s1 = ring_pair_score<1>(hw + r, (uint32_t)t_lo);
-            const uint32_t m = (y < ry1) ? colmask : 0u;
-            const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
-            if (m != 0u) *reinterpret_cast<uint32_t*>(sdst + (size_t)y * spitch) = sc;
-            if (cells && sc) {
-                const uint32_t strong =
-                    __byte_perm(lanes_ge(s0, (uint32_t)t_hi), lanes_ge(s1, (uint32_t)t_hi), 0x6420) & m;
-                if (strong) {
-                    const int f = fbase + (y >= y_next ? lcw : 0);
-                    if (strong & mask_a) atomicOr(&sflag[f], 1u);
-                    if (strong & ~mask_a) atomicOr(&sflag[f + 1], 1u);
+            for (int k = 0; k < 7; ++k) load_row(k);
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                if (r >= nrows) break;
+                const int y = Y0 + ty * RPT + r;
+                if (r > 0) load_row(r + 6);
+                // Pixel pairs (x, x+1) and (x+2, x+3), one after the other.
+                const uint32_t s0 = ring_pair_score<0>(hw + r, (uint32_t)t_lo);
+                const uint32_t s1 = ring_pair_score<1>(hw + r, (uint32_t)t_lo);
+                const uint32_t m = colmask;  // y < ry1 here
+                const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
+                if (m != 0u) *reinterpret_cast<uint32_t*>(sdst + (size_t)y * spitch) = sc;
+                if (cells && sc) {
+                    const uint32_t strong =
+                        __byte_perm(lanes_ge(s0, (uint32_t)t_hi), lanes_ge(s1, (uint32_t)t_hi), 0x6420) & m;
+                    if (strong) {
+                        const int f = fbase + (y >= y_next ? lcw : 0);
+                        if (strong & mask_a) atomicOr(&sflag[f], 1u);
+                        if (strong & ~mask_a) atomicOr(&sflag[f + 1], 1u);
+                    }
                 }
             }
         }

@@ -279,53 +279,58 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         }
         if (!FINAL) __syncthreads();
 
-        // 2. Strict 3x3 maxima, two pixels per register.
+        // 2. Strict 3x3 maxima, two pixels per register.  Rows of this warp
+        //    inside the detect region (warp-uniform); rows below it hold no
+        //    survivor, so a warp entirely below it only takes part in the queue.
         {
+            const int nrows = min(RPT, ry1 - (Y0 + ty * RPT));
             uint32_t smask = 0u;  // survivor bits: (2 * row + pair) * 2 + lane
-            uint32_t hw[RPT + 2][6];
-            // FINAL: the in-region bytes of the three words this thread reads.
-            uint32_t cm_m = 0xFFFFFFFFu, cm_c = 0xFFFFFFFFu, cm_q = 0xFFFFFFFFu;
-            if (FINAL) {
-                const int xc = X0 + 4 * lane;
-                cm_m = range_mask4(xc - 4, lox, hix);
-                cm_c = range_mask4(xc, lox, hix);
-                cm_q = range_mask4(xc + 4, lox, hix);
-            }
-#pragma unroll
-            for (int k = 0; k < RPT + 2; ++k) {
-                const uint8_t* row = sS + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
-                uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
-                uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
-                uint32_t wq = *reinterpret_cast<const uint32_t*>(row + 4);
+            if (nrows > 0) {
+                uint32_t hw[RPT + 2][6];
+                // FINAL: the in-region bytes of the three words this thread reads.
+                uint32_t cm_m = 0xFFFFFFFFu, cm_c = 0xFFFFFFFFu, cm_q = 0xFFFFFFFFu;
                 if (FINAL) {
-                    const int iy = Y0 - 1 + ty * RPT + k;
-                    const uint32_t rm = (iy >= ry0 && iy < ry1) ? 0xFFFFFFFFu : 0u;
-                    wm &= cm_m & rm;
-                    wc &= cm_c & rm;
-                    wq &= cm_q & rm;
+                    const int xc = X0 + 4 * lane;
+                    cm_m = range_mask4(xc - 4, lox, hix);
+                    cm_c = range_mask4(xc, lox, hix);
+                    cm_q = range_mask4(xc + 4, lox, hix);
                 }
-                hw[k][1] = __byte_perm(wm, 0u, 0x4342);  // (x-2, x-1)
-                hw[k][2] = __byte_perm(wc, 0u, 0x4140);  // (x, x+1)
-                hw[k][3] = __byte_perm(wc, 0u, 0x4342);  // (x+2, x+3)
-                hw[k][4] = __byte_perm(wq, 0u, 0x4140);  // (x+4, x+5)
-            }
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) {
+                for (int k = 0; k < RPT + 2; ++k) {
+                    const uint8_t* row = sS + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
+                    uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+                    uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+                    uint32_t wq = *reinterpret_cast<const uint32_t*>(row + 4);
+                    if (FINAL) {
+                        const int iy = Y0 - 1 + ty * RPT + k;
+                        const uint32_t rm = (iy >= ry0 && iy < ry1) ? 0xFFFFFFFFu : 0u;
+                        wm &= cm_m & rm;
+                        wc &= cm_c & rm;
+                        wq &= cm_q & rm;
+                    }
+                    hw[k][1] = __byte_perm(wm, 0u, 0x4342);  // (x-2, x-1)
+                    hw[k][2] = __byte_perm(wc, 0u, 0x4140);  // (x, x+1)
+                    hw[k][3] = __byte_perm(wc, 0u, 0x4342);  // (x+2, x+3)
+                    hw[k][4] = __byte_perm(wq, 0u, 0x4140);  // (x+4, x+5)
+                }
 #pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    const uint32_t* a = hw[r];
-                    const uint32_t* c = hw[r + 1];
-                    const uint32_t* d = hw[r + 2];
-                    const int j = 2 + pr;
-                    const uint32_t am = __byte_perm(a[j - 1], a[j], 0x5432), ap = __byte_perm(a[j], a[j + 1], 0x5432);
-                    const uint32_t cm = __byte_perm(c[j - 1], c[j], 0x5432), cp = __byte_perm(c[j], c[j + 1], 0x5432);
-                    const uint32_t dm = __byte_perm(d[j - 1], d[j], 0x5432), dp = __byte_perm(d[j], d[j + 1], 0x5432);
-                    const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(am, a[j], ap), __vimax3_u16x2(cm, cp, dm),
-                                                       __vimax3_u16x2(d[j], dp, dp));
-                    // Lane bit 15 set when centre > neighbours (values <= 255).
-                    const uint32_t keep = (c[j] + 0x7FFF7FFFu - nb) & 0x80008000u;
-                    const int bit = 2 * (2 * r + pr);
-                    smask |= ((keep >> 15) & 1u) << bit | (keep >> 31) << (bit + 1);
+                for (int r = 0; r < RPT; ++r) {
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) {
+                        const uint32_t* a = hw[r];
+                        const uint32_t* c = hw[r + 1];
+                        const uint32_t* d = hw[r + 2];
+                        const int j = 2 + pr;
+                        const uint32_t am = __byte_perm(a[j - 1], a[j], 0x5432), ap = __byte_perm(a[j], a[j + 1], 0x5432);
+                        const uint32_t cm = __byte_perm(c[j - 1], c[j], 0x5432), cp = __byte_perm(c[j], c[j + 1], 0x5432);
+                        const uint32_t dm = __byte_perm(d[j - 1], d[j], 0x5432), dp = __byte_perm(d[j], d[j + 1], 0x5432);
+                        const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(am, a[j], ap), __vimax3_u16x2(cm, cp, dm),
+                                                           __vimax3_u16x2(d[j], dp, dp));
+                        // Lane bit 15 set when centre > neighbours (values <= 255).
+                        const uint32_t keep = (c[j] + 0x7FFF7FFFu - nb) & 0x80008000u;
+                        const int bit = 2 * (2 * r + pr);
+                        smask |= ((keep >> 15) & 1u) << bit | (keep >> 31) << (bit + 1);
+                    }
                 }
             }
             // Queue the survivors: a warp scan of the per-thread counts and one
