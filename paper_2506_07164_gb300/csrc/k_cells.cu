@@ -53,24 +53,28 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
     for (int band = blockIdx.x; band < n_bands; band += gridDim.x) {
         const int j = find_tile_job(band_prefix, n_list, band);
         const Img& I = imgs[__ldg(list + j)];
-        if (!cells && !I.pmask) continue;  // block-uniform
+        // The image's fields, read once (the stores below could alias them).
+        const uint8_t* const pmask = I.pmask;
+        uint8_t* const score = I.score;
+        const int spitch = I.spitch, ncx = I.ncx, tiles_x = I.tiles_x, tile_x0 = I.tile_x0;
+        if (!cells && !pmask) continue;  // block-uniform
         const int cy = band - __ldg(band_prefix + j);
         const int rx1 = I.w - border, ry1 = I.h - border;
         const int xb0 = border & ~15;  // first chunk column
         const int n_chunks = (rx1 - xb0 + 15) >> 4;
-        uint32_t* crow = I.cell + (size_t)cy * I.ncx;
+        uint32_t* crow = I.cell + (size_t)cy * ncx;
         const int y0 = border + cy * cell, y1 = min(y0 + cell, ry1);
         const uint32_t* fl = crow;
         if (FLAGS && cells) {
             __syncthreads();  // the previous band's readers are done with bflag and colmask
-            for (int i = tid; i < I.ncx; i += CA_THREADS) bflag[i] = 0u;
+            for (int i = tid; i < ncx; i += CA_THREADS) bflag[i] = 0u;
             __syncthreads();
             for (int c0 = 0; c0 < n_chunks; c0 += 128) {
                 uint4 acc[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) acc[k] = make_uint4(0u, 0u, 0u, 0u);
                 for (int y = y0 + warp; y < y1; y += CA_THREADS / 32) {
-                    const uint8_t* srow = I.score + (size_t)y * I.spitch;
+                    const uint8_t* srow = score + (size_t)y * spitch;
                     const int py = (y - border) >> 5;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -78,7 +82,7 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                         if (c >= n_chunks) continue;
                         const int x = xb0 + 16 * c;
                         // Scores outside proposed tiles are stale: they do not count.
-                        if (I.pmask && I.pmask[(size_t)py * 4 * I.tiles_x + ((x - I.tile_x0) >> 5)] == 0) continue;
+                        if (pmask && pmask[(size_t)py * 4 * tiles_x + ((x - tile_x0) >> 5)] == 0) continue;
                         const uint4 v = *reinterpret_cast<const uint4*>(srow + x);
                         acc[k].x |= bytes_at_least(v.x, (uint32_t)t_hi);
                         acc[k].y |= bytes_at_least(v.y, (uint32_t)t_hi);
@@ -107,7 +111,7 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                 }
             }
             __syncthreads();
-            for (int i = tid; i < I.ncx; i += CA_THREADS) crow[i] = bflag[i];
+            for (int i = tid; i < ncx; i += CA_THREADS) crow[i] = bflag[i];
             fl = bflag;
         }
         for (int s0 = 0; s0 < n_chunks; s0 += CA_SEG) {
@@ -134,7 +138,7 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
             }
             __syncthreads();
             for (int y = y0 + warp; y < y1; y += CA_THREADS / 32) {
-                uint8_t* srow = I.score + (size_t)y * I.spitch;
+                uint8_t* srow = score + (size_t)y * spitch;
                 const int py = (y - border) >> 5;
                 for (int c0 = s0; c0 < s1; c0 += 128) {
                     uint4 v[4];
@@ -149,7 +153,7 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                         if (c >= s1) continue;
                         const int x = xb0 + 16 * c;
                         uint4 nv;
-                        if (I.pmask && I.pmask[(size_t)py * 4 * I.tiles_x + ((x - I.tile_x0) >> 5)] == 0) {
+                        if (pmask && pmask[(size_t)py * 4 * tiles_x + ((x - tile_x0) >> 5)] == 0) {
                             // Outside the proposed tiles the region's bytes become 0.
                             nv.x = v[k].x & ~range_mask4(x, border, rx1);
                             nv.y = v[k].y & ~range_mask4(x + 4, border, rx1);
