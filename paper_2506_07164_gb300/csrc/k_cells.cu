@@ -1,6 +1,8 @@
 // Per-cell threshold applied to FAST score maps in place.
 //
-// After the general FAST kernel the maps hold s(p) where s(p) >= t_lo.  Each
+// After the general FAST kernel the maps hold s(p) where s(p) >= t_lo, as
+// the offset score s(p) - (t_lo - 1) (0 elsewhere); thresholds are compared
+// in those units (t_hi - t_lo + 1).  Each
 // cell (anchored at the border) is flagged when some pixel scores >= t_hi --
 // by FAST itself, or here (FLAGS) from the maps, band by band.  This pass
 // turns the maps into the candidate scores NMS keys on,
@@ -49,6 +51,7 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
     __shared__ uint32_t bflag[FLAGS ? CA_MAX_CELLS : 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool cells = t_hi != t_lo;
+    const uint32_t th = (uint32_t)(t_hi - t_lo + 1);  // t_hi in the maps' offset scores (s - (t_lo - 1))
     const uint32_t magic = 0xFFFFFFFFu / (uint32_t)cell + 1u;  // n / cell == umulhi(n, magic) for n < 2^16
     for (int band = blockIdx.x; band < n_bands; band += gridDim.x) {
         const int j = find_tile_job(band_prefix, n_list, band);
@@ -84,10 +87,10 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                         // Scores outside proposed tiles are stale: they do not count.
                         if (pmask && pmask[(size_t)py * 4 * tiles_x + ((x - tile_x0) >> 5)] == 0) continue;
                         const uint4 v = *reinterpret_cast<const uint4*>(srow + x);
-                        acc[k].x |= bytes_at_least(v.x, (uint32_t)t_hi);
-                        acc[k].y |= bytes_at_least(v.y, (uint32_t)t_hi);
-                        acc[k].z |= bytes_at_least(v.z, (uint32_t)t_hi);
-                        acc[k].w |= bytes_at_least(v.w, (uint32_t)t_hi);
+                        acc[k].x |= bytes_at_least(v.x, th);
+                        acc[k].y |= bytes_at_least(v.y, th);
+                        acc[k].z |= bytes_at_least(v.z, th);
+                        acc[k].w |= bytes_at_least(v.w, th);
                     }
                 }
 #pragma unroll
@@ -161,10 +164,10 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                             nv.w = v[k].w & ~range_mask4(x + 12, border, rx1);
                         } else {
                             const uint4 fm = *reinterpret_cast<const uint4*>(colmask + 16 * (c - s0));
-                            nv.x = apply_word(v[k].x, fm.x, (uint32_t)t_hi);
-                            nv.y = apply_word(v[k].y, fm.y, (uint32_t)t_hi);
-                            nv.z = apply_word(v[k].z, fm.z, (uint32_t)t_hi);
-                            nv.w = apply_word(v[k].w, fm.w, (uint32_t)t_hi);
+                            nv.x = apply_word(v[k].x, fm.x, th);
+                            nv.y = apply_word(v[k].y, fm.y, th);
+                            nv.z = apply_word(v[k].z, fm.z, th);
+                            nv.w = apply_word(v[k].w, fm.w, th);
                         }
                         if (nv.x != v[k].x || nv.y != v[k].y || nv.z != v[k].z || nv.w != v[k].w)
                             *reinterpret_cast<uint4*>(srow + x) = nv;

@@ -9,8 +9,11 @@
 // The arc terms use the three-input packed min/max of sm_90+ (DPX):
 // minima of 3 contiguous ring pixels, then of 9 = three 3-runs 3 apart, then
 // the maximum over the 16 starts -- 40 instructions per side for 2 pixels,
-// no branches.  The map stores s(p) where s(p) >= t_lo (the lowest threshold
-// in use), else 0.
+// no branches.  The map stores the offset score s(p) - (t_lo - 1) where
+// s(p) >= t_lo (the lowest threshold in use), else 0: an order-preserving
+// shift that costs nothing (the final maximum's floor is 256 + t_lo - 1 per
+// lane instead of 256) and replaces a clip below t_lo; readers of the map
+// shift their thresholds (t_hi -> t_hi - t_lo + 1) and the reported score back.
 //
 // Data movement.  A thread owns 4 adjacent pixels x..x+3 over RPT rows.  Each
 // staged row gives it three 32-bit words (bytes x-4..x+7); one byte permute
@@ -73,12 +76,15 @@ __device__ __forceinline__ uint32_t arc_side(const uint32_t (&q)[16]) {
     return g(g(a0, a1, a2), a3, g(a4, m9[15], m9[15]));
 }
 
-// s(p) for the two pixels of a pair: lanes of max(amax - c, c - amin, 0).
-__device__ __forceinline__ uint32_t pair_score(const uint32_t (&q)[16], uint32_t c) {
+constexpr uint32_t PAIR_BIAS = 0x01000100u;  // +256 per lane keeps each difference positive
+
+// For the two pixels of a pair, lanes of max(amax - c, c - amin, off) - off,
+// with floor = PAIR_BIAS + off per lane: s(p) for off = 0, the offset score
+// max(s(p) - off, 0) otherwise.
+__device__ __forceinline__ uint32_t pair_score(const uint32_t (&q)[16], uint32_t c, uint32_t floor) {
     const uint32_t amax = arc_side<true>(q);
     const uint32_t amin = arc_side<false>(q);
-    constexpr uint32_t B = 0x01000100u;  // +256 per lane keeps each difference positive
-    return __vimax3_u16x2(amax + B - c, c + B - amin, B) - B;
+    return __vimax3_u16x2(amax + PAIR_BIAS - c, c + PAIR_BIAS - amin, floor) - floor;
 }
 
 // 0xFFFF in each 16-bit lane whose value is >= t (values and t below 2^15).
@@ -88,21 +94,20 @@ __device__ __forceinline__ uint32_t lanes_ge(uint32_t v, uint32_t t) {
 }
 
 // Score of pixel pair E (pixels x+2E, x+2E+1) of an output row from the pair
-// words of staged rows y-3 .. y+3 (hw[0..6]).
+// words of staged rows y-3 .. y+3 (hw[0..6]), offset by floor - PAIR_BIAS.
 template <int E>
-__device__ __forceinline__ uint32_t ring_pair_raw(const uint32_t (*hw)[6]) {
+__device__ __forceinline__ uint32_t ring_pair_score(const uint32_t (*hw)[6], uint32_t floor) {
     uint32_t q[16];
 #define OF_LOAD_RING(i, dx, dy) q[i] = pair_at<(dx) + 2 * E>(hw[3 + (dy)]);
     OF_RING(OF_LOAD_RING)
 #undef OF_LOAD_RING
-    return pair_score(q, hw[3][2 + E]);
+    return pair_score(q, hw[3][2 + E], floor);
 }
 
-// The same, clipped below t_lo.
+// s(p) itself.
 template <int E>
-__device__ __forceinline__ uint32_t ring_pair_score(const uint32_t (*hw)[6], uint32_t t_lo) {
-    const uint32_t se = ring_pair_raw<E>(hw);
-    return se & lanes_ge(se, t_lo);
+__device__ __forceinline__ uint32_t ring_pair_raw(const uint32_t (*hw)[6]) {
+    return ring_pair_score<E>(hw, PAIR_BIAS);
 }
 
 // Store the bytes of v selected by mask (0xFF per byte) at d: one word store
@@ -246,6 +251,9 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         // straight to the tile barrier, leaving its issue slots to others.
         const int nrows = min(RPT, ry1 - (Y0 + ty * RPT));
         const uint32_t colmask = range_mask4(x, rx0, rx1) & lane_on;
+        // Offset scores: floor of the score's final maximum, and t_hi in offset units.
+        const uint32_t floor = PAIR_BIAS + (uint32_t)(t_lo - 1) * 0x00010001u;
+        const uint32_t th = (uint32_t)(t_hi - t_lo + 1);
         // The score map's address, read once (the stores below could alias the image's fields).
         uint8_t* const sdst = I.score + x;
         const size_t spitch = (size_t)I.spitch;
@@ -267,14 +275,14 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                 const int y = Y0 + ty * RPT + r;
                 if (r > 0) load_row(r + 6);
                 // Pixel pairs (x, x+1) and (x+2, x+3), one after the other.
-                const uint32_t s0 = ring_pair_score<0>(hw + r, (uint32_t)t_lo);
-                const uint32_t s1 = ring_pair_score<1>(hw + r, (uint32_t)t_lo);
+                const uint32_t s0 = ring_pair_score<0>(hw + r, floor);
+                const uint32_t s1 = ring_pair_score<1>(hw + r, floor);
                 const uint32_t m = colmask;  // y < ry1 here
                 const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
                 if (m != 0u) *reinterpret_cast<uint32_t*>(sdst + (size_t)y * spitch) = sc;
                 if (cells && sc) {
                     const uint32_t strong =
-                        __byte_perm(lanes_ge(s0, (uint32_t)t_hi), lanes_ge(s1, (uint32_t)t_hi), 0x6420) & m;
+                        __byte_perm(lanes_ge(s0, th), lanes_ge(s1, th), 0x6420) & m;
                     if (strong) {
                         const int f = fbase + (y >= y_next ? lcw : 0);
                         if (strong & mask_a) atomicOr(&sflag[f], 1u);
@@ -338,7 +346,8 @@ int fast_blocks_per_sm(int tile_h) {
 // whole cell rows high (4 x 2 cells = 120 x 60 pixels for 30-pixel cells),
 // so it sees every pixel of its cells: it scores them, ORs each cell's "a
 // pixel scores >= t_hi" flag in shared memory, and writes the candidate score
-// S(p) = s(p) if s(p) >= T(cell(p)) else 0 -- what NMS keys on -- and the
+// S(p) = s(p) if s(p) >= T(cell(p)) else 0 -- what NMS keys on, stored as
+// the offset score S(p) - (t_lo - 1) where nonzero -- and the
 // cell flags.  Nothing is accumulated across tiles, so no threshold pass runs
 // between FAST and NMS.  A tile's writes wait for its flags: they happen in
 // the next iteration, right after the one barrier that ends each tile, from
@@ -463,12 +472,16 @@ k_fast_cells(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                     kk[i] = 0x8000u - (uint32_t)(flagged ? t_hi : t_lo);
                 }
                 const uint32_t K0 = kk[0] | (kk[1] << 16), K1 = kk[2] | (kk[3] << 16);
+                const uint32_t off = (uint32_t)(t_lo - 1) * 0x00010001u;
 #pragma unroll
                 for (int r = 0; r < CT_RPT; ++r) {
                     const int y = row0 + r;
                     if (y >= y1) break;
-                    const uint32_t s0 = sv[r][0] & ((((sv[r][0] + K0) >> 15) & 0x00010001u) * 0xFFFFu);
-                    const uint32_t s1 = sv[r][1] & ((((sv[r][1] + K1) >> 15) & 0x00010001u) * 0xFFFFu);
+                    // Kept lanes (s >= T >= t_lo) store the offset score s - (t_lo - 1).
+                    const uint32_t k0 = (((sv[r][0] + K0) >> 15) & 0x00010001u) * 0xFFFFu;
+                    const uint32_t k1 = (((sv[r][1] + K1) >> 15) & 0x00010001u) * 0xFFFFu;
+                    const uint32_t s0 = (sv[r][0] & k0) - (off & k0);
+                    const uint32_t s1 = (sv[r][1] & k1) - (off & k1);
                     store_bytes(I.score + (size_t)y * I.spitch + x, __byte_perm(s0, s1, 0x6420), colmask);
                 }
             }

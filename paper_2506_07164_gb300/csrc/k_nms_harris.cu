@@ -271,7 +271,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                     if (cells && val) {
                         const int rc = rcell[r];
                         const uint32_t fm = (sflag[rc + fa] ? ma : 0u) | (sflag[rc + fb] ? mb : 0u);
-                        val &= ~(fm & bytes_lt(val, (uint32_t)t_hi));
+                        val &= ~(fm & bytes_lt(val, (uint32_t)(t_hi - t_lo + 1)));  // maps hold s - (t_lo - 1)
                     }
                 }
                 *wp = val;

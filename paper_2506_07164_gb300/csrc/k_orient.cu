@@ -106,7 +106,7 @@ k_orient(const Img* __restrict__ imgs, int img_begin, int n_img, int slot_begin,
         k.x_l = x;
         k.y_l = y;
         k.level = I.level;
-        k.fast_score = I.score[(size_t)y * I.spitch + x];
+        k.fast_score = I.score[(size_t)y * I.spitch + x] + (call->t_lo - 1);  // the map holds s - (t_lo - 1)
         k.response = (float)resp;
         k.angle = (m10 == 0 && m01 == 0) ? 0.0f : atan2f((float)m01, (float)m10);
         k.A = a;
@@ -158,6 +158,17 @@ __global__ void k_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst) {
 void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t* dst,
                           void* stream) {
     k_inspect_cells<<<64, 256, 0, (cudaStream_t)stream>>>(imgs, img, t_hi, t_lo, dst);
+}
+
+// Score-map copies: the map's offset scores back to S(p) (nonzero bytes + off).
+__global__ void k_inspect_score(uint8_t* d, int64_t n, int off) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (d[i]) d[i] = (uint8_t)(d[i] + off);
+}
+
+void launch_inspect_score(uint8_t* dst, int64_t n, int off, void* stream) {
+    if (n <= 0 || off == 0) return;
+    k_inspect_score<<<256, 256, 0, (cudaStream_t)stream>>>(dst, n, off);
 }
 
 void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream) {

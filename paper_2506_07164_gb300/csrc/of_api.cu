@@ -1503,6 +1503,8 @@ int64_t of_inspect(of_handle* H, int what, int frame, int level, void* dst, int6
             OF_CK(cudaMemcpy2DAsync(d + (size_t)s.border * I.w + s.border, I.w,
                                     I.score + (size_t)s.border * I.spitch + s.border, I.spitch, rw,
                                     rh, cudaMemcpyDeviceToDevice, st));
+        ofk::launch_inspect_score(d, bytes, s.t_lo - 1, st);  // the maps hold s - (t_lo - 1)
+        OF_CK(cudaGetLastError());
     } else if (what == OF_BUF_CELLT) {
         ofk::launch_inspect_cells(P->d_img(), frame * nl + level, s.t_hi, s.t_lo, d, st);
         OF_CK(cudaGetLastError());

@@ -154,6 +154,7 @@ void launch_orient_range(const Img* imgs, int img_begin, int n_img, int slot_beg
 void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t* dst,
                           void* stream);
 void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream);
+void launch_inspect_score(uint8_t* dst, int64_t n, int off, void* stream);
 int select_smem_bytes(int max_quota);
 // Paper ablation variants (k_ablation.cu); returns the number of launches.
 int launch_variant(int fast_v, int harris_v, const uint8_t* img, int w, int h, int pitch, int t, int border,
