@@ -76,15 +76,15 @@ __device__ __forceinline__ uint32_t arc_side(const uint32_t (&q)[16]) {
     return g(g(a0, a1, a2), a3, g(a4, m9[15], m9[15]));
 }
 
-constexpr uint32_t PAIR_BIAS = 0x01000100u;  // +256 per lane keeps each difference positive
+constexpr uint32_t PAIR_BIAS = 0x02000200u;  // 512 per lane: every biased difference stays positive
 
-// For the two pixels of a pair, lanes of max(amax - c, c - amin, off) - off,
-// with floor = PAIR_BIAS + off per lane: s(p) for off = 0, the offset score
-// max(s(p) - off, 0) otherwise.
-__device__ __forceinline__ uint32_t pair_score(const uint32_t (&q)[16], uint32_t c, uint32_t floor) {
+// For the two pixels of a pair, lanes of 512 + max(amax - c - off, c - amin - off, 0)
+// with kb = PAIR_BIAS - off per lane (0 <= off <= 254): the low byte of each
+// lane is the offset score max(s(p) - off, 0) (s(p) itself for off = 0).
+__device__ __forceinline__ uint32_t pair_score(const uint32_t (&q)[16], uint32_t c, uint32_t kb) {
     const uint32_t amax = arc_side<true>(q);
     const uint32_t amin = arc_side<false>(q);
-    return __vimax3_u16x2(amax + PAIR_BIAS - c, c + PAIR_BIAS - amin, floor) - floor;
+    return __vimax3_u16x2(amax + kb - c, c + kb - amin, PAIR_BIAS);
 }
 
 // 0xFFFF in each 16-bit lane whose value is >= t (values and t below 2^15).
@@ -93,21 +93,21 @@ __device__ __forceinline__ uint32_t lanes_ge(uint32_t v, uint32_t t) {
     return ((d >> 15) & 0x00010001u) * 0xFFFFu;
 }
 
-// Score of pixel pair E (pixels x+2E, x+2E+1) of an output row from the pair
-// words of staged rows y-3 .. y+3 (hw[0..6]), offset by floor - PAIR_BIAS.
+// Biased offset score (pair_score) of pixel pair E (pixels x+2E, x+2E+1) of
+// an output row from the pair words of staged rows y-3 .. y+3 (hw[0..6]).
 template <int E>
-__device__ __forceinline__ uint32_t ring_pair_score(const uint32_t (*hw)[6], uint32_t floor) {
+__device__ __forceinline__ uint32_t ring_pair_score(const uint32_t (*hw)[6], uint32_t kb) {
     uint32_t q[16];
 #define OF_LOAD_RING(i, dx, dy) q[i] = pair_at<(dx) + 2 * E>(hw[3 + (dy)]);
     OF_RING(OF_LOAD_RING)
 #undef OF_LOAD_RING
-    return pair_score(q, hw[3][2 + E], floor);
+    return pair_score(q, hw[3][2 + E], kb);
 }
 
-// s(p) itself.
+// s(p) itself, in 16-bit lanes.
 template <int E>
 __device__ __forceinline__ uint32_t ring_pair_raw(const uint32_t (*hw)[6]) {
-    return ring_pair_score<E>(hw, PAIR_BIAS);
+    return ring_pair_score<E>(hw, PAIR_BIAS) - PAIR_BIAS;
 }
 
 // Store the bytes of v selected by mask (0xFF per byte) at d: one word store
@@ -251,9 +251,9 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         // straight to the tile barrier, leaving its issue slots to others.
         const int nrows = min(RPT, ry1 - (Y0 + ty * RPT));
         const uint32_t colmask = range_mask4(x, rx0, rx1) & lane_on;
-        // Offset scores: floor of the score's final maximum, and t_hi in offset units.
-        const uint32_t floor = PAIR_BIAS + (uint32_t)(t_lo - 1) * 0x00010001u;
-        const uint32_t th = (uint32_t)(t_hi - t_lo + 1);
+        // Offset scores: the bias of the score's terms, and t_hi in biased offset units.
+        const uint32_t kb = PAIR_BIAS - (uint32_t)(t_lo - 1) * 0x00010001u;
+        const uint32_t th = (uint32_t)(t_hi - t_lo + 1) + 512u;
         // The score map's address, read once (the stores below could alias the image's fields).
         uint8_t* const sdst = I.score + x;
         const size_t spitch = (size_t)I.spitch;
@@ -275,8 +275,8 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                 const int y = Y0 + ty * RPT + r;
                 if (r > 0) load_row(r + 6);
                 // Pixel pairs (x, x+1) and (x+2, x+3), one after the other.
-                const uint32_t s0 = ring_pair_score<0>(hw + r, floor);
-                const uint32_t s1 = ring_pair_score<1>(hw + r, floor);
+                const uint32_t s0 = ring_pair_score<0>(hw + r, kb);  // 512 + offset score per lane
+                const uint32_t s1 = ring_pair_score<1>(hw + r, kb);
                 const uint32_t m = colmask;  // y < ry1 here
                 const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
                 if (m != 0u) *reinterpret_cast<uint32_t*>(sdst + (size_t)y * spitch) = sc;
