@@ -220,13 +220,14 @@ struct Plan {
         int dl_begin = 0, n_list = 0, det_tiles = 0, dp_off = 0;
         int fast_tiles = 0, fp_off = 0;             // cell-tile FAST: tiles and prefix offset in gp_fast
         int nms64_tiles = 0, np_off = 0;            // NMS with 64-row tiles: tiles and prefix offset in gp_nms64
+        int fast128_tiles = 0, f128_off = 0;        // FAST with 128-row tiles: tiles and prefix offset in gp_fast128
         int n_bands = 0, rp_off = 0;                // threshold pass: cell rows and prefix offset in gp_rows
         int slot_begin = 0, slot_end = 0;
         std::vector<int> rs_job, rs_n;              // per level: first resize job, jobs
         std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
     };
     std::vector<Group> groups[kMaxGroups + 1];
-    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64;
+    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_fast128;
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
     bool apply_flags = false;    // the threshold pass sets the cell flags (the general FAST kernel does not)
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
@@ -235,7 +236,7 @@ struct Plan {
     Call h_call{};
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0;
-    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0;
+    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gf128 = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -268,6 +269,7 @@ struct Plan {
     const int32_t* d_gfp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfp); }
     const int32_t* d_grp() const { return reinterpret_cast<const int32_t*>(dbuf + off_grp); }
     const int32_t* d_gnp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gnp); }
+    const int32_t* d_gf128() const { return reinterpret_cast<const int32_t*>(dbuf + off_gf128); }
 };
 
 // Resident blocks per SM of the plan's FAST kernel.
@@ -364,6 +366,10 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list, G.nms64_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                             H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, false, 64);
+            else if (P->apply_flags && P->tun.fast_tile_h == 128)
+                launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gf128() + G.f128_off, G.n_list,
+                            G.fast128_tiles, P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, false, 128);
             else
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
@@ -630,10 +636,13 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             G.fp_off = (int)P->gp_fast.size();
             G.rp_off = (int)P->gp_rows.size();
             G.np_off = (int)P->gp_nms64.size();
+            G.f128_off = (int)P->gp_fast128.size();
             for (int j = j0; j < j1; ++j) {
                 const Img& I = P->h_img[P->det_list[j]];
                 P->gp_nms64.push_back(G.nms64_tiles);
                 G.nms64_tiles += I.tiles_x * ((I.h - 2 * s.border + 63) / 64);
+                P->gp_fast128.push_back(G.fast128_tiles);
+                G.fast128_tiles += I.tiles_x * ((I.h - 2 * s.border + 127) / 128);
                 P->gp_fast.push_back(G.fast_tiles);
                 G.fast_tiles += P->cell_tiles ? I.ftiles_x * ((I.ncy + ct_cell_rows(s.cell) - 1) / ct_cell_rows(s.cell)) : 0;
                 P->gp_rows.push_back(G.n_bands);
@@ -691,6 +700,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
     P->tun.nms_tile_h = 64;
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64);  // also raises its shared-memory limit before any capture
+    fast_blocks_per_sm(128);  // raises the 128-row FAST kernel's shared-memory limit before any capture
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
 
@@ -744,6 +754,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_rows.size(), 1), 16);
     P->off_gnp = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_nms64.size(), 1), 16);
+    P->off_gf128 = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_fast128.size(), 1), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -769,6 +781,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_gfp, P->gp_fast.data(), sizeof(int32_t) * P->gp_fast.size());
     put(P->off_grp, P->gp_rows.data(), sizeof(int32_t) * P->gp_rows.size());
     put(P->off_gnp, P->gp_nms64.data(), sizeof(int32_t) * P->gp_nms64.size());
+    put(P->off_gf128, P->gp_fast128.data(), sizeof(int32_t) * P->gp_fast128.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);
@@ -1009,10 +1022,10 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     // where the cell size allows it; fast_ms below is FAST + NMS.
     best = 1e30f;
     int bb = P->tun.fast_blocks_per_sm, bo = 0, bv = P->tun.fast_cell_tiles, bt = P->tun.fast_tile_h;
-    // Forms: 0 = general kernel (32- or 64-row tiles when the pass sets the flags), 1 = cell tiles.
-    for (int cand = 0; cand < 3 && rc == OF_OK; ++cand) {
-        const int v = cand == 2 ? 1 : 0, th = cand == 1 ? 64 : 32;
-        if ((v == 1 && !P->cell_tiles) || (th == 64 && !P->apply_flags)) continue;
+    // Forms: general kernel (32-row tiles; 64 or 128 rows when the pass sets the flags), cell tiles.
+    for (int cand = 0; cand < 4 && rc == OF_OK; ++cand) {
+        const int v = cand == 3 ? 1 : 0, th = cand == 1 ? 64 : cand == 2 ? 128 : 32;
+        if ((v == 1 && !P->cell_tiles) || (th > 32 && !P->apply_flags)) continue;
         P->tun.fast_cell_tiles = v;
         P->tun.fast_tile_h = th;
         for (int bp = 1; bp <= plan_fast_bps(P) && rc == OF_OK; ++bp) {
@@ -1278,7 +1291,8 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         (t->resize_tma != 0 && t->resize_tma != 1) || t->fast_blocks_per_sm < 1 ||
         t->fast_blocks_per_sm > std::max(fast_blocks_per_sm(), fast_cells_blocks_per_sm(CT_MAX_CELL)) ||
         t->nms_blocks_per_sm < 1 ||
-        (t->nms_tile_h != 32 && t->nms_tile_h != 64) || (t->fast_tile_h != 32 && t->fast_tile_h != 64) ||
+        (t->nms_tile_h != 32 && t->nms_tile_h != 64) ||
+        (t->fast_tile_h != 32 && t->fast_tile_h != 64 && t->fast_tile_h != 128) ||
         t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h == 64 ? 64 : 32) || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
         (t->fast_cell_tiles != 0 && t->fast_cell_tiles != 1))
