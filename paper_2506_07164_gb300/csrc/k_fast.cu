@@ -141,17 +141,17 @@ __device__ __forceinline__ TileInfo tile_info(const Img* __restrict__ imgs, cons
 
 constexpr int FAST_BOX = IMG_BOX_ROWS * SROW;           // bytes per TMA box (160 x 40)
 constexpr int FAST_BUF = (FAST_BOX + 127) / 128 * 128;  // buffer stride in shared memory
-// Dynamic shared memory of the 128-row kernel: two buffers of four stacked boxes + alignment slack.
-constexpr int FAST128_DYN = 2 * ((128 + 8 + IMG_BOX_ROWS - 1) / IMG_BOX_ROWS) * FAST_BUF + 128;
+// Dynamic shared memory of the TH-row kernel: two buffers of stacked boxes + alignment slack.
+constexpr int fast_dyn_bytes(int th) { return 2 * ((th + 8 + IMG_BOX_ROWS - 1) / IMG_BOX_ROWS) * FAST_BUF + 128; }
 
 // Persistent: each block walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // Thread 0 fetches the next tile by TMA into the other buffer while the
 // block scores the current one.  FLAGS: also set the per-cell "a pixel
 // scores >= t_hi" flags (else the threshold pass computes them).  TH: tile
-// rows, 32 or (without FLAGS) 64 or 128 -- a taller tile stacks more image
-// boxes and divides the barriers per pixel and the staged rows per output
-// row; 128-row tiles keep their buffers in dynamic shared memory (over the
-// 48 KB static limit).
+// rows, 32 or (without FLAGS) 64, 128 or 256 -- a taller tile stacks more
+// image boxes and divides the barriers per pixel and the staged rows per
+// output row; 128- and 256-row tiles keep their buffers in dynamic shared
+// memory (over the 48 KB static limit).
 template <bool FLAGS, int TH>
 __global__ void __launch_bounds__(DET_THREADS, TH == 32 ? 3 : 2)
 k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
@@ -326,8 +326,13 @@ void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_p
         k_fast<false, 64><<<grid, DET_THREADS, 0, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps, call,
                                                          t_hi, t_lo, border, cell, order);
     else if (tile_h == 128)
-        k_fast<false, 128><<<grid, DET_THREADS, FAST128_DYN, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps,
-                                                                   call, t_hi, t_lo, border, cell, order);
+        k_fast<false, 128><<<grid, DET_THREADS, fast_dyn_bytes(128), st>>>(imgs, img_list, tile_prefix, n_list,
+                                                                           n_tiles, maps, call, t_hi, t_lo, border,
+                                                                           cell, order);
+    else if (tile_h == 256)
+        k_fast<false, 256><<<grid, DET_THREADS, fast_dyn_bytes(256), st>>>(imgs, img_list, tile_prefix, n_list,
+                                                                           n_tiles, maps, call, t_hi, t_lo, border,
+                                                                           cell, order);
     else
         k_fast<false, 32><<<grid, DET_THREADS, 0, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps, call,
                                                          t_hi, t_lo, border, cell, order);
@@ -340,16 +345,25 @@ int fast_blocks_per_sm() {
     return n;
 }
 
+template <int TH>
+static cudaError_t tall_fast_occupancy(int* n) {
+    cudaError_t e = cudaFuncSetAttribute(k_fast<false, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         fast_dyn_bytes(TH));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_fast<false, TH>, DET_THREADS, fast_dyn_bytes(TH));
+    return e;
+}
+
 // Resident blocks per SM of the flag-free kernel with tile_h-row tiles (for
-// 128 rows it also raises the kernel's dynamic shared-memory limit, before any
-// launch or capture uses it).
+// 128 and 256 rows it also raises the kernel's dynamic shared-memory limit,
+// before any launch or capture uses it).
 int fast_blocks_per_sm(int tile_h) {
     int n = 0;
     cudaError_t e;
     if (tile_h == 128) {
-        e = cudaFuncSetAttribute(k_fast<false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, FAST128_DYN);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<false, 128>, DET_THREADS, FAST128_DYN);
+        e = tall_fast_occupancy<128>(&n);
+    } else if (tile_h == 256) {
+        e = tall_fast_occupancy<256>(&n);
     } else {
         e = tile_h == 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<false, 64>, DET_THREADS, 0)
                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<false, 32>, DET_THREADS, 0);

@@ -220,14 +220,14 @@ struct Plan {
         int dl_begin = 0, n_list = 0, det_tiles = 0, dp_off = 0;
         int fast_tiles = 0, fp_off = 0;             // cell-tile FAST: tiles and prefix offset in gp_fast
         int nms64_tiles = 0, np_off = 0;            // NMS with 64-row tiles: tiles and prefix offset in gp_nms64
-        int fast128_tiles = 0, f128_off = 0;        // FAST with 128-row tiles: tiles and prefix offset in gp_fast128
+        int ftall_tiles[2] = {0, 0}, ftall_off[2] = {0, 0};  // FAST on FT_HS[i]-row tiles: tiles, offset in gp_ftall[i]
         int n_bands = 0, rp_off = 0;                // threshold pass: cell rows and prefix offset in gp_rows
         int slot_begin = 0, slot_end = 0;
         std::vector<int> rs_job, rs_n;              // per level: first resize job, jobs
         std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
     };
     std::vector<Group> groups[kMaxGroups + 1];
-    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_fast128;
+    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_ftall[2];
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
     bool apply_flags = false;    // the threshold pass sets the cell flags (the general FAST kernel does not)
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
@@ -236,7 +236,7 @@ struct Plan {
     Call h_call{};
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0;
-    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gf128 = 0;
+    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gft[2] = {0, 0};
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -269,7 +269,7 @@ struct Plan {
     const int32_t* d_gfp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfp); }
     const int32_t* d_grp() const { return reinterpret_cast<const int32_t*>(dbuf + off_grp); }
     const int32_t* d_gnp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gnp); }
-    const int32_t* d_gf128() const { return reinterpret_cast<const int32_t*>(dbuf + off_gf128); }
+    const int32_t* d_gft(int i) const { return reinterpret_cast<const int32_t*>(dbuf + off_gft[i]); }
 };
 
 // Resident blocks per SM of the plan's FAST kernel.
@@ -366,10 +366,12 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list, G.nms64_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                             H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, false, 64);
-            else if (P->apply_flags && P->tun.fast_tile_h == 128)
-                launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gf128() + G.f128_off, G.n_list,
-                            G.fast128_tiles, P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, false, 128);
+            else if (P->apply_flags && (P->tun.fast_tile_h == FT_HS[0] || P->tun.fast_tile_h == FT_HS[1])) {
+                const int i = P->tun.fast_tile_h == FT_HS[0] ? 0 : 1;
+                launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gft(i) + G.ftall_off[i], G.n_list,
+                            G.ftall_tiles[i], P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, false, FT_HS[i]);
+            }
             else
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
@@ -636,13 +638,15 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             G.fp_off = (int)P->gp_fast.size();
             G.rp_off = (int)P->gp_rows.size();
             G.np_off = (int)P->gp_nms64.size();
-            G.f128_off = (int)P->gp_fast128.size();
+            for (int i = 0; i < 2; ++i) G.ftall_off[i] = (int)P->gp_ftall[i].size();
             for (int j = j0; j < j1; ++j) {
                 const Img& I = P->h_img[P->det_list[j]];
                 P->gp_nms64.push_back(G.nms64_tiles);
                 G.nms64_tiles += I.tiles_x * ((I.h - 2 * s.border + 63) / 64);
-                P->gp_fast128.push_back(G.fast128_tiles);
-                G.fast128_tiles += I.tiles_x * ((I.h - 2 * s.border + 127) / 128);
+                for (int i = 0; i < 2; ++i) {
+                    P->gp_ftall[i].push_back(G.ftall_tiles[i]);
+                    G.ftall_tiles[i] += I.tiles_x * ((I.h - 2 * s.border + FT_HS[i] - 1) / FT_HS[i]);
+                }
                 P->gp_fast.push_back(G.fast_tiles);
                 G.fast_tiles += P->cell_tiles ? I.ftiles_x * ((I.ncy + ct_cell_rows(s.cell) - 1) / ct_cell_rows(s.cell)) : 0;
                 P->gp_rows.push_back(G.n_bands);
@@ -700,7 +704,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
     P->tun.nms_tile_h = 64;
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64);  // also raises its shared-memory limit before any capture
-    fast_blocks_per_sm(128);  // raises the 128-row FAST kernel's shared-memory limit before any capture
+    for (int i = 0; i < 2; ++i) fast_blocks_per_sm(FT_HS[i]);  // raise the tall kernels' limits before any capture
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
 
@@ -754,8 +758,10 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_rows.size(), 1), 16);
     P->off_gnp = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_nms64.size(), 1), 16);
-    P->off_gf128 = off;
-    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_fast128.size(), 1), 16);
+    for (int i = 0; i < 2; ++i) {
+        P->off_gft[i] = off;
+        off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_ftall[i].size(), 1), 16);
+    }
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -781,7 +787,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_gfp, P->gp_fast.data(), sizeof(int32_t) * P->gp_fast.size());
     put(P->off_grp, P->gp_rows.data(), sizeof(int32_t) * P->gp_rows.size());
     put(P->off_gnp, P->gp_nms64.data(), sizeof(int32_t) * P->gp_nms64.size());
-    put(P->off_gf128, P->gp_fast128.data(), sizeof(int32_t) * P->gp_fast128.size());
+    for (int i = 0; i < 2; ++i) put(P->off_gft[i], P->gp_ftall[i].data(), sizeof(int32_t) * P->gp_ftall[i].size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);
@@ -1022,9 +1028,9 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     // where the cell size allows it; fast_ms below is FAST + NMS.
     best = 1e30f;
     int bb = P->tun.fast_blocks_per_sm, bo = 0, bv = P->tun.fast_cell_tiles, bt = P->tun.fast_tile_h;
-    // Forms: general kernel (32-row tiles; 64 or 128 rows when the pass sets the flags), cell tiles.
-    for (int cand = 0; cand < 4 && rc == OF_OK; ++cand) {
-        const int v = cand == 3 ? 1 : 0, th = cand == 1 ? 64 : cand == 2 ? 128 : 32;
+    // Forms: general kernel (32-row tiles; 64, 128 or 256 rows when the pass sets the flags), cell tiles.
+    for (int cand = 0; cand < 5 && rc == OF_OK; ++cand) {
+        const int v = cand == 4 ? 1 : 0, th = cand == 4 ? 32 : 32 << cand;
         if ((v == 1 && !P->cell_tiles) || (th > 32 && !P->apply_flags)) continue;
         P->tun.fast_cell_tiles = v;
         P->tun.fast_tile_h = th;
@@ -1292,7 +1298,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         t->fast_blocks_per_sm > std::max(fast_blocks_per_sm(), fast_cells_blocks_per_sm(CT_MAX_CELL)) ||
         t->nms_blocks_per_sm < 1 ||
         (t->nms_tile_h != 32 && t->nms_tile_h != 64) ||
-        (t->fast_tile_h != 32 && t->fast_tile_h != 64 && t->fast_tile_h != 128) ||
+        (t->fast_tile_h != 32 && t->fast_tile_h != 64 && t->fast_tile_h != FT_HS[0] && t->fast_tile_h != FT_HS[1]) ||
         t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h == 64 ? 64 : 32) || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
         (t->fast_cell_tiles != 0 && t->fast_cell_tiles != 1))

@@ -28,6 +28,8 @@ constexpr int SCORE_BOX_ROWS = TILE_H + 2; // score TMA box: rows Y0-1 .. Y0+TIL
 // CT_MAX_CELL pixels.  A warp scores CT_RPT rows of one cell row, so a cell
 // row takes ct_warps(cell) warps; a tile's staged rows fit two stacked
 // 40-row image boxes.
+// Tall tiles of the flag-free FAST kernel (dynamic shared memory).
+constexpr int FT_HS[2] = {128, 256};
 constexpr int CT_MAX_W = 124;
 constexpr int CT_MIN_CELL = 8;
 constexpr int CT_MAX_CELL = 30;
