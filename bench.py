@@ -293,7 +293,7 @@ FAST_OPS_PER_PX = 40.5
 # DRAM bytes of one k_fast launch per frame, from the ncu capture summarised in
 # profiles/k_fast_1080p8.md (64-frame launch, scaled per frame), valid while
 # k_fast.cu has this SHA-1.
-FAST_TRAFFIC = {"sha1": "6cf446cd6e3bc16767c4b8b38c3410207a331e4e", "bytes_per_frame": (489448704 + 349216768) / 64}
+FAST_TRAFFIC = {"sha1": "e741cfaa3ed4bc94cfb22221a3adacd4de4b2dda", "bytes_per_frame": (456577536 + 348346880) / 64}
 
 
 def file_sha1(path):
