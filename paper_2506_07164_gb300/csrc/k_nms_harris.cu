@@ -22,6 +22,8 @@
 //    in the image's list.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "of_internal.h"
 #include "of_tile.cuh"
 #include "of_tma.cuh"
@@ -119,8 +121,8 @@ struct NmsGeom {
 // FINAL: the score maps already hold S(p) inside the detect region (the
 // cell-tile FAST kernel applied the cell thresholds); the kernel then skips the
 // cell bookkeeping and the candidate pass and masks the region in registers.
-// TH: tile rows (32; or 64 with FINAL -- fewer barriers per pixel and ~2x the
-// survivors per Harris phase).  Buffers live in dynamic shared memory
+// TH: tile rows (32; or 64 or 128 with FINAL -- fewer barriers per pixel and
+// more survivors per Harris phase).  Buffers live in dynamic shared memory
 // (NmsGeom<TH>::DYN_BYTES, from a 128-byte boundary).
 template <bool FINAL, int TH>
 __global__ void __launch_bounds__(DET_THREADS, TH == 32 ? 5 : 4)
@@ -284,7 +286,9 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         //    survivor, so a warp entirely below it only takes part in the queue.
         {
             const int nrows = min(RPT, ry1 - (Y0 + ty * RPT));
-            uint32_t smask = 0u;  // survivor bits: (2 * row + pair) * 2 + lane
+            // Survivor bits (2 * row + pair) * 2 + lane: 4 per row, 64-bit beyond 8 rows.
+            using SMask = typename std::conditional<(RPT > 8), unsigned long long, uint32_t>::type;
+            SMask smask = 0u;
             if (nrows > 0) {
                 uint32_t hw[RPT + 2][6];
                 // FINAL: the in-region bytes of the three words this thread reads.
@@ -329,13 +333,13 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                         // Lane bit 15 set when centre > neighbours (values <= 255).
                         const uint32_t keep = (c[j] + 0x7FFF7FFFu - nb) & 0x80008000u;
                         const int bit = 2 * (2 * r + pr);
-                        smask |= ((keep >> 15) & 1u) << bit | (keep >> 31) << (bit + 1);
+                        smask |= (SMask)((keep >> 15) & 1u) << bit | (SMask)(keep >> 31) << (bit + 1);
                     }
                 }
             }
             // Queue the survivors: a warp scan of the per-thread counts and one
             // shared atomic per warp.
-            const int mine = __popc(smask);
+            const int mine = RPT > 8 ? __popcll((unsigned long long)smask) : __popc((uint32_t)smask);
             int incl = mine;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -346,7 +350,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             if (lane == 31 && incl) wbase = atomicAdd(&nq, incl);
             int slot = __shfl_sync(0xFFFFFFFFu, wbase, 31) + incl - mine;
             while (smask) {
-                const int bit = __ffs(smask) - 1;
+                const int bit = (RPT > 8 ? __ffsll((long long)smask) : __ffs((int)smask)) - 1;
                 smask &= smask - 1u;
                 queue[slot++] = ((uint32_t)(ty * RPT + (bit >> 2)) << 16) |
                                 (uint32_t)(4 * lane + 2 * ((bit >> 1) & 1) + (bit & 1));
@@ -406,6 +410,9 @@ void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* 
     else if (tile_h == 64)
         launch_nms_t<true, 64>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
                                border, cell, grid, order, stream);
+    else if (tile_h == 128)
+        launch_nms_t<true, 128>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
+                                border, cell, grid, order, stream);
     else
         launch_nms_t<true, 32>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
                                border, cell, grid, order, stream);
@@ -414,15 +421,23 @@ void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* 
 // Resident blocks per SM of the NMS kernel with TH-row tiles (final scores;
 // the 32-row general variant has the same occupancy).  Raises the dynamic
 // shared-memory limit where the buffers need it.
+template <int TH>
+static cudaError_t tall_nms_occupancy(int* n) {
+    cudaError_t e = cudaFuncSetAttribute(k_nms_harris<true, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         NmsGeom<TH>::DYN_BYTES);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_nms_harris<true, TH>, DET_THREADS,
+                                                          NmsGeom<TH>::DYN_BYTES);
+    return e;
+}
+
 int nms_blocks_per_sm(int tile_h) {
     int n = 0;
     cudaError_t e;
     if (tile_h == 64) {
-        e = cudaFuncSetAttribute(k_nms_harris<true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 NmsGeom<64>::DYN_BYTES);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_harris<true, 64>, DET_THREADS,
-                                                              NmsGeom<64>::DYN_BYTES);
+        e = tall_nms_occupancy<64>(&n);
+    } else if (tile_h == 128) {
+        e = tall_nms_occupancy<128>(&n);
     } else {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_harris<false, 32>, DET_THREADS,
                                                           NmsGeom<32>::DYN_BYTES);

@@ -386,6 +386,11 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                                   G.nms64_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
                                   s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, true,
                                   64);
+            else if (P->tun.nms_tile_h == FT_HS[0])  // same tiling as the 128-row FAST tiles
+                launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gft(0) + G.ftall_off[0], G.n_list,
+                                  G.ftall_tiles[0], P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi,
+                                  s.t_lo, s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st,
+                                  true, FT_HS[0]);
             else
                 launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list,
                                   G.det_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
@@ -705,6 +710,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.nms_tile_h = 64;
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64);  // also raises its shared-memory limit before any capture
     for (int i = 0; i < 2; ++i) fast_blocks_per_sm(FT_HS[i]);  // raise the tall kernels' limits before any capture
+    nms_blocks_per_sm(FT_HS[0]);
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
 
@@ -1057,11 +1063,11 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     P->tun.fast_order = bo;
     P->tun.fast_ms = best;
     // NMS + Harris (appends candidates: clear the counters before each run),
-    // 32- or 64-row tiles.
+    // 32-, 64- or 128-row tiles.
     best = 1e30f;
     bb = P->tun.nms_blocks_per_sm, bo = 0;
     int bth = P->tun.nms_tile_h;
-    for (int th = 32; th <= 64 && rc == OF_OK; th += 32)
+    for (int th = 32; th <= 128 && rc == OF_OK; th *= 2)
     for (int bp = 1; bp <= nms_blocks_per_sm(th) && rc == OF_OK; ++bp) {
         for (int order = 0; order < 2 && rc == OF_OK; ++order) {
             P->tun.nms_tile_h = th;
@@ -1297,9 +1303,9 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         (t->resize_tma != 0 && t->resize_tma != 1) || t->fast_blocks_per_sm < 1 ||
         t->fast_blocks_per_sm > std::max(fast_blocks_per_sm(), fast_cells_blocks_per_sm(CT_MAX_CELL)) ||
         t->nms_blocks_per_sm < 1 ||
-        (t->nms_tile_h != 32 && t->nms_tile_h != 64) ||
+        (t->nms_tile_h != 32 && t->nms_tile_h != 64 && t->nms_tile_h != 128) ||
         (t->fast_tile_h != 32 && t->fast_tile_h != 64 && t->fast_tile_h != FT_HS[0] && t->fast_tile_h != FT_HS[1]) ||
-        t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h == 64 ? 64 : 32) || (t->fast_order != 0 && t->fast_order != 1) ||
+        t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h) || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
         (t->fast_cell_tiles != 0 && t->fast_cell_tiles != 1))
         return fail(OF_ERR_ARG, "tuning field out of range");

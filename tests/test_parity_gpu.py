@@ -368,7 +368,7 @@ def test_frame_groups_equal_one_group_and_oracle():
     got = {}
     for groups in (1, 2, 3, 5):
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
-                           stream_groups=groups, nms_tile_h=64 if groups % 2 else 32,
+                           stream_groups=groups, nms_tile_h={1: 64, 2: 32, 3: 128, 5: 128}[groups],
                            fast_tile_h={1: 32, 2: 64, 3: 128, 5: 256}[groups])
         det.set_tuning(dev, tun, levels=6, fast_t=20, n_features=400)
         det.detect_batch(dev, levels=6, fast_t=20, n_features=400)
@@ -397,7 +397,7 @@ def test_cell_sizes_both_fast_forms(cell):
     dev = torch.from_numpy(img).cuda()
     det = ofg.Detector(900, 700, max_levels=3, max_features=600, fast_t_lo=6, cell=cell)
     ora = oracle.detect(img, levels=3, scale=1.2, fast_t=22, fast_t_lo=6, n_features=600, cell=cell)
-    for form, nms_h, fast_h in ((0, 32, 32), (1, 64, 32), (0, 64, 64), (0, 64, 128), (0, 32, 256)):
+    for form, nms_h, fast_h in ((0, 32, 32), (1, 64, 32), (0, 64, 64), (0, 128, 128), (0, 32, 256), (1, 128, 32)):
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
                            stream_groups=1, fast_cell_tiles=form, nms_tile_h=nms_h, fast_tile_h=fast_h)
         det.set_tuning([dev], tun, levels=3, scale=1.2, fast_t=22, n_features=600)
