@@ -725,7 +725,10 @@ def main():
         cpu = cpu_baseline(pool, min(cores, 16), frames_np, n)
     pool.close()
 
-    kernels_per_step = ((LEVELS - 1) + 4) * int(tuning.get("stream_groups", 1))
+    # Per frame group: one resize per level after the first, FAST, the threshold
+    # pass (general FAST form only), NMS + Harris, top-N, orientation.
+    per_group = (LEVELS - 1) + 4 + (0 if int(tuning.get("fast_cell_tiles", 0)) else 1)
+    kernels_per_step = per_group * int(tuning.get("stream_groups", 1))
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_b / args.steps, 4),
