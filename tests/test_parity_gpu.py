@@ -295,6 +295,31 @@ def test_batch_then_sync_ok():
     det.close()
 
 
+# ------------------------------------------------------------ full size
+def test_full_size_batch_autotuned_matches_oracle():
+    """The benchmark's workload at its full size and launch configuration:
+    128 frames of 1920x1080, 8 levels at scale 1.2, t = 20 with fallback 7,
+    1000 features, autotuned (forked frame groups, tall tiles).  Every
+    frame's records equal those of the frame it copies (4 distinct scenes
+    in 128 separate device buffers), and the 4 scenes' records equal the
+    oracle's."""
+    distinct = [synth.scene(1920, 1080, seed, background="pink") for seed in range(4)]
+    src = [torch.from_numpy(f).cuda() for f in distinct]
+    dev = [src[i % 4].clone() for i in range(128)]
+    det = ofg.Detector(1920, 1080, max_levels=8, max_features=1000, max_batch=128, fast_t_lo=7)
+    tun = det.autotune(dev, levels=8, fast_t=20, n_features=1000, reps=1)
+    assert 1 <= tun.stream_groups <= 8
+    det.detect_batch(dev, levels=8, fast_t=20, n_features=1000)
+    torch.cuda.synchronize()
+    res = det.batch_results(128, 1000)
+    for i in range(128):
+        assert np.array_equal(res[i].view(np.uint8), res[i % 4].view(np.uint8)), i
+    for k in range(4):
+        compare_keypoints(res[k], oracle.detect(distinct[k], levels=8, scale=1.2, fast_t=20, fast_t_lo=7,
+                                                n_features=1000))
+    det.close()
+
+
 # ------------------------------------------------------------ autotuner
 def test_autotuner_choice_is_valid_and_results_unchanged():
     sizes = [(720, 540), (1080, 720), (640, 480)]
