@@ -11,9 +11,10 @@
 // the maximum over the 16 starts -- 40 instructions per side for 2 pixels,
 // no branches.  The map stores the offset score s(p) - (t_lo - 1) where
 // s(p) >= t_lo (the lowest threshold in use), else 0: an order-preserving
-// shift that costs nothing (the final maximum's floor is 256 + t_lo - 1 per
-// lane instead of 256) and replaces a clip below t_lo; readers of the map
-// shift their thresholds (t_hi -> t_hi - t_lo + 1) and the reported score back.
+// shift that costs nothing (both terms of the final maximum carry a bias of
+// 512 - (t_lo - 1) per lane and its floor is 512, so each lane's low byte is
+// the offset score) and replaces a clip below t_lo; readers of the map shift
+// their thresholds (t_hi -> t_hi - t_lo + 1) and the reported score back.
 //
 // Data movement.  A thread owns 4 adjacent pixels x..x+3 over RPT rows.  Each
 // staged row gives it three 32-bit words (bytes x-4..x+7); one byte permute
@@ -21,13 +22,17 @@
 // x.., x+2.., x+4.., x+6..).  A ring pixel at an even column offset is one of
 // those words; at an odd offset one more permute joins two of them.
 //
-// Per-cell fallback: a cell with any pixel scoring >= t_hi is flagged
-// (shared-memory flags per tile, then one global atomicOr per flagged cell).
+// Per-cell fallback: a cell with any pixel scoring >= t_hi is flagged.  The
+// FLAGS variant (32-row tiles) sets the flags itself (shared-memory flags per
+// tile, then one global atomicOr per flagged cell); otherwise the threshold
+// pass computes them, or the cell-tile kernel at the end of this file, whose
+// tiles hold whole cells, applies the thresholds directly.
 //
 // Persistent launch: a grid of a few blocks per SM walks all tiles of the
-// batch; tiles arrive by TMA (one 160 x 40 box per tile, zero-filled outside
-// the image) into two shared-memory buffers, so the next tile's load overlaps
-// the current tile's arithmetic.
+// batch; a 128 x TH tile (TH = 32, 64, 128 or 256 rows) arrives by TMA as
+// 1, 2, 4 or 7 stacked 160 x 40 boxes (zero-filled outside the image) into
+// one of two shared-memory buffers, so the next tile's load overlaps the
+// current tile's arithmetic.  Warps below the detect region skip their rows.
 #include <cuda_runtime.h>
 
 #include "of_internal.h"

@@ -1,22 +1,28 @@
 // Candidate selection, strict 3x3 non-maximum suppression and the Harris key
-// of every survivor, fused per 128 x 32 tile (the FAST -> Harris fusion of
-// Sec. 5.2: the survivors' Harris sums are computed from the same shared
-// memory tile, with no round trip of points through global memory).
+// of every survivor, fused per 128 x TH tile, TH = 32, 64 or 128 rows (the
+// FAST -> Harris fusion of Sec. 5.2: the survivors' Harris sums are computed
+// from the same shared-memory tile, with no round trip of points through
+// global memory).  The score maps hold offset scores s - (t_lo - 1) (0 where
+// s < t_lo); NMS compares them as they are (the shift keeps the order).
 //
-// Persistent launch; per tile, one thread fetches two TMA boxes into the
-// next buffer pair while the block works on the current one: the score tile
-// (160 x 34, +1 row/col halo) and the image tile (160 x 40, +4 halo).
-// 1. S(p) in place: s(p) when p is a candidate at its cell's threshold, else
-//    0; 0 outside the detect region.  Each thread keeps one staged word
-//    column, whose in-region bytes lie in at most two cells.
+// Persistent launch; per tile, one thread fetches the TMA boxes into the next
+// buffer pair while the block works on the current one: the score rows
+// (160 x 34 boxes at a 32-row step, +1 row/col halo) and the image rows
+// (160 x 40 boxes, +4 halo), stacked.
+// 1. (32-row general variant only: the final-score variants get maps that
+//    already hold S(p) and mask the detect region in registers.)  S(p) in
+//    place: s(p) when p is a candidate at its cell's threshold, else 0; 0
+//    outside the detect region.  Each thread keeps one staged word column,
+//    whose in-region bytes lie in at most two cells.
 // 2. NMS, two pixels per register in 16-bit lanes: p survives when S(p) > the
 //    three-input maximum of its 8 neighbours.  Survivors go to a queue (one
 //    shared atomic per warp).
 // 3. Harris (Eqs. 2-4, Alg. 3): one thread per survivor slides down the 9 x 9
 //    footprint keeping three rows of the horizontal Sobel passes (difference
-//    [-1 0 1] and smoothing [1 2 1]) in registers -- the circular buffer of
-//    Alg. 3 -- and combines them vertically into gx, gy, accumulating the
-//    exact int32 sums A = sum gx^2, B = sum gy^2, C = sum gx gy over 7 x 7.
+//    [-1 0 1] and smoothing [1 2 1], one byte dot product each from a 4-byte
+//    window) in registers -- the circular buffer of Alg. 3 -- and combines
+//    them vertically into gx, gy, accumulating the exact int32 sums
+//    A = sum gx^2, B = sum gy^2, C = sum gx gy over 7 x 7.
 //    key = kden (AB - C^2) - knum (A+B)^2 (int64, exact for k = knum/kden).
 // 4. One atomicAdd per warp of the Harris phase reserves its survivors' slots
 //    in the image's list.
