@@ -169,7 +169,8 @@ int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int6
 /* Autotuner (batched path): for this batch shape, time each candidate
  * launch configuration -- pyramid kernel (staged tiles of 32 or 64 rows, or
  * the persistent TMA kernel), persistent grid size and tile order of the FAST
- * and NMS kernels, the FAST and NMS tile heights, the FAST form (cell-tile kernel or general kernel +
+ * and NMS kernels, the FAST tile height (32..256 rows) and NMS tile height
+ * (32..128 rows), the FAST form (cell-tile kernel or general kernel +
  * threshold pass), and whether the frames run as one group or as 2..8 groups
  * on forked graph branches -- with CUDA events on these frames (reps
  * timed repetitions each, 1..100), keep the fastest for every later call with

@@ -107,9 +107,9 @@ struct NmsTile {
 
 // Geometry of TH-row NMS tiles: the score box (34 rows) and the image box (40
 // rows) are loaded as many times as the tile's rows need, stacked in shared
-// memory on 128-byte boundaries (a 64-row tile takes two of each): score box k
-// lands at staged row 32k (its first two rows repeat the previous box's last
-// two, same bytes), image box k at staged row 40k.
+// memory on 128-byte boundaries (a 64-row tile takes two of each, a 128-row
+// tile four): score box k lands at staged row 32k (its first two rows repeat
+// the previous box's last two, same bytes), image box k at staged row 40k.
 template <int TH>
 struct NmsGeom {
     static constexpr int RPT_N = TH / 8;                                    // rows per thread

@@ -987,12 +987,17 @@ int prepare_batch(of_handle* H, const of_frame* frames, int n_frames, int levels
 
 // Time the candidate launch configurations of a bound plan on its own data
 // and keep the fastest per stage:
-//   pyramid  resize output tile 128 x 32 or 128 x 64;
-//   FAST     1 .. max resident blocks per SM, round-robin or contiguous tiles;
-//   NMS      the same choices.
-// Stages are timed one at a time with CUDA events (median-free mean of a few
-// repetitions after a warm-up); select and orientation are not tuned.  The
-// plan's graphs are re-captured with the winners.
+//   pyramid  staged kernel with 128 x 32 or 128 x 64 output tiles, or the
+//            persistent TMA kernel;
+//   FAST     general kernel on 32-, 64-, 128- or 256-row tiles (the tall
+//            ones when the threshold pass sets the flags) or the cell-tile
+//            kernel; 1 .. max resident blocks per SM; round-robin or
+//            contiguous tiles (timed together with NMS);
+//   NMS      32-, 64- or 128-row tiles, blocks per SM, tile order;
+//   groups   the batch as 1 .. 8 frame groups on forked graph branches.
+// Stages are timed one at a time with CUDA events (mean of a few repetitions
+// after a warm-up); select and orientation are not tuned.  The plan's graphs
+// are re-captured with the winners.
 int autotune_plan(of_handle* H, Plan* P, int reps) {
     cudaStream_t st = H->stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
