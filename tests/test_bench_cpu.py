@@ -1,0 +1,38 @@
+"""bench.py's reference arm (the CPU oracle timed on the host) keeps the
+benchmark's JSON contract: one line with the metric, value, unit, the
+cpu_baseline description and an e2e entry without device copies."""
+
+import json
+
+import pytest
+
+import bench
+
+
+def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
+    monkeypatch.setattr(bench.os, "cpu_count", lambda: 1)  # one frame per step, one oracle process
+
+    class A:
+        steps, warmup, gpus = 1, 0, 1
+
+    assert bench.run_reference(A(), rank=0, world=1) == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "frames/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["frames_per_step"] == 1
+
+
+def test_code_hash_ignores_comments(tmp_path):
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    a.write_text("int f() {  // one\n    return 1;\n}\n")
+    b.write_text("// header\n\nint f() {  // two\n    return 1;   \n}\n")
+    assert bench.code_sha1(str(a)) == bench.code_sha1(str(b))
+    b.write_text("int f() {\n    return 2;\n}\n")
+    assert bench.code_sha1(str(a)) != bench.code_sha1(str(b))
