@@ -608,6 +608,213 @@ int fast_cells_blocks_per_sm(int cell) {
     return n;
 }
 
+// ---------------------------------------------------------------------------
+// Cell-aligned tiles (cells of 15 or 30 pixels): the general kernel's
+// arithmetic on 120 x 120 tiles that hold whole cells, so the per-cell
+// threshold is applied here and no threshold pass runs before NMS.
+//
+// A tile is AL_T x AL_T pixels from (border + 120 i, border + 120 j); warp w
+// scores rows 15w .. 15w+14 (one cell row's part: 15 divides the cell), a
+// lane the 4-aligned 4-pixel group gx0 + 4 lane (gx0 = x_lo rounded down to
+// 4; the first and last groups straddle the tile edge and store only their
+// in-tile bytes).  The tile's packed offset scores go to shared memory while
+// each warp ORs, per cell, whether a pixel scores >= t_hi; after a barrier
+// every thread clears the bytes below t_hi in flagged cells and stores its
+// rows, and the tile's cell flags are written.  Image rows y0-3 .. y0+122
+// arrive as four stacked 160 x 40 TMA boxes from x = (gx0 - 4) rounded down
+// to 16 bytes.
+constexpr int AL_T = FAST_AL_T;                                         // tile side
+constexpr int AL_RPT = AL_T / (DET_THREADS / 32);                        // rows per warp: 15
+constexpr int AL_LOADS = (AL_T + 6 + IMG_BOX_ROWS - 1) / IMG_BOX_ROWS;  // image boxes per tile: 4
+constexpr int AL_BUF = AL_LOADS * FAST_BUF;
+constexpr int AL_SCO = AL_T * 32 * 4;                                   // packed scores of one tile
+constexpr int AL_DYN = 2 * AL_BUF + AL_SCO + 128;                       // + alignment slack
+static_assert(AL_RPT * (DET_THREADS / 32) == AL_T, "warps cover the tile's rows");
+
+// 0xFF in each byte of v that is below t (t <= 255).
+__device__ __forceinline__ uint32_t bytes_lt(uint32_t v, uint32_t t) {
+    const uint32_t tt = (0x8000u - t) * 0x00010001u;
+    const uint32_t lo = __byte_perm(v, 0u, 0x4140) + tt, hi = __byte_perm(v, 0u, 0x4342) + tt;
+    return ~__byte_perm((lo >> 15 & 0x00010001u) * 0xFFu, (hi >> 15 & 0x00010001u) * 0xFFu, 0x6420);
+}
+
+__global__ void __launch_bounds__(DET_THREADS, 2)
+k_fast_aligned(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ prefix,
+               int n_list, int n_tiles, const CUtensorMap* __restrict__ maps, const Call* __restrict__ call,
+               int t_hi, int t_lo, int border, int cell, int order) {
+    extern __shared__ __align__(128) uint8_t al_dyn[];
+    uint8_t* const sbuf = al_dyn + ((128u - (smem_u32(al_dyn) & 127u)) & 127u);
+    uint32_t* const sco = reinterpret_cast<uint32_t*>(sbuf + 2 * AL_BUF);  // [row][lane]
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ CellTile tinfo[2];
+    __shared__ int any_on[2];
+    __shared__ uint32_t cflag[AL_T / 15];  // per cell row of the tile: one bit per cell
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const bool cells = t_hi != t_lo;
+    const int cpt = AL_T / cell;                // cells per tile row and per tile column
+    const int wcr = (AL_RPT * w) / cell;        // this warp's cell row in the tile
+    const uint32_t kb = PAIR_BIAS - (uint32_t)(t_lo - 1) * 0x00010001u;
+    const uint32_t th = (uint32_t)(t_hi - t_lo + 1);  // t_hi in offset units
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_barrier_init();
+    }
+    if (tid < AL_T / 15) cflag[tid] = 0u;
+    __syncthreads();
+    auto issue = [&](int t, int b) {
+        const int j = find_tile_job(prefix, n_list, t);
+        const int ii = __ldg(list + j);
+        const Img& I = imgs[ii];
+        const int tt = t - __ldg(prefix + j);
+        const int x_lo = border + (tt % I.ftiles_x) * AL_T, y0 = border + (tt / I.ftiles_x) * AL_T;
+        const int box_x = ((x_lo & ~3) - 4) & ~15;
+        // Learned path: does any proposal tile under this work tile hold a proposed pixel?
+        int on = 1;
+        if (I.pmask) {
+            on = 0;
+            const int x_hi = min(x_lo + AL_T, I.w - border) - 1, y_hi = min(y0 + AL_T, I.h - border) - 1;
+            for (int py = (y0 - border) >> 5; py <= (y_hi - border) >> 5 && !on; ++py)
+                for (int px = (x_lo - I.tile_x0) >> 5; px <= (x_hi - I.tile_x0) >> 5 && !on; ++px)
+                    on = I.pmask[(size_t)py * 4 * I.tiles_x + px] != 0;
+        }
+        tinfo[b] = CellTile{ii, x_lo, y0, box_x};
+        any_on[b] = on;
+        tensormap_acquire(maps + ii);
+        mbar_arrive_expect_tx(&mbar[b], AL_LOADS * FAST_BOX);
+#pragma unroll
+        for (int k = 0; k < AL_LOADS; ++k)
+            tma_load_2d(sbuf + b * AL_BUF + k * FAST_BOX, maps + ii, box_x, y0 - 3 + k * IMG_BOX_ROWS, &mbar[b]);
+    };
+    const int g = gridDim.x;
+    if (tid == 0 && tile_of(order, blockIdx.x, g, n_tiles, 0) < n_tiles)
+        issue(tile_of(order, blockIdx.x, g, n_tiles, 0), 0);
+
+    for (int it = 0;; ++it) {
+        const int t = tile_of(order, blockIdx.x, g, n_tiles, it);
+        if (t >= n_tiles) break;
+        const int tn = tile_of(order, blockIdx.x, g, n_tiles, it + 1);
+        const int b = it & 1;
+        if (tid == 0) {
+#pragma unroll
+            for (int i = 0; i < AL_T / 15; ++i) cflag[i] = 0u;  // last read before the previous tile's final barrier
+            if (tn < n_tiles) {
+                fence_proxy_async_smem();
+                issue(tn, b ^ 1);
+            }
+        }
+        const bool ok = mbar_wait(&mbar[b], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(call->status, OF_DEV_TIMEOUT);
+                // Let this block's copies in flight land before its shared memory goes away.
+                mbar_wait(&mbar[b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (tn < n_tiles) mbar_wait(&mbar[b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+            }
+            return;
+        }
+        const CellTile ti = tinfo[b];
+        const Img& I = imgs[ti.img];
+        const uint8_t* const pmask = I.pmask;
+        uint8_t* const score = I.score;
+        const size_t spitch = (size_t)I.spitch;
+        const int rx1 = I.w - border, ry1 = I.h - border;
+        const int x_hi = min(ti.x_lo + AL_T, rx1);
+        const int gx0 = ti.x_lo & ~3;
+        const int x = gx0 + 4 * lane;
+        const int row0 = ti.y0 + AL_RPT * w;
+        const int nrows = min(AL_RPT, min(ti.y0 + AL_T, ry1) - row0);  // warp-uniform
+        const uint32_t colmask = range_mask4(x, ti.x_lo, x_hi);
+        // Cells of this lane's bytes: ca for the bytes in mask_a, ca + 1 for the rest.
+        const int ca = (max(x, ti.x_lo) - ti.x_lo) / cell;
+        const uint32_t mask_a = colmask & range_mask4(x, 0, ti.x_lo + (ca + 1) * cell);
+        const uint32_t mask_b = colmask & ~mask_a;
+        uint32_t* const srow = sco + (size_t)(AL_RPT * w) * 32 + lane;
+        if (any_on[b] && nrows > 0) {
+            const uint8_t* const s = sbuf + b * AL_BUF;
+            const int xoff = gx0 - ti.box_x + 4 * lane;  // >= 4, multiple of 4
+            // Six pair words per staged row (staged row 0 = tile row -3), loaded just in time.
+            uint32_t hw[AL_RPT + 6][6];
+            auto load_row = [&](int k) {
+                const uint8_t* row = s + (AL_RPT * w + k) * SROW + xoff;
+                const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+                const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+                const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
+                hw[k][0] = __byte_perm(wm, 0u, 0x4140);
+                hw[k][1] = __byte_perm(wm, 0u, 0x4342);
+                hw[k][2] = __byte_perm(wc, 0u, 0x4140);
+                hw[k][3] = __byte_perm(wc, 0u, 0x4342);
+                hw[k][4] = __byte_perm(wp, 0u, 0x4140);
+                hw[k][5] = __byte_perm(wp, 0u, 0x4342);
+            };
+            uint32_t u0 = 0u, u1 = 0u;  // running maxima of the biased offset scores (16-bit lanes)
+#pragma unroll
+            for (int k = 0; k < 7; ++k) load_row(k);
+#pragma unroll
+            for (int r = 0; r < AL_RPT; ++r) {
+                if (r >= nrows) break;
+                if (r > 0) load_row(r + 6);
+                uint32_t s0 = ring_pair_score<0>(hw + r, kb);  // 512 + offset score per lane
+                uint32_t s1 = ring_pair_score<1>(hw + r, kb);
+                if (pmask && colmask) {
+                    // Outside the proposed tiles the scores are 0 and do not count (lanes
+                    // in the region only: their proposal tile lies inside the mask).
+                    const int px = (x - I.tile_x0) >> 5, py = (row0 + r - border) >> 5;
+                    if (pmask[(size_t)py * 4 * I.tiles_x + px] == 0) s0 = s1 = 0u;
+                }
+                u0 = __vimax3_u16x2(u0, s0, s0);
+                u1 = __vimax3_u16x2(u1, s1, s1);
+                srow[r * 32] = __byte_perm(s0, s1, 0x6420);  // packed offset scores
+            }
+            if (cells) {
+                const uint32_t su = __byte_perm(lanes_ge(u0, th + 512u), lanes_ge(u1, th + 512u), 0x6420);
+                uint32_t bits = ((su & mask_a) ? 1u << ca : 0u) | ((su & mask_b) ? 2u << ca : 0u);
+                bits = __reduce_or_sync(0xFFFFFFFFu, bits);
+                if (lane == 0 && bits) atomicOr(&cflag[wcr], bits);
+            }
+        }
+        __syncthreads();  // the tile's flags are complete
+        if (tid < cpt * cpt) {
+            const int cx = (ti.x_lo - border) / cell + tid % cpt, cy = (ti.y0 - border) / cell + tid / cpt;
+            if (cx < I.ncx && cy < I.ncy) I.cell[cy * I.ncx + cx] = (cflag[tid / cpt] >> (tid % cpt)) & 1u;
+        }
+        if (nrows > 0 && colmask != 0u) {
+            const uint32_t flags = cflag[wcr];
+            const uint32_t fm = (((flags >> ca) & 1u) ? mask_a : 0u) | (((flags >> (ca + 1)) & 1u) ? mask_b : 0u);
+            uint8_t* const dst = score + x;
+            const bool on = any_on[b];
+#pragma unroll
+            for (int r = 0; r < AL_RPT; ++r) {
+                if (r >= nrows) break;
+                const uint32_t v = on ? srow[r * 32] : 0u;
+                store_bytes(dst + (size_t)(row0 + r) * spitch, v & ~(fm & bytes_lt(v, th)), colmask);
+            }
+        }
+        fence_proxy_async_smem();  // this thread's buffer accesses before the next TMA into them
+        __syncthreads();           // buffer b, the packed scores and cflag are free
+    }
+}
+
+void launch_fast_aligned(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
+                         int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
+                         int cell, int grid, int order, void* stream) {
+    if (n_tiles <= 0) return;
+    grid = grid < n_tiles ? grid : n_tiles;
+    k_fast_aligned<<<grid, DET_THREADS, AL_DYN, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list,
+                                                                         n_tiles, maps, call, t_hi, t_lo, border,
+                                                                         cell, order);
+}
+
+// Resident blocks per SM of the cell-aligned kernel (raises its dynamic
+// shared-memory limit first).
+int fast_aligned_blocks_per_sm() {
+    int n = 0;
+    cudaError_t e = cudaFuncSetAttribute(k_fast_aligned, cudaFuncAttributeMaxDynamicSharedMemorySize, AL_DYN);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_aligned, DET_THREADS, AL_DYN);
+    return (e != cudaSuccess || n < 1) ? 1 : n;
+}
+
 // A block that waits, with the same bounded wait as the tile loads, on a flag
 // nothing sets; exercises the timeout path without any copy in flight.
 __global__ void k_wait_test(const int32_t* flag, int32_t* status, uint64_t limit_ns) {

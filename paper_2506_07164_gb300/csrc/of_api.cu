@@ -221,14 +221,16 @@ struct Plan {
         int fast_tiles = 0, fp_off = 0;             // cell-tile FAST: tiles and prefix offset in gp_fast
         int nms64_tiles = 0, np_off = 0;            // NMS with 64-row tiles: tiles and prefix offset in gp_nms64
         int ftall_tiles[2] = {0, 0}, ftall_off[2] = {0, 0};  // FAST on FT_HS[i]-row tiles: tiles, offset in gp_ftall[i]
+        int fal_tiles = 0, fal_off = 0;             // cell-aligned FAST: tiles and prefix offset in gp_fal
         int n_bands = 0, rp_off = 0;                // threshold pass: cell rows and prefix offset in gp_rows
         int slot_begin = 0, slot_end = 0;
         std::vector<int> rs_job, rs_n;              // per level: first resize job, jobs
         std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
     };
     std::vector<Group> groups[kMaxGroups + 1];
-    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_ftall[2];
+    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_ftall[2], gp_fal;
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
+    bool aligned_ok = false;     // ... and the cell-aligned general FAST kernel (cells of 15 or 30 pixels)
     bool apply_flags = false;    // the threshold pass sets the cell flags (the general FAST kernel does not)
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
     std::vector<int> rt_bps;        // TMA resize resident blocks per SM of level l
@@ -236,7 +238,7 @@ struct Plan {
     Call h_call{};
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0;
-    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gft[2] = {0, 0};
+    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gft[2] = {0, 0}, off_gfal = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -270,10 +272,12 @@ struct Plan {
     const int32_t* d_grp() const { return reinterpret_cast<const int32_t*>(dbuf + off_grp); }
     const int32_t* d_gnp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gnp); }
     const int32_t* d_gft(int i) const { return reinterpret_cast<const int32_t*>(dbuf + off_gft[i]); }
+    const int32_t* d_gfal() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfal); }
 };
 
 // Resident blocks per SM of the plan's FAST kernel.
 int plan_fast_bps(const Plan* P) {
+    if (P->aligned_ok && P->tun.fast_cell_tiles == 2) return fast_aligned_blocks_per_sm();
     if (P->cell_tiles && P->tun.fast_cell_tiles) return fast_cells_blocks_per_sm(P->s.cell);
     return P->apply_flags ? fast_blocks_per_sm(P->tun.fast_tile_h) : fast_blocks_per_sm();
 }
@@ -358,7 +362,11 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
         case 1:
             // The cell-tile kernel writes final candidate scores S(p); the
             // general kernel's maps get the threshold pass at the start of stage 2.
-            if (P->cell_tiles && P->tun.fast_cell_tiles)
+            if (P->aligned_ok && P->tun.fast_cell_tiles == 2)
+                launch_fast_aligned(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfal() + G.fal_off, G.n_list,
+                                    G.fal_tiles, P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                                    H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+            else if (P->cell_tiles && P->tun.fast_cell_tiles)
                 launch_fast_cells(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfp() + G.fp_off, G.n_list, G.fast_tiles,
                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                                   H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
@@ -488,6 +496,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->n_img = nf * nl;
     // Cell tiles: FAST applies the per-cell threshold itself (cells of 8..30 pixels).
     P->cell_tiles = s.cell >= CT_MIN_CELL && s.cell <= CT_MAX_CELL;
+    P->aligned_ok = P->cell_tiles && fast_aligned_ok(s.cell);
     // The threshold pass flags the cells itself when a band's cells fit its shared array.
     P->apply_flags = true;
     for (const auto& L : P->lay.img)
@@ -644,6 +653,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             G.rp_off = (int)P->gp_rows.size();
             G.np_off = (int)P->gp_nms64.size();
             for (int i = 0; i < 2; ++i) G.ftall_off[i] = (int)P->gp_ftall[i].size();
+            G.fal_off = (int)P->gp_fal.size();
             for (int j = j0; j < j1; ++j) {
                 const Img& I = P->h_img[P->det_list[j]];
                 P->gp_nms64.push_back(G.nms64_tiles);
@@ -651,6 +661,11 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
                 for (int i = 0; i < 2; ++i) {
                     P->gp_ftall[i].push_back(G.ftall_tiles[i]);
                     G.ftall_tiles[i] += I.tiles_x * ((I.h - 2 * s.border + FT_HS[i] - 1) / FT_HS[i]);
+                }
+                P->gp_fal.push_back(G.fal_tiles);
+                if (P->aligned_ok) {
+                    const int cr = FAST_AL_T / s.cell;  // cell rows per tile
+                    G.fal_tiles += I.ftiles_x * ((I.ncy + cr - 1) / cr);
                 }
                 P->gp_fast.push_back(G.fast_tiles);
                 G.fast_tiles += P->cell_tiles ? I.ftiles_x * ((I.ncy + ct_cell_rows(s.cell) - 1) / ct_cell_rows(s.cell)) : 0;
@@ -711,6 +726,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64);  // also raises its shared-memory limit before any capture
     for (int i = 0; i < 2; ++i) fast_blocks_per_sm(FT_HS[i]);  // raise the tall kernels' limits before any capture
     nms_blocks_per_sm(FT_HS[0]);
+    fast_aligned_blocks_per_sm();  // raises the cell-aligned kernel's shared-memory limit
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
 
@@ -768,6 +784,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
         P->off_gft[i] = off;
         off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_ftall[i].size(), 1), 16);
     }
+    P->off_gfal = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_fal.size(), 1), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -794,6 +812,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_grp, P->gp_rows.data(), sizeof(int32_t) * P->gp_rows.size());
     put(P->off_gnp, P->gp_nms64.data(), sizeof(int32_t) * P->gp_nms64.size());
     for (int i = 0; i < 2; ++i) put(P->off_gft[i], P->gp_ftall[i].data(), sizeof(int32_t) * P->gp_ftall[i].size());
+    put(P->off_gfal, P->gp_fal.data(), sizeof(int32_t) * P->gp_fal.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);
@@ -1039,10 +1058,11 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     // where the cell size allows it; fast_ms below is FAST + NMS.
     best = 1e30f;
     int bb = P->tun.fast_blocks_per_sm, bo = 0, bv = P->tun.fast_cell_tiles, bt = P->tun.fast_tile_h;
-    // Forms: general kernel (32-row tiles; 64, 128 or 256 rows when the pass sets the flags), cell tiles.
-    for (int cand = 0; cand < 5 && rc == OF_OK; ++cand) {
-        const int v = cand == 4 ? 1 : 0, th = cand == 4 ? 32 : 32 << cand;
-        if ((v == 1 && !P->cell_tiles) || (th > 32 && !P->apply_flags)) continue;
+    // Forms: general kernel (32-row tiles; 64, 128 or 256 rows when the pass
+    // sets the flags), cell tiles (1), cell-aligned general kernel (2).
+    for (int cand = 0; cand < 6 && rc == OF_OK; ++cand) {
+        const int v = cand < 4 ? 0 : cand - 3, th = cand < 4 ? 32 << cand : 32;
+        if ((v == 1 && !P->cell_tiles) || (v == 2 && !P->aligned_ok) || (th > 32 && !P->apply_flags)) continue;
         P->tun.fast_cell_tiles = v;
         P->tun.fast_tile_h = th;
         for (int bp = 1; bp <= plan_fast_bps(P) && rc == OF_OK; ++bp) {
@@ -1312,7 +1332,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         (t->fast_tile_h != 32 && t->fast_tile_h != 64 && t->fast_tile_h != FT_HS[0] && t->fast_tile_h != FT_HS[1]) ||
         t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h) || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
-        (t->fast_cell_tiles != 0 && t->fast_cell_tiles != 1))
+        t->fast_cell_tiles < 0 || t->fast_cell_tiles > 2)
         return fail(OF_ERR_ARG, "tuning field out of range");
     Plan* P = nullptr;
     const int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
@@ -1320,7 +1340,8 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     if (rc != OF_OK) return rc;
     P->tun.resize_tile_h = t->resize_tile_h;
     P->tun.resize_tma = t->resize_tma;
-    P->tun.fast_cell_tiles = P->cell_tiles ? t->fast_cell_tiles : 0;
+    // Forms the cell size does not allow fall back: aligned -> cell tiles -> general.
+    P->tun.fast_cell_tiles = !P->cell_tiles ? 0 : (t->fast_cell_tiles == 2 && !P->aligned_ok) ? 1 : t->fast_cell_tiles;
     P->tun.fast_tile_h = P->apply_flags ? t->fast_tile_h : 32;
     P->tun.fast_blocks_per_sm = std::min(t->fast_blocks_per_sm, plan_fast_bps(P));
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;

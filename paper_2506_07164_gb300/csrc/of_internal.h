@@ -138,6 +138,13 @@ void launch_fast_cells(const Img* imgs, const int32_t* img_list, const int32_t* 
                        int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
                        int cell, int grid, int order, void* stream);
 int fast_cells_blocks_per_sm(int cell);
+// Cell-aligned general FAST (120 x 120 tiles of whole cells; cells of 15 or 30 pixels).
+constexpr int FAST_AL_T = 120;
+inline bool fast_aligned_ok(int cell) { return cell == 15 || cell == 30; }
+void launch_fast_aligned(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
+                         int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
+                         int cell, int grid, int order, void* stream);
+int fast_aligned_blocks_per_sm();
 int fast_blocks_per_sm(int tile_h);  // the flag-free general kernel
 void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
                        int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags);

@@ -152,6 +152,37 @@ def test_labels_equal_oracle_labels():
     det.close()
 
 
+def test_partial_proposal_same_under_every_fast_form():
+    """With the committed network and threshold (about 3/4 of the tiles
+    proposed), the learned path gives the same records whichever FAST form
+    the plan runs: general kernel + threshold pass, cell tiles, or the
+    cell-aligned general kernel -- each restricts scores and cell flags to
+    the proposed tiles the same way."""
+    import json
+
+    meta = json.load(open(learned.DEFAULT_META))
+    net = learned.TileNet(0).load(learned.DEFAULT_WEIGHTS)
+    frames = [synth.scene(1920, 1080, 950 + i, background="pink") for i in range(2)]
+    dev = [torch.from_numpy(f).cuda() for f in frames]
+    fr = [(t, t.shape[1], t.shape[0], t.stride(0)) for t in dev]
+    det = ofg.Detector(1920, 1080, max_levels=8, max_features=1000, max_batch=2, fast_t_lo=7)
+    got = []
+    for form in (0, 1, 2):
+        tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
+                           stream_groups=1, fast_cell_tiles=form, nms_tile_h=64, fast_tile_h=128)
+        det.set_tuning(dev, tun, levels=8, fast_t=20, n_features=1000)
+        st = ofg.of_detect_learned(det.h, fr, 8, 1.2, 20, 0.04, 1000, net.net, meta["threshold"],
+                                   meta["min_confidence"], meta["dilate"], det.out, det.counts)
+        assert 0 < st["proposed"] < st["tiles"], st
+        torch.cuda.synchronize()
+        got.append(det.batch_results(2, 1000))
+    for k in (1, 2):
+        for a, b in zip(got[0], got[k]):
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), k
+    det.close()
+    net.close()
+
+
 def test_training_skips_work_at_high_recall():
     """A short training run: the loss drops, the trained proposal skips tiles
     while keeping most keypoints, and a random proposal keeping the same
