@@ -51,10 +51,19 @@ class OfParams(C.Structure):
 
 
 class OfTuning(C.Structure):
+    """of_tuning: launch configuration of one batch shape.
+
+    resize_tile_h (32/64) and resize_tma (0/1): pyramid kernel; fast_blocks_per_sm,
+    nms_blocks_per_sm, fast_order, nms_order: persistent grids and tile order;
+    stream_groups (1..8): frame groups on forked graph branches; fast_cell_tiles:
+    0 general FAST + threshold pass, 1 cell-tile kernel, 2 cell-aligned general kernel;
+    fast_tile_h (32/64/128/256) and nms_tile_h (32/64/128): tile heights.  The last
+    four fields report the autotuner's search (candidates, best stage times in ms)."""
+
     _fields_ = [("resize_tile_h", C.c_int32), ("fast_blocks_per_sm", C.c_int32),
                 ("nms_blocks_per_sm", C.c_int32), ("fast_order", C.c_int32), ("nms_order", C.c_int32),
-                ("resize_tma", C.c_int32), ("stream_groups", C.c_int32), ("fast_cell_tiles", C.c_int32), ("nms_tile_h", C.c_int32),
-                ("fast_tile_h", C.c_int32),
+                ("resize_tma", C.c_int32), ("stream_groups", C.c_int32), ("fast_cell_tiles", C.c_int32),
+                ("nms_tile_h", C.c_int32), ("fast_tile_h", C.c_int32),
                 ("candidates_tried", C.c_int32), ("resize_ms", C.c_float), ("fast_ms", C.c_float),
                 ("nms_ms", C.c_float)]
 
