@@ -293,7 +293,7 @@ FAST_OPS_PER_PX = 40.5
 # DRAM bytes of one k_fast launch per frame, from the ncu capture summarised in
 # profiles/k_fast_1080p8.md (64-frame launch, scaled per frame), valid while
 # k_fast.cu's code (comments and blank lines removed: code_sha1) has this SHA-1.
-FAST_TRAFFIC = {"code_sha1": "d7fa8b7094665cbba655e47e1727f86386263a75", "bytes_per_frame": (457449984 + 348266752) / 64}
+FAST_TRAFFIC = {"code_sha1": "d78cf16d738bf9b07f48ede0fcf7b7e109859a22", "bytes_per_frame": (519807488 + 353865472) / 64}
 
 
 def code_sha1(path):

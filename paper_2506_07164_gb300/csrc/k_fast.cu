@@ -714,62 +714,73 @@ k_fast_aligned(const Img* __restrict__ imgs, const int32_t* __restrict__ list, c
             }
             return;
         }
+        // Only what the scoring loop needs stays live across it; the masks of
+        // the flag and store passes are derived again after it.
+        uint32_t* const srow = sco + (size_t)(AL_RPT * w) * 32 + lane;
+        int nrows;
+        {
+            const CellTile ti = tinfo[b];
+            const Img& I = imgs[ti.img];
+            nrows = min(AL_RPT, min(ti.y0 + AL_T, I.h - border) - (ti.y0 + AL_RPT * w));  // warp-uniform
+            if (any_on[b] && nrows > 0) {
+                const uint8_t* const s = sbuf + b * AL_BUF;
+                const int xoff = (ti.x_lo & ~3) - ti.box_x + 4 * lane;  // >= 4, multiple of 4
+                // Six pair words per staged row (staged row 0 = tile row -3), loaded just in time.
+                uint32_t hw[AL_RPT + 6][6];
+                auto load_row = [&](int k) {
+                    const uint8_t* row = s + (AL_RPT * w + k) * SROW + xoff;
+                    const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+                    const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+                    const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
+                    hw[k][0] = __byte_perm(wm, 0u, 0x4140);
+                    hw[k][1] = __byte_perm(wm, 0u, 0x4342);
+                    hw[k][2] = __byte_perm(wc, 0u, 0x4140);
+                    hw[k][3] = __byte_perm(wc, 0u, 0x4342);
+                    hw[k][4] = __byte_perm(wp, 0u, 0x4140);
+                    hw[k][5] = __byte_perm(wp, 0u, 0x4342);
+                };
+#pragma unroll
+                for (int k = 0; k < 7; ++k) load_row(k);
+#pragma unroll
+                for (int r = 0; r < AL_RPT; ++r) {
+                    if (r >= nrows) break;
+                    if (r > 0) load_row(r + 6);
+                    const uint32_t s0 = ring_pair_score<0>(hw + r, kb);  // 512 + offset score per lane
+                    const uint32_t s1 = ring_pair_score<1>(hw + r, kb);
+                    srow[r * 32] = __byte_perm(s0, s1, 0x6420);          // packed offset scores
+                }
+            }
+        }
         const CellTile ti = tinfo[b];
         const Img& I = imgs[ti.img];
-        const uint8_t* const pmask = I.pmask;
-        uint8_t* const score = I.score;
-        const size_t spitch = (size_t)I.spitch;
-        const int rx1 = I.w - border, ry1 = I.h - border;
+        const int rx1 = I.w - border;
         const int x_hi = min(ti.x_lo + AL_T, rx1);
-        const int gx0 = ti.x_lo & ~3;
-        const int x = gx0 + 4 * lane;
+        const int x = (ti.x_lo & ~3) + 4 * lane;
         const int row0 = ti.y0 + AL_RPT * w;
-        const int nrows = min(AL_RPT, min(ti.y0 + AL_T, ry1) - row0);  // warp-uniform
         const uint32_t colmask = range_mask4(x, ti.x_lo, x_hi);
         // Cells of this lane's bytes: ca for the bytes in mask_a, ca + 1 for the rest.
         const int ca = (max(x, ti.x_lo) - ti.x_lo) / cell;
         const uint32_t mask_a = colmask & range_mask4(x, 0, ti.x_lo + (ca + 1) * cell);
         const uint32_t mask_b = colmask & ~mask_a;
-        uint32_t* const srow = sco + (size_t)(AL_RPT * w) * 32 + lane;
-        if (any_on[b] && nrows > 0) {
-            const uint8_t* const s = sbuf + b * AL_BUF;
-            const int xoff = gx0 - ti.box_x + 4 * lane;  // >= 4, multiple of 4
-            // Six pair words per staged row (staged row 0 = tile row -3), loaded just in time.
-            uint32_t hw[AL_RPT + 6][6];
-            auto load_row = [&](int k) {
-                const uint8_t* row = s + (AL_RPT * w + k) * SROW + xoff;
-                const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
-                const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
-                const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
-                hw[k][0] = __byte_perm(wm, 0u, 0x4140);
-                hw[k][1] = __byte_perm(wm, 0u, 0x4342);
-                hw[k][2] = __byte_perm(wc, 0u, 0x4140);
-                hw[k][3] = __byte_perm(wc, 0u, 0x4342);
-                hw[k][4] = __byte_perm(wp, 0u, 0x4140);
-                hw[k][5] = __byte_perm(wp, 0u, 0x4342);
-            };
-            uint32_t u0 = 0u, u1 = 0u;  // running maxima of the biased offset scores (16-bit lanes)
-#pragma unroll
-            for (int k = 0; k < 7; ++k) load_row(k);
-#pragma unroll
-            for (int r = 0; r < AL_RPT; ++r) {
-                if (r >= nrows) break;
-                if (r > 0) load_row(r + 6);
-                uint32_t s0 = ring_pair_score<0>(hw + r, kb);  // 512 + offset score per lane
-                uint32_t s1 = ring_pair_score<1>(hw + r, kb);
+        const bool on = any_on[b];
+        if (on && nrows > 0) {
+            // Flags: bytes >= t_hi of the in-region, proposed pixels.  Scores
+            // outside the proposed tiles (learned path) become 0 here.
+            const uint8_t* const pmask = I.pmask;
+            uint32_t acc = 0u;
+            for (int r = 0; r < nrows; ++r) {
+                uint32_t v = srow[r * 32] & colmask;
                 if (pmask && colmask) {
-                    // Outside the proposed tiles the scores are 0 and do not count (lanes
-                    // in the region only: their proposal tile lies inside the mask).
                     const int px = (x - I.tile_x0) >> 5, py = (row0 + r - border) >> 5;
-                    if (pmask[(size_t)py * 4 * I.tiles_x + px] == 0) s0 = s1 = 0u;
+                    if (pmask[(size_t)py * 4 * I.tiles_x + px] == 0) {
+                        v = 0u;
+                        srow[r * 32] = 0u;
+                    }
                 }
-                u0 = __vimax3_u16x2(u0, s0, s0);
-                u1 = __vimax3_u16x2(u1, s1, s1);
-                srow[r * 32] = __byte_perm(s0, s1, 0x6420);  // packed offset scores
+                acc |= ~bytes_lt(v, th);
             }
             if (cells) {
-                const uint32_t su = __byte_perm(lanes_ge(u0, th + 512u), lanes_ge(u1, th + 512u), 0x6420);
-                uint32_t bits = ((su & mask_a) ? 1u << ca : 0u) | ((su & mask_b) ? 2u << ca : 0u);
+                uint32_t bits = ((acc & mask_a) ? 1u << ca : 0u) | ((acc & mask_b) ? 2u << ca : 0u);
                 bits = __reduce_or_sync(0xFFFFFFFFu, bits);
                 if (lane == 0 && bits) atomicOr(&cflag[wcr], bits);
             }
@@ -782,9 +793,9 @@ k_fast_aligned(const Img* __restrict__ imgs, const int32_t* __restrict__ list, c
         if (nrows > 0 && colmask != 0u) {
             const uint32_t flags = cflag[wcr];
             const uint32_t fm = (((flags >> ca) & 1u) ? mask_a : 0u) | (((flags >> (ca + 1)) & 1u) ? mask_b : 0u);
-            uint8_t* const dst = score + x;
-            const bool on = any_on[b];
-#pragma unroll
+            uint8_t* const dst = I.score + x;
+            const size_t spitch = (size_t)I.spitch;
+#pragma unroll 5
             for (int r = 0; r < AL_RPT; ++r) {
                 if (r >= nrows) break;
                 const uint32_t v = on ? srow[r * 32] : 0u;
