@@ -1,0 +1,136 @@
+"""Index arithmetic of the tiled kernels, checked on the CPU.
+
+The constants below restate the tiling of csrc/of_internal.h and the kernels
+(tile sizes, TMA boxes, rows per warp).  For every level of a range of frame
+sizes and pyramid scales, and for every tile kind the kernels use, the tests
+check what the kernels rely on without checking it at run time:
+
+  - every TMA box starts at an x coordinate that is a multiple of 16 bytes
+    (the tiled-copy alignment rule for 8-bit data);
+  - every staged row and column a thread reads lies inside the boxes loaded
+    into its shared-memory buffer;
+  - the tiles cover the detect region [b, w - b) x [b, h - b).
+"""
+
+import math
+
+import pytest
+
+import paper_2506_07164_gb300 as ofg
+
+TILE_W, HALO_X, SROW = 128, 16, 160
+IMG_BOX_ROWS, SCORE_BOX_ROWS = 40, 34
+WARPS = 8                      # DET_THREADS / 32
+CT_MAX_W, CT_RPT, CT_MAX_WARPS, CT_MAX_TILE_ROWS = 124, 5, 12, 64
+AL_T, AL_RPT = 120, 15
+
+SIZES = [(1920, 1080), (1280, 720), (640, 480), (3840, 2160), (720, 540), (1440, 1080), (333, 217),
+         (129, 77), (1000, 41), (41, 1000), (161, 161), (1283, 723)]
+SCALES = [1.05, 1.2, 2.0]
+
+
+def levels(w, h, scale, n=8):
+    ws, hs, _ = ofg.of_plan_levels(w, h, n, scale, 1000)
+    return list(zip(ws, hs))
+
+
+def det_levels(border=19):
+    for (W, H) in SIZES:
+        for scale in SCALES:
+            for w, h in levels(W, H, scale):
+                if w - 2 * border > 0 and h - 2 * border > 0:
+                    yield w, h
+
+
+def ceil_div(a, b):
+    return -(-a // b)
+
+
+@pytest.mark.parametrize("th", [32, 64, 128, 256])
+def test_general_fast_tiles(th):
+    """k_fast<*, TH>: 128 x TH tiles, boxes at (X0 - 16, Y0 - 4 + 40k)."""
+    b = 19
+    rpt = th // WARPS
+    loads = ceil_div(th + 8, IMG_BOX_ROWS)
+    # Staged rows a warp reads: (w * RPT + k + 1), k < RPT + 6 (row 0 = Y0 - 4).
+    assert (WARPS - 1) * rpt + (rpt + 5) + 1 < loads * IMG_BOX_ROWS
+    # Columns: HALO_X + 4 lane - 4 .. + 7.
+    assert HALO_X - 4 >= 0 and HALO_X + 4 * 31 + 7 < SROW
+    for w, h in det_levels(b):
+        tile_x0 = b & ~15
+        tiles_x = ceil_div(w - b - tile_x0, TILE_W)
+        tiles_y = ceil_div(h - 2 * b, th)
+        assert tile_x0 <= b and tile_x0 + TILE_W * tiles_x >= w - b
+        assert b + th * tiles_y >= h - b
+        for tx in range(tiles_x):
+            assert (tile_x0 + TILE_W * tx - HALO_X) % 16 == 0
+
+
+@pytest.mark.parametrize("th", [32, 64, 128])
+def test_nms_tiles(th):
+    """k_nms_harris<*, TH>: score boxes every 32 rows from Y0 - 1, image boxes every 40 from Y0 - 4."""
+    rpt = th // WARPS
+    s_rows = th + 2
+    s_loads = ceil_div(s_rows - SCORE_BOX_ROWS, 32) + 1
+    i_loads = ceil_div(th + 8, IMG_BOX_ROWS)
+    # 3x3 test: staged score rows w * RPT + k, k < RPT + 2.
+    assert (WARPS - 1) * rpt + rpt + 1 < (s_loads - 1) * 32 + SCORE_BOX_ROWS
+    # Harris: image rows ly + 4 + v, ly < TH, |v| <= 4; words w0 .. w0 + 2 of each row.
+    assert th - 1 + 8 < i_loads * IMG_BOX_ROWS
+    for lx in range(TILE_W):
+        w0 = (HALO_X + lx - 4) >> 2
+        assert w0 >= 0 and 4 * (w0 + 2) + 3 < SROW
+    # Score and image boxes at the tile's origin - 16: aligned (origins are multiples of 16).
+    b = 19
+    assert ((b & ~15) - HALO_X) % 16 == 0
+
+
+def ct_cell_rows(cell):
+    nw = ceil_div(cell, CT_RPT)
+    return min(CT_MAX_TILE_ROWS // cell, CT_MAX_WARPS // nw)
+
+
+@pytest.mark.parametrize("cell", range(8, 31))
+def test_cell_tiles(cell):
+    """k_fast_cells: cpt x cr whole cells; 4-pixel groups from x_lo & ~3; boxes from (gx0 - 4) & ~15."""
+    b = 19
+    cpt, nw, cr = CT_MAX_W // cell, ceil_div(cell, CT_RPT), ct_cell_rows(cell)
+    assert cr >= 1 and nw * cr <= CT_MAX_WARPS
+    tw, th = cpt * cell, cr * cell
+    loads = ceil_div((cr - 1) * cell + CT_RPT * nw + 6, IMG_BOX_ROWS)
+    assert loads <= 2
+    # Staged rows: warp (wcr, wr) reads wcr * cell + 5 wr + k, k < 11.
+    assert (cr - 1) * cell + CT_RPT * (nw - 1) + 10 < loads * IMG_BOX_ROWS
+    for w, h in det_levels(b):
+        ncx = ceil_div(w - 2 * b, cell)
+        ftiles_x = ceil_div(ncx, cpt)
+        for ftx in range(ftiles_x):
+            x_lo = b + ftx * tw
+            gx0 = x_lo & ~3
+            box_x = (gx0 - 4) & ~15
+            assert box_x % 16 == 0 and box_x >= 0
+            xoff0 = gx0 - box_x
+            assert xoff0 >= 4 and xoff0 + 4 * 31 + 7 < SROW  # reads xoff - 4 .. xoff + 7
+            assert gx0 + 4 * 32 >= x_lo + tw                # the lanes cover the tile
+        assert b + ftiles_x * tw >= w - b
+
+
+@pytest.mark.parametrize("cell", [15, 30])
+def test_cell_aligned_tiles(cell):
+    """k_fast_aligned: 120 x 120 tiles of whole cells, 8 warps x 15 rows, four boxes from gx0 - 4."""
+    b = 19
+    assert AL_T % cell == 0 and cell % AL_RPT == 0 and AL_RPT * WARPS == AL_T
+    loads = ceil_div(AL_T + 6, IMG_BOX_ROWS)
+    assert AL_RPT * (WARPS - 1) + (AL_RPT - 1) + 6 < loads * IMG_BOX_ROWS
+    for w, h in det_levels(b):
+        ncx, ncy = ceil_div(w - 2 * b, cell), ceil_div(h - 2 * b, cell)
+        ftiles_x, ftiles_y = ceil_div(ncx, AL_T // cell), ceil_div(ncy, AL_T // cell)
+        for ftx in range(ftiles_x):
+            x_lo = b + ftx * AL_T
+            gx0 = x_lo & ~3
+            box_x = (gx0 - 4) & ~15
+            assert box_x % 16 == 0 and box_x >= 0
+            xoff0 = gx0 - box_x
+            assert xoff0 >= 4 and xoff0 + 4 * 31 + 7 < SROW
+            assert gx0 + 4 * 32 >= x_lo + AL_T
+        assert b + ftiles_x * AL_T >= w - b and b + ftiles_y * AL_T >= h - b
