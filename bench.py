@@ -290,9 +290,10 @@ def summarize_clocks(path: str):
 # detect tiles.
 ALU_LANES_PER_SM_CLK = 64
 FAST_OPS_PER_PX = 40.5
-# DRAM bytes of one k_fast launch per frame, from the ncu capture summarised in
-# profiles/k_fast_1080p8.md (64-frame launch, scaled per frame), valid while
-# k_fast.cu's code (comments and blank lines removed: code_sha1) has this SHA-1.
+# DRAM bytes of one k_fast launch per frame: dram__bytes_read.sum +
+# dram__bytes_write.sum of an ncu capture of one general-form launch over 64
+# 1080p frames with 8 levels, divided by 64.  Valid while k_fast.cu's code
+# (comments and blank lines removed: code_sha1) has this SHA-1.
 FAST_TRAFFIC = {"code_sha1": "d78cf16d738bf9b07f48ede0fcf7b7e109859a22", "bytes_per_frame": (519807488 + 353865472) / 64}
 
 

@@ -158,13 +158,22 @@ int of_detect_batch(of_handle* h, const of_frame* frames, int n_frames, int leve
  *   OF_BUF_CELLT  per-cell threshold, ncx x ncy bytes (fast_t or fast_t_lo)
  *   OF_BUF_CAND   NMS survivors, count x 16 bytes {int64 key; int32 x; int32 y},
  *                 in no particular order
+ *   OF_BUF_PMASK  (after of_detect_learned only) the tile mask the exact path
+ *                 ran on, gx x gy bytes, 1 = tile kept (proposed, a dilated
+ *                 neighbour, or every tile of a fallback image)
+ *   OF_BUF_LOGIT  (after of_detect_learned only) the network's logit of each
+ *                 proposal tile, gx x gy float32
  * dst [device] may be NULL to query the size.  dims [host] receives
- * {w, h, count_or_ncx, ncy}.  Returns the byte size, or a negative OF_ERR_*.
- * Synchronises the handle's stream. */
+ * {w, h, count_or_ncx, ncy}, or {gx, gy, 0, 0} for the two tile buffers
+ * (tile (i, j) covers x in [tile_x0 + 32 i, +32), y in [border + 32 j, +32),
+ * tile_x0 = border rounded down to a multiple of 16).  Returns the byte
+ * size, or a negative OF_ERR_*.  Synchronises the handle's stream. */
 #define OF_BUF_LEVEL 0
 #define OF_BUF_SCORE 1
 #define OF_BUF_CELLT 2
 #define OF_BUF_CAND 3
+#define OF_BUF_PMASK 4
+#define OF_BUF_LOGIT 5
 int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int64_t dst_bytes,
                    int32_t* dims);
 
@@ -237,9 +246,11 @@ int of_time_stages(of_handle* h, void* const* events);
  * it until the process exits.  A frame whose buffers do not fit returns
  * OF_ERR_TOO_LARGE (a 1920x1080 frame fits).  The first call on each device
  * looks the array's address up with cudaGetSymbolAddress, with that device
- * current; make that first call before any stream capture.  Calls share the
- * array: each call clears what must start at zero, and calls whose work
- * overlaps on the GPU race -- serialise them.  Returns OF_OK or OF_ERR_*. */
+ * current; make that first call before any stream capture.  The address is
+ * kept for the life of the process, so a device reset (cudaDeviceReset or
+ * any teardown of the primary context) is not supported afterwards.  Calls
+ * share the array: each call clears what must start at zero, and calls whose
+ * work overlaps on the GPU race -- serialise them.  Returns OF_OK or OF_ERR_*. */
 #define OF_NOALLOC_SCRATCH_BYTES (16u << 20)
 int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pitch, int fast_t,
                             int fast_t_lo, float harris_k, int n_features,

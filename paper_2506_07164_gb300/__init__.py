@@ -29,11 +29,11 @@ __all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspec
            "of_tcnn_set_params", "of_tcnn_get_params", "of_tcnn_forward", "of_tcnn_loss_grad", "of_tcnn_adam",
            "of_tcnn_save", "of_tcnn_load", "of_detect_learned", "of_extract_tiles",
            "of_last_error", "of_version", "OfParams", "OfFrame", "OfKeypoint", "KEYPOINT_DTYPE",
-           "OF_BUF_LEVEL", "OF_BUF_SCORE", "OF_BUF_CELLT", "OF_BUF_CAND", "OfError", "load",
+           "OF_BUF_LEVEL", "OF_BUF_SCORE", "OF_BUF_CELLT", "OF_BUF_CAND", "OF_BUF_PMASK", "OF_BUF_LOGIT", "OfError", "load",
            "Detector", "keypoints_to_numpy"]
 
 OF_OK, OF_ERR_ARG, OF_ERR_TOO_LARGE, OF_ERR_CUDA, OF_ERR_TIMEOUT, OF_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
-OF_BUF_LEVEL, OF_BUF_SCORE, OF_BUF_CELLT, OF_BUF_CAND = 0, 1, 2, 3
+OF_BUF_LEVEL, OF_BUF_SCORE, OF_BUF_CELLT, OF_BUF_CAND, OF_BUF_PMASK, OF_BUF_LOGIT = 0, 1, 2, 3, 4, 5
 
 
 class OfError(RuntimeError):

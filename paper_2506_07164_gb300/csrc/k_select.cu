@@ -21,6 +21,8 @@
 // bandwidth-bound), and the passes over key bytes do not read positions.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "of_internal.h"
 
 namespace ofk {
@@ -277,8 +279,19 @@ void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, 
                                                                                       select_sort_cap(mq));
 }
 
+// The limit is a per-device attribute of the kernel shared by every handle,
+// server slot and allocation-free call, so it only ever grows: a later caller
+// with a smaller quota must not lower it under an earlier one.
 void set_select_smem_limit(int bytes) {
-    cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    static std::mutex mu;
+    static int limit[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && bytes <= limit[dev]) return;
+    if (cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+        dev >= 0 && dev < 64)
+        limit[dev] = bytes;
 }
 
 }  // namespace ofk

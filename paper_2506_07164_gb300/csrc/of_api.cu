@@ -1525,12 +1525,25 @@ int64_t of_inspect(of_handle* H, int what, int frame, int level, void* dst, int6
     const Settings& s = P->s;
     int32_t d4[4] = {I.w, I.h, 0, 0};
     int64_t bytes = 0;
+    int lj = -1;  // position of the image in the detect list (learned buffers)
     if (what == OF_BUF_LEVEL || what == OF_BUF_SCORE) {
         bytes = (int64_t)I.w * I.h;
     } else if (what == OF_BUF_CELLT) {
         d4[2] = I.ncx;
         d4[3] = I.ncy;
         bytes = (int64_t)I.ncx * I.ncy;
+    } else if (what == OF_BUF_PMASK || what == OF_BUF_LOGIT) {
+        if (!P->lbuf || !P->pmask_on) return fail(OF_ERR_ARG, "the last call was not of_detect_learned");
+        const int ii = frame * nl + level;
+        for (size_t j = 0; j < P->det_list.size(); ++j)
+            if (P->det_list[j] == ii) {
+                lj = (int)j;
+                break;
+            }
+        d4[0] = 4 * I.tiles_x;
+        d4[1] = I.tiles_y;
+        if (lj < 0) d4[0] = d4[1] = 0;  // no detect region: no tiles
+        bytes = (int64_t)d4[0] * d4[1] * (what == OF_BUF_LOGIT ? (int64_t)sizeof(float) : 1);
     } else if (what == OF_BUF_CAND) {
         int32_t n = 0;
         OF_CK(cudaStreamSynchronize(H->stream));
@@ -1560,6 +1573,11 @@ int64_t of_inspect(of_handle* H, int what, int frame, int level, void* dst, int6
     } else if (what == OF_BUF_CELLT) {
         ofk::launch_inspect_cells(P->d_img(), frame * nl + level, s.t_hi, s.t_lo, d, st);
         OF_CK(cudaGetLastError());
+    } else if (what == OF_BUF_PMASK) {
+        OF_CK(cudaMemcpyAsync(d, P->lbuf + P->off_mask + P->ptile_prefix[lj], bytes, cudaMemcpyDeviceToDevice, st));
+    } else if (what == OF_BUF_LOGIT) {
+        OF_CK(cudaMemcpyAsync(d, P->lbuf + P->off_logit + sizeof(float) * P->ptile_prefix[lj], bytes,
+                              cudaMemcpyDeviceToDevice, st));
     } else {
         ofk::launch_inspect_cands(P->d_img(), frame * nl + level, (int)(bytes / 16), d, st);
         OF_CK(cudaGetLastError());

@@ -16,7 +16,10 @@
 //   - Host code cannot use the array's name as a device address.  The first
 //     call on each device looks the address up with cudaGetSymbolAddress
 //     (and raises the top-N kernel's shared-memory limit) with that device
-//     current; make that first call before any stream capture begins.
+//     current; make that first call before any stream capture begins.  The
+//     address is cached per device for the life of the process: a device
+//     reset (cudaDeviceReset, primary-context teardown) is not supported
+//     after it.
 //   - Every call shares the array and it keeps the last call's contents; each
 //     call clears the counters and flags it needs.  Calls whose work overlaps
 //     on the GPU (different streams, or different host threads) race on the

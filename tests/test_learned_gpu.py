@@ -202,3 +202,123 @@ def test_training_skips_work_at_high_recall():
     assert ev["recall"] > rnd + 0.05, (ev, rnd)
     det.close()
     net.close()
+
+
+def _oracle_on_tiles(img, masks, levels=8, scale=1.2, n_features=1000, border=19, cell=30, t_hi=20, t_lo=7):
+    """The exact detector restricted to kept tiles, from oracle primitives:
+    s(p) = 0 outside the kept 32 x 32 tiles of each level, then the cell
+    thresholds, NMS, Harris keys, per-level quota and orientation as in the
+    plain path.  Returns (level, x_l, y_l, key, A, B, C, m10, m01, angle)
+    rows in output order."""
+    import oracle
+
+    num, den = oracle.k_fraction(0.04)
+    quota = oracle.level_quotas(n_features, levels, scale)
+    x0 = border & ~15
+    rows = []
+    for lvl in range(levels):
+        lev = oracle.pyramid_level(img, levels, scale, lvl)
+        h, w = lev.shape
+        if w - 2 * border <= 0 or h - 2 * border <= 0:
+            continue
+        sm = oracle.score_map(lev, border)
+        keep = np.zeros_like(sm, dtype=bool)
+        gy, gx = masks[lvl].shape
+        for j in range(gy):
+            for i in range(gx):
+                if masks[lvl][j, i]:
+                    keep[border + 32 * j: border + 32 * j + 32, x0 + 32 * i: x0 + 32 * i + 32] = True
+        sm = np.where(keep, sm, 0).astype(np.uint8)
+        T = oracle.cell_thresh(sm, border, cell, t_hi, t_lo)
+        surv = oracle.nms(sm, border, cell, T)
+        if len(surv) == 0:
+            continue
+        sums = [oracle.harris_sums(lev, x, y) for x, y in surv]
+        keys = [oracle.harris_key(a, b, c, num, den) for a, b, c in sums]
+        k, xs, ys = oracle.rank_sort(keys, surv[:, 0], surv[:, 1])
+        at = {(int(x), int(y)): s for (x, y), s in zip(surv, sums)}
+        for i in range(min(int(quota[lvl]), len(k))):
+            x, y = int(xs[i]), int(ys[i])
+            m10, m01, th = oracle.orient(lev, x, y)
+            rows.append((lvl, x, y, int(k[i]), *at[(x, y)], m10, m01, th))
+    return rows
+
+
+def test_full_frame_fallback_below_min_confidence():
+    """A min_confidence between the images' confidences sends some (frame,
+    level) images to the full-frame fallback and leaves the others on their
+    proposed tiles.  The inspected tile masks follow the network's logits
+    (threshold, dilation, all ones where the image fell back); fallen-back
+    images give exactly the plain path's records for that level; and every
+    frame equals the oracle restricted to the kept tiles."""
+    import json
+
+    meta = json.load(open(learned.DEFAULT_META))
+    thr, dil = meta["threshold"], meta["dilate"]
+    net = learned.TileNet(0).load(learned.DEFAULT_WEIGHTS)
+    frames = [synth.scene(1920, 1080, 960, background="pink"), synth.scene(1920, 1080, 961)]
+    dev = [torch.from_numpy(f).cuda() for f in frames]
+    fr = [(t, t.shape[1], t.shape[0], t.stride(0)) for t in dev]
+    N, L = 1000, 8
+    det = ofg.Detector(1920, 1080, max_levels=L, max_features=N, max_batch=2, fast_t_lo=7)
+
+    def tile_buf(what, f, lvl, dtype):
+        raw, dims = det.inspect(what, f, lvl)
+        return raw.view(dtype).reshape(dims[1], dims[0])
+
+    ofg.of_detect_learned(det.h, fr, L, 1.2, 20, 0.04, N, net.net, thr, 0.0, dil, det.out, det.counts)
+    logit = {(f, l): tile_buf(ofg.OF_BUF_LOGIT, f, l, np.float32) for f in range(2) for l in range(L)}
+    conf = {k: float(np.mean(np.abs(2.0 / (1.0 + np.exp(-z.astype(np.float64))) - 1.0))) for k, z in logit.items()}
+    c = np.sort(np.array(list(conf.values())))
+    gaps = c[1:] - c[:-1]
+    g = int(np.argmax(gaps))
+    assert gaps[g] > 1e-3, c  # a min_confidence that no rounding difference can move across an image
+    min_conf = float(0.5 * (c[g] + c[g + 1]))
+    fallback = {k for k, v in conf.items() if v < min_conf}
+    assert 0 < len(fallback) < 2 * L
+
+    st = ofg.of_detect_learned(det.h, fr, L, 1.2, 20, 0.04, N, net.net, thr, min_conf, dil, det.out, det.counts)
+    assert st["fallback_images"] == len(fallback), (st, sorted(conf.values()), min_conf)
+    masks = {k: tile_buf(ofg.OF_BUF_PMASK, *k, np.uint8) for k in logit}
+    torch.cuda.synchronize()
+    got = det.batch_results(2, N)
+    det.detect_batch(dev, levels=L, fast_t=20, n_features=N)
+    plain = det.batch_results(2, N)
+
+    for (f, l), m in masks.items():
+        if (f, l) in fallback:
+            assert m.all(), (f, l)
+            a, b = got[f][got[f]["level"] == l], plain[f][plain[f]["level"] == l]
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), (f, l)
+        else:
+            p = 1.0 / (1.0 + np.exp(-logit[(f, l)].astype(np.float64)))
+            pos = p >= thr
+            if dil:
+                q = np.pad(pos, 1)
+                pos = np.zeros_like(pos)
+                for dy in range(3):
+                    for dx in range(3):
+                        pos |= q[dy: dy + pos.shape[0], dx: dx + pos.shape[1]]
+            sure = np.abs(p - thr) > 1e-6  # tiles whose decision no float rounding can flip
+            if dil:
+                s = np.pad(~sure, 1)
+                near = np.zeros_like(sure)
+                for dy in range(3):
+                    for dx in range(3):
+                        near |= s[dy: dy + sure.shape[0], dx: dx + sure.shape[1]]
+                sure = ~near
+            np.testing.assert_array_equal(m.astype(bool)[sure], pos[sure], err_msg=str((f, l)))
+            assert not m.all() or pos.all(), (f, l)
+    assert any(not masks[k].all() for k in masks)  # some images ran on their proposed tiles only
+
+    for f in range(2):
+        rows = _oracle_on_tiles(frames[f], [masks[(f, l)].astype(bool) for l in range(L)], n_features=N)
+        g = got[f]
+        assert len(g) == len(rows), (f, len(g), len(rows))
+        ora = np.array([r[:9] for r in rows], np.int64)
+        for col, name in enumerate(["level", "x_l", "y_l", "key", "A", "B", "C", "m10", "m01"]):
+            np.testing.assert_array_equal(g[name].astype(np.int64), ora[:, col], err_msg=name)
+        d = (g["angle"].astype(np.float64) - np.array([r[9] for r in rows]) + np.pi) % (2 * np.pi) - np.pi
+        assert np.abs(d).max() <= 1e-5
+    det.close()
+    net.close()

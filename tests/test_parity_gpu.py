@@ -88,10 +88,11 @@ def test_single_level_640x480(seed):
     det.close()
 
 
-# ------------------------------------------------------------ config 2
-def test_pyramid_1080p_8_levels_with_cell_fallback():
-    img = synth.scene(1920, 1080, 7, background="pink")
-    det = ofg.Detector(1920, 1080, max_levels=8, max_features=1000, fast_t_lo=7)
+# ------------------------------------------------------------ config 2 (and the serving mix's 4K frames)
+@pytest.mark.parametrize("w,h,seed", [(1920, 1080, 7), (3840, 2160, 8)])
+def test_pyramid_8_levels_with_cell_fallback(w, h, seed):
+    img = synth.scene(w, h, seed, background="pink")
+    det = ofg.Detector(w, h, max_levels=8, max_features=1000, fast_t_lo=7)
     kp = det.detect(torch.from_numpy(img).cuda(), levels=8, scale=1.2, fast_t=20, n_features=1000)
     ora = oracle.detect(img, levels=8, scale=1.2, fast_t=20, fast_t_lo=7, n_features=1000)
     compare_keypoints(kp, ora)

@@ -1,15 +1,18 @@
 """Serving loop with continuous batching (of_server_*).
 
-Requests of mixed resolutions (and stereo pairs) arrive from a client thread
-while earlier batches are on the GPU; every result must equal of_detect on
-the same frame alone (bit-exact integer fields, response 1e-6 relative,
-angle 1e-5 rad), batches must hold several frames, and batches on different
-slots must overlap in time.
+Requests of mixed resolutions -- 640x480, 1280x720, 1920x1080 and 3840x2160,
+with stereo pairs -- arrive from a client thread while earlier batches are on
+the GPU.  Every result must equal the CPU oracle on the same frame and
+of_detect on the frame alone (bit-exact integer fields, response 1e-6
+relative, angle 1e-5 rad); batches must hold several frames, and batches on
+different slots must overlap in time.
 """
 
 import math
+import multiprocessing
 import threading
 import time
+from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
 import pytest
@@ -19,10 +22,13 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+import oracle  # noqa: E402
 import paper_2506_07164_gb300 as ofg  # noqa: E402
 
-EXACT = ["x_l", "y_l", "level", "fast_score", "A", "B", "C", "m10", "m01", "key", "x", "y"]
+EXACT = ["x_l", "y_l", "level", "fast_score", "A", "B", "C", "m10", "m01", "key"]
 CFG = dict(levels=8, scale=1.2, fast_t=20, harris_k=0.04, n_features=500)
+FULL_MIX = [(640, 480), (1280, 720), (1920, 1080), (3840, 2160), (640, 480), (1280, 720)]
+SMALL_MIX = [(640, 480), (1280, 720), (1920, 1080), (640, 480), (1280, 720)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -34,10 +40,13 @@ def _built():
 
 
 def same(a, b):
+    """b: of_detect's records or the oracle's (float64 x, y, response, angle)."""
     assert len(a) == len(b)
     for f in EXACT:
         np.testing.assert_array_equal(a[f], b[f], err_msg=f)
-    np.testing.assert_allclose(a["response"], b["response"], rtol=1e-6, atol=0)
+    for f in ("x", "y"):
+        np.testing.assert_array_equal(a[f], b[f].astype(np.float32), err_msg=f)
+    np.testing.assert_allclose(a["response"].astype(np.float64), b["response"], rtol=1e-6, atol=0)
     if len(a):
         d = (a["angle"].astype(np.float64) - b["angle"] + math.pi) % (2 * math.pi) - math.pi
         assert np.abs(d).max() <= 1e-5
@@ -50,19 +59,29 @@ def stereo_right(left: np.ndarray, disparity: int) -> np.ndarray:
     return right
 
 
-def make_requests():
+def _pool():
+    # spawn: the workers never inherit this process's CUDA context
+    return ProcessPoolExecutor(max_workers=min(8, multiprocessing.cpu_count()),
+                               mp_context=multiprocessing.get_context("spawn"))
+
+
+def make_requests(sizes=SMALL_MIX, reps=3, pool=None):
+    jobs = [(w, h, 300 + i, "pink" if i % 2 else "flat") for i, (w, h) in enumerate(sizes * reps)]
+    if pool is None:
+        frames = [synth.scene(w, h, seed, background=bg) for w, h, seed, bg in jobs]
+    else:  # module-level functions only, so the workers import synth / oracle and nothing else
+        frames = [f.result() for f in [pool.submit(synth.scene, w, h, seed, background=bg)
+                                       for w, h, seed, bg in jobs]]
     reqs = []
-    sizes = [(640, 480), (1280, 720), (1920, 1080), (640, 480), (1280, 720)]
-    for i, (w, h) in enumerate(sizes * 3):
-        img = synth.scene(w, h, 300 + i, background="pink" if i % 2 else "flat")
+    for i, img in enumerate(frames):
         reqs.append(img)
         if i % 4 == 1:  # a stereo pair: the right view is the left shifted by a seeded disparity
             reqs.append(stereo_right(img, 5 + i % 7))
     return reqs
 
 
-def run_server(reqs, **params):
-    srv = ofg.of_server_create(max_w=1920, max_h=1080, **{k: v for k, v in CFG.items()}, **params)
+def run_server(reqs, max_w=1920, max_h=1080, **params):
+    srv = ofg.of_server_create(max_w=max_w, max_h=max_h, **{k: v for k, v in CFG.items()}, **params)
     results = {}
     ids = {}
 
@@ -89,20 +108,27 @@ def run_server(reqs, **params):
 
 
 def alone(reqs):
-    det = ofg.Detector(1920, 1080, max_levels=8, max_features=CFG["n_features"])
+    W = max(img.shape[1] for img in reqs)
+    H = max(img.shape[0] for img in reqs)
+    det = ofg.Detector(W, H, max_levels=8, max_features=CFG["n_features"])
     out = [det.detect(torch.from_numpy(img).cuda(), levels=8, scale=1.2, fast_t=20, harris_k=0.04,
                       n_features=CFG["n_features"]) for img in reqs]
     det.close()
     return out
 
 
-def test_mixed_stream_equals_alone_and_batches_overlap():
-    reqs = make_requests()
-    results, stats = run_server(reqs, slots=3, max_batch=4, memory_budget=3 << 30)
-    ref = alone(reqs)
+def test_mixed_stream_equals_oracle_and_alone_and_batches_overlap():
+    with _pool() as pool:
+        reqs = make_requests(FULL_MIX, 2, pool)
+        assert {img.shape for img in reqs} == {(h, w) for w, h in FULL_MIX}
+        expect = [pool.submit(oracle.detect, img, **CFG) for img in reqs]  # on the host while the GPU serves
+        results, stats = run_server(reqs, max_w=3840, max_h=2160, slots=3, max_batch=4, memory_budget=3 << 30)
+        ref = alone(reqs)
+        expect = [f.result() for f in expect]
     for i, img in enumerate(reqs):
         r, kp = results[i]
         assert r.count >= 0 and (r.w, r.h) == (img.shape[1], img.shape[0])
+        same(kp, expect[i])
         same(kp, ref[i])
     # Continuous batching: some batches carried several frames ...
     assert max(r.batch_frames for r, _ in results.values()) > 1

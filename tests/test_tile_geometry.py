@@ -13,6 +13,8 @@ check what the kernels rely on without checking it at run time:
 """
 
 import math
+import os
+import re
 
 import pytest
 
@@ -23,6 +25,34 @@ IMG_BOX_ROWS, SCORE_BOX_ROWS = 40, 34
 WARPS = 8                      # DET_THREADS / 32
 CT_MAX_W, CT_RPT, CT_MAX_WARPS, CT_MAX_TILE_ROWS = 124, 5, 12, 64
 AL_T, AL_RPT = 120, 15
+
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2506_07164_gb300", "csrc")
+
+
+def source_constants(*files):
+    """`constexpr int NAME = EXPR;` lines of the given sources, evaluated in
+    order (integer arithmetic; names refer to earlier constants)."""
+    env = {}
+    pat = re.compile(r"^\s*constexpr\s+int\s+(\w+)\s*=\s*([^;]+);", re.M)
+    for f in files:
+        for name, expr in pat.findall(open(os.path.join(CSRC, f)).read()):
+            try:
+                env[name] = eval(expr.replace("/", "//"), {"__builtins__": {}}, dict(env))
+            except Exception:
+                pass  # an expression this restatement does not need
+    return env
+
+
+def test_constants_match_the_sources():
+    """The tiling restated here is the tiling the kernels are built with."""
+    c = source_constants("of_internal.h", "k_fast.cu", "k_nms_harris.cu")
+    assert (c["TILE_W"], c["HALO_X"], c["SROW"]) == (TILE_W, HALO_X, SROW)
+    assert (c["IMG_BOX_ROWS"], c["SCORE_BOX_ROWS"]) == (IMG_BOX_ROWS, SCORE_BOX_ROWS)
+    assert c["DET_THREADS"] // 32 == WARPS
+    assert (c["CT_MAX_W"], c["CT_RPT"], c["CT_MAX_WARPS"], c["CT_MAX_TILE_ROWS"]) == \
+        (CT_MAX_W, CT_RPT, CT_MAX_WARPS, CT_MAX_TILE_ROWS)
+    assert (c["AL_T"], c["AL_RPT"]) == (AL_T, AL_RPT)
+
 
 SIZES = [(1920, 1080), (1280, 720), (640, 480), (3840, 2160), (720, 540), (1440, 1080), (333, 217),
          (129, 77), (1000, 41), (41, 1000), (161, 161), (1283, 723)]
