@@ -81,9 +81,10 @@ def _gen_sized(args):
     return synth.scene(w, h, seed, background="pink")
 
 
-def serving_leg(pool, seconds: float, rate: float, seed: int = 0):
-    """Poisson arrivals at `rate` frames/s of the mixed-size workload, through the
-    continuous-batching server; returns latency percentiles and throughput."""
+def serving_leg(pool, seconds: float, rate: float, seed: int = 0, clients: int = 1):
+    """Poisson arrivals at `rate` frames/s of the mixed-size workload (split
+    over `clients` submitting threads), through the continuous-batching
+    server; returns latency percentiles and throughput."""
     import threading
 
     import numpy as np
@@ -95,12 +96,12 @@ def serving_leg(pool, seconds: float, rate: float, seed: int = 0):
     srv = ofg.of_server_create(max_w=3840, max_h=2160, levels=LEVELS, scale=SCALE, fast_t=FAST_T,
                                fast_t_lo=FAST_T_LO, harris_k=HARRIS_K, n_features=NFEAT, slots=4,
                                max_batch=16, memory_budget=12 << 30)
-    rng = np.random.default_rng(seed)
     done = []
-    submitted = [0]
-    t_end = [None]
+    submitted = [0] * clients
+    crate = rate / clients
 
-    def client():
+    def client(c):
+        rng = np.random.default_rng(seed + 1000 * c)
         t0 = time.perf_counter()
         t_next = t0
         while t_next - t0 < seconds:
@@ -116,13 +117,12 @@ def serving_leg(pool, seconds: float, rate: float, seed: int = 0):
                 right[:, img.shape[1] - d:] = img[:, -1:]
                 ofg.of_server_submit(srv, img, tag=1)
                 ofg.of_server_submit(srv, right, tag=2)
-                submitted[0] += 2
-                t_next += float(rng.exponential(2.0 / rate))
+                submitted[c] += 2
+                t_next += float(rng.exponential(2.0 / crate))
             else:
                 ofg.of_server_submit(srv, img, tag=0)
-                submitted[0] += 1
-                t_next += float(rng.exponential(1.0 / rate))
-        t_end[0] = time.perf_counter()
+                submitted[c] += 1
+                t_next += float(rng.exponential(1.0 / crate))
 
     # Warm the plans of each size class (first use captures a graph) before timing.
     for sz in SERVE_SIZES:
@@ -131,22 +131,25 @@ def serving_leg(pool, seconds: float, rate: float, seed: int = 0):
     got = 0
     while got < 2 * len(SERVE_SIZES):
         got += len(ofg.of_server_poll(srv, 64, NFEAT, wait_ms=100))
-    th = threading.Thread(target=client)
+    ths = [threading.Thread(target=client, args=(c,)) for c in range(clients)]
     wall0 = time.perf_counter()
-    th.start()
-    while th.is_alive() or len(done) < submitted[0]:
+    for th in ths:
+        th.start()
+    while any(th.is_alive() for th in ths) or len(done) < sum(submitted):
         for r, _ in ofg.of_server_poll(srv, 256, NFEAT, wait_ms=20):
             done.append((r.t_submit, r.t_done, r.count, r.batch_frames, r.w * r.h))
-        if not th.is_alive() and time.perf_counter() - wall0 > seconds + 60:
+        if not any(th.is_alive() for th in ths) and time.perf_counter() - wall0 > seconds + 60:
             break
-    th.join()
+    for th in ths:
+        th.join()
     stats = ofg.of_server_stats(srv)
     ofg.of_server_destroy(srv)
     lat = np.array([b - a for a, b, *_ in done]) * 1000.0
     first = min(a for a, *_ in done)
     last = max(b for _, b, *_ in done)
     ok = sum(1 for d in done if d[2] >= 0)
-    return {"offered_rate_fps": round(submitted[0] / seconds, 1), "frames": len(done), "ok": ok,
+    return {"offered_rate_fps": round(sum(submitted) / seconds, 1), "client_threads": clients,
+            "frames": len(done), "ok": ok,
             "frames_per_s": round(len(done) / (last - first), 1),
             "mpix_per_s": round(sum(d[4] for d in done) / (last - first) / 1e6, 1),
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
@@ -295,6 +298,13 @@ FAST_OPS_PER_PX = 40.5
 # 1080p frames with 8 levels, divided by 64.  Valid while k_fast.cu's code
 # (comments and blank lines removed: code_sha1) has this SHA-1.
 FAST_TRAFFIC = {"code_sha1": "d78cf16d738bf9b07f48ede0fcf7b7e109859a22", "bytes_per_frame": (519807488 + 353865472) / 64}
+# L2 (lts__t_bytes.sum) and DRAM (dram__bytes_read.sum + dram__bytes_write.sum)
+# bytes per frame of each stage's kernels, from one ncu capture of the
+# per-stage launches (of_time_stages) over a batch of 1080p frames with 8
+# levels, divided by the frames.  Valid while the kernels' code
+# (kernels_sha1) and the per-stage launch choices below are the ones captured;
+# otherwise the line reports null.
+STAGE_TRAFFIC = None
 
 
 def code_sha1(path):
@@ -306,6 +316,21 @@ def code_sha1(path):
     with open(path) as f:
         lines = [re.sub(r"//.*$", "", l).rstrip() for l in f.read().splitlines()]
     return hashlib.sha1("\n".join(l for l in lines if l.strip()).encode()).hexdigest()
+
+
+def kernels_sha1():
+    """SHA-1 over the code (comments and blank lines removed) of every kernel
+    source and header of the library."""
+    import glob
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_2506_07164_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "k_*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                   [os.path.join(csrc, "of_internal.h")])
+    return hashlib.sha1("".join(code_sha1(f) for f in files).encode()).hexdigest()
+
+
+STAGE_TUNING_FIELDS = ("resize_tma", "resize_tile_h", "fast_cell_tiles", "fast_tile_h", "nms_tile_h")
 
 
 def detect_region_pixels(lw, lh):
@@ -320,6 +345,39 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def measure_read_peaks(ofg, torch, stream, reps: int = 3):
+    """Read bandwidth with the library's probe: L2 (buffers of 8..48 MB, read
+    many times; best) and HBM (a 4 GiB buffer).  GB/s of bytes read."""
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = {}
+    for name, sizes, total in (("l2", [8 << 20, 16 << 20, 32 << 20, 48 << 20], 24e9), ("hbm", [4 << 30], 16e9)):
+        best = 0.0
+        for nb in sizes:
+            buf = torch.ones(nb, dtype=torch.uint8, device="cuda")
+            r = max(1, int(total / nb))
+            with torch.cuda.stream(stream):
+                ofg.of_probe_read(buf, nb, r, sink, stream)  # warm (and load the buffer into L2)
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ofg.of_probe_read(buf, nb, r, sink, stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    best = max(best, nb * r / (e0.elapsed_time(e1) / 1000.0) / 1e9)
+            del buf
+        out[name] = round(best, 1)
+    torch.cuda.synchronize()
+    return out
+
+
+def floor_bytes_per_frame(levels_w, levels_h, kept):
+    """Least HBM traffic of one frame with every level kept resident: read the
+    input, write levels 1..L-1, read every level once for detection, write
+    the keypoint records."""
+    px = [w * h for w, h in zip(levels_w, levels_h)]
+    return px[0] + sum(px[1:]) + sum(px) + 64 * kept
 
 
 def stage_bytes(levels_w, levels_h, cand_counts, kept_counts):
@@ -401,6 +459,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true", help="skip the per-frame path (profiling)")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving leg duration (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=500.0, help="Poisson arrival rate, frames/s")
+    ap.add_argument("--serve-sat-rate", type=float, default=6000.0,
+                    help="offered rate of the saturated serving leg, frames/s (0: skip)")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-buffer path (profiling)")
     ap.add_argument("--skip-learned", action="store_true", help="skip the learned tile-proposal leg")
     ap.add_argument("--skip-ablation", action="store_true", help="skip the paper-variant ablation leg")
@@ -661,6 +721,29 @@ def main():
                      "stage_share": {n: round(x, 4) for n, x in zip(ofg.STAGE_NAMES, shares)},
                      "stage_frac_of_hbm": stage_hbm,
                      "algorithmic_bytes_per_frame": dict(zip(ofg.STAGE_NAMES, per_frame))})
+    # L2 beside HBM: measured read peaks (library probe), and each stage's
+    # captured L2 and DRAM bytes over its live stage time.
+    peaks_rd = measure_read_peaks(ofg, torch, stream)
+    roofline["read_peaks_gbs"] = {"l2": peaks_rd["l2"], "hbm": peaks_rd["hbm"],
+                                  "how": "of_probe_read: 16-byte L2-only loads, 8x256 threads per SM; L2: best "
+                                         "of 8..48 MB buffers read repeatedly; HBM: a 4 GiB buffer"}
+    st_ok = (STAGE_TRAFFIC is not None and STAGE_TRAFFIC["code_sha1"] == kernels_sha1() and
+             all(int(tuning.get(k, -1)) == STAGE_TRAFFIC["tuning"][k] for k in STAGE_TUNING_FIELDS))
+    if st_ok:
+        l2b, drb = STAGE_TRAFFIC["l2_bytes_per_frame"], STAGE_TRAFFIC["dram_bytes_per_frame"]
+        roofline["stage_l2_gbs"] = {n: round(l2b[n] * B / (stage_ms[i] / 1000.0) / 1e9, 1)
+                                    for i, n in enumerate(ofg.STAGE_NAMES)}
+        roofline["stage_frac_of_l2"] = {n: round(v / peaks_rd["l2"], 4) for n, v in roofline["stage_l2_gbs"].items()}
+        roofline["stage_dram_gbs"] = {n: round(drb[n] * B / (stage_ms[i] / 1000.0) / 1e9, 1)
+                                      for i, n in enumerate(ofg.STAGE_NAMES)}
+        roofline["stage_dram_frac_of_hbm"] = {n: round(v / peak, 4) for n, v in roofline["stage_dram_gbs"].items()}
+    else:
+        roofline["stage_l2_gbs"] = roofline["stage_frac_of_l2"] = None
+        roofline["stage_traffic_note"] = "kernels or launch choices differ from the captured ones"
+    # The whole step against the memory roofline: least HBM bytes per frame
+    # (input, resident levels written once and read once, records) at the
+    # measured frame rate.
+    floor = floor_bytes_per_frame(lw, lh, float(np.mean(counts)))
 
     # Learned tile proposal on the same batch: committed network and threshold.
     learned_out = None
@@ -720,9 +803,11 @@ def main():
     if not args.skip_ablation and rank == 0:
         ablation = ablation_leg(pool, batched, stream)
 
-    serving = None
+    serving = serving_sat = None
     if args.serve_seconds > 0:
         serving = serving_leg(pool, args.serve_seconds, args.serve_rate)
+        if args.serve_sat_rate > 0:
+            serving_sat = serving_leg(pool, args.serve_seconds, args.serve_sat_rate, seed=1, clients=4)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -743,6 +828,9 @@ def main():
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {B} frames x {W_ * H_ / 1e6:.2f} MB per step"},
         "mpix_per_s": round(value * mpix, 1),
+        "memory_roofline": {"floor_bytes_per_frame": round(floor), "achieved_gbs": round(floor * value / 1e9, 1),
+                            "peak_gbs": peak, "peak_kind": peak_kind, "frac": round(floor * value / 1e9 / peak, 4),
+                            "floor": "input + levels 1..7 written + all levels read once + 64 B records"},
         "staged_ms_per_step": round(ms_stages / args.steps, 4),
         "plain": {"value": round(plain_fps, 2), "unit": "frames/s", "mpix_per_s": round(plain_fps * mpix, 1),
                   "steps": plain_steps, "frames_per_step": plain_frames,
@@ -758,6 +846,7 @@ def main():
         "learned": learned_out,
         "ablation": ablation,
         "serving": serving,
+        "serving_saturated": serving_sat,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": kernels_per_step * args.steps,

@@ -425,6 +425,17 @@ int of_variant_detect(int fast_variant, int harris_variant, const uint8_t* img, 
 int of_plan_levels(int W, int H, int levels, float scale, int n_features, int32_t* ws,
                    int32_t* hs, int32_t* quota);
 
+/* Bandwidth probe for reporting kernels against a measured peak; the paper
+ * has no counterpart and the detector does not use it.  Reads `bytes` of
+ * buf [device, 16-byte aligned] `reps` times with 16-byte loads that are
+ * cached in L2 only, from 8 blocks of 256 threads per SM; writes a value
+ * folded from the data into *sink [device, one uint32] only in a case that
+ * practically never occurs (it keeps the loads).  A buffer that fits in L2
+ * measures the L2 read bandwidth (bytes * reps / elapsed time on `stream`,
+ * timed by the caller), one much larger than L2 the HBM read bandwidth.
+ * Asynchronous.  Returns OF_OK, OF_ERR_ARG or OF_ERR_CUDA.  Allocates nothing. */
+int of_probe_read(const void* buf, int64_t bytes, int reps, uint32_t* sink, void* stream);
+
 /* Message for the last error on this host thread ("" if none). */
 const char* of_last_error(void);
 

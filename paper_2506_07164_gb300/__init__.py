@@ -21,7 +21,7 @@ import numpy as np
 from .build import LIB, build  # noqa: F401
 
 __all__ = ["of_create", "of_destroy", "of_detect", "of_detect_batch", "of_inspect", "of_plan_levels",
-           "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc", "of_sync",
+           "of_time_stages", "OF_N_STAGES", "STAGE_NAMES", "of_detect_level_noalloc", "of_probe_read", "of_sync",
            "of_test_timeout", "OF_ERR_TIMEOUT", "of_autotune", "of_variant_detect", "OfVarPoint",
            "VAR_POINT_DTYPE", "of_set_tuning", "OfTuning", "of_batch_bytes",
            "of_server_create", "of_server_destroy", "of_server_submit", "of_server_poll", "of_server_stats",
@@ -160,6 +160,8 @@ def load(path: str | None = None):
     L.of_detect_level_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_float, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     L.of_detect_level_noalloc.restype = C.c_int
+    L.of_probe_read.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]
+    L.of_probe_read.restype = C.c_int
     L.of_variant_detect.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                     C.c_float, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
     L.of_variant_detect.restype = C.c_int
@@ -304,6 +306,12 @@ def of_detect_level_noalloc(img, w: int, h: int, pitch: int, fast_t: int, fast_t
     s = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
     return _check(load().of_detect_level_noalloc(_ptr(img), w, h, pitch, fast_t, fast_t_lo, harris_k,
                                                  n_features, _ptr(out_kpts), _ptr(out_count), s))
+
+
+def of_probe_read(buf, nbytes: int, reps: int, sink, stream=None) -> None:
+    """Read nbytes of a device buffer reps times (bandwidth probe; see include/ofast.h). Asynchronous."""
+    s = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    _check(load().of_probe_read(_ptr(buf), nbytes, reps, _ptr(sink), s))
 
 
 def of_variant_detect(fast_variant: int, harris_variant: int, img, w: int, h: int, pitch: int, fast_t: int,
