@@ -1,23 +1,24 @@
 // Per-cell threshold applied to FAST score maps in place.
 //
 // After the general FAST kernel the maps hold s(p) where s(p) >= t_lo, as
-// the offset score s(p) - (t_lo - 1) (0 elsewhere); thresholds are compared
-// in those units (t_hi - t_lo + 1).  Each
-// cell (anchored at the border) is flagged when some pixel scores >= t_hi --
-// by FAST itself, or here (FLAGS) from the maps, band by band.  This pass
+// the offset score s(p) - (t_lo - 1) (0 elsewhere), and the cell flags are
+// set (a cell is flagged when some pixel in it scores >= t_hi).  This pass
 // turns the maps into the candidate scores NMS keys on,
 // S(p) = s(p) if s(p) >= T(cell(p)) else 0 with T = t_hi in flagged cells:
-// in a flagged cell the bytes below t_hi are cleared.  On the learned path it
-// also clears the scores outside the proposed 32 x 32 tiles.
+// in a flagged cell the bytes below t_hi (t_hi - t_lo + 1 in offset units)
+// are cleared.  On the learned path it also clears the scores outside the
+// proposed 32 x 32 tiles.
 //
 // One block per band of cell rows (one cell high) of one image.  With FLAGS
-// the block first ORs, per lane and 16-byte chunk, the bytes >= t_hi over the
-// band's rows, maps them to cells in shared memory and stores the band's
-// flags.  Then it writes, for up to 4096 columns at a time, a byte 0xFF where
-// the column's cell in this band is flagged (all rows of a band share their
-// cells' flags), and its warps stream the band's rows in 16-byte chunks
-// against that mask, four chunks in flight per lane, writing a chunk back
-// only when it changes (the second read of a band mostly hits L1/L2).
+// (when the FAST kernel did not set the flags) the block first ORs, per lane
+// and 16-byte chunk, a "byte >= t_hi" bit over the band's rows (three
+// instructions per word), maps the set bits to cells in shared memory and
+// stores the band's flags.  Then it writes, for up to 4096 columns at a time,
+// a byte 0xFF where the column's cell in this band is flagged (all rows of a
+// band share their cells' flags), and its warps stream the band's rows in
+// 16-byte chunks against that mask, four chunks in flight per lane, writing a
+// chunk back only when it changes (the second read of a band mostly hits
+// L2).  The byte test "b >= t" takes five instructions per word (bytes_ge).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,24 +27,36 @@
 
 namespace ofk {
 
-// 0xFF in each byte of v that is below t (t <= 255).
-__device__ __forceinline__ uint32_t bytes_below(uint32_t v, uint32_t t) {
-    const uint32_t tt = (0x8000u - t) * 0x00010001u;
-    const uint32_t lo = __byte_perm(v, 0u, 0x4140) + tt, hi = __byte_perm(v, 0u, 0x4342) + tt;
-    return ~__byte_perm((lo >> 15 & 0x00010001u) * 0xFFu, (hi >> 15 & 0x00010001u) * 0xFFu, 0x6420);
-}
-
 constexpr int CA_THREADS = 256;
 constexpr int CA_SEG = 256;  // 16-byte chunks per column-mask segment (4096 columns)
 
-__device__ __forceinline__ uint32_t apply_word(uint32_t v, uint32_t fm, uint32_t t_hi) {
-    return v & ~(fm & bytes_below(v, t_hi));
+// 0xFF in each byte of v that is >= t, for 1 <= t <= 128: (b | 0x80) - t has
+// no borrow out of its byte and bit 7 set exactly when the low seven bits are
+// >= t; a byte with bit 7 set is >= 128 >= t itself.
+__device__ __forceinline__ uint32_t bytes_ge(uint32_t v, uint32_t t) {
+    const uint32_t g = (((v | 0x80808080u) - t * 0x01010101u) | v) & 0x80808080u;
+    return (g >> 7) * 0xFFu;
 }
 
-// 0xFF in each byte of v that is >= t.
-__device__ __forceinline__ uint32_t bytes_at_least(uint32_t v, uint32_t t) { return ~bytes_below(v, t); }
+// The same for any t <= 255, in 16-bit lanes.
+__device__ __forceinline__ uint32_t bytes_ge_any(uint32_t v, uint32_t t) {
+    const uint32_t tt = (0x8000u - t) * 0x00010001u;
+    const uint32_t lo = __byte_perm(v, 0u, 0x4140) + tt, hi = __byte_perm(v, 0u, 0x4342) + tt;
+    return __byte_perm((lo >> 15 & 0x00010001u) * 0xFFu, (hi >> 15 & 0x00010001u) * 0xFFu, 0x6420);
+}
 
-template <bool FLAGS>
+// Bit 7 of each byte of the result is set when that byte of v is >= t
+// (1 <= t <= 128; the other bits are garbage): ORed over many words, then
+// masked with 0x80808080 once.
+__device__ __forceinline__ uint32_t ge_bits(uint32_t v, uint32_t t) { return ((v | 0x80808080u) - t * 0x01010101u) | v; }
+
+// Clear the bytes of v below t where fm is 0xFF (flagged cells).
+template <bool SMALL_T>
+__device__ __forceinline__ uint32_t apply_word(uint32_t v, uint32_t fm, uint32_t t) {
+    return v & ((SMALL_T ? bytes_ge(v, t) : bytes_ge_any(v, t)) | ~fm);
+}
+
+template <bool FLAGS, bool SMALL_T>
 __global__ void __launch_bounds__(CA_THREADS)
 k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ band_prefix,
              int n_list, int n_bands, int t_hi, int t_lo, int border, int cell) {
@@ -65,9 +78,9 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
         const int rx1 = I.w - border, ry1 = I.h - border;
         const int xb0 = border & ~15;  // first chunk column
         const int n_chunks = (rx1 - xb0 + 15) >> 4;
-        uint32_t* crow = I.cell + (size_t)cy * ncx;
-        const int y0 = border + cy * cell, y1 = min(y0 + cell, ry1);
+        uint32_t* const crow = I.cell + (size_t)cy * ncx;
         const uint32_t* fl = crow;
+        const int y0 = border + cy * cell, y1 = min(y0 + cell, ry1);
         if (FLAGS && cells) {
             __syncthreads();  // the previous band's readers are done with bflag and colmask
             for (int i = tid; i < ncx; i += CA_THREADS) bflag[i] = 0u;
@@ -87,10 +100,17 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                         // Scores outside proposed tiles are stale: they do not count.
                         if (pmask && pmask[(size_t)py * 4 * tiles_x + ((x - tile_x0) >> 5)] == 0) continue;
                         const uint4 v = *reinterpret_cast<const uint4*>(srow + x);
-                        acc[k].x |= bytes_at_least(v.x, th);
-                        acc[k].y |= bytes_at_least(v.y, th);
-                        acc[k].z |= bytes_at_least(v.z, th);
-                        acc[k].w |= bytes_at_least(v.w, th);
+                        if (SMALL_T) {
+                            acc[k].x |= ge_bits(v.x, th);
+                            acc[k].y |= ge_bits(v.y, th);
+                            acc[k].z |= ge_bits(v.z, th);
+                            acc[k].w |= ge_bits(v.w, th);
+                        } else {
+                            acc[k].x |= bytes_ge_any(v.x, th);
+                            acc[k].y |= bytes_ge_any(v.y, th);
+                            acc[k].z |= bytes_ge_any(v.z, th);
+                            acc[k].w |= bytes_ge_any(v.w, th);
+                        }
                     }
                 }
 #pragma unroll
@@ -98,12 +118,14 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                     const int c = c0 + lane + 32 * k;
                     if (c >= n_chunks) continue;
                     const int x = xb0 + 16 * c;
-                    const uint32_t wd[4] = {acc[k].x, acc[k].y, acc[k].z, acc[k].w};
+                    const uint32_t wd[4] = {acc[k].x & 0x80808080u, acc[k].y & 0x80808080u,
+                                            acc[k].z & 0x80808080u, acc[k].w & 0x80808080u};
+                    if ((wd[0] | wd[1] | wd[2] | wd[3]) == 0u) continue;
                     int last = -1;  // last cell flagged by this chunk (adjacent bytes share cells)
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const int xx = x + i;
-                        if (((wd[i >> 2] >> (8 * (i & 3))) & 1u) && xx >= border && xx < rx1) {
+                        if (((wd[i >> 2] >> (8 * (i & 3) + 7)) & 1u) && xx >= border && xx < rx1) {
                             const int cx = (int)__umulhi((uint32_t)(xx - border), magic);
                             if (cx != last) {
                                 atomicOr(&bflag[cx], 1u);
@@ -121,6 +143,7 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
             const int s1 = min(s0 + CA_SEG, n_chunks);
             __syncthreads();  // earlier readers of colmask are done
             // Column mask of the segment: 0xFF where the column is in the region and its cell is flagged.
+            int any = 0;
             for (int c = s0 + tid; c < s1; c += CA_THREADS) {
                 const int x = xb0 + 16 * c;
                 uint32_t w[4];
@@ -136,10 +159,12 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                         }
                     }
                     w[q] = m;
+                    any |= m != 0u;
                 }
                 *reinterpret_cast<uint4*>(colmask + 16 * (c - s0)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            __syncthreads();
+            // A segment with no flagged cell keeps its bytes (unless proposal tiles clear some).
+            if (!__syncthreads_or(any) && !pmask) continue;
             for (int y = y0 + warp; y < y1; y += CA_THREADS / 32) {
                 uint8_t* srow = score + (size_t)y * spitch;
                 const int py = (y - border) >> 5;
@@ -164,10 +189,10 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
                             nv.w = v[k].w & ~range_mask4(x + 12, border, rx1);
                         } else {
                             const uint4 fm = *reinterpret_cast<const uint4*>(colmask + 16 * (c - s0));
-                            nv.x = apply_word(v[k].x, fm.x, th);
-                            nv.y = apply_word(v[k].y, fm.y, th);
-                            nv.z = apply_word(v[k].z, fm.z, th);
-                            nv.w = apply_word(v[k].w, fm.w, th);
+                            nv.x = apply_word<SMALL_T>(v[k].x, fm.x, th);
+                            nv.y = apply_word<SMALL_T>(v[k].y, fm.y, th);
+                            nv.z = apply_word<SMALL_T>(v[k].z, fm.z, th);
+                            nv.w = apply_word<SMALL_T>(v[k].w, fm.w, th);
                         }
                         if (nv.x != v[k].x || nv.y != v[k].y || nv.z != v[k].z || nv.w != v[k].w)
                             *reinterpret_cast<uint4*>(srow + x) = nv;
@@ -182,12 +207,18 @@ void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* 
                        int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags) {
     if (n_bands <= 0) return;
     grid = grid < n_bands ? grid : n_bands;
-    if (flags)
-        k_cell_apply<true><<<grid, CA_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, band_prefix, n_list,
-                                                                           n_bands, t_hi, t_lo, border, cell);
-    else
-        k_cell_apply<false><<<grid, CA_THREADS, 0, (cudaStream_t)stream>>>(imgs, img_list, band_prefix, n_list,
-                                                                            n_bands, t_hi, t_lo, border, cell);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const bool small_t = t_hi - t_lo + 1 <= 128;
+#define OF_CA_LAUNCH(FL, SM) \
+    k_cell_apply<FL, SM><<<grid, CA_THREADS, 0, st>>>(imgs, img_list, band_prefix, n_list, n_bands, t_hi, t_lo, border, cell)
+    if (flags) {
+        if (small_t) OF_CA_LAUNCH(true, true);
+        else OF_CA_LAUNCH(true, false);
+    } else {
+        if (small_t) OF_CA_LAUNCH(false, true);
+        else OF_CA_LAUNCH(false, false);
+    }
+#undef OF_CA_LAUNCH
 }
 
 }  // namespace ofk

@@ -23,10 +23,14 @@
 // those words; at an odd offset one more permute joins two of them.
 //
 // Per-cell fallback: a cell with any pixel scoring >= t_hi is flagged.  The
-// FLAGS variant (32-row tiles) sets the flags itself (shared-memory flags per
-// tile, then one global atomicOr per flagged cell); otherwise the threshold
-// pass computes them, or the cell-tile kernel at the end of this file, whose
-// tiles hold whole cells, applies the thresholds directly.
+// general kernel sets the flags itself: a thread keeps the running maximum of
+// its pixels' scores per cell row (one packed maximum per pixel pair and
+// row), compares it with t_hi once per cell row, and ORs its (at most two)
+// cells' flags into a per-tile table in shared memory; the tile's flagged
+// cells reach the global flags with one atomicOr each, in the next iteration
+// after its first barrier.  The threshold pass then only applies them.  The
+// cell-tile kernels further down, whose tiles hold whole cells, apply the
+// thresholds directly.
 //
 // Persistent launch: a grid of a few blocks per SM walks all tiles of the
 // batch; a 128 x TH tile (TH = 32, 64, 128 or 256 rows) arrives by TMA as
@@ -149,20 +153,31 @@ constexpr int FAST_BUF = (FAST_BOX + 127) / 128 * 128;  // buffer stride in shar
 // Dynamic shared memory of the TH-row kernel: two buffers of stacked boxes + alignment slack.
 constexpr int fast_dyn_bytes(int th) { return 2 * ((th + 8 + IMG_BOX_ROWS - 1) / IMG_BOX_ROWS) * FAST_BUF + 128; }
 
+// Cells a 128 x TH tile can overlap (cells of at least 8 pixels).
+template <int TH>
+struct FastCells {
+    static constexpr int LCW = TILE_W / 8 + 2, LCH = TH / 8 + 2, N = LCW * LCH;
+};
+
+// The per-tile cell-flag table of one tile, for its flush in the next iteration.
+struct FlagTile {
+    uint32_t* cell;  // the image's global flags
+    int32_t ncx, ncy, cx0, cy0, lcw, n;
+};
+
 // Persistent: each block walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // Thread 0 fetches the next tile by TMA into the other buffer while the
-// block scores the current one.  FLAGS: also set the per-cell "a pixel
-// scores >= t_hi" flags (else the threshold pass computes them).  TH: tile
-// rows, 32 or (without FLAGS) 64, 128 or 256 -- a taller tile stacks more
-// image boxes and divides the barriers per pixel and the staged rows per
-// output row; 128- and 256-row tiles keep their buffers in dynamic shared
-// memory (over the 48 KB static limit).
+// block scores the current one, and the block sets the per-cell "a pixel
+// scores >= t_hi" flags.  TH: tile rows, 32, 64, 128 or 256 -- a taller tile
+// stacks more image boxes and divides the barriers per pixel and the staged
+// rows per output row; 128- and 256-row tiles keep their buffers in dynamic
+// shared memory (over the 48 KB static limit).
 template <bool FLAGS, int TH>
 __global__ void __launch_bounds__(DET_THREADS, TH == 32 ? 3 : 2)
 k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
        const int32_t* __restrict__ prefix, int n_list, int n_tiles, const CUtensorMap* __restrict__ maps,
-       const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, int order) {
-    static_assert(!FLAGS || TH == TILE_H, "the cell-flag variant uses 32-row tiles");
+       const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, uint32_t cell_magic, int order) {
+    // cell_magic = 2^32 / cell rounded up: n / cell == umulhi(n, cell_magic) for 0 <= n < 2^16.
     constexpr int RPT = TH / 8;                                    // rows per thread
     constexpr int LOADS = (TH + 8 + IMG_BOX_ROWS - 1) / IMG_BOX_ROWS;  // image boxes per tile
     constexpr int BUF = LOADS * FAST_BUF;
@@ -172,7 +187,8 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     uint8_t* const sbuf = DYN ? fast_dyn + ((128u - (smem_u32(fast_dyn) & 127u)) & 127u) : sbuf_static;
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ TileInfo tinfo[2];
-    __shared__ uint32_t sflag[MAX_CELLS_LOCAL];
+    __shared__ uint32_t sflag[2][FLAGS ? FastCells<TH>::N : 1];  // per-tile cell flags, by tile parity
+    __shared__ FlagTile finfo[2];
 
     const int tid = threadIdx.x;
     const bool cells = FLAGS && t_hi != t_lo;
@@ -180,9 +196,21 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         fence_barrier_init();
+        finfo[0].n = finfo[1].n = 0;
     }
-    for (int i = tid; i < MAX_CELLS_LOCAL; i += blockDim.x) sflag[i] = 0u;
+    for (int i = tid; i < (FLAGS ? 2 * FastCells<TH>::N : 2); i += blockDim.x) (&sflag[0][0])[i] = 0u;
     __syncthreads();
+    // The flagged cells of a finished tile (table b) go to the global flags; the table is cleared.
+    auto flush_flags = [&](int b) {
+        const FlagTile f = finfo[b];
+        for (int i = tid; i < f.n; i += blockDim.x) {
+            if (sflag[b][i]) {
+                const int cx = f.cx0 + i % f.lcw, cy = f.cy0 + i / f.lcw;
+                if (cx < f.ncx && cy < f.ncy) atomicOr(&f.cell[cy * f.ncx + cx], 1u);
+                sflag[b][i] = 0u;
+            }
+        }
+    };
     auto issue = [&](int t, int b) {
         const TileInfo ti = tile_info(imgs, list, prefix, n_list, t, border, TH);
         tinfo[b] = ti;
@@ -197,7 +225,8 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     if (tid == 0 && tile_of(order, blockIdx.x, g, n_tiles, 0) < n_tiles) issue(tile_of(order, blockIdx.x, g, n_tiles, 0), 0);
 
     const int lane = tid & 31, ty = tid >> 5;
-    for (int it = 0;; ++it) {
+    int it = 0;
+    for (;; ++it) {
         const int t = tile_of(order, blockIdx.x, g, n_tiles, it);
         if (t >= n_tiles) break;
         const int tn = tile_of(order, blockIdx.x, g, n_tiles, it + 1);
@@ -216,6 +245,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             }
             return;
         }
+        if (cells && it > 0) flush_flags(b ^ 1);  // the previous tile's table (its writers passed the barrier)
         const TileInfo ti = tinfo[b];
         const Img& I = imgs[ti.img];
         const uint8_t* s = sbuf + b * BUF;
@@ -233,6 +263,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                 pm_any |= *reinterpret_cast<const uint32_t*>(I.pmask + (size_t)(tyt + k) * 4 * I.tiles_x + 4 * tx);
         }
         if (pm_any == 0u) {
+            if (tid == 0) finfo[b].n = 0;
             __syncthreads();
             continue;
         }
@@ -242,6 +273,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int cy0 = (Y0 - border) / cell;
         const int lcw = TILE_W / cell + 2;
         const int x = X0 + 4 * lane;
+        if (tid == 0) finfo[b] = FlagTile{I.cell, I.ncx, I.ncy, cx0, cy0, lcw, cells ? lcw * (TH / cell + 2) : 0};
 
         // Six pair words per staged row: rows y-3 .. y+RPT+2 (staged row 0 is
         // Y0-4), each loaded just before the first output row that needs it.
@@ -269,14 +301,25 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         // The score map's address, read once (the stores below could alias the image's fields).
         uint8_t* const sdst = I.score + x;
         const size_t spitch = (size_t)I.spitch;
-        // Cells of this thread's 4 x RPT pixels (cell >= 8 > RPT, 4): at most
-        // two cell columns (the bytes in mask_a lie in the first) and two cell
-        // rows (the second from row y_next on); no division per pixel.
-        const int ca = (max(x, rx0) - rx0) / cell;
-        const uint32_t mask_a = range_mask4(x, 0, rx0 + (ca + 1) * cell);
-        const int cr = (Y0 + ty * RPT - border) / cell;
-        const int y_next = border + (cr + 1) * cell;
-        const int fbase = (cr - cy0) * lcw + (ca - cx0);
+        // Cell flags: running maxima of the biased offset scores over the
+        // current cell row, per pixel pair (two lanes each); the cell row
+        // changes at rows y_next, y_next + cell, ...  The cells of a flush are
+        // worked out there (the thread's 4 pixels lie in at most two cell
+        // columns, the bytes in mask_a in the first), so that nothing but the
+        // maxima and y_next stays live across the rows.
+        int y_next = border + ((Y0 + ty * RPT - border) / cell + 1) * cell;
+        uint32_t mx0 = 0u, mx1 = 0u;
+        auto flag_cells = [&](int yc) {  // yc: a row of the cell row being flushed
+            const uint32_t strong = __byte_perm(lanes_ge(mx0, th), lanes_ge(mx1, th), 0x6420) & colmask;
+            if (strong) {
+                const int ca = (int)__umulhi((uint32_t)(max(x, rx0) - rx0), cell_magic);
+                const uint32_t mask_a = range_mask4(x, 0, rx0 + (ca + 1) * cell);
+                uint32_t* const f =
+                    &sflag[b][((int)__umulhi((uint32_t)(yc - border), cell_magic) - cy0) * lcw + (ca - cx0)];
+                if (strong & mask_a) atomicOr(f, 1u);
+                if (strong & ~mask_a) atomicOr(f + 1, 1u);
+            }
+        };
 
         if (nrows > 0) {
 #pragma unroll
@@ -286,36 +329,27 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                 if (r >= nrows) break;
                 const int y = Y0 + ty * RPT + r;
                 if (r > 0) load_row(r + 6);
+                if (cells && y == y_next) {  // warp-uniform
+                    flag_cells(y - 1);
+                    mx0 = mx1 = 0u;
+                    y_next += cell;
+                }
                 // Pixel pairs (x, x+1) and (x+2, x+3), one after the other.
                 const uint32_t s0 = ring_pair_score<0>(hw + r, kb);  // 512 + offset score per lane
                 const uint32_t s1 = ring_pair_score<1>(hw + r, kb);
                 const uint32_t m = colmask;  // y < ry1 here
                 const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
                 if (m != 0u) *reinterpret_cast<uint32_t*>(sdst + (size_t)y * spitch) = sc;
-                if (cells && sc) {
-                    const uint32_t strong =
-                        __byte_perm(lanes_ge(s0, th), lanes_ge(s1, th), 0x6420) & m;
-                    if (strong) {
-                        const int f = fbase + (y >= y_next ? lcw : 0);
-                        if (strong & mask_a) atomicOr(&sflag[f], 1u);
-                        if (strong & ~mask_a) atomicOr(&sflag[f + 1], 1u);
-                    }
+                if (FLAGS) {
+                    mx0 = __vimax3_u16x2(mx0, s0, s0);
+                    mx1 = __vimax3_u16x2(mx1, s1, s1);
                 }
             }
+            if (cells) flag_cells(y_next - 1);
         }
-        if (cells) {
-            __syncthreads();
-            const int lch = TH / cell + 2;
-            for (int i = tid; i < lcw * lch; i += blockDim.x) {
-                if (sflag[i]) {
-                    const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
-                    if (cx < I.ncx && cy < I.ncy) atomicOr(&I.cell[cy * I.ncx + cx], 1u);
-                    sflag[i] = 0u;
-                }
-            }
-        }
-        __syncthreads();  // buffer b is free for the tile after next
+        __syncthreads();  // buffer b is free for the tile after next; the flag table is complete
     }
+    if (cells && it > 0) flush_flags((it - 1) & 1);  // the last tile's table
 }
 
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
@@ -324,55 +358,47 @@ void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_p
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
     const cudaStream_t st = (cudaStream_t)stream;
-    if (flags)
-        k_fast<true, 32><<<grid, DET_THREADS, 0, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps, call, t_hi,
-                                                        t_lo, border, cell, order);
-    else if (tile_h == 64)
-        k_fast<false, 64><<<grid, DET_THREADS, 0, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps, call,
-                                                         t_hi, t_lo, border, cell, order);
-    else if (tile_h == 128)
-        k_fast<false, 128><<<grid, DET_THREADS, fast_dyn_bytes(128), st>>>(imgs, img_list, tile_prefix, n_list,
-                                                                           n_tiles, maps, call, t_hi, t_lo, border,
-                                                                           cell, order);
-    else if (tile_h == 256)
-        k_fast<false, 256><<<grid, DET_THREADS, fast_dyn_bytes(256), st>>>(imgs, img_list, tile_prefix, n_list,
-                                                                           n_tiles, maps, call, t_hi, t_lo, border,
-                                                                           cell, order);
-    else
-        k_fast<false, 32><<<grid, DET_THREADS, 0, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps, call,
-                                                         t_hi, t_lo, border, cell, order);
+    const uint32_t magic = 0xFFFFFFFFu / (uint32_t)cell + 1u;
+#define OF_FAST_LAUNCH(FL, TH, DYN)                                                                            \
+    k_fast<FL, TH><<<grid, DET_THREADS, DYN, st>>>(imgs, img_list, tile_prefix, n_list, n_tiles, maps, call, t_hi, \
+                                                   t_lo, border, cell, magic, order)
+    if (flags) {
+        if (tile_h == 64) OF_FAST_LAUNCH(true, 64, 0);
+        else if (tile_h == 128) OF_FAST_LAUNCH(true, 128, fast_dyn_bytes(128));
+        else if (tile_h == 256) OF_FAST_LAUNCH(true, 256, fast_dyn_bytes(256));
+        else OF_FAST_LAUNCH(true, 32, 0);
+    } else {
+        if (tile_h == 64) OF_FAST_LAUNCH(false, 64, 0);
+        else if (tile_h == 128) OF_FAST_LAUNCH(false, 128, fast_dyn_bytes(128));
+        else if (tile_h == 256) OF_FAST_LAUNCH(false, 256, fast_dyn_bytes(256));
+        else OF_FAST_LAUNCH(false, 32, 0);
+    }
+#undef OF_FAST_LAUNCH
 }
 
-int fast_blocks_per_sm() {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<true, 32>, DET_THREADS, 0) != cudaSuccess || n < 1)
-        n = 1;
-    return n;
-}
+int fast_blocks_per_sm() { return fast_blocks_per_sm(32, true); }
 
-template <int TH>
-static cudaError_t tall_fast_occupancy(int* n) {
-    cudaError_t e = cudaFuncSetAttribute(k_fast<false, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         fast_dyn_bytes(TH));
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_fast<false, TH>, DET_THREADS, fast_dyn_bytes(TH));
+template <bool FL, int TH>
+static cudaError_t fast_occupancy(int* n) {
+    const int dyn = TH > 64 ? fast_dyn_bytes(TH) : 0;
+    cudaError_t e = cudaSuccess;
+    if (dyn) e = cudaFuncSetAttribute(k_fast<FL, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_fast<FL, TH>, DET_THREADS, dyn);
     return e;
 }
 
-// Resident blocks per SM of the flag-free kernel with tile_h-row tiles (for
-// 128 and 256 rows it also raises the kernel's dynamic shared-memory limit,
-// before any launch or capture uses it).
-int fast_blocks_per_sm(int tile_h) {
+// Resident blocks per SM of the general kernel with tile_h-row tiles, with or
+// without the cell flags (for 128 and 256 rows it also raises the kernel's
+// dynamic shared-memory limit, before any launch or capture uses it).
+int fast_blocks_per_sm(int tile_h, bool flags) {
     int n = 0;
     cudaError_t e;
-    if (tile_h == 128) {
-        e = tall_fast_occupancy<128>(&n);
-    } else if (tile_h == 256) {
-        e = tall_fast_occupancy<256>(&n);
-    } else {
-        e = tile_h == 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<false, 64>, DET_THREADS, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast<false, 32>, DET_THREADS, 0);
-    }
+    if (flags)
+        e = tile_h == 64 ? fast_occupancy<true, 64>(&n) : tile_h == 128 ? fast_occupancy<true, 128>(&n)
+          : tile_h == 256 ? fast_occupancy<true, 256>(&n) : fast_occupancy<true, 32>(&n);
+    else
+        e = tile_h == 64 ? fast_occupancy<false, 64>(&n) : tile_h == 128 ? fast_occupancy<false, 128>(&n)
+          : tile_h == 256 ? fast_occupancy<false, 256>(&n) : fast_occupancy<false, 32>(&n);
     return (e != cudaSuccess || n < 1) ? 1 : n;
 }
 

@@ -230,8 +230,8 @@ struct Plan {
     std::vector<Group> groups[kMaxGroups + 1];
     std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_ftall[2], gp_fal;
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
+    bool apply_flags = false;    // the threshold pass sets the cell flags (else the general FAST kernel does)
     bool aligned_ok = false;     // ... and the cell-aligned general FAST kernel (cells of 15 or 30 pixels)
-    bool apply_flags = false;    // the threshold pass sets the cell flags (the general FAST kernel does not)
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
     std::vector<int> rt_bps;        // TMA resize resident blocks per SM of level l
     int det_tiles = 0, max_quota = 0, total_slots = 0, n_img = 0;
@@ -279,7 +279,7 @@ struct Plan {
 int plan_fast_bps(const Plan* P) {
     if (P->aligned_ok && P->tun.fast_cell_tiles == 2) return fast_aligned_blocks_per_sm();
     if (P->cell_tiles && P->tun.fast_cell_tiles) return fast_cells_blocks_per_sm(P->s.cell);
-    return P->apply_flags ? fast_blocks_per_sm(P->tun.fast_tile_h) : fast_blocks_per_sm();
+    return fast_blocks_per_sm(P->tun.fast_tile_h, !P->apply_flags);
 }
 
 void free_plan(Plan* p) {
@@ -370,15 +370,15 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                 launch_fast_cells(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfp() + G.fp_off, G.n_list, G.fast_tiles,
                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                                   H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
-            else if (P->apply_flags && P->tun.fast_tile_h == 64)
+            else if (P->tun.fast_tile_h == 64)
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list, G.nms64_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, false, 64);
-            else if (P->apply_flags && (P->tun.fast_tile_h == FT_HS[0] || P->tun.fast_tile_h == FT_HS[1])) {
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, !P->apply_flags, 64);
+            else if (P->tun.fast_tile_h == FT_HS[0] || P->tun.fast_tile_h == FT_HS[1]) {
                 const int i = P->tun.fast_tile_h == FT_HS[0] ? 0 : 1;
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gft(i) + G.ftall_off[i], G.n_list,
                             G.ftall_tiles[i], P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, false, FT_HS[i]);
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, !P->apply_flags, FT_HS[i]);
             }
             else
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
@@ -497,7 +497,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     // Cell tiles: FAST applies the per-cell threshold itself (cells of 8..30 pixels).
     P->cell_tiles = s.cell >= CT_MIN_CELL && s.cell <= CT_MAX_CELL;
     P->aligned_ok = P->cell_tiles && fast_aligned_ok(s.cell);
-    // The threshold pass flags the cells itself when a band's cells fit its shared array.
+    // The threshold pass flags the cells itself when a band's cells fit its
+    // shared array; otherwise the general FAST kernel sets them.
     P->apply_flags = true;
     for (const auto& L : P->lay.img)
         if (L.ncx > CA_MAX_CELLS) P->apply_flags = false;
@@ -724,7 +725,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
     P->tun.nms_tile_h = 64;
     P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64);  // also raises its shared-memory limit before any capture
-    for (int i = 0; i < 2; ++i) fast_blocks_per_sm(FT_HS[i]);  // raise the tall kernels' limits before any capture
+    for (int i = 0; i < 2; ++i)  // raise the tall kernels' limits before any capture
+        for (int fl = 0; fl < 2; ++fl) fast_blocks_per_sm(FT_HS[i], fl != 0);
     nms_blocks_per_sm(FT_HS[0]);
     fast_aligned_blocks_per_sm();  // raises the cell-aligned kernel's shared-memory limit
     P->tun.fast_order = 0;
@@ -1062,7 +1064,7 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     // sets the flags), cell tiles (1), cell-aligned general kernel (2).
     for (int cand = 0; cand < 6 && rc == OF_OK; ++cand) {
         const int v = cand < 4 ? 0 : cand - 3, th = cand < 4 ? 32 << cand : 32;
-        if ((v == 1 && !P->cell_tiles) || (v == 2 && !P->aligned_ok) || (th > 32 && !P->apply_flags)) continue;
+        if ((v == 1 && !P->cell_tiles) || (v == 2 && !P->aligned_ok)) continue;
         P->tun.fast_cell_tiles = v;
         P->tun.fast_tile_h = th;
         for (int bp = 1; bp <= plan_fast_bps(P) && rc == OF_OK; ++bp) {
@@ -1342,7 +1344,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     P->tun.resize_tma = t->resize_tma;
     // Forms the cell size does not allow fall back: aligned -> cell tiles -> general.
     P->tun.fast_cell_tiles = !P->cell_tiles ? 0 : (t->fast_cell_tiles == 2 && !P->aligned_ok) ? 1 : t->fast_cell_tiles;
-    P->tun.fast_tile_h = P->apply_flags ? t->fast_tile_h : 32;
+    P->tun.fast_tile_h = t->fast_tile_h;
     P->tun.fast_blocks_per_sm = std::min(t->fast_blocks_per_sm, plan_fast_bps(P));
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
     P->tun.nms_tile_h = t->nms_tile_h;

@@ -130,6 +130,8 @@ void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, i
 void launch_resize_tma(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
                        const CUtensorMap* maps, const Call* call, int buf_bytes, int grid, void* stream);
 int resize_tma_blocks_per_sm(int buf_bytes);  // also raises the kernel's shared-memory limit
+// General FAST on 128 x tile_h tiles (32, 64, 128 or 256 rows); flags: also
+// set the cell flags (else the threshold pass sets them).
 void launch_fast(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                  int n_list, int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi,
                  int t_lo, int border, int cell, int grid, int order, void* stream, bool flags = true,
@@ -145,7 +147,9 @@ void launch_fast_aligned(const Img* imgs, const int32_t* img_list, const int32_t
                          int n_tiles, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
                          int cell, int grid, int order, void* stream);
 int fast_aligned_blocks_per_sm();
-int fast_blocks_per_sm(int tile_h);  // the flag-free general kernel
+int fast_blocks_per_sm(int tile_h, bool flags);  // the general kernel
+// Threshold pass: applies the cell flags; flags: first sets them (when the
+// general FAST kernel did not).
 void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
                        int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags);
 constexpr int CA_MAX_CELLS = 1024;  // cells per band row the threshold pass can flag itself
