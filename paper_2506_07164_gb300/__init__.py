@@ -56,7 +56,8 @@ class OfTuning(C.Structure):
     resize_tile_h (32/64) and resize_tma (0/1): pyramid kernel; fast_blocks_per_sm,
     nms_blocks_per_sm, fast_order, nms_order: persistent grids and tile order;
     stream_groups (1..8): frame groups on forked graph branches; fast_cell_tiles:
-    0 general FAST + threshold pass, 1 cell-tile kernel, 2 cell-aligned general kernel;
+    0 general FAST + threshold pass, 1 cell-tile kernel, 2 cell-aligned general kernel,
+    3 general FAST with per-warp pipelines + threshold pass;
     fast_tile_h (32/64/128/256) and nms_tile_h (32/64/128): tile heights.  The last
     four fields report the autotuner's search (candidates, best stage times in ms)."""
 

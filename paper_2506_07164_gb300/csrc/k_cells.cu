@@ -30,21 +30,6 @@ namespace ofk {
 constexpr int CA_THREADS = 256;
 constexpr int CA_SEG = 256;  // 16-byte chunks per column-mask segment (4096 columns)
 
-// 0xFF in each byte of v that is >= t, for 1 <= t <= 128: (b | 0x80) - t has
-// no borrow out of its byte and bit 7 set exactly when the low seven bits are
-// >= t; a byte with bit 7 set is >= 128 >= t itself.
-__device__ __forceinline__ uint32_t bytes_ge(uint32_t v, uint32_t t) {
-    const uint32_t g = (((v | 0x80808080u) - t * 0x01010101u) | v) & 0x80808080u;
-    return (g >> 7) * 0xFFu;
-}
-
-// The same for any t <= 255, in 16-bit lanes.
-__device__ __forceinline__ uint32_t bytes_ge_any(uint32_t v, uint32_t t) {
-    const uint32_t tt = (0x8000u - t) * 0x00010001u;
-    const uint32_t lo = __byte_perm(v, 0u, 0x4140) + tt, hi = __byte_perm(v, 0u, 0x4342) + tt;
-    return __byte_perm((lo >> 15 & 0x00010001u) * 0xFFu, (hi >> 15 & 0x00010001u) * 0xFFu, 0x6420);
-}
-
 // Bit 7 of each byte of the result is set when that byte of v is >= t
 // (1 <= t <= 128; the other bits are garbage): ORed over many words, then
 // masked with 0x80808080 once.
@@ -56,7 +41,7 @@ __device__ __forceinline__ uint32_t apply_word(uint32_t v, uint32_t fm, uint32_t
     return v & ((SMALL_T ? bytes_ge(v, t) : bytes_ge_any(v, t)) | ~fm);
 }
 
-template <bool FLAGS, bool SMALL_T>
+template <bool FLAGS, bool APPLY, bool SMALL_T>
 __global__ void __launch_bounds__(CA_THREADS)
 k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ band_prefix,
              int n_list, int n_bands, int t_hi, int t_lo, int border, int cell) {
@@ -139,6 +124,7 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
             for (int i = tid; i < ncx; i += CA_THREADS) crow[i] = bflag[i];
             fl = bflag;
         }
+        if (!APPLY) continue;  // flags only: NMS applies them on its staged tiles
         for (int s0 = 0; s0 < n_chunks; s0 += CA_SEG) {
             const int s1 = min(s0 + CA_SEG, n_chunks);
             __syncthreads();  // earlier readers of colmask are done
@@ -204,19 +190,23 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
 }
 
 void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
-                       int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags) {
+                       int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags, bool apply) {
     if (n_bands <= 0) return;
     grid = grid < n_bands ? grid : n_bands;
     const cudaStream_t st = (cudaStream_t)stream;
     const bool small_t = t_hi - t_lo + 1 <= 128;
-#define OF_CA_LAUNCH(FL, SM) \
-    k_cell_apply<FL, SM><<<grid, CA_THREADS, 0, st>>>(imgs, img_list, band_prefix, n_list, n_bands, t_hi, t_lo, border, cell)
-    if (flags) {
-        if (small_t) OF_CA_LAUNCH(true, true);
-        else OF_CA_LAUNCH(true, false);
+#define OF_CA_LAUNCH(FL, AP, SM)                                                                              \
+    k_cell_apply<FL, AP, SM><<<grid, CA_THREADS, 0, st>>>(imgs, img_list, band_prefix, n_list, n_bands, t_hi, t_lo, \
+                                                          border, cell)
+    if (flags && !apply) {
+        if (small_t) OF_CA_LAUNCH(true, false, true);
+        else OF_CA_LAUNCH(true, false, false);
+    } else if (flags) {
+        if (small_t) OF_CA_LAUNCH(true, true, true);
+        else OF_CA_LAUNCH(true, true, false);
     } else {
-        if (small_t) OF_CA_LAUNCH(false, true);
-        else OF_CA_LAUNCH(false, false);
+        if (small_t) OF_CA_LAUNCH(false, true, true);
+        else OF_CA_LAUNCH(false, true, false);
     }
 #undef OF_CA_LAUNCH
 }

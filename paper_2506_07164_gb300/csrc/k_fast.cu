@@ -119,6 +119,39 @@ __device__ __forceinline__ uint32_t ring_pair_raw(const uint32_t (*hw)[6]) {
     return ring_pair_score<E>(hw, PAIR_BIAS) - PAIR_BIAS;
 }
 
+// Interleaved pixel pairs (general kernel): a thread's pixels x..x+3 as the
+// pairs (x, x+2) and (x+1, x+3).  Then every ring pixel of either pair, at
+// any column offset, is one word of its staged row: e[o + 3] = (c_o, c_{o+2})
+// for o = -3..4, c_j the byte at column x + j -- ten instructions per staged
+// row (six byte picks and four cross-word joins) and none per output row.
+__device__ __forceinline__ void staged_row_words(const uint8_t* row, uint32_t (&e)[8]) {
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(row - 4);
+    const uint32_t w1 = *reinterpret_cast<const uint32_t*>(row);
+    const uint32_t w2 = *reinterpret_cast<const uint32_t*>(row + 4);
+    const uint32_t w0e = __byte_perm(w0, 0u, 0x4240), w0o = __byte_perm(w0, 0u, 0x4341);  // (c-4, c-2), (c-3, c-1)
+    const uint32_t w1e = __byte_perm(w1, 0u, 0x4240), w1o = __byte_perm(w1, 0u, 0x4341);  // (c0, c2), (c1, c3)
+    const uint32_t w2e = __byte_perm(w2, 0u, 0x4240), w2o = __byte_perm(w2, 0u, 0x4341);  // (c4, c6), (c5, c7)
+    e[0] = w0o;
+    e[1] = __byte_perm(w0e, w1e, 0x5432);  // (c-2, c0): high lane of one, low lane of the next
+    e[2] = __byte_perm(w0o, w1o, 0x5432);  // (c-1, c1)
+    e[3] = w1e;
+    e[4] = w1o;
+    e[5] = __byte_perm(w1e, w2e, 0x5432);  // (c2, c4)
+    e[6] = __byte_perm(w1o, w2o, 0x5432);  // (c3, c5)
+    e[7] = w2e;
+}
+
+// Biased offset score (pair_score) of interleaved pair C (0: pixels x, x+2;
+// 1: x+1, x+3) of an output row from the words of staged rows y-3 .. y+3.
+template <int C>
+__device__ __forceinline__ uint32_t ring_ipair_score(const uint32_t (*e)[8], uint32_t kb) {
+    uint32_t q[16];
+#define OF_LOAD_IRING(i, dx, dy) q[i] = e[3 + (dy)][(dx) + C + 3];
+    OF_RING(OF_LOAD_IRING)
+#undef OF_LOAD_IRING
+    return pair_score(q, e[3][C + 3], kb);
+}
+
 // Store the bytes of v selected by mask (0xFF per byte) at d: one word store
 // when all four are selected, else byte stores (the other bytes may belong
 // to a tile another block writes at the same time).
@@ -275,20 +308,12 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int x = X0 + 4 * lane;
         if (tid == 0) finfo[b] = FlagTile{I.cell, I.ncx, I.ncy, cx0, cy0, lcw, cells ? lcw * (TH / cell + 2) : 0};
 
-        // Six pair words per staged row: rows y-3 .. y+RPT+2 (staged row 0 is
-        // Y0-4), each loaded just before the first output row that needs it.
-        uint32_t hw[RPT + 6][6];
+        // Eight interleaved pair words per staged row: rows y-3 .. y+RPT+2
+        // (staged row 0 is Y0-4), each built just before the first output row
+        // that needs it.
+        uint32_t hw[RPT + 6][8];
         auto load_row = [&](int k) {
-            const uint8_t* row = s + (ty * RPT + k + 1) * SROW + HALO_X + 4 * lane;
-            const uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
-            const uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
-            const uint32_t wp = *reinterpret_cast<const uint32_t*>(row + 4);
-            hw[k][0] = __byte_perm(wm, 0u, 0x4140);
-            hw[k][1] = __byte_perm(wm, 0u, 0x4342);
-            hw[k][2] = __byte_perm(wc, 0u, 0x4140);
-            hw[k][3] = __byte_perm(wc, 0u, 0x4342);
-            hw[k][4] = __byte_perm(wp, 0u, 0x4140);
-            hw[k][5] = __byte_perm(wp, 0u, 0x4342);
+            staged_row_words(s + (ty * RPT + k + 1) * SROW + HALO_X + 4 * lane, hw[k]);
         };
         // Rows of this warp inside the detect region (warp-uniform): a warp
         // below the region's last row (the last tile row of a level) goes
@@ -310,7 +335,7 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         int y_next = border + ((Y0 + ty * RPT - border) / cell + 1) * cell;
         uint32_t mx0 = 0u, mx1 = 0u;
         auto flag_cells = [&](int yc) {  // yc: a row of the cell row being flushed
-            const uint32_t strong = __byte_perm(lanes_ge(mx0, th), lanes_ge(mx1, th), 0x6420) & colmask;
+            const uint32_t strong = __byte_perm(lanes_ge(mx0, th), lanes_ge(mx1, th), 0x6240) & colmask;
             if (strong) {
                 const int ca = (int)__umulhi((uint32_t)(max(x, rx0) - rx0), cell_magic);
                 const uint32_t mask_a = range_mask4(x, 0, rx0 + (ca + 1) * cell);
@@ -334,11 +359,11 @@ k_fast(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                     mx0 = mx1 = 0u;
                     y_next += cell;
                 }
-                // Pixel pairs (x, x+1) and (x+2, x+3), one after the other.
-                const uint32_t s0 = ring_pair_score<0>(hw + r, kb);  // 512 + offset score per lane
-                const uint32_t s1 = ring_pair_score<1>(hw + r, kb);
+                // Pixel pairs (x, x+2) and (x+1, x+3), one after the other.
+                const uint32_t s0 = ring_ipair_score<0>(hw + r, kb);  // 512 + offset score per lane
+                const uint32_t s1 = ring_ipair_score<1>(hw + r, kb);
                 const uint32_t m = colmask;  // y < ry1 here
-                const uint32_t sc = __byte_perm(s0, s1, 0x6420) & m;
+                const uint32_t sc = __byte_perm(s0, s1, 0x6240) & m;
                 if (m != 0u) *reinterpret_cast<uint32_t*>(sdst + (size_t)y * spitch) = sc;
                 if (FLAGS) {
                     mx0 = __vimax3_u16x2(mx0, s0, s0);
@@ -400,6 +425,130 @@ int fast_blocks_per_sm(int tile_h, bool flags) {
         e = tile_h == 64 ? fast_occupancy<false, 64>(&n) : tile_h == 128 ? fast_occupancy<false, 128>(&n)
           : tile_h == 256 ? fast_occupancy<false, 256>(&n) : fast_occupancy<false, 32>(&n);
     return (e != cudaSuccess || n < 1) ? 1 : n;
+}
+
+// ---------------------------------------------------------------------------
+// General FAST with per-warp pipelines: no block barriers.
+//
+// Each warp is its own persistent worker over the 128 x 32 detect tiles of
+// the launch.  Lane 0 fetches the warp's next tile -- one 160 x 40 TMA box,
+// rows Y0-4 .. Y0+35, the box the 32-row block kernel uses -- into the warp's
+// other shared-memory buffer while the lanes score the current one;
+// completion on the warp's own mbarrier, so a warp never waits for another
+// warp's tile.  A lane scores 4 pixels (two interleaved pairs) of every row,
+// as two unrolled halves of 16 rows (the staged-row window is rebuilt at the
+// start of each half).  The score map is as the general kernel's; the cell
+// flags are left to the threshold pass.
+
+constexpr int FW_WARPS = DET_THREADS / 32;
+constexpr int FW_DYN = FW_WARPS * 2 * FAST_BUF + 128;  // two buffers per warp + alignment slack
+
+__global__ void __launch_bounds__(DET_THREADS, 2)
+k_fast_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ prefix,
+            int n_list, int n_tiles, const CUtensorMap* __restrict__ maps, const Call* __restrict__ call, int t_lo,
+            int border, int order) {
+    extern __shared__ __align__(128) uint8_t fw_dyn[];
+    uint8_t* const base = fw_dyn + ((128u - (smem_u32(fw_dyn) & 127u)) & 127u);
+    __shared__ __align__(8) uint64_t mbar[FW_WARPS][2];
+    __shared__ TileInfo tinfo[FW_WARPS][2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint8_t* const wbuf = base + w * 2 * FAST_BUF;
+    if (lane == 0) {
+        mbar_init(&mbar[w][0], 1);
+        mbar_init(&mbar[w][1], 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    const int nw = gridDim.x * FW_WARPS, gw = blockIdx.x * FW_WARPS + w;
+    auto issue = [&](int t, int b) {  // lane 0
+        const TileInfo ti = tile_info(imgs, list, prefix, n_list, t, border, TILE_H);
+        tinfo[w][b] = ti;
+        tensormap_acquire(maps + ti.img);
+        mbar_arrive_expect_tx(&mbar[w][b], FAST_BOX);
+        tma_load_2d(wbuf + b * FAST_BUF, maps + ti.img, ti.x0 - HALO_X, ti.y0 - 4, &mbar[w][b]);
+    };
+    if (lane == 0 && tile_of(order, gw, nw, n_tiles, 0) < n_tiles) issue(tile_of(order, gw, nw, n_tiles, 0), 0);
+    const uint32_t kb = PAIR_BIAS - (uint32_t)(t_lo - 1) * 0x00010001u;
+    for (int it = 0;; ++it) {
+        const int t = tile_of(order, gw, nw, n_tiles, it);
+        if (t >= n_tiles) break;
+        const int tn = tile_of(order, gw, nw, n_tiles, it + 1);
+        const int b = it & 1;
+        if (lane == 0 && tn < n_tiles) {
+            fence_proxy_async_smem();
+            issue(tn, b ^ 1);
+        }
+        const bool ok = mbar_wait(&mbar[w][b], (it >> 1) & 1);
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            if (lane == 0) {
+                atomicOr(call->status, OF_DEV_TIMEOUT);
+                // Let this warp's copies in flight land before the block's shared memory can go away.
+                mbar_wait(&mbar[w][b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (tn < n_tiles) mbar_wait(&mbar[w][b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+            }
+            __syncwarp();
+            return;
+        }
+        const TileInfo ti = tinfo[w][b];
+        const Img& I = imgs[ti.img];
+        const uint8_t* const s = wbuf + b * FAST_BUF;
+        const int X0 = ti.x0, Y0 = ti.y0;
+        // Learned path: the tile's 4 proposal tiles; skip the tile when all are off.
+        uint32_t lane_on = 0xFFFFFFFFu;
+        if (I.pmask) {
+            const int tx = (X0 - I.tile_x0) / TILE_W, band = (Y0 - border) / TILE_H;
+            const uint32_t pm =
+                band < I.tiles_y ? *reinterpret_cast<const uint32_t*>(I.pmask + (size_t)band * 4 * I.tiles_x + 4 * tx)
+                                 : 0u;
+            lane_on = ((pm >> (8 * (lane >> 3))) & 0xFFu) ? 0xFFFFFFFFu : 0u;
+            if (pm == 0u) {
+                __syncwarp();
+                continue;
+            }
+        }
+        const int x = X0 + 4 * lane;
+        const int nrows = min(TILE_H, I.h - border - Y0);
+        const uint32_t colmask = range_mask4(x, border, I.w - border) & lane_on;
+        uint8_t* const sdst = I.score + x;
+        const size_t spitch = (size_t)I.spitch;
+#pragma unroll 1
+        for (int r0 = 0; r0 < nrows; r0 += 16) {
+            uint32_t hw[16 + 6][8];
+            const uint8_t* const srow = s + (r0 + 1) * SROW + HALO_X + 4 * lane;  // staged row of output row r0 - 3
+#pragma unroll
+            for (int k = 0; k < 7; ++k) staged_row_words(srow + k * SROW, hw[k]);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                if (r0 + r >= nrows) break;
+                if (r > 0) staged_row_words(srow + (r + 6) * SROW, hw[r + 6]);
+                const uint32_t s0 = ring_ipair_score<0>(hw + r, kb);  // 512 + offset score per lane
+                const uint32_t s1 = ring_ipair_score<1>(hw + r, kb);
+                if (colmask != 0u)
+                    *reinterpret_cast<uint32_t*>(sdst + (size_t)(Y0 + r0 + r) * spitch) =
+                        __byte_perm(s0, s1, 0x6240) & colmask;
+            }
+        }
+        __syncwarp();  // every lane is done with buffer b before lane 0 refills it
+    }
+}
+
+void launch_fast_warp(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list, int n_tiles,
+                      const CUtensorMap* maps, const Call* call, int t_lo, int border, int grid, int order,
+                      void* stream) {
+    if (n_tiles <= 0) return;
+    const int warps = (n_tiles + FW_WARPS - 1) / FW_WARPS;
+    grid = grid < warps ? grid : warps;
+    k_fast_warp<<<grid, DET_THREADS, FW_DYN, (cudaStream_t)stream>>>(imgs, img_list, tile_prefix, n_list, n_tiles,
+                                                                     maps, call, t_lo, border, order);
+}
+
+// Resident blocks per SM (also raises the kernel's dynamic shared-memory limit).
+int fast_warp_blocks_per_sm() {
+    int n = 0;
+    if (cudaFuncSetAttribute(k_fast_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_DYN) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_warp, DET_THREADS, FW_DYN) != cudaSuccess || n < 1)
+        n = 1;
+    return n;
 }
 
 // ---------------------------------------------------------------------------

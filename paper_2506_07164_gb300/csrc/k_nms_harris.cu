@@ -9,11 +9,13 @@
 // buffer pair while the block works on the current one: the score rows
 // (160 x 34 boxes at a 32-row step, +1 row/col halo) and the image rows
 // (160 x 40 boxes, +4 halo), stacked.
-// 1. (32-row general variant only: the final-score variants get maps that
-//    already hold S(p) and mask the detect region in registers.)  S(p) in
-//    place: s(p) when p is a candidate at its cell's threshold, else 0; 0
-//    outside the detect region.  Each thread keeps one staged word column,
-//    whose in-region bytes lie in at most two cells.
+// 1. (APPLY variant: the maps hold s(p) where s(p) >= t_lo and the cell
+//    flags are set; the final-score variants get maps that already hold S(p)
+//    and mask the detect region in registers.)  S(p) in place on the staged
+//    score rows: s(p) when p is a candidate at its cell's threshold, else 0;
+//    0 outside the detect region and outside proposed tiles.  Each thread
+//    keeps one staged word column, whose in-region bytes lie in at most two
+//    cells, and a run of rows (one flag lookup per cell row it enters).
 // 2. NMS, two pixels per register in 16-bit lanes: p survives when S(p) > the
 //    three-input maximum of its 8 neighbours.  Survivors go to a queue (one
 //    shared atomic per warp).
@@ -41,14 +43,6 @@ constexpr int I_BOX = IMG_BOX_ROWS * SROW;       // 6400
 constexpr int S_W0 = HALO_X / 4 - 1;             // first staged word the 3x3 test reads (X0-4)
 constexpr int S_WORDS = TILE_W / 4 + 2;          // words X0-4 .. X0+TILE_W+3
 constexpr int S_GROUPS = DET_THREADS / S_WORDS;  // row groups of the S(p) pass
-
-// 0xFF in each byte of v that is below t (t <= 255).
-__device__ __forceinline__ uint32_t bytes_lt(uint32_t v, uint32_t t) {
-    const uint32_t tt = (0x8000u - t) * 0x00010001u;
-    const uint32_t lo = __byte_perm(v, 0u, 0x4140) + tt, hi = __byte_perm(v, 0u, 0x4342) + tt;
-    // bit 15 of a lane set <=> byte >= t
-    return ~__byte_perm((lo >> 15 & 0x00010001u) * 0xFFu, (hi >> 15 & 0x00010001u) * 0xFFu, 0x6420);
-}
 
 // Unsigned bytes of a times signed bytes of b, summed, plus c.
 __device__ __forceinline__ int dp4a_us(uint32_t a, uint32_t b, int c) {
@@ -124,20 +118,21 @@ struct NmsGeom {
     static_assert((S_STEP * SROW) % 128 == 0 && I_BOX % 128 == 0, "TMA destinations on 128-byte boundaries");
 };
 
-// FINAL: the score maps already hold S(p) inside the detect region (the
-// cell-tile FAST kernel applied the cell thresholds); the kernel then skips the
-// cell bookkeeping and the candidate pass and masks the region in registers.
-// TH: tile rows (32; or 64 or 128 with FINAL -- fewer barriers per pixel and
-// more survivors per Harris phase).  Buffers live in dynamic shared memory
-// (NmsGeom<TH>::DYN_BYTES, from a 128-byte boundary).
+// FINAL: the score maps already hold S(p) inside the detect region (a FAST
+// kernel or the threshold pass applied the cell thresholds); the kernel masks
+// the region in registers.  Otherwise (APPLY) it turns the staged score rows
+// into S(p) first.  TH: tile rows (32, 64 or 128 -- fewer barriers per pixel
+// and more survivors per Harris phase).  Buffers live in dynamic shared
+// memory (NmsGeom<TH>::DYN_BYTES, from a 128-byte boundary).
 template <bool FINAL, int TH>
 __global__ void __launch_bounds__(DET_THREADS, TH == 32 ? 5 : 4)
 k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
              const int32_t* __restrict__ prefix, int n_list, int n_tiles,
              const CUtensorMap* __restrict__ img_maps, const CUtensorMap* __restrict__ score_maps,
-             const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, int order) {
+             const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, uint32_t cell_magic,
+             int order) {
+    // cell_magic = 2^32 / cell rounded up: n / cell == umulhi(n, cell_magic) for 0 <= n < 2^16.
     using G = NmsGeom<TH>;
-    static_assert(FINAL || TH == TILE_H, "the cell bookkeeping path uses 32-row tiles");
     constexpr int RPT = G::RPT_N, S_ROWS = G::S_ROWS_N, S_BUF = G::S_BUF_N, I_BUF = G::I_BUF_N;
     extern __shared__ __align__(128) uint8_t nms_dyn_raw[];
     uint8_t* nms_dyn = nms_dyn_raw + ((128u - (smem_u32(nms_dyn_raw) & 127u)) & 127u);
@@ -146,8 +141,6 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     uint32_t* queue = reinterpret_cast<uint32_t*>(nms_dyn + 2 * I_BUF + 2 * S_BUF);
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ NmsTile tinfo[2];
-    __shared__ uint32_t sflag[FINAL ? 1 : MAX_CELLS_LOCAL];
-    __shared__ int32_t rcell[FINAL ? 1 : S_ROWS];   // staged row -> (local cell row) * lcw
     __shared__ int nq;
 
     const int tid = threadIdx.x;
@@ -223,69 +216,62 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
         const int rx0 = border, rx1 = I.w - border, ry0 = border, ry1 = I.h - border;
         // Only columns X0-1 .. X0+TILE_W feed the 3x3 test; the rest become 0.
         const int lox = max(rx0, X0 - 1), hix = min(rx1, X0 + TILE_W + 1);
-        const int cx0 = (max(X0 - 1, rx0) - rx0) / cell;
-        const int cy0 = (max(Y0 - 1, ry0) - ry0) / cell;
-        const int lcw = (TILE_W + 2) / cell + 2;
-        const int lch = (TH + 2) / cell + 2;
-        if (cells && !FINAL) {
-            // Cell flags of the tile, and the cell row of each staged row.
-            for (int i = tid; i < lcw * lch; i += blockDim.x) {
-                const int cx = cx0 + i % lcw, cy = cy0 + i / lcw;
-                sflag[i] = (cx < I.ncx && cy < I.ncy) ? I.cell[cy * I.ncx + cx] : 0u;
-            }
-            if (tid < S_ROWS) {
-                const int iy = Y0 - 1 + tid;
-                rcell[tid] = (iy >= ry0 && iy < ry1) ? ((iy - ry0) / cell - cy0) * lcw : 0;
+
+        // 1. S(p) in place for rows Y0-1 .. Y0+TH, on the staged words the 3x3
+        //    test reads (X0-4 .. X0+TILE_W+3).  A thread keeps one word column
+        //    (its in-region byte mask and the at most two cells of its bytes are
+        //    fixed for the tile) and a run of consecutive rows.
+        if (!FINAL) {
+            const int k = S_W0 + tid % S_WORDS, rg = tid / S_WORDS;
+            if (rg < S_GROUPS) {
+                const int ix = X0 - HALO_X + 4 * k;
+                const uint32_t cmask = range_mask4(ix, lox, hix);
+                const uint32_t th = (uint32_t)(t_hi - t_lo + 1);  // t_hi in the maps' offset scores
+                const bool cells = t_hi != t_lo;
+                int ca = 0;
+                uint32_t ma = 0u, mb = 0u;
+                if (cells && cmask) {
+                    ca = (int)__umulhi((uint32_t)(max(ix, lox) - rx0), cell_magic);
+                    ma = cmask & range_mask4(ix, 0, rx0 + (ca + 1) * cell);
+                    mb = cmask & ~ma;
+                }
+                int px = 0;
+                bool col_on = cmask != 0u;
+                if (I.pmask) {
+                    px = (ix - I.tile_x0) >> 5;
+                    col_on = col_on && ix >= I.tile_x0 && px < 4 * I.tiles_x;
+                }
+                constexpr int RUN = (S_ROWS + S_GROUPS - 1) / S_GROUPS;
+                const int r0 = rg * RUN, r1 = min(r0 + RUN, S_ROWS);
+                int y_next = -1;  // first row of the next cell row (none entered yet)
+                uint32_t fm = 0u;
+                for (int r = r0; r < r1; ++r) {
+                    const int iy = Y0 - 1 + r;
+                    uint32_t* wp = reinterpret_cast<uint32_t*>(sS + r * SROW) + k;
+                    uint32_t val = 0u;
+                    bool on = col_on && iy >= ry0 && iy < ry1;
+                    if (on && I.pmask) {
+                        // Outside the proposed tiles S is 0 (each staged word lies in one proposal tile).
+                        const int py = (iy - ry0) >> 5;
+                        on = py < I.tiles_y && I.pmask[(size_t)py * 4 * I.tiles_x + px] != 0;
+                    }
+                    if (on) {
+                        val = *wp & cmask;
+                        if (cells && val) {
+                            if (iy >= y_next) {  // entering a cell row: its flags for this word's bytes
+                                const int cy = (int)__umulhi((uint32_t)(iy - ry0), cell_magic);
+                                y_next = ry0 + (cy + 1) * cell;
+                                const uint32_t* fr = I.cell + (size_t)cy * I.ncx + ca;
+                                fm = (ma && fr[0] ? ma : 0u) | (mb && fr[1] ? mb : 0u);
+                            }
+                            val = apply_cell_threshold(val, fm, th);
+                        }
+                    }
+                    *wp = val;
+                }
             }
             __syncthreads();
         }
-
-        // 1. S(p) in place for rows Y0-1 .. Y0+TILE_H, on the staged words the
-        //    3x3 test reads (X0-4 .. X0+TILE_W+3).  A thread keeps one word
-        //    column: its in-region byte mask and the (at most two) cells of its
-        //    bytes are fixed for the tile.
-        if (!FINAL && tid < S_WORDS * S_GROUPS) {
-            const int k = S_W0 + tid % S_WORDS, rg = tid / S_WORDS;
-            const int ix = X0 - HALO_X + 4 * k;
-            const uint32_t cmask = range_mask4(ix, lox, hix);
-            int fa = 0, fb = 0;
-            uint32_t ma = 0u, mb = 0u;
-            if (cells && cmask) {
-                const int ca = (max(ix, lox) - rx0) / cell, cb = (min(ix + 3, hix - 1) - rx0) / cell;
-                ma = cmask & range_mask4(ix, 0, rx0 + (ca + 1) * cell);
-                mb = cmask & ~ma;
-                fa = ca - cx0;
-                fb = cb - cx0;
-            }
-            int px = 0;
-            bool col_on = cmask != 0u;
-            if (I.pmask) {
-                px = (ix - I.tile_x0) >> 5;
-                col_on = col_on && ix >= I.tile_x0 && px < 4 * I.tiles_x;
-            }
-            for (int r = rg; r < S_ROWS; r += S_GROUPS) {
-                const int iy = Y0 - 1 + r;
-                uint32_t* wp = reinterpret_cast<uint32_t*>(sS + r * SROW) + k;
-                uint32_t val = 0u;
-                bool on = col_on && iy >= ry0 && iy < ry1;
-                if (on && I.pmask) {
-                    // Outside the proposed tiles S is 0 (each staged word lies in one proposal tile).
-                    const int py = (iy - ry0) >> 5;
-                    on = py < I.tiles_y && I.pmask[(size_t)py * 4 * I.tiles_x + px] != 0;
-                }
-                if (on) {
-                    val = *wp & cmask;
-                    // Bytes below t_hi survive only when their cell has no strong pixel.
-                    if (cells && val) {
-                        const int rc = rcell[r];
-                        const uint32_t fm = (sflag[rc + fa] ? ma : 0u) | (sflag[rc + fb] ? mb : 0u);
-                        val &= ~(fm & bytes_lt(val, (uint32_t)(t_hi - t_lo + 1)));  // maps hold s - (t_lo - 1)
-                    }
-                }
-                *wp = val;
-            }
-        }
-        if (!FINAL) __syncthreads();
 
         // 2. Strict 3x3 maxima, two pixels per register.  Rows of this warp
         //    inside the detect region (warp-uniform); rows below it hold no
@@ -400,8 +386,10 @@ template <bool FINAL, int TH>
 void launch_nms_t(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list, int n_tiles,
                   const CUtensorMap* img_maps, const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,
                   int border, int cell, int grid, int order, void* stream) {
+    const uint32_t magic = 0xFFFFFFFFu / (uint32_t)cell + 1u;
     k_nms_harris<FINAL, TH><<<grid, DET_THREADS, NmsGeom<TH>::DYN_BYTES, (cudaStream_t)stream>>>(
-        imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, order);
+        imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, magic,
+        order);
 }
 
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
@@ -410,47 +398,45 @@ void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* 
                        void* stream, bool final_scores, int tile_h) {
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
-    if (!final_scores)
-        launch_nms_t<false, 32>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
-                                border, cell, grid, order, stream);
-    else if (tile_h == 64)
-        launch_nms_t<true, 64>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
-                               border, cell, grid, order, stream);
-    else if (tile_h == 128)
-        launch_nms_t<true, 128>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
-                                border, cell, grid, order, stream);
-    else
-        launch_nms_t<true, 32>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo,
-                               border, cell, grid, order, stream);
+#define OF_NMS_LAUNCH(FI, TH)                                                                                  \
+    launch_nms_t<FI, TH>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, \
+                         border, cell, grid, order, stream)
+    if (final_scores) {
+        if (tile_h == 64) OF_NMS_LAUNCH(true, 64);
+        else if (tile_h == 128) OF_NMS_LAUNCH(true, 128);
+        else OF_NMS_LAUNCH(true, 32);
+    } else {
+        if (tile_h == 64) OF_NMS_LAUNCH(false, 64);
+        else if (tile_h == 128) OF_NMS_LAUNCH(false, 128);
+        else OF_NMS_LAUNCH(false, 32);
+    }
+#undef OF_NMS_LAUNCH
 }
 
-// Resident blocks per SM of the NMS kernel with TH-row tiles (final scores;
-// the 32-row general variant has the same occupancy).  Raises the dynamic
-// shared-memory limit where the buffers need it.
-template <int TH>
-static cudaError_t tall_nms_occupancy(int* n) {
-    cudaError_t e = cudaFuncSetAttribute(k_nms_harris<true, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+// Resident blocks per SM of the NMS kernel with TH-row tiles.  Raises the
+// dynamic shared-memory limit where the buffers need it.
+template <bool FI, int TH>
+static cudaError_t nms_occupancy(int* n) {
+    cudaError_t e = cudaFuncSetAttribute(k_nms_harris<FI, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          NmsGeom<TH>::DYN_BYTES);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_nms_harris<true, TH>, DET_THREADS,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_nms_harris<FI, TH>, DET_THREADS,
                                                           NmsGeom<TH>::DYN_BYTES);
     return e;
 }
 
-int nms_blocks_per_sm(int tile_h) {
+int nms_blocks_per_sm(int tile_h, bool final_scores) {
     int n = 0;
     cudaError_t e;
-    if (tile_h == 64) {
-        e = tall_nms_occupancy<64>(&n);
-    } else if (tile_h == 128) {
-        e = tall_nms_occupancy<128>(&n);
-    } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_harris<false, 32>, DET_THREADS,
-                                                          NmsGeom<32>::DYN_BYTES);
-    }
+    if (final_scores)
+        e = tile_h == 64 ? nms_occupancy<true, 64>(&n) : tile_h == 128 ? nms_occupancy<true, 128>(&n)
+                                                                        : nms_occupancy<true, 32>(&n);
+    else
+        e = tile_h == 64 ? nms_occupancy<false, 64>(&n) : tile_h == 128 ? nms_occupancy<false, 128>(&n)
+                                                                         : nms_occupancy<false, 32>(&n);
     return (e != cudaSuccess || n < 1) ? 1 : n;
 }
 
-int nms_blocks_per_sm() { return nms_blocks_per_sm(32); }
+int nms_blocks_per_sm() { return nms_blocks_per_sm(32, false); }
 
 }  // namespace ofk

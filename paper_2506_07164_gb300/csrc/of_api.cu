@@ -276,10 +276,26 @@ struct Plan {
 };
 
 // Resident blocks per SM of the plan's FAST kernel.
+// How the per-cell thresholds reach NMS with the general FAST form:
+//   0 the threshold pass sets the cell flags and applies them to the maps (NMS on final scores)
+//   1 the pass sets the flags only; NMS applies them on its staged tiles
+//   2 the FAST kernel sets the flags; no pass; NMS applies them
+// -1: a cell-tile FAST form wrote final scores (no pass, NMS on final scores).
+// Mode 2 is also the fallback when the pass cannot flag a band's cells; the
+// per-warp general kernel (form 3) sets no flags and then runs as form 0.
+constexpr int kThrMode = 0;
+bool cell_form(const Plan* P) { return P->cell_tiles && (P->tun.fast_cell_tiles == 1 || P->tun.fast_cell_tiles == 2); }
+bool warp_form(const Plan* P) { return P->tun.fast_cell_tiles == 3 && P->apply_flags && kThrMode != 2; }
+int thr_mode(const Plan* P) {
+    if (cell_form(P)) return -1;
+    return (kThrMode != 2 && !P->apply_flags) ? 2 : kThrMode;
+}
+
 int plan_fast_bps(const Plan* P) {
     if (P->aligned_ok && P->tun.fast_cell_tiles == 2) return fast_aligned_blocks_per_sm();
-    if (P->cell_tiles && P->tun.fast_cell_tiles) return fast_cells_blocks_per_sm(P->s.cell);
-    return fast_blocks_per_sm(P->tun.fast_tile_h, !P->apply_flags);
+    if (cell_form(P)) return fast_cells_blocks_per_sm(P->s.cell);
+    if (warp_form(P)) return fast_warp_blocks_per_sm();
+    return fast_blocks_per_sm(P->tun.fast_tile_h, thr_mode(P) == 2);
 }
 
 void free_plan(Plan* p) {
@@ -366,45 +382,52 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                 launch_fast_aligned(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfal() + G.fal_off, G.n_list,
                                     G.fal_tiles, P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                                     H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
-            else if (P->cell_tiles && P->tun.fast_cell_tiles)
+            else if (cell_form(P))
                 launch_fast_cells(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfp() + G.fp_off, G.n_list, G.fast_tiles,
                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                                   H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+            else if (warp_form(P))
+                launch_fast_warp(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
+                                 P->d_maps(), P->d_call(), s.t_lo, s.border, H->n_sms * P->tun.fast_blocks_per_sm,
+                                 P->tun.fast_order, st);
             else if (P->tun.fast_tile_h == 64)
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list, G.nms64_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, !P->apply_flags, 64);
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, thr_mode(P) == 2, 64);
             else if (P->tun.fast_tile_h == FT_HS[0] || P->tun.fast_tile_h == FT_HS[1]) {
                 const int i = P->tun.fast_tile_h == FT_HS[0] ? 0 : 1;
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gft(i) + G.ftall_off[i], G.n_list,
                             G.ftall_tiles[i], P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, !P->apply_flags, FT_HS[i]);
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, thr_mode(P) == 2, FT_HS[i]);
             }
             else
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, !P->apply_flags, 32);
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, thr_mode(P) == 2, 32);
             break;
-        case 2:
-            if (!(P->cell_tiles && P->tun.fast_cell_tiles))
+        case 2: {
+            const int mode = thr_mode(P);
+            if (mode == 0 || mode == 1)
                 launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list, G.n_bands,
-                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st, P->apply_flags);
+                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st, true, mode == 0);
+            const bool fin = mode <= 0;
             if (P->tun.nms_tile_h == 64)
                 launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list,
                                   G.nms64_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
-                                  s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, true,
+                                  s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, fin,
                                   64);
             else if (P->tun.nms_tile_h == FT_HS[0])  // same tiling as the 128-row FAST tiles
                 launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gft(0) + G.ftall_off[0], G.n_list,
                                   G.ftall_tiles[0], P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi,
                                   s.t_lo, s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st,
-                                  true, FT_HS[0]);
+                                  fin, FT_HS[0]);
             else
                 launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list,
                                   G.det_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
-                                  s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, true,
+                                  s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, fin,
                                   32);
             break;
+        }
         case 3:
             launch_select(P->d_img() + G.img_begin, G.n_img, P->d_call(), P->max_quota, st);
             break;
@@ -724,11 +747,13 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.fast_tile_h = 32;
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
     P->tun.nms_tile_h = 64;
-    P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64);  // also raises its shared-memory limit before any capture
-    for (int i = 0; i < 2; ++i)  // raise the tall kernels' limits before any capture
+    P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64, thr_mode(P) <= 0);
+    for (int i = 0; i < 2; ++i)  // raise the tall kernels' shared-memory limits before any capture
         for (int fl = 0; fl < 2; ++fl) fast_blocks_per_sm(FT_HS[i], fl != 0);
-    nms_blocks_per_sm(FT_HS[0]);
+    for (int th = 32; th <= 128; th *= 2)
+        for (int fin = 0; fin < 2; ++fin) nms_blocks_per_sm(th, fin != 0);
     fast_aligned_blocks_per_sm();  // raises the cell-aligned kernel's shared-memory limit
+    fast_warp_blocks_per_sm();     // ... and the per-warp kernel's
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
 
@@ -1060,9 +1085,9 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     // where the cell size allows it; fast_ms below is FAST + NMS.
     best = 1e30f;
     int bb = P->tun.fast_blocks_per_sm, bo = 0, bv = P->tun.fast_cell_tiles, bt = P->tun.fast_tile_h;
-    // Forms: general kernel (32-row tiles; 64, 128 or 256 rows when the pass
-    // sets the flags), cell tiles (1), cell-aligned general kernel (2).
-    for (int cand = 0; cand < 6 && rc == OF_OK; ++cand) {
+    // Forms: general kernel (32-, 64-, 128- or 256-row tiles), cell tiles (1),
+    // cell-aligned general kernel (2), general kernel with per-warp pipelines (3).
+    for (int cand = 0; cand < 7 && rc == OF_OK; ++cand) {
         const int v = cand < 4 ? 0 : cand - 3, th = cand < 4 ? 32 << cand : 32;
         if ((v == 1 && !P->cell_tiles) || (v == 2 && !P->aligned_ok)) continue;
         P->tun.fast_cell_tiles = v;
@@ -1095,7 +1120,7 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     bb = P->tun.nms_blocks_per_sm, bo = 0;
     int bth = P->tun.nms_tile_h;
     for (int th = 32; th <= 128 && rc == OF_OK; th *= 2)
-    for (int bp = 1; bp <= nms_blocks_per_sm(th) && rc == OF_OK; ++bp) {
+    for (int bp = 1; bp <= nms_blocks_per_sm(th, thr_mode(P) <= 0) && rc == OF_OK; ++bp) {
         for (int order = 0; order < 2 && rc == OF_OK; ++order) {
             P->tun.nms_tile_h = th;
             P->tun.nms_blocks_per_sm = bp;
@@ -1332,9 +1357,9 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         t->nms_blocks_per_sm < 1 ||
         (t->nms_tile_h != 32 && t->nms_tile_h != 64 && t->nms_tile_h != 128) ||
         (t->fast_tile_h != 32 && t->fast_tile_h != 64 && t->fast_tile_h != FT_HS[0] && t->fast_tile_h != FT_HS[1]) ||
-        t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h) || (t->fast_order != 0 && t->fast_order != 1) ||
+        t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h, false) || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
-        t->fast_cell_tiles < 0 || t->fast_cell_tiles > 2)
+        t->fast_cell_tiles < 0 || t->fast_cell_tiles > 3)
         return fail(OF_ERR_ARG, "tuning field out of range");
     Plan* P = nullptr;
     const int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
@@ -1343,7 +1368,10 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     P->tun.resize_tile_h = t->resize_tile_h;
     P->tun.resize_tma = t->resize_tma;
     // Forms the cell size does not allow fall back: aligned -> cell tiles -> general.
-    P->tun.fast_cell_tiles = !P->cell_tiles ? 0 : (t->fast_cell_tiles == 2 && !P->aligned_ok) ? 1 : t->fast_cell_tiles;
+    P->tun.fast_cell_tiles = t->fast_cell_tiles == 3                     ? 3
+                             : !P->cell_tiles                           ? 0
+                             : (t->fast_cell_tiles == 2 && !P->aligned_ok) ? 1
+                                                                          : t->fast_cell_tiles;
     P->tun.fast_tile_h = t->fast_tile_h;
     P->tun.fast_blocks_per_sm = std::min(t->fast_blocks_per_sm, plan_fast_bps(P));
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
@@ -1570,7 +1598,10 @@ int64_t of_inspect(of_handle* H, int what, int frame, int level, void* dst, int6
             OF_CK(cudaMemcpy2DAsync(d + (size_t)s.border * I.w + s.border, I.w,
                                     I.score + (size_t)s.border * I.spitch + s.border, I.spitch, rw,
                                     rh, cudaMemcpyDeviceToDevice, st));
-        ofk::launch_inspect_score(d, bytes, s.t_lo - 1, st);  // the maps hold s - (t_lo - 1)
+        if (thr_mode(P) >= 1)  // NMS applies the thresholds and proposal tiles itself: apply them here too
+            ofk::launch_inspect_score_apply(P->d_img(), frame * nl + level, d, s.t_hi, s.t_lo, s.border, s.cell, st);
+        else
+            ofk::launch_inspect_score(d, bytes, s.t_lo - 1, st);  // the maps hold s - (t_lo - 1)
         OF_CK(cudaGetLastError());
     } else if (what == OF_BUF_CELLT) {
         ofk::launch_inspect_cells(P->d_img(), frame * nl + level, s.t_hi, s.t_lo, d, st);

@@ -148,17 +148,22 @@ void launch_fast_aligned(const Img* imgs, const int32_t* img_list, const int32_t
                          int cell, int grid, int order, void* stream);
 int fast_aligned_blocks_per_sm();
 int fast_blocks_per_sm(int tile_h, bool flags);  // the general kernel
-// Threshold pass: applies the cell flags; flags: first sets them (when the
-// general FAST kernel did not).
+// General FAST with per-warp pipelines over the 128 x 32 detect tiles (no cell flags).
+void launch_fast_warp(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list, int n_tiles,
+                      const CUtensorMap* maps, const Call* call, int t_lo, int border, int grid, int order,
+                      void* stream);
+int fast_warp_blocks_per_sm();
+// Threshold pass: flags: sets the cell flags (when the general FAST kernel
+// did not); apply: applies them to the maps (else NMS applies them).
 void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
-                       int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags);
+                       int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags, bool apply = true);
 constexpr int CA_MAX_CELLS = 1024;  // cells per band row the threshold pass can flag itself
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                        int n_list, int n_tiles, const CUtensorMap* img_maps,
                        const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,
                        int border, int cell, int grid, int order, void* stream,
                        bool final_scores = false, int tile_h = 32);
-int nms_blocks_per_sm(int tile_h);
+int nms_blocks_per_sm(int tile_h, bool final_scores);
 void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, void* stream);
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
 // Slots [slot_begin, slot_end) of images [img_begin, img_begin + n_img) (one frame group).
@@ -168,6 +173,8 @@ void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t*
                           void* stream);
 void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream);
 void launch_inspect_score(uint8_t* dst, int64_t n, int off, void* stream);
+void launch_inspect_score_apply(const Img* imgs, int img, uint8_t* dst, int t_hi, int t_lo, int border, int cell,
+                                void* stream);
 int select_smem_bytes(int max_quota);
 // Paper ablation variants (k_ablation.cu); returns the number of launches.
 int launch_variant(int fast_v, int harris_v, const uint8_t* img, int w, int h, int pitch, int t, int border,

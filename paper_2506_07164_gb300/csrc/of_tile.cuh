@@ -67,4 +67,25 @@ __device__ __forceinline__ uint32_t range_mask4(int x, int lo, int hi) {
     return m;
 }
 
+// 0xFF in each byte of v that is >= t, for 1 <= t <= 128: (b | 0x80) - t has
+// no borrow out of its byte and bit 7 set exactly when the low seven bits are
+// >= t; a byte with bit 7 set is >= 128 >= t itself.  Five instructions.
+__device__ __forceinline__ uint32_t bytes_ge(uint32_t v, uint32_t t) {
+    const uint32_t g = (((v | 0x80808080u) - t * 0x01010101u) | v) & 0x80808080u;
+    return (g >> 7) * 0xFFu;
+}
+
+// The same for any t <= 255, in 16-bit lanes.
+__device__ __forceinline__ uint32_t bytes_ge_any(uint32_t v, uint32_t t) {
+    const uint32_t tt = (0x8000u - t) * 0x00010001u;
+    const uint32_t lo = __byte_perm(v, 0u, 0x4140) + tt, hi = __byte_perm(v, 0u, 0x4342) + tt;
+    return __byte_perm((lo >> 15 & 0x00010001u) * 0xFFu, (hi >> 15 & 0x00010001u) * 0xFFu, 0x6420);
+}
+
+// Per-cell threshold on a word of offset scores: the bytes of v below t are
+// cleared where fm is 0xFF (flagged cells).
+__device__ __forceinline__ uint32_t apply_cell_threshold(uint32_t v, uint32_t fm, uint32_t t) {
+    return v & ((t <= 128u ? bytes_ge(v, t) : bytes_ge_any(v, t)) | ~fm);
+}
+
 }  // namespace ofk
