@@ -704,7 +704,8 @@ def main():
         ops = FAST_OPS_PER_PX * detect_region_pixels(lw, lh) * B
         achieved = ops / (stage_ms[dom] / 1000.0) / 1e9
         peak_alu = n_sms * ALU_LANES_PER_SM_CLK * sm_max * 1e6 / 1e9
-        kname = {0: "k_fast", 1: "k_fast_cells", 2: "k_fast_aligned", 3: "k_fast_warp"}[int(tuning.get("fast_cell_tiles", 0))]
+        kname = {0: "k_fast", 1: "k_fast_cells", 2: "k_fast_aligned", 3: "k_fast_warp",
+                 4: "k_fast_cstrip"}[int(tuning.get("fast_cell_tiles", 0))]
         ok = kname == "k_fast" and code_sha1(
             os.path.join(ROOT, "paper_2506_07164_gb300", "csrc", "k_fast.cu")) == FAST_TRAFFIC["code_sha1"]
         roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 1), "peak": round(peak_alu, 1),

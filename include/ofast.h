@@ -87,7 +87,9 @@ typedef struct of_tuning {
                                      itself (cells of 8..30 pixels); 2: the same on 120 x 120 cell-aligned
                                      tiles with the general kernel's layout (cells of 15 or 30 pixels);
                                      0: general FAST (fast_tile_h rows), then a threshold pass; 3: general
-                                     FAST on 128 x 32 tiles with per-warp pipelines, then the pass */
+                                     FAST on 128 x 32 tiles with per-warp pipelines, then the pass; 4: the
+                                     same on strips one cell row high, which also set the cell flags, then
+                                     the pass applies them (cells of 8..33 pixels) */
     int32_t nms_tile_h;           /* NMS + Harris tile height: 32, 64 or 128 rows */
     int32_t fast_tile_h;          /* general FAST tile height: 32, 64, 128 or 256 rows */
     int32_t candidates_tried;     /* configurations timed */
@@ -199,8 +201,9 @@ int of_autotune(of_handle* h, const of_frame* frames, int n_frames, int levels, 
  * needed and its graphs re-captured with *tuning [host].  Fields checked:
  * resize_tile_h 32 or 64, resize_tma 0 or 1, fast/nms_blocks_per_sm in
  * 1..the kernel's occupancy, fast/nms_order 0 or 1, stream_groups 1..8
- * (capped at the number of frames), fast_cell_tiles 0..3 (1 and 2 become 0
- * for cells outside 8..30 pixels; 2 becomes 1 for cells other than 15 and 30),
+ * (capped at the number of frames), fast_cell_tiles 0..4 (1 and 2 become 0
+ * for cells outside 8..30 pixels, 4 for cells over 33; 2 becomes 1 for cells
+ * other than 15 and 30),
  * nms_tile_h 32, 64 or 128, fast_tile_h 32, 64, 128 or 256 (else
  * OF_ERR_ARG); the
  * remaining fields are ignored.  Launches nothing.  Arguments as

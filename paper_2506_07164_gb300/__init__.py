@@ -57,7 +57,8 @@ class OfTuning(C.Structure):
     nms_blocks_per_sm, fast_order, nms_order: persistent grids and tile order;
     stream_groups (1..8): frame groups on forked graph branches; fast_cell_tiles:
     0 general FAST + threshold pass, 1 cell-tile kernel, 2 cell-aligned general kernel,
-    3 general FAST with per-warp pipelines + threshold pass;
+    3 general FAST with per-warp pipelines + threshold pass, 4 the same on cell-row strips
+    that also set the cell flags + the pass applying them;
     fast_tile_h (32/64/128/256) and nms_tile_h (32/64/128): tile heights.  The last
     four fields report the autotuner's search (candidates, best stage times in ms)."""
 

@@ -44,7 +44,8 @@ __device__ __forceinline__ uint32_t apply_word(uint32_t v, uint32_t fm, uint32_t
 template <bool FLAGS, bool APPLY, bool SMALL_T>
 __global__ void __launch_bounds__(CA_THREADS)
 k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ band_prefix,
-             int n_list, int n_bands, int t_hi, int t_lo, int border, int cell) {
+             int n_list, int n_bands, int t_hi, int t_lo, int border, int cell, int pmask_only) {
+    // FLAGS: set the cell flags (only for images with proposal tiles when pmask_only).
     __shared__ __align__(16) uint8_t colmask[16 * CA_SEG];
     __shared__ uint32_t bflag[FLAGS ? CA_MAX_CELLS : 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -66,7 +67,7 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
         uint32_t* const crow = I.cell + (size_t)cy * ncx;
         const uint32_t* fl = crow;
         const int y0 = border + cy * cell, y1 = min(y0 + cell, ry1);
-        if (FLAGS && cells) {
+        if (FLAGS && cells && (pmask || !pmask_only)) {
             __syncthreads();  // the previous band's readers are done with bflag and colmask
             for (int i = tid; i < ncx; i += CA_THREADS) bflag[i] = 0u;
             __syncthreads();
@@ -190,14 +191,14 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
 }
 
 void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
-                       int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags, bool apply) {
+                       int t_hi, int t_lo, int border, int cell, int grid, void* stream, int flags, bool apply) {
     if (n_bands <= 0) return;
     grid = grid < n_bands ? grid : n_bands;
     const cudaStream_t st = (cudaStream_t)stream;
     const bool small_t = t_hi - t_lo + 1 <= 128;
 #define OF_CA_LAUNCH(FL, AP, SM)                                                                              \
     k_cell_apply<FL, AP, SM><<<grid, CA_THREADS, 0, st>>>(imgs, img_list, band_prefix, n_list, n_bands, t_hi, t_lo, \
-                                                          border, cell)
+                                                          border, cell, flags == 2)
     if (flags && !apply) {
         if (small_t) OF_CA_LAUNCH(true, false, true);
         else OF_CA_LAUNCH(true, false, false);

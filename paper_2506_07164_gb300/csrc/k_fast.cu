@@ -165,6 +165,10 @@ __device__ __forceinline__ void store_bytes(uint8_t* d, uint32_t v, uint32_t mas
     }
 }
 
+struct CellTile {
+    int32_t img, x_lo, y0, box_x;
+};
+
 // Tile t of the launch: its image and origin.
 struct TileInfo {
     int32_t img, x0, y0;
@@ -552,6 +556,157 @@ int fast_warp_blocks_per_sm() {
 }
 
 // ---------------------------------------------------------------------------
+// Cell-row strips with per-warp pipelines: the general layout, with the cell
+// flags set exactly and cheaply (the threshold pass then only applies them).
+//
+// A work item is one cell row (cell <= 33 rows) of one 128-column detect tile
+// column of one image: x in [X0, X0 + 128), y in [y0, y0 + cell), y0 =
+// border + cy cell, cut to the detect region; one 160 x 40 TMA box from
+// (X0 - 16, y0 - 4) covers its rows and halo.  Warps work as the per-warp
+// general kernel (own buffers and mbarriers, no block barriers).  Since the
+// strip is exactly one cell row, a lane keeps one running maximum per pixel
+// pair over all its rows; at the end one warp OR-reduction gives a bit per
+// cell the strip touches (at most 128 / 8 + 2 = 18), and one lane per
+// flagged cell ORs it into the global flags (cells at the strip's sides are
+// shared with the neighbouring strips).  Images with proposal tiles (the
+// learned path) get their flags from the threshold pass instead, which sees
+// only proposed pixels; nothing in the row loop depends on the proposal.
+
+__global__ void __launch_bounds__(DET_THREADS, 2)
+k_fast_cstrip(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ prefix,
+              int n_list, int n_tiles, const CUtensorMap* __restrict__ maps, const Call* __restrict__ call,
+              int t_hi, int t_lo, int border, int cell, uint32_t cell_magic, int order) {
+    // cell_magic = 2^32 / cell rounded up: n / cell == umulhi(n, cell_magic) for 0 <= n < 2^16.
+    extern __shared__ __align__(128) uint8_t fw_dyn[];
+    uint8_t* const base = fw_dyn + ((128u - (smem_u32(fw_dyn) & 127u)) & 127u);
+    __shared__ __align__(8) uint64_t mbar[FW_WARPS][2];
+    __shared__ TileInfo tinfo[FW_WARPS][2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint8_t* const wbuf = base + w * 2 * FAST_BUF;
+    if (lane == 0) {
+        mbar_init(&mbar[w][0], 1);
+        mbar_init(&mbar[w][1], 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    const int nw = gridDim.x * FW_WARPS, gw = blockIdx.x * FW_WARPS + w;
+    auto issue = [&](int t, int b) {  // lane 0
+        const int j = find_tile_job(prefix, n_list, t);
+        const int ii = __ldg(list + j);
+        const Img& I = imgs[ii];
+        const int tt = t - __ldg(prefix + j);
+        const TileInfo ti{ii, I.tile_x0 + (tt % I.tiles_x) * TILE_W, border + (tt / I.tiles_x) * cell};
+        tinfo[w][b] = ti;
+        tensormap_acquire(maps + ii);
+        mbar_arrive_expect_tx(&mbar[w][b], FAST_BOX);
+        tma_load_2d(wbuf + b * FAST_BUF, maps + ii, ti.x0 - HALO_X, ti.y0 - 4, &mbar[w][b]);
+    };
+    if (lane == 0 && tile_of(order, gw, nw, n_tiles, 0) < n_tiles) issue(tile_of(order, gw, nw, n_tiles, 0), 0);
+    const bool cells = t_hi != t_lo;
+    const uint32_t kb = PAIR_BIAS - (uint32_t)(t_lo - 1) * 0x00010001u;
+    const uint32_t th_b = (uint32_t)(t_hi - t_lo + 1) + 512u;  // t_hi in biased offset units
+    for (int it = 0;; ++it) {
+        const int t = tile_of(order, gw, nw, n_tiles, it);
+        if (t >= n_tiles) break;
+        const int tn = tile_of(order, gw, nw, n_tiles, it + 1);
+        const int b = it & 1;
+        if (lane == 0 && tn < n_tiles) {
+            fence_proxy_async_smem();
+            issue(tn, b ^ 1);
+        }
+        const bool ok = mbar_wait(&mbar[w][b], (it >> 1) & 1);
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            if (lane == 0) {
+                atomicOr(call->status, OF_DEV_TIMEOUT);
+                // Let this warp's copies in flight land before the block's shared memory can go away.
+                mbar_wait(&mbar[w][b], (it >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+                if (tn < n_tiles) mbar_wait(&mbar[w][b ^ 1], ((it + 1) >> 1) & 1, OF_WAIT_LIMIT_NS / 8);
+            }
+            __syncwarp();
+            return;
+        }
+        const TileInfo ti = tinfo[w][b];
+        const Img& I = imgs[ti.img];
+        const uint8_t* const s = wbuf + b * FAST_BUF;
+        const int X0 = ti.x0, y0 = ti.y0;
+        const int rx0 = border, rx1 = I.w - border;
+        const int x = X0 + 4 * lane;
+        const uint32_t colmask = range_mask4(x, rx0, rx1);
+        const int nrows = min(cell, I.h - border - y0);
+        uint8_t* const sdst = I.score + (size_t)y0 * I.spitch + x;
+        const size_t spitch = (size_t)I.spitch;
+        // Learned path: skip a strip with no proposed tile under it (at most 2 x 4
+        // proposal tiles; lanes 0..7 look one up each).  The threshold pass zeroes
+        // the scores outside proposed tiles and sets the cell flags of such images.
+        const uint8_t* const pmask = I.pmask;
+        if (pmask) {
+            const int py = ((y0 - border) >> 5) + (lane >> 2);
+            const int pxl = ((X0 - I.tile_x0) >> 5) + (lane & 3);
+            const bool on = lane < 8 && py <= ((y0 + nrows - 1 - border) >> 5) && py < I.tiles_y &&
+                            pmask[(size_t)py * 4 * I.tiles_x + pxl] != 0;
+            if (!__any_sync(0xFFFFFFFFu, on)) {
+                __syncwarp();
+                continue;
+            }
+        }
+        uint32_t mx0 = 0u, mx1 = 0u;
+        const uint8_t* const srow = s + SROW + HALO_X + 4 * lane;  // staged row of output row -3
+#pragma unroll 1
+        for (int r0 = 0; r0 < nrows; r0 += 16) {
+            uint32_t hw[16 + 6][8];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) staged_row_words(srow + (r0 + k) * SROW, hw[k]);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                if (r0 + r >= nrows) break;
+                if (r > 0) staged_row_words(srow + (r0 + r + 6) * SROW, hw[r + 6]);
+                const uint32_t s0 = ring_ipair_score<0>(hw + r, kb);  // 512 + offset score per lane
+                const uint32_t s1 = ring_ipair_score<1>(hw + r, kb);
+                mx0 = __vimax3_u16x2(mx0, s0, s0);
+                mx1 = __vimax3_u16x2(mx1, s1, s1);
+                if (colmask != 0u)
+                    *reinterpret_cast<uint32_t*>(sdst + (size_t)(r0 + r) * spitch) =
+                        __byte_perm(s0, s1, 0x6240) & colmask;
+            }
+        }
+        if (cells && !pmask) {
+            // Bit c: cell cx0 + c of this cell row holds a pixel scoring >= t_hi.
+            const int cx0 = (int)__umulhi((uint32_t)(max(X0, rx0) - rx0), cell_magic);
+            const int ca = (int)__umulhi((uint32_t)(max(x, rx0) - rx0), cell_magic);
+            const uint32_t mask_a = colmask & range_mask4(x, 0, rx0 + (ca + 1) * cell);
+            const uint32_t strong = __byte_perm(lanes_ge(mx0, th_b), lanes_ge(mx1, th_b), 0x6240) & colmask;
+            const uint32_t bits = ((strong & mask_a) ? 1u << (ca - cx0) : 0u) |
+                                  ((strong & ~mask_a) ? 2u << (ca - cx0) : 0u);
+            const uint32_t flags = __reduce_or_sync(0xFFFFFFFFu, bits);
+            if ((flags >> lane) & 1u)
+                atomicOr(&I.cell[(size_t)__umulhi((uint32_t)(y0 - border), cell_magic) * I.ncx + cx0 + lane], 1u);
+        }
+        __syncwarp();  // every lane is done with buffer b before lane 0 refills it
+    }
+}
+
+void launch_fast_cstrip(const Img* imgs, const int32_t* img_list, const int32_t* strip_prefix, int n_list,
+                        int n_strips, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
+                        int cell, int grid, int order, void* stream) {
+    if (n_strips <= 0) return;
+    const int warps = (n_strips + FW_WARPS - 1) / FW_WARPS;
+    grid = grid < warps ? grid : warps;
+    const uint32_t magic = 0xFFFFFFFFu / (uint32_t)cell + 1u;
+    k_fast_cstrip<<<grid, DET_THREADS, FW_DYN, (cudaStream_t)stream>>>(imgs, img_list, strip_prefix, n_list,
+                                                                       n_strips, maps, call, t_hi, t_lo, border,
+                                                                       cell, magic, order);
+}
+
+int fast_cstrip_blocks_per_sm() {
+    int n = 0;
+    if (cudaFuncSetAttribute(k_fast_cstrip, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_DYN) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_cstrip, DET_THREADS, FW_DYN) != cudaSuccess ||
+        n < 1)
+        n = 1;
+    return n;
+}
+
+// ---------------------------------------------------------------------------
 // Cell tiles: FAST with the per-cell threshold applied in the same kernel.
 //
 // A tile is cpt = floor(124 / cell) whole cells wide and cr = ct_cell_rows
@@ -571,9 +726,6 @@ int fast_warp_blocks_per_sm() {
 // row).  The TMA boxes are 160 x 40 image boxes at x = (group origin - 4)
 // rounded down to 16 bytes, starting 3 rows above the tile, stacked.
 
-struct CellTile {
-    int32_t img, x_lo, y0, box_x;
-};
 
 constexpr int CT_BUF = 2 * FAST_BUF;  // two stacked image boxes
 

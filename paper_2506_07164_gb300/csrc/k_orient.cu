@@ -171,34 +171,6 @@ void launch_inspect_score(uint8_t* dst, int64_t n, int off, void* stream) {
     k_inspect_score<<<256, 256, 0, (cudaStream_t)stream>>>(dst, n, off);
 }
 
-// A copy (w x h, packed) of a map that still holds s(p) where s(p) >= t_lo
-// (offset scores) while NMS applies the cell thresholds and proposal tiles
-// on its staged tiles: S(p) as NMS sees it, without the offset.
-__global__ void k_inspect_score_apply(const Img* imgs, int img, uint8_t* d, int t_hi, int t_lo, int border,
-                                      int cell) {
-    const Img& I = imgs[img];
-    const int64_t n = (int64_t)I.w * I.h;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int v = d[i];
-        if (!v) continue;
-        const int x = (int)(i % I.w), y = (int)(i / I.w);
-        bool keep = true;
-        if (t_hi != t_lo && v < t_hi - t_lo + 1 && I.cell[((y - border) / cell) * I.ncx + (x - border) / cell])
-            keep = false;
-        if (I.pmask) {
-            const int px = (x - I.tile_x0) >> 5, py = (y - border) >> 5;
-            if (x < I.tile_x0 || px >= 4 * I.tiles_x || py >= I.tiles_y || !I.pmask[(size_t)py * 4 * I.tiles_x + px])
-                keep = false;
-        }
-        d[i] = keep ? (uint8_t)(v + t_lo - 1) : (uint8_t)0;
-    }
-}
-
-void launch_inspect_score_apply(const Img* imgs, int img, uint8_t* dst, int t_hi, int t_lo, int border, int cell,
-                                void* stream) {
-    k_inspect_score_apply<<<256, 256, 0, (cudaStream_t)stream>>>(imgs, img, dst, t_hi, t_lo, border, cell);
-}
-
 void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream) {
     if (n <= 0) return;
     k_inspect_cands<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(imgs, img, n, dst);

@@ -219,6 +219,7 @@ struct Plan {
         int img_begin = 0, n_img = 0;
         int dl_begin = 0, n_list = 0, det_tiles = 0, dp_off = 0;
         int fast_tiles = 0, fp_off = 0;             // cell-tile FAST: tiles and prefix offset in gp_fast
+        int cs_strips = 0, cs_off = 0;              // cell-strip FAST: strips and prefix offset in gp_cstrip
         int nms64_tiles = 0, np_off = 0;            // NMS with 64-row tiles: tiles and prefix offset in gp_nms64
         int ftall_tiles[2] = {0, 0}, ftall_off[2] = {0, 0};  // FAST on FT_HS[i]-row tiles: tiles, offset in gp_ftall[i]
         int fal_tiles = 0, fal_off = 0;             // cell-aligned FAST: tiles and prefix offset in gp_fal
@@ -228,9 +229,10 @@ struct Plan {
         std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
     };
     std::vector<Group> groups[kMaxGroups + 1];
-    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_ftall[2], gp_fal;
+    std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_ftall[2], gp_fal, gp_cstrip;
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
-    bool apply_flags = false;    // the threshold pass sets the cell flags (else the general FAST kernel does)
+    bool apply_flags = false;    // the threshold pass can set the cell flags (else the general FAST kernel does)
+    bool strip_ok = false;       // the cell size allows the cell-row strip kernel (cells of 8..33 pixels)
     bool aligned_ok = false;     // ... and the cell-aligned general FAST kernel (cells of 15 or 30 pixels)
     std::vector<int> rt_buf;        // TMA resize buffer bytes of level l (0: staged kernel only)
     std::vector<int> rt_bps;        // TMA resize resident blocks per SM of level l
@@ -238,7 +240,8 @@ struct Plan {
     Call h_call{};
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0;
-    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gft[2] = {0, 0}, off_gfal = 0;
+    size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gft[2] = {0, 0}, off_gfal = 0,
+           off_gcs = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -270,32 +273,32 @@ struct Plan {
     const int32_t* d_grs() const { return reinterpret_cast<const int32_t*>(dbuf + off_grs); }
     const int32_t* d_gfp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfp); }
     const int32_t* d_grp() const { return reinterpret_cast<const int32_t*>(dbuf + off_grp); }
+    const int32_t* d_gcs() const { return reinterpret_cast<const int32_t*>(dbuf + off_gcs); }
     const int32_t* d_gnp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gnp); }
     const int32_t* d_gft(int i) const { return reinterpret_cast<const int32_t*>(dbuf + off_gft[i]); }
     const int32_t* d_gfal() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfal); }
 };
 
 // Resident blocks per SM of the plan's FAST kernel.
-// How the per-cell thresholds reach NMS with the general FAST form:
-//   0 the threshold pass sets the cell flags and applies them to the maps (NMS on final scores)
-//   1 the pass sets the flags only; NMS applies them on its staged tiles
-//   2 the FAST kernel sets the flags; no pass; NMS applies them
-// -1: a cell-tile FAST form wrote final scores (no pass, NMS on final scores).
-// Mode 2 is also the fallback when the pass cannot flag a band's cells; the
-// per-warp general kernel (form 3) sets no flags and then runs as form 0.
-constexpr int kThrMode = 0;
-bool cell_form(const Plan* P) { return P->cell_tiles && (P->tun.fast_cell_tiles == 1 || P->tun.fast_cell_tiles == 2); }
-bool warp_form(const Plan* P) { return P->tun.fast_cell_tiles == 3 && P->apply_flags && kThrMode != 2; }
-int thr_mode(const Plan* P) {
-    if (cell_form(P)) return -1;
-    return (kThrMode != 2 && !P->apply_flags) ? 2 : kThrMode;
+// How the per-cell thresholds reach NMS.  The cell-tile forms (1, 2) write
+// final scores themselves.  Otherwise the threshold pass applies the cell
+// flags to the maps; it also sets them, unless the FAST kernel did: the
+// cell-row strips (form 4) always, the general block kernel when the pass
+// cannot flag a band's cells (more than CA_MAX_CELLS cells per row).
+bool cell_form(const Plan* P) {
+    const int f = P->tun.fast_cell_tiles;
+    return P->cell_tiles && (f == 1 || f == 2);
 }
+bool strip_form(const Plan* P) { return P->strip_ok && P->tun.fast_cell_tiles == 4; }
+bool warp_form(const Plan* P) { return P->tun.fast_cell_tiles == 3 && P->apply_flags; }
+bool fast_sets_flags(const Plan* P) { return strip_form(P) || (!cell_form(P) && !P->apply_flags); }
 
 int plan_fast_bps(const Plan* P) {
     if (P->aligned_ok && P->tun.fast_cell_tiles == 2) return fast_aligned_blocks_per_sm();
     if (cell_form(P)) return fast_cells_blocks_per_sm(P->s.cell);
+    if (strip_form(P)) return fast_cstrip_blocks_per_sm();
     if (warp_form(P)) return fast_warp_blocks_per_sm();
-    return fast_blocks_per_sm(P->tun.fast_tile_h, thr_mode(P) == 2);
+    return fast_blocks_per_sm(P->tun.fast_tile_h, fast_sets_flags(P));
 }
 
 void free_plan(Plan* p) {
@@ -382,6 +385,10 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                 launch_fast_aligned(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfal() + G.fal_off, G.n_list,
                                     G.fal_tiles, P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                                     H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+            else if (strip_form(P))
+                launch_fast_cstrip(P->d_img(), P->d_dl() + G.dl_begin, P->d_gcs() + G.cs_off, G.n_list, G.cs_strips,
+                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                                   H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
             else if (cell_form(P))
                 launch_fast_cells(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfp() + G.fp_off, G.n_list, G.fast_tiles,
                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
@@ -393,24 +400,25 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
             else if (P->tun.fast_tile_h == 64)
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list, G.nms64_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, thr_mode(P) == 2, 64);
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, fast_sets_flags(P), 64);
             else if (P->tun.fast_tile_h == FT_HS[0] || P->tun.fast_tile_h == FT_HS[1]) {
                 const int i = P->tun.fast_tile_h == FT_HS[0] ? 0 : 1;
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gft(i) + G.ftall_off[i], G.n_list,
                             G.ftall_tiles[i], P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, thr_mode(P) == 2, FT_HS[i]);
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, fast_sets_flags(P),
+                            FT_HS[i]);
             }
             else
                 launch_fast(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
                             P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, thr_mode(P) == 2, 32);
+                            H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, fast_sets_flags(P), 32);
             break;
         case 2: {
-            const int mode = thr_mode(P);
-            if (mode == 0 || mode == 1)
+            if (!cell_form(P))
                 launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list, G.n_bands,
-                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st, true, mode == 0);
-            const bool fin = mode <= 0;
+                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st,
+                                  strip_form(P) ? 2 : fast_sets_flags(P) ? 0 : 1, true);
+            const bool fin = true;
             if (P->tun.nms_tile_h == 64)
                 launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list,
                                   G.nms64_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
@@ -520,6 +528,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     // Cell tiles: FAST applies the per-cell threshold itself (cells of 8..30 pixels).
     P->cell_tiles = s.cell >= CT_MIN_CELL && s.cell <= CT_MAX_CELL;
     P->aligned_ok = P->cell_tiles && fast_aligned_ok(s.cell);
+    P->strip_ok = s.cell <= CS_MAX_CELL;
     // The threshold pass flags the cells itself when a band's cells fit its
     // shared array; otherwise the general FAST kernel sets them.
     P->apply_flags = true;
@@ -678,6 +687,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             G.np_off = (int)P->gp_nms64.size();
             for (int i = 0; i < 2; ++i) G.ftall_off[i] = (int)P->gp_ftall[i].size();
             G.fal_off = (int)P->gp_fal.size();
+            G.cs_off = (int)P->gp_cstrip.size();
             for (int j = j0; j < j1; ++j) {
                 const Img& I = P->h_img[P->det_list[j]];
                 P->gp_nms64.push_back(G.nms64_tiles);
@@ -695,6 +705,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
                 G.fast_tiles += P->cell_tiles ? I.ftiles_x * ((I.ncy + ct_cell_rows(s.cell) - 1) / ct_cell_rows(s.cell)) : 0;
                 P->gp_rows.push_back(G.n_bands);
                 G.n_bands += I.ncy;
+                P->gp_cstrip.push_back(G.cs_strips);
+                G.cs_strips += P->strip_ok ? I.tiles_x * I.ncy : 0;
             }
             G.slot_begin = P->h_img[G.img_begin].slot0;
             G.slot_end = f1 < nf ? P->h_img[f1 * nl].slot0 : P->total_slots;
@@ -747,13 +759,14 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.fast_tile_h = 32;
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
     P->tun.nms_tile_h = 64;
-    P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64, thr_mode(P) <= 0);
+    P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64, true);
     for (int i = 0; i < 2; ++i)  // raise the tall kernels' shared-memory limits before any capture
         for (int fl = 0; fl < 2; ++fl) fast_blocks_per_sm(FT_HS[i], fl != 0);
     for (int th = 32; th <= 128; th *= 2)
         for (int fin = 0; fin < 2; ++fin) nms_blocks_per_sm(th, fin != 0);
     fast_aligned_blocks_per_sm();  // raises the cell-aligned kernel's shared-memory limit
-    fast_warp_blocks_per_sm();     // ... and the per-warp kernel's
+    fast_warp_blocks_per_sm();     // ... and the per-warp kernels'
+    fast_cstrip_blocks_per_sm();
     P->tun.fast_order = 0;
     P->tun.nms_order = 0;
 
@@ -813,6 +826,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     }
     P->off_gfal = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_fal.size(), 1), 16);
+    P->off_gcs = off;
+    off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_cstrip.size(), 1), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -840,6 +855,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_gnp, P->gp_nms64.data(), sizeof(int32_t) * P->gp_nms64.size());
     for (int i = 0; i < 2; ++i) put(P->off_gft[i], P->gp_ftall[i].data(), sizeof(int32_t) * P->gp_ftall[i].size());
     put(P->off_gfal, P->gp_fal.data(), sizeof(int32_t) * P->gp_fal.size());
+    put(P->off_gcs, P->gp_cstrip.data(), sizeof(int32_t) * P->gp_cstrip.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);
@@ -1086,10 +1102,11 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     best = 1e30f;
     int bb = P->tun.fast_blocks_per_sm, bo = 0, bv = P->tun.fast_cell_tiles, bt = P->tun.fast_tile_h;
     // Forms: general kernel (32-, 64-, 128- or 256-row tiles), cell tiles (1),
-    // cell-aligned general kernel (2), general kernel with per-warp pipelines (3).
-    for (int cand = 0; cand < 7 && rc == OF_OK; ++cand) {
+    // cell-aligned general kernel (2), general kernel with per-warp pipelines
+    // (3), cell strips with per-warp pipelines (4).
+    for (int cand = 0; cand < 8 && rc == OF_OK; ++cand) {
         const int v = cand < 4 ? 0 : cand - 3, th = cand < 4 ? 32 << cand : 32;
-        if ((v == 1 && !P->cell_tiles) || (v == 2 && !P->aligned_ok)) continue;
+        if ((v == 1 && !P->cell_tiles) || (v == 2 && !P->aligned_ok) || (v == 4 && !P->strip_ok)) continue;
         P->tun.fast_cell_tiles = v;
         P->tun.fast_tile_h = th;
         for (int bp = 1; bp <= plan_fast_bps(P) && rc == OF_OK; ++bp) {
@@ -1120,7 +1137,7 @@ int autotune_plan(of_handle* H, Plan* P, int reps) {
     bb = P->tun.nms_blocks_per_sm, bo = 0;
     int bth = P->tun.nms_tile_h;
     for (int th = 32; th <= 128 && rc == OF_OK; th *= 2)
-    for (int bp = 1; bp <= nms_blocks_per_sm(th, thr_mode(P) <= 0) && rc == OF_OK; ++bp) {
+    for (int bp = 1; bp <= nms_blocks_per_sm(th, true) && rc == OF_OK; ++bp) {
         for (int order = 0; order < 2 && rc == OF_OK; ++order) {
             P->tun.nms_tile_h = th;
             P->tun.nms_blocks_per_sm = bp;
@@ -1359,7 +1376,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         (t->fast_tile_h != 32 && t->fast_tile_h != 64 && t->fast_tile_h != FT_HS[0] && t->fast_tile_h != FT_HS[1]) ||
         t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h, false) || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
-        t->fast_cell_tiles < 0 || t->fast_cell_tiles > 3)
+        t->fast_cell_tiles < 0 || t->fast_cell_tiles > 4)
         return fail(OF_ERR_ARG, "tuning field out of range");
     Plan* P = nullptr;
     const int rc = prepare_batch(H, frames, n_frames, levels, scale, fast_t, harris_k, n_features, out_kpts,
@@ -1368,10 +1385,11 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
     P->tun.resize_tile_h = t->resize_tile_h;
     P->tun.resize_tma = t->resize_tma;
     // Forms the cell size does not allow fall back: aligned -> cell tiles -> general.
-    P->tun.fast_cell_tiles = t->fast_cell_tiles == 3                     ? 3
-                             : !P->cell_tiles                           ? 0
-                             : (t->fast_cell_tiles == 2 && !P->aligned_ok) ? 1
-                                                                          : t->fast_cell_tiles;
+    P->tun.fast_cell_tiles = t->fast_cell_tiles == 3                              ? 3
+                             : t->fast_cell_tiles == 4                            ? (P->strip_ok ? 4 : 0)
+                             : !P->cell_tiles                                     ? 0
+                             : (t->fast_cell_tiles == 2 && !P->aligned_ok)        ? 1
+                                                                                   : t->fast_cell_tiles;
     P->tun.fast_tile_h = t->fast_tile_h;
     P->tun.fast_blocks_per_sm = std::min(t->fast_blocks_per_sm, plan_fast_bps(P));
     P->tun.nms_blocks_per_sm = t->nms_blocks_per_sm;
@@ -1598,10 +1616,7 @@ int64_t of_inspect(of_handle* H, int what, int frame, int level, void* dst, int6
             OF_CK(cudaMemcpy2DAsync(d + (size_t)s.border * I.w + s.border, I.w,
                                     I.score + (size_t)s.border * I.spitch + s.border, I.spitch, rw,
                                     rh, cudaMemcpyDeviceToDevice, st));
-        if (thr_mode(P) >= 1)  // NMS applies the thresholds and proposal tiles itself: apply them here too
-            ofk::launch_inspect_score_apply(P->d_img(), frame * nl + level, d, s.t_hi, s.t_lo, s.border, s.cell, st);
-        else
-            ofk::launch_inspect_score(d, bytes, s.t_lo - 1, st);  // the maps hold s - (t_lo - 1)
+        ofk::launch_inspect_score(d, bytes, s.t_lo - 1, st);  // the maps hold s - (t_lo - 1)
         OF_CK(cudaGetLastError());
     } else if (what == OF_BUF_CELLT) {
         ofk::launch_inspect_cells(P->d_img(), frame * nl + level, s.t_hi, s.t_lo, d, st);

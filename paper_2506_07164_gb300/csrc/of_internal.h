@@ -153,10 +153,18 @@ void launch_fast_warp(const Img* imgs, const int32_t* img_list, const int32_t* t
                       const CUtensorMap* maps, const Call* call, int t_lo, int border, int grid, int order,
                       void* stream);
 int fast_warp_blocks_per_sm();
-// Threshold pass: flags: sets the cell flags (when the general FAST kernel
-// did not); apply: applies them to the maps (else NMS applies them).
+// Cell-row strips (one cell row of one 128-column tile per warp item; cells
+// of 8..33 pixels): general FAST that also sets the cell flags exactly.
+constexpr int CS_MAX_CELL = 33;
+void launch_fast_cstrip(const Img* imgs, const int32_t* img_list, const int32_t* strip_prefix, int n_list,
+                        int n_strips, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
+                        int cell, int grid, int order, void* stream);
+int fast_cstrip_blocks_per_sm();
+// Threshold pass: flags 1: sets the cell flags (when the FAST kernel did
+// not), 2: only for images with proposal tiles, 0: never; apply: applies them
+// to the maps (else NMS applies them on its staged tiles).
 void launch_cell_apply(const Img* imgs, const int32_t* img_list, const int32_t* band_prefix, int n_list, int n_bands,
-                       int t_hi, int t_lo, int border, int cell, int grid, void* stream, bool flags, bool apply = true);
+                       int t_hi, int t_lo, int border, int cell, int grid, void* stream, int flags, bool apply = true);
 constexpr int CA_MAX_CELLS = 1024;  // cells per band row the threshold pass can flag itself
 void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix,
                        int n_list, int n_tiles, const CUtensorMap* img_maps,
@@ -173,8 +181,6 @@ void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t*
                           void* stream);
 void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream);
 void launch_inspect_score(uint8_t* dst, int64_t n, int off, void* stream);
-void launch_inspect_score_apply(const Img* imgs, int img, uint8_t* dst, int t_hi, int t_lo, int border, int cell,
-                                void* stream);
 int select_smem_bytes(int max_quota);
 // Paper ablation variants (k_ablation.cu); returns the number of launches.
 int launch_variant(int fast_v, int harris_v, const uint8_t* img, int w, int h, int pitch, int t, int border,

@@ -156,9 +156,9 @@ def test_partial_proposal_same_under_every_fast_form():
     """With the committed network and threshold (about 3/4 of the tiles
     proposed), the learned path gives the same records whichever FAST form
     the plan runs: general kernel + threshold pass, cell tiles, the
-    cell-aligned general kernel, or the per-warp general kernel + threshold
-    pass -- each restricts scores and cell flags to the proposed tiles the
-    same way."""
+    cell-aligned general kernel, the per-warp general kernel + threshold
+    pass, or the per-warp cell strips -- each restricts scores and cell flags
+    to the proposed tiles the same way."""
     import json
 
     meta = json.load(open(learned.DEFAULT_META))
@@ -168,7 +168,7 @@ def test_partial_proposal_same_under_every_fast_form():
     fr = [(t, t.shape[1], t.shape[0], t.stride(0)) for t in dev]
     det = ofg.Detector(1920, 1080, max_levels=8, max_features=1000, max_batch=2, fast_t_lo=7)
     got = []
-    for form in (0, 1, 2, 3):
+    for form in (0, 1, 2, 3, 4):
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
                            stream_groups=1, fast_cell_tiles=form, nms_tile_h=64, fast_tile_h=128)
         det.set_tuning(dev, tun, levels=8, fast_t=20, n_features=1000)
@@ -177,7 +177,7 @@ def test_partial_proposal_same_under_every_fast_form():
         assert 0 < st["proposed"] < st["tiles"], st
         torch.cuda.synchronize()
         got.append(det.batch_results(2, 1000))
-    for k in (1, 2, 3):
+    for k in (1, 2, 3, 4):
         for a, b in zip(got[0], got[k]):
             assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), k
     det.close()

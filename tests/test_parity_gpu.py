@@ -376,7 +376,7 @@ def test_set_tuning_rejects_out_of_range_fields():
     good = dict(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=1, nms_blocks_per_sm=1, stream_groups=1,
                 nms_tile_h=32, fast_tile_h=32)
     for bad in (dict(resize_tile_h=48), dict(resize_tma=2), dict(fast_blocks_per_sm=0),
-                dict(nms_blocks_per_sm=1000), dict(fast_order=2), dict(stream_groups=9), dict(stream_groups=0), dict(fast_cell_tiles=4),
+                dict(nms_blocks_per_sm=1000), dict(fast_order=2), dict(stream_groups=9), dict(stream_groups=0), dict(fast_cell_tiles=5),
                 dict(nms_tile_h=48), dict(fast_tile_h=16)):
         with pytest.raises(ofg.OfError):
             det.set_tuning([img], ofg.OfTuning(**{**good, **bad}), levels=2, n_features=50)
@@ -424,7 +424,7 @@ def test_cell_sizes_both_fast_forms(cell):
     det = ofg.Detector(900, 700, max_levels=3, max_features=600, fast_t_lo=6, cell=cell)
     ora = oracle.detect(img, levels=3, scale=1.2, fast_t=22, fast_t_lo=6, n_features=600, cell=cell)
     for form, nms_h, fast_h in ((0, 32, 32), (1, 64, 32), (0, 64, 64), (0, 128, 128), (0, 32, 256), (1, 128, 32),
-                                (2, 64, 32), (3, 64, 32)):
+                                (2, 64, 32), (3, 64, 32), (4, 64, 32)):
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
                            stream_groups=1, fast_cell_tiles=form, nms_tile_h=nms_h, fast_tile_h=fast_h)
         det.set_tuning([dev], tun, levels=3, scale=1.2, fast_t=22, n_features=600)

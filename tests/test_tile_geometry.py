@@ -164,3 +164,42 @@ def test_cell_aligned_tiles(cell):
             assert xoff0 >= 4 and xoff0 + 4 * 31 + 7 < SROW
             assert gx0 + 4 * 32 >= x_lo + AL_T
         assert b + ftiles_x * AL_T >= w - b and b + ftiles_y * AL_T >= h - b
+
+
+def test_per_warp_general_tiles():
+    """k_fast_warp: one 128 x 32 detect tile per warp item, one 160 x 40 box from
+    (X0 - 16, Y0 - 4); two halves of 16 rows, each reading staged rows r0 + 1 .. r0 + 22."""
+    b = 19
+    for r0 in (0, 16):
+        assert r0 + 1 >= 0 and r0 + 15 + 7 < IMG_BOX_ROWS
+    assert HALO_X - 4 >= 0 and HALO_X + 4 * 31 + 7 < SROW
+    for w, h in det_levels(b):
+        tile_x0 = b & ~15
+        tiles_x = ceil_div(w - b - tile_x0, TILE_W)
+        for tx in range(tiles_x):
+            assert (tile_x0 + tx * TILE_W - HALO_X) % 16 == 0
+        assert tile_x0 + tiles_x * TILE_W >= w - b
+
+
+@pytest.mark.parametrize("cell", range(8, 34))
+def test_cell_row_strips(cell):
+    """k_fast_cstrip: one cell row of one 128-column detect tile column per warp item; one
+    160 x 40 box from (X0 - 16, y0 - 4); output row r < cell reads staged rows r + 1 .. r + 7;
+    the strip's cells fit the flag word."""
+    b = 19
+    assert (cell - 1) + 7 < IMG_BOX_ROWS
+    assert TILE_W // cell + 2 <= 32
+    for w, h in det_levels(b):
+        tile_x0 = b & ~15
+        tiles_x = ceil_div(w - b - tile_x0, TILE_W)
+        ncy = ceil_div(h - 2 * b, cell)
+        for tx in range(tiles_x):
+            X0 = tile_x0 + tx * TILE_W
+            assert (X0 - HALO_X) % 16 == 0
+            cx0 = (max(X0, b) - b) // cell
+            for lane in range(32):
+                x = X0 + 4 * lane
+                for xx in range(x, x + 4):
+                    if b <= xx < w - b:
+                        assert 0 <= (xx - b) // cell - cx0 < 32
+        assert b + ncy * cell >= h - b
