@@ -282,7 +282,10 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             using SMask = typename std::conditional<(RPT > 8), unsigned long long, uint32_t>::type;
             SMask smask = 0u;
             if (nrows > 0) {
-                uint32_t hw[RPT + 2][6];
+                // Interleaved pixel pairs: lanes (x, x+2) and (x+1, x+3).  Per staged
+                // row the words e0 = (x-1, x+1), e1 = (x, x+2), e2 = (x+1, x+3),
+                // e3 = (x+2, x+4) hold every horizontal neighbour of both pairs.
+                uint32_t hw[RPT + 2][4];
                 // FINAL: the in-region bytes of the three words this thread reads.
                 uint32_t cm_m = 0xFFFFFFFFu, cm_c = 0xFFFFFFFFu, cm_q = 0xFFFFFFFFu;
                 if (FINAL) {
@@ -304,26 +307,24 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
                         wc &= cm_c & rm;
                         wq &= cm_q & rm;
                     }
-                    hw[k][1] = __byte_perm(wm, 0u, 0x4342);  // (x-2, x-1)
-                    hw[k][2] = __byte_perm(wc, 0u, 0x4140);  // (x, x+1)
-                    hw[k][3] = __byte_perm(wc, 0u, 0x4342);  // (x+2, x+3)
-                    hw[k][4] = __byte_perm(wq, 0u, 0x4140);  // (x+4, x+5)
+                    hw[k][0] = __byte_perm(wm, wc, 0x0503) & 0x00FF00FFu;  // (x-1, x+1)
+                    hw[k][1] = __byte_perm(wc, 0u, 0x4240);                 // (x, x+2)
+                    hw[k][2] = __byte_perm(wc, 0u, 0x4341);                 // (x+1, x+3)
+                    hw[k][3] = __byte_perm(wc, wq, 0x0402) & 0x00FF00FFu;  // (x+2, x+4)
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
 #pragma unroll
                     for (int pr = 0; pr < 2; ++pr) {
+                        // Pair pr: centre hw[.][1 + pr], left neighbour hw[.][pr], right hw[.][2 + pr].
                         const uint32_t* a = hw[r];
                         const uint32_t* c = hw[r + 1];
                         const uint32_t* d = hw[r + 2];
-                        const int j = 2 + pr;
-                        const uint32_t am = __byte_perm(a[j - 1], a[j], 0x5432), ap = __byte_perm(a[j], a[j + 1], 0x5432);
-                        const uint32_t cm = __byte_perm(c[j - 1], c[j], 0x5432), cp = __byte_perm(c[j], c[j + 1], 0x5432);
-                        const uint32_t dm = __byte_perm(d[j - 1], d[j], 0x5432), dp = __byte_perm(d[j], d[j + 1], 0x5432);
-                        const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(am, a[j], ap), __vimax3_u16x2(cm, cp, dm),
-                                                           __vimax3_u16x2(d[j], dp, dp));
+                        const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(a[pr], a[1 + pr], a[2 + pr]),
+                                                           __vimax3_u16x2(c[pr], c[2 + pr], d[pr]),
+                                                           __vimax3_u16x2(d[1 + pr], d[2 + pr], d[2 + pr]));
                         // Lane bit 15 set when centre > neighbours (values <= 255).
-                        const uint32_t keep = (c[j] + 0x7FFF7FFFu - nb) & 0x80008000u;
+                        const uint32_t keep = (c[1 + pr] + 0x7FFF7FFFu - nb) & 0x80008000u;
                         const int bit = 2 * (2 * r + pr);
                         smask |= (SMask)((keep >> 15) & 1u) << bit | (SMask)(keep >> 31) << (bit + 1);
                     }
@@ -344,8 +345,9 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             while (smask) {
                 const int bit = (RPT > 8 ? __ffsll((long long)smask) : __ffs((int)smask)) - 1;
                 smask &= smask - 1u;
+                // bit = 2 (2 row + pair) + lane: column 4 lane + pair + 2 lane
                 queue[slot++] = ((uint32_t)(ty * RPT + (bit >> 2)) << 16) |
-                                (uint32_t)(4 * lane + 2 * ((bit >> 1) & 1) + (bit & 1));
+                                (uint32_t)(4 * lane + ((bit >> 1) & 1) + 2 * (bit & 1));
             }
         }
         __syncthreads();
