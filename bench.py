@@ -293,18 +293,13 @@ def summarize_clocks(path: str):
 # detect tiles.
 ALU_LANES_PER_SM_CLK = 64
 FAST_OPS_PER_PX = 40.5
-# DRAM bytes of one k_fast launch per frame: dram__bytes_read.sum +
-# dram__bytes_write.sum of an ncu capture of one general-form launch over 64
-# 1080p frames with 8 levels, divided by 64.  Valid while k_fast.cu's code
-# (comments and blank lines removed: code_sha1) has this SHA-1.
-FAST_TRAFFIC = {"code_sha1": "d78cf16d738bf9b07f48ede0fcf7b7e109859a22", "bytes_per_frame": (519807488 + 353865472) / 64}
 # L2 (lts__t_bytes.sum) and DRAM (dram__bytes_read.sum + dram__bytes_write.sum)
 # bytes per frame of each stage's kernels, from one ncu capture of the
 # per-stage launches (of_time_stages) over a batch of 1080p frames with 8
 # levels, divided by the frames.  Valid while the kernels' code
 # (kernels_sha1) and the per-stage launch choices below are the ones captured;
 # otherwise the line reports null.
-STAGE_TRAFFIC = None
+STAGE_TRAFFIC = {"code_sha1": "83b2538e12334fff38ec7f01ac3d34f9d8833fe4", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 64}, "l2_bytes_per_frame": {"pyramid": 24137080, "fast": 29983456, "nms_harris": 52119019, "select": 3258846, "orient": 2463215}, "dram_bytes_per_frame": {"pyramid": 7739336, "fast": 12126084, "nms_harris": 22777044, "select": 1480648, "orient": 530292}}
 
 
 def code_sha1(path):
@@ -331,6 +326,12 @@ def kernels_sha1():
 
 
 STAGE_TUNING_FIELDS = ("resize_tma", "resize_tile_h", "fast_cell_tiles", "fast_tile_h", "nms_tile_h")
+
+
+def traffic_ok(tuning):
+    """STAGE_TRAFFIC describes these kernels and launch choices."""
+    return (STAGE_TRAFFIC is not None and STAGE_TRAFFIC["code_sha1"] == kernels_sha1() and
+            all(int(tuning.get(k, -1)) == STAGE_TRAFFIC["tuning"][k] for k in STAGE_TUNING_FIELDS))
 
 
 def detect_region_pixels(lw, lh):
@@ -706,12 +707,10 @@ def main():
         peak_alu = n_sms * ALU_LANES_PER_SM_CLK * sm_max * 1e6 / 1e9
         kname = {0: "k_fast", 1: "k_fast_cells", 2: "k_fast_aligned", 3: "k_fast_warp",
                  4: "k_fast_cstrip"}[int(tuning.get("fast_cell_tiles", 0))]
-        ok = kname == "k_fast" and code_sha1(
-            os.path.join(ROOT, "paper_2506_07164_gb300", "csrc", "k_fast.cu")) == FAST_TRAFFIC["code_sha1"]
         roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 1), "peak": round(peak_alu, 1),
                     "peak_kind": f"derived: {n_sms} SMs x {ALU_LANES_PER_SM_CLK} ALU lanes/clk x {sm_max:.0f} MHz",
                     "unit": "Gop/s", "frac": round(achieved / peak_alu, 4),
-                    "traffic": round(FAST_TRAFFIC["bytes_per_frame"] * B) if ok else None,
+                    "traffic": round(STAGE_TRAFFIC["dram_bytes_per_frame"]["fast"] * B) if traffic_ok(tuning) else None,
                     "algorithmic_bytes": per_frame[1] * B,
                     "hbm_frac_of_measured": stage_hbm["fast"], "hbm_peak_gbs": peak}
     else:
@@ -728,9 +727,7 @@ def main():
     roofline["read_peaks_gbs"] = {"l2": peaks_rd["l2"], "hbm": peaks_rd["hbm"],
                                   "how": "of_probe_read: 16-byte L2-only loads, 8x256 threads per SM; L2: best "
                                          "of 8..48 MB buffers read repeatedly; HBM: a 4 GiB buffer"}
-    st_ok = (STAGE_TRAFFIC is not None and STAGE_TRAFFIC["code_sha1"] == kernels_sha1() and
-             all(int(tuning.get(k, -1)) == STAGE_TRAFFIC["tuning"][k] for k in STAGE_TUNING_FIELDS))
-    if st_ok:
+    if traffic_ok(tuning):
         l2b, drb = STAGE_TRAFFIC["l2_bytes_per_frame"], STAGE_TRAFFIC["dram_bytes_per_frame"]
         roofline["stage_l2_gbs"] = {n: round(l2b[n] * B / (stage_ms[i] / 1000.0) / 1e9, 1)
                                     for i, n in enumerate(ofg.STAGE_NAMES)}
