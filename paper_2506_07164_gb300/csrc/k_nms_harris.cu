@@ -114,9 +114,131 @@ struct NmsGeom {
     static constexpr int S_BUF_N = (((S_LOADS - 1) * S_STEP + SCORE_BOX_ROWS) * SROW + 127) / 128 * 128;
     static constexpr int I_BUF_N = (I_LOADS * I_BOX + 127) / 128 * 128;
     static constexpr int QCAP_N = TILE_W * TH / 4;                          // strict maxima are never adjacent
-    static constexpr int DYN_BYTES = 2 * I_BUF_N + 2 * S_BUF_N + 4 * QCAP_N + 128;  // + alignment slack
+    static constexpr int QBYTES = (2 * QCAP_N + 127) / 128 * 128;             // 16-bit entries
+    static constexpr int DYN_BYTES = 2 * I_BUF_N + 2 * S_BUF_N + QBYTES + 128;  // + alignment slack
     static_assert((S_STEP * SROW) % 128 == 0 && I_BOX % 128 == 0, "TMA destinations on 128-byte boundaries");
 };
+
+// Queue entries: (tile row << 7) | tile column (rows and columns below 128).
+__device__ __forceinline__ uint16_t q_entry(int row, int col) { return (uint16_t)((row << 7) | col); }
+
+// Step 2 for one thread: strict 3x3 maxima of its 4 columns x RPT rows of the
+// staged score rows sS (staged row 0 = tile row -1), appended to queue with
+// one shared atomic per warp (count in *nq).  MASK: the staged scores are the
+// raw maps, so bytes outside [lox, hix) x [ry0, ry1) are masked here.  Rows
+// below the detect region hold no survivor; a warp entirely below it only
+// takes part in the queue.
+template <bool MASK, int RPT>
+__device__ __forceinline__ void nms_queue(const uint8_t* __restrict__ sS, int X0, int Y0, int lox, int hix, int ry0,
+                                          int ry1, int lane, int ty, uint16_t* __restrict__ queue, int* nq) {
+    const int nrows = min(RPT, ry1 - (Y0 + ty * RPT));
+    // Survivor bits (2 * row + pair) * 2 + lane: 4 per row, 64-bit beyond 8 rows.
+    using SMask = typename std::conditional<(RPT > 8), unsigned long long, uint32_t>::type;
+    SMask smask = 0u;
+    if (nrows > 0) {
+        // Interleaved pixel pairs: lanes (x, x+2) and (x+1, x+3).  Per staged
+        // row the words e0 = (x-1, x+1), e1 = (x, x+2), e2 = (x+1, x+3),
+        // e3 = (x+2, x+4) hold every horizontal neighbour of both pairs.
+        uint32_t hw[RPT + 2][4];
+        // MASK: the in-region bytes of the three words this thread reads.
+        uint32_t cm_m = 0xFFFFFFFFu, cm_c = 0xFFFFFFFFu, cm_q = 0xFFFFFFFFu;
+        if (MASK) {
+            const int xc = X0 + 4 * lane;
+            cm_m = range_mask4(xc - 4, lox, hix);
+            cm_c = range_mask4(xc, lox, hix);
+            cm_q = range_mask4(xc + 4, lox, hix);
+        }
+#pragma unroll
+        for (int k = 0; k < RPT + 2; ++k) {
+            const uint8_t* row = sS + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
+            uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
+            uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
+            uint32_t wq = *reinterpret_cast<const uint32_t*>(row + 4);
+            if (MASK) {
+                const int iy = Y0 - 1 + ty * RPT + k;
+                const uint32_t rm = (iy >= ry0 && iy < ry1) ? 0xFFFFFFFFu : 0u;
+                wm &= cm_m & rm;
+                wc &= cm_c & rm;
+                wq &= cm_q & rm;
+            }
+            hw[k][0] = __byte_perm(wm, wc, 0x0503) & 0x00FF00FFu;  // (x-1, x+1)
+            hw[k][1] = __byte_perm(wc, 0u, 0x4240);                 // (x, x+2)
+            hw[k][2] = __byte_perm(wc, 0u, 0x4341);                 // (x+1, x+3)
+            hw[k][3] = __byte_perm(wc, wq, 0x0402) & 0x00FF00FFu;  // (x+2, x+4)
+        }
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {
+                // Pair pr: centre hw[.][1 + pr], left neighbour hw[.][pr], right hw[.][2 + pr].
+                const uint32_t* a = hw[r];
+                const uint32_t* c = hw[r + 1];
+                const uint32_t* d = hw[r + 2];
+                const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(a[pr], a[1 + pr], a[2 + pr]),
+                                                   __vimax3_u16x2(c[pr], c[2 + pr], d[pr]),
+                                                   __vimax3_u16x2(d[1 + pr], d[2 + pr], d[2 + pr]));
+                // Lane bit 15 set when centre > neighbours (values <= 255).
+                const uint32_t keep = (c[1 + pr] + 0x7FFF7FFFu - nb) & 0x80008000u;
+                const int bit = 2 * (2 * r + pr);
+                smask |= (SMask)((keep >> 15) & 1u) << bit | (SMask)(keep >> 31) << (bit + 1);
+            }
+        }
+    }
+    // A warp scan of the per-thread counts and one shared atomic per warp.
+    const int mine = RPT > 8 ? __popcll((unsigned long long)smask) : __popc((uint32_t)smask);
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int wbase = 0;
+    if (lane == 31 && incl) wbase = atomicAdd(nq, incl);
+    int slot = __shfl_sync(0xFFFFFFFFu, wbase, 31) + incl - mine;
+    while (smask) {
+        const int bit = (RPT > 8 ? __ffsll((long long)smask) : __ffs((int)smask)) - 1;
+        smask &= smask - 1u;
+        // bit = 2 (2 row + pair) + lane: column 4 lane + pair + 2 lane
+        queue[slot++] = q_entry(ty * RPT + (bit >> 2), 4 * lane + ((bit >> 1) & 1) + 2 * (bit & 1));
+    }
+}
+
+// Step 3-4 for the block: Harris sums and key of every queued survivor of the
+// tile at (X0, Y0) of image I, from its staged image rows sI; each warp
+// reserves its entries' slots in the image's candidate list with one atomic
+// (its latency hides behind the sums).  Block-uniform loop.
+template <int NT>
+__device__ __forceinline__ void harris_phase(const uint8_t* __restrict__ sI, const uint16_t* __restrict__ queue,
+                                             int count, const Img& I, int X0, int Y0, int64_t knum, int64_t kden,
+                                             int tid) {
+    const int lane = tid & 31, ty = tid >> 5;
+    for (int i0 = 0; i0 < count; i0 += NT) {
+        const int i = i0 + tid;
+        const int n_w = min(max(count - (i0 + 32 * ty), 0), 32);
+        int wb = 0;
+        if (lane == 0 && n_w > 0) wb = atomicAdd(&I.ctr[0], n_w);
+        int32_t A = 0, B = 0, C = 0;
+        int lx = 0, ly = 0;
+        if (i < count) {
+            const uint32_t e = queue[i];
+            lx = (int)(e & 127u);
+            ly = (int)(e >> 7);
+            harris_sums(sI, lx, ly, A, B, C);
+        }
+        const int slot = __shfl_sync(0xFFFFFFFFu, wb, 0) + lane;
+        if (i < count) {
+            const int64_t det = (int64_t)A * B - (int64_t)C * C;
+            const int64_t tr = (int64_t)A + B;
+            const int64_t key = kden * det - knum * tr * tr;
+            if (slot < I.cand_cap) {
+                I.ckey[slot] = (uint64_t)key ^ 0x8000000000000000ull;
+                I.cyx[slot] = ((uint32_t)(Y0 + ly) << 16) | (uint32_t)(X0 + lx);
+            } else {
+                I.ctr[2] = 1;  // cannot happen: survivors are an independent set
+            }
+        }
+    }
+}
 
 // FINAL: the score maps already hold S(p) inside the detect region (a FAST
 // kernel or the threshold pass applied the cell thresholds); the kernel masks
@@ -138,7 +260,7 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     uint8_t* nms_dyn = nms_dyn_raw + ((128u - (smem_u32(nms_dyn_raw) & 127u)) & 127u);
     uint8_t* ibuf = nms_dyn;
     uint8_t* sbuf = nms_dyn + 2 * I_BUF;
-    uint32_t* queue = reinterpret_cast<uint32_t*>(nms_dyn + 2 * I_BUF + 2 * S_BUF);
+    uint16_t* queue = reinterpret_cast<uint16_t*>(nms_dyn + 2 * I_BUF + 2 * S_BUF);
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ NmsTile tinfo[2];
     __shared__ int nq;
@@ -273,112 +395,11 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
             __syncthreads();
         }
 
-        // 2. Strict 3x3 maxima, two pixels per register.  Rows of this warp
-        //    inside the detect region (warp-uniform); rows below it hold no
-        //    survivor, so a warp entirely below it only takes part in the queue.
-        {
-            const int nrows = min(RPT, ry1 - (Y0 + ty * RPT));
-            // Survivor bits (2 * row + pair) * 2 + lane: 4 per row, 64-bit beyond 8 rows.
-            using SMask = typename std::conditional<(RPT > 8), unsigned long long, uint32_t>::type;
-            SMask smask = 0u;
-            if (nrows > 0) {
-                // Interleaved pixel pairs: lanes (x, x+2) and (x+1, x+3).  Per staged
-                // row the words e0 = (x-1, x+1), e1 = (x, x+2), e2 = (x+1, x+3),
-                // e3 = (x+2, x+4) hold every horizontal neighbour of both pairs.
-                uint32_t hw[RPT + 2][4];
-                // FINAL: the in-region bytes of the three words this thread reads.
-                uint32_t cm_m = 0xFFFFFFFFu, cm_c = 0xFFFFFFFFu, cm_q = 0xFFFFFFFFu;
-                if (FINAL) {
-                    const int xc = X0 + 4 * lane;
-                    cm_m = range_mask4(xc - 4, lox, hix);
-                    cm_c = range_mask4(xc, lox, hix);
-                    cm_q = range_mask4(xc + 4, lox, hix);
-                }
-#pragma unroll
-                for (int k = 0; k < RPT + 2; ++k) {
-                    const uint8_t* row = sS + (ty * RPT + k) * SROW + HALO_X + 4 * lane;
-                    uint32_t wm = *reinterpret_cast<const uint32_t*>(row - 4);
-                    uint32_t wc = *reinterpret_cast<const uint32_t*>(row);
-                    uint32_t wq = *reinterpret_cast<const uint32_t*>(row + 4);
-                    if (FINAL) {
-                        const int iy = Y0 - 1 + ty * RPT + k;
-                        const uint32_t rm = (iy >= ry0 && iy < ry1) ? 0xFFFFFFFFu : 0u;
-                        wm &= cm_m & rm;
-                        wc &= cm_c & rm;
-                        wq &= cm_q & rm;
-                    }
-                    hw[k][0] = __byte_perm(wm, wc, 0x0503) & 0x00FF00FFu;  // (x-1, x+1)
-                    hw[k][1] = __byte_perm(wc, 0u, 0x4240);                 // (x, x+2)
-                    hw[k][2] = __byte_perm(wc, 0u, 0x4341);                 // (x+1, x+3)
-                    hw[k][3] = __byte_perm(wc, wq, 0x0402) & 0x00FF00FFu;  // (x+2, x+4)
-                }
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-#pragma unroll
-                    for (int pr = 0; pr < 2; ++pr) {
-                        // Pair pr: centre hw[.][1 + pr], left neighbour hw[.][pr], right hw[.][2 + pr].
-                        const uint32_t* a = hw[r];
-                        const uint32_t* c = hw[r + 1];
-                        const uint32_t* d = hw[r + 2];
-                        const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(a[pr], a[1 + pr], a[2 + pr]),
-                                                           __vimax3_u16x2(c[pr], c[2 + pr], d[pr]),
-                                                           __vimax3_u16x2(d[1 + pr], d[2 + pr], d[2 + pr]));
-                        // Lane bit 15 set when centre > neighbours (values <= 255).
-                        const uint32_t keep = (c[1 + pr] + 0x7FFF7FFFu - nb) & 0x80008000u;
-                        const int bit = 2 * (2 * r + pr);
-                        smask |= (SMask)((keep >> 15) & 1u) << bit | (SMask)(keep >> 31) << (bit + 1);
-                    }
-                }
-            }
-            // Queue the survivors: a warp scan of the per-thread counts and one
-            // shared atomic per warp.
-            const int mine = RPT > 8 ? __popcll((unsigned long long)smask) : __popc((uint32_t)smask);
-            int incl = mine;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            int wbase = 0;
-            if (lane == 31 && incl) wbase = atomicAdd(&nq, incl);
-            int slot = __shfl_sync(0xFFFFFFFFu, wbase, 31) + incl - mine;
-            while (smask) {
-                const int bit = (RPT > 8 ? __ffsll((long long)smask) : __ffs((int)smask)) - 1;
-                smask &= smask - 1u;
-                // bit = 2 (2 row + pair) + lane: column 4 lane + pair + 2 lane
-                queue[slot++] = ((uint32_t)(ty * RPT + (bit >> 2)) << 16) |
-                                (uint32_t)(4 * lane + ((bit >> 1) & 1) + 2 * (bit & 1));
-            }
-        }
+        // 2. Strict 3x3 maxima, two pixels per register, into the queue.
+        nms_queue<FINAL, RPT>(sS, X0, Y0, lox, hix, ry0, ry1, lane, ty, queue, &nq);
         __syncthreads();
-        const int count = nq;
-        for (int i0 = 0; i0 < count; i0 += DET_THREADS) {  // block-uniform
-            const int i = i0 + tid;
-            // Each warp reserves its entries' slots in the image's list; the
-            // atomic's latency hides behind the Harris sums.
-            const int n_w = min(max(count - (i0 + 32 * ty), 0), 32);
-            int wb = 0;
-            if (lane == 0 && n_w > 0) wb = atomicAdd(&I.ctr[0], n_w);
-            int32_t A = 0, B = 0, C = 0;
-            uint32_t e = 0u;
-            if (i < count) {
-                e = queue[i];
-                harris_sums(sI, (int)(e & 0xFFFFu), (int)(e >> 16), A, B, C);
-            }
-            const int slot = __shfl_sync(0xFFFFFFFFu, wb, 0) + lane;
-            if (i < count) {
-                const int lx = (int)(e & 0xFFFFu), ly = (int)(e >> 16);
-                const int64_t det = (int64_t)A * B - (int64_t)C * C;
-                const int64_t tr = (int64_t)A + B;
-                const int64_t key = kden * det - knum * tr * tr;
-                if (slot < I.cand_cap) {
-                    I.ckey[slot] = (uint64_t)key ^ 0x8000000000000000ull;
-                    I.cyx[slot] = ((uint32_t)(Y0 + ly) << 16) | (uint32_t)(X0 + lx);
-                } else {
-                    I.ctr[2] = 1;  // cannot happen: survivors are an independent set
-                }
-            }
-        }
+        // 3-4. Harris sums and keys of the survivors.
+        harris_phase<DET_THREADS>(sI, queue, nq, I, X0, Y0, knum, kden, tid);
         fence_proxy_async_smem();  // this thread's buffer accesses before the next TMA into them
         __syncthreads();
     }
