@@ -299,7 +299,7 @@ FAST_OPS_PER_PX = 40.5
 # levels, divided by the frames.  Valid while the kernels' code
 # (kernels_sha1) and the per-stage launch choices below are the ones captured;
 # otherwise the line reports null.
-STAGE_TRAFFIC = {"code_sha1": "83b2538e12334fff38ec7f01ac3d34f9d8833fe4", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 64}, "l2_bytes_per_frame": {"pyramid": 24137080, "fast": 29983456, "nms_harris": 52119019, "select": 3258846, "orient": 2463215}, "dram_bytes_per_frame": {"pyramid": 7739336, "fast": 12126084, "nms_harris": 22777044, "select": 1480648, "orient": 530292}}
+STAGE_TRAFFIC = {"code_sha1": "245d6ecc139c29fd721763648734be441ece8d6e", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 64}, "l2_bytes_per_frame": {"pyramid": 24117727, "fast": 29983730, "nms_harris": 52110658, "select": 3256850, "orient": 2453118}, "dram_bytes_per_frame": {"pyramid": 7739848, "fast": 12116776, "nms_harris": 22741904, "select": 1479320, "orient": 530304}}
 
 
 def code_sha1(path):
