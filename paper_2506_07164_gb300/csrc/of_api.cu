@@ -755,7 +755,10 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.resize_tile_h = RS_TILE_HS[1];
     P->tun.resize_tma = 1;
     P->tun.stream_groups = 1;
-    P->tun.fast_cell_tiles = P->cell_tiles ? 1 : 0;
+    // Untuned plans: a few frames per call are launch-bound, where the cell-tile
+    // form saves the threshold pass's launch; larger batches take the
+    // cell-row strips (form 4), the autotuner's choice on 1080p batches.
+    P->tun.fast_cell_tiles = (nf >= 4 && P->strip_ok) ? 4 : P->cell_tiles ? 1 : 0;
     P->tun.fast_tile_h = 32;
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
     P->tun.nms_tile_h = 64;

@@ -211,6 +211,40 @@ def test_other_scales_k_and_borders():
     det.close()
 
 
+@pytest.mark.parametrize("border,cell", [(4, 8), (8, 33), (31, 12), (15, 16)])
+def test_per_warp_fast_forms_other_borders_and_cells(border, cell):
+    """The per-warp FAST kernels (form 3, and form 4 whose strips are one cell
+    row high, cells up to 33 rows) on borders whose tile columns start at
+    x = 0 or 16 and on ragged sizes: the oracle's keypoints, cell thresholds
+    and candidate scores, in a 4-frame batch."""
+    sizes = [(701, 389), (333, 217), (640, 480), (129, 77)]
+    imgs = [synth.scene(w, h, 70 + i + cell, background="pink") for i, (w, h) in enumerate(sizes)]
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    radius = min(15, border)  # the centroid disc stays inside the image
+    det = ofg.Detector(701, 480, max_levels=4, max_features=400, max_batch=4, fast_t_lo=6, border=border, cell=cell,
+                       orient_radius=radius)
+    ora = [oracle.detect(im, levels=4, scale=1.2, fast_t=21, fast_t_lo=6, n_features=400, border=border, cell=cell,
+                         radius=radius) for im in imgs]
+    for form in (3, 4):
+        tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
+                           stream_groups=2, fast_cell_tiles=form, nms_tile_h=64, fast_tile_h=32)
+        det.set_tuning(dev, tun, levels=4, scale=1.2, fast_t=21, n_features=400)
+        det.detect_batch(dev, levels=4, scale=1.2, fast_t=21, n_features=400)
+        torch.cuda.synchronize()
+        for f, (im, got) in enumerate(zip(imgs, det.batch_results(len(imgs), 400))):
+            compare_keypoints(got, ora[f])
+            lev = oracle.pyramid_level(im, 4, 1.2, 1)
+            if lev.shape[0] <= 2 * border or lev.shape[1] <= 2 * border:
+                continue
+            sm, T, _ = oracle_cands(lev, border, cell, 21, 6)
+            g_T, _ = det.inspect(ofg.OF_BUF_CELLT, f, 1)
+            np.testing.assert_array_equal(g_T.reshape(T.shape), T, err_msg=f"form {form} frame {f} cells")
+            g_sm, _ = det.inspect(ofg.OF_BUF_SCORE, f, 1)
+            np.testing.assert_array_equal(g_sm.reshape(lev.shape), candidate_scores(sm, T, border, cell),
+                                          err_msg=f"form {form} frame {f} scores")
+    det.close()
+
+
 def test_rebinding_new_pointers():
     """Same shape, new frame pointers every call: level-0 tensor maps are
     rewritten in place between launches and must never be read stale."""
