@@ -299,7 +299,7 @@ FAST_OPS_PER_PX = 40.5
 # levels, divided by the frames.  Valid while the kernels' code
 # (kernels_sha1) and the per-stage launch choices below are the ones captured;
 # otherwise the line reports null.
-STAGE_TRAFFIC = {"code_sha1": "245d6ecc139c29fd721763648734be441ece8d6e", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 64}, "l2_bytes_per_frame": {"pyramid": 24117727, "fast": 29983730, "nms_harris": 52110658, "select": 3256850, "orient": 2453118}, "dram_bytes_per_frame": {"pyramid": 7739848, "fast": 12116776, "nms_harris": 22741904, "select": 1479320, "orient": 530304}}
+STAGE_TRAFFIC = {"code_sha1": "4472753352e8bd97efe6b35df646859ee9fcf15e", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 64}, "l2_bytes_per_frame": {"pyramid": 24169070, "fast": 30096538, "nms_harris": 52124423, "select": 3258757, "orient": 2455777}, "dram_bytes_per_frame": {"pyramid": 7737716, "fast": 12119084, "nms_harris": 22750364, "select": 1481184, "orient": 530344}}
 
 
 def code_sha1(path):

@@ -168,10 +168,12 @@ def test_cell_aligned_tiles(cell):
 
 def test_per_warp_general_tiles():
     """k_fast_warp: one 128 x 32 detect tile per warp item, one 160 x 40 box from
-    (X0 - 16, Y0 - 4); two halves of 16 rows, each reading staged rows r0 + 1 .. r0 + 22."""
+    (X0 - 16, Y0 - 4); chunks of FW_CHUNK rows, chunk r0 reading staged rows
+    r0 + 1 .. r0 + FW_CHUNK + 6."""
     b = 19
-    for r0 in (0, 16):
-        assert r0 + 1 >= 0 and r0 + 15 + 7 < IMG_BOX_ROWS
+    chunk = source_constants("of_internal.h", "k_fast.cu")["FW_CHUNK"]
+    for r0 in range(0, 32, chunk):
+        assert r0 + 1 >= 0 and r0 + 1 + chunk + 6 - 1 < IMG_BOX_ROWS
     assert HALO_X - 4 >= 0 and HALO_X + 4 * 31 + 7 < SROW
     for w, h in det_levels(b):
         tile_x0 = b & ~15
