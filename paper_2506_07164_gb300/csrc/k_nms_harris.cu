@@ -124,13 +124,14 @@ __device__ __forceinline__ uint16_t q_entry(int row, int col) { return (uint16_t
 
 // Step 2 for one thread: strict 3x3 maxima of its 4 columns x RPT rows of the
 // staged score rows sS (staged row 0 = tile row -1), appended to queue with
-// one shared atomic per warp (count in *nq).  MASK: the staged scores are the
+// one shared atomic per warp (count in *nq; with nq null the queue is the
+// warp's own and the count is returned).  MASK: the staged scores are the
 // raw maps, so bytes outside [lox, hix) x [ry0, ry1) are masked here.  Rows
 // below the detect region hold no survivor; a warp entirely below it only
 // takes part in the queue.
 template <bool MASK, int RPT>
-__device__ __forceinline__ void nms_queue(const uint8_t* __restrict__ sS, int X0, int Y0, int lox, int hix, int ry0,
-                                          int ry1, int lane, int ty, uint16_t* __restrict__ queue, int* nq) {
+__device__ __forceinline__ int nms_queue(const uint8_t* __restrict__ sS, int X0, int Y0, int lox, int hix, int ry0,
+                                         int ry1, int lane, int ty, uint16_t* __restrict__ queue, int* nq) {
     const int nrows = min(RPT, ry1 - (Y0 + ty * RPT));
     // Survivor bits (2 * row + pair) * 2 + lane: 4 per row, 64-bit beyond 8 rows.
     using SMask = typename std::conditional<(RPT > 8), unsigned long long, uint32_t>::type;
@@ -192,15 +193,18 @@ __device__ __forceinline__ void nms_queue(const uint8_t* __restrict__ sS, int X0
         const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= o) incl += v;
     }
+    // nq null: the queue is the warp's own (entries from 0; the count is returned).
     int wbase = 0;
-    if (lane == 31 && incl) wbase = atomicAdd(nq, incl);
+    if (nq != nullptr && lane == 31 && incl) wbase = atomicAdd(nq, incl);
     int slot = __shfl_sync(0xFFFFFFFFu, wbase, 31) + incl - mine;
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     while (smask) {
         const int bit = (RPT > 8 ? __ffsll((long long)smask) : __ffs((int)smask)) - 1;
         smask &= smask - 1u;
         // bit = 2 (2 row + pair) + lane: column 4 lane + pair + 2 lane
         queue[slot++] = q_entry(ty * RPT + (bit >> 2), 4 * lane + ((bit >> 1) & 1) + 2 * (bit & 1));
     }
+    return total;
 }
 
 // Step 3-4 for the block: Harris sums and key of every queued survivor of the
@@ -405,6 +409,305 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Per-warp pipelines on the 128 x 32 detect tiles.  Each warp walks its own
+// tiles with two shared-memory buffers of its own, one per box -- the tile's
+// 34 score rows (160 x 34 from (X0-16, Y0-1)) and its 40 image rows (160 x 40
+// from (X0-16, Y0-4)) -- each with its own mbarrier.  Per tile: wait for the
+// score box, run the 3x3 test into the warp's queue and refill the score
+// buffer with the next tile's box; wait for the image box, compute the Harris
+// keys of the queued survivors (rounds of 32, one survivor per lane; a 32-row
+// tile holds ~90 at t = 20, so lanes are ~90 % busy) and refill the image
+// buffer.  No block barrier: a warp never waits for another warp.
+//
+// APPLY: the maps hold s(p) - (t_lo - 1) where s(p) >= t_lo (FAST's output)
+// and the cell flags are set.  Each staged score word becomes S(p) in
+// registers as it is read (bytes below t_hi cleared in flagged cells), so
+// the maps need no threshold pass.  A lane thresholds its own word and the
+// halo word of the warp's edge (lane 0: columns X0-4..X0-1, lane 31:
+// X0+128..X0+131); the 3x3 test's outer neighbours come from lanes +-1.
+// A chunk of NW_CHUNK output rows reads 8 new staged rows, which lie in at
+// most two cell rows for cells of 8 or more rows.  Otherwise the maps hold
+// S(p) and only the detect region is masked.
+
+constexpr int NW_QCAP = TILE_W * TILE_H / 4;             // strict maxima are never adjacent
+constexpr int NW_SBUF = (S_BOX + 127) / 128 * 128;       // 5504
+constexpr int NW_BYTES = NW_SBUF + I_BOX + 2 * NW_QCAP;  // per warp: score box, image box, queue
+constexpr int NW_WARPS = DET_THREADS / 32;
+constexpr int NW_DYN = NW_WARPS * NW_BYTES + 128;        // + alignment slack
+constexpr int NW_CHUNK = 8;                              // output rows per unrolled chunk
+static_assert(NW_BYTES % 128 == 0 && NW_SBUF % 128 == 0, "TMA destinations on 128-byte boundaries");
+static_assert(TILE_H % NW_CHUNK == 0, "whole chunks per tile");
+
+// Bytes of a staged word in the detect region, split by cell: ma in cell ca,
+// mb in cell ca + 1 (a word's 4 bytes span at most two cells).
+struct WordCells {
+    uint32_t ma, mb;
+    int ca;
+};
+
+__device__ __forceinline__ WordCells word_cells(int xw, uint32_t cm, int lox, int rx0, int cell, uint32_t magic) {
+    WordCells c{0u, 0u, 0};
+    if (cm) {
+        c.ca = (int)__umulhi((uint32_t)(max(xw, lox) - rx0), magic);
+        c.ma = cm & range_mask4(xw, 0, rx0 + (c.ca + 1) * cell);
+        c.mb = cm & ~c.ma;
+    }
+    return c;
+}
+
+// 0xFF over the bytes of a word whose cell in cell row `crow` is flagged.
+__device__ __forceinline__ uint32_t word_flags(const WordCells& c, const uint32_t* __restrict__ crow) {
+    return (c.ma && crow[c.ca] ? c.ma : 0u) | (c.mb && crow[c.ca + 1] ? c.mb : 0u);
+}
+
+template <bool SMALL_T>
+__device__ __forceinline__ uint32_t threshold_word(uint32_t v, uint32_t fm, uint32_t th) {
+    return v & ((SMALL_T ? bytes_ge(v, th) : bytes_ge_any(v, th)) | ~fm);
+}
+
+template <bool APPLY, bool SMALL_T>
+__global__ void __launch_bounds__(DET_THREADS, 2)
+k_nms_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ prefix,
+           int n_list, int n_tiles, const CUtensorMap* __restrict__ img_maps,
+           const CUtensorMap* __restrict__ score_maps, const Call* __restrict__ call, int t_hi, int t_lo,
+           int border, int cell, uint32_t cell_magic, int order) {
+    extern __shared__ __align__(128) uint8_t nw_raw[];
+    uint8_t* const dyn = nw_raw + ((128u - (smem_u32(nw_raw) & 127u)) & 127u);
+    __shared__ __align__(8) uint64_t mbar[NW_WARPS][2];  // [0] score box, [1] image box
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint8_t* const sS = dyn + w * NW_BYTES;
+    uint8_t* const sI = sS + NW_SBUF;
+    uint16_t* const queue = reinterpret_cast<uint16_t*>(sI + I_BOX);
+    if (lane == 0) {
+        mbar_init(&mbar[w][0], 1);
+        mbar_init(&mbar[w][1], 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    const int nw = gridDim.x * NW_WARPS, gw = blockIdx.x * NW_WARPS + w;
+    auto locate = [&](int t) {
+        const int j = find_tile_job(prefix, n_list, t);
+        const int ii = __ldg(list + j);
+        const Img& I = imgs[ii];
+        const int tt = t - __ldg(prefix + j);
+        return NmsTile{ii, I.tile_x0 + (tt % I.tiles_x) * TILE_W, border + (tt / I.tiles_x) * TILE_H};
+    };
+    auto issue_s = [&](const NmsTile& ti) {  // lane 0
+        tensormap_acquire(score_maps + ti.img);
+        mbar_arrive_expect_tx(&mbar[w][0], S_BOX);
+        tma_load_2d(sS, score_maps + ti.img, ti.x0 - HALO_X, ti.y0 - 1, &mbar[w][0]);
+    };
+    auto issue_i = [&](const NmsTile& ti) {  // lane 0
+        tensormap_acquire(img_maps + ti.img);
+        mbar_arrive_expect_tx(&mbar[w][1], I_BOX);
+        tma_load_2d(sI, img_maps + ti.img, ti.x0 - HALO_X, ti.y0 - 4, &mbar[w][1]);
+    };
+    int t = tile_of(order, gw, nw, n_tiles, 0);
+    NmsTile cur{0, 0, 0};
+    if (t < n_tiles) {
+        cur = locate(t);
+        if (lane == 0) {
+            issue_s(cur);
+            issue_i(cur);
+        }
+    }
+    const int64_t knum = call->knum, kden = call->kden;
+    const uint32_t th = (uint32_t)(t_hi - t_lo + 1);  // t_hi in the maps' offset scores
+    for (int it = 0; t < n_tiles; ++it) {
+        const int tn = tile_of(order, gw, nw, n_tiles, it + 1);
+        const NmsTile nxt = tn < n_tiles ? locate(tn) : cur;
+        const uint32_t par = (uint32_t)(it & 1);
+        bool ok = mbar_wait(&mbar[w][0], par);
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            if (lane == 0) {
+                atomicOr(call->status, OF_DEV_TIMEOUT);
+                // Let this warp's copies in flight land before the block's shared memory can go away.
+                mbar_wait(&mbar[w][0], par, OF_WAIT_LIMIT_NS / 8);
+                mbar_wait(&mbar[w][1], par, OF_WAIT_LIMIT_NS / 8);
+            }
+            __syncwarp();
+            return;
+        }
+        const Img& I = imgs[cur.img];
+        const int X0 = cur.x0, Y0 = cur.y0;
+        int n = 0;
+        // Learned path: a tile whose four proposal tiles are off holds no survivor.
+        bool skip = false;
+        if (I.pmask) {
+            const int py = (Y0 - border) / TILE_H, px = (X0 - I.tile_x0) / TILE_W;
+            skip = *reinterpret_cast<const uint32_t*>(I.pmask + (size_t)py * 4 * I.tiles_x + 4 * px) == 0u;
+        }
+        if (!skip) {
+            const int rx0 = border, rx1 = I.w - border, ry0 = border, ry1 = I.h - border;
+            const int lox = max(rx0, X0 - 1), hix = min(rx1, X0 + TILE_W + 1);
+            const int xc = X0 + 4 * lane;
+            const int xh = lane == 0 ? X0 - 4 : X0 + TILE_W;  // the halo word (used by lanes 0 and 31)
+            const uint32_t cm_c = range_mask4(xc, lox, hix), cm_h = range_mask4(xh, lox, hix);
+            const int nrows = min(TILE_H, ry1 - Y0);
+            const uint8_t* const srow = sS + HALO_X + 4 * lane;
+            const int hoff = xh - xc;
+            WordCells wc_c{0u, 0u, 0}, wc_h{0u, 0u, 0};
+            const uint32_t* cellp = I.cell;
+            const int ncx = I.ncx;
+            if (APPLY) {
+                wc_c = word_cells(xc, cm_c, lox, rx0, cell, cell_magic);
+                wc_h = word_cells(xh, cm_h, lox, rx0, cell, cell_magic);
+            }
+            // Flag masks of staged row iy (APPLY): cell row of iy (rows outside the region are masked anyway).
+            auto flags_of = [&](int iy, uint32_t& fc, uint32_t& fh) {
+                const int cy = (int)__umulhi((uint32_t)max(iy - ry0, 0), cell_magic);
+                const uint32_t* crow = cellp + (size_t)min(cy, I.ncy - 1) * ncx;
+                fc = word_flags(wc_c, crow);
+                fh = word_flags(wc_h, crow);
+            };
+            // Staged row k (image row Y0 - 1 + k) as the four pair words of the 3x3 test.
+            auto load_row = [&](int k, uint32_t fc, uint32_t fh, uint32_t (&h)[4]) {
+                const int iy = Y0 - 1 + k;
+                const bool in = iy >= ry0 && iy < ry1;
+                const uint8_t* row = srow + k * SROW;
+                uint32_t vc = *reinterpret_cast<const uint32_t*>(row) & (in ? cm_c : 0u);
+                uint32_t vh = *reinterpret_cast<const uint32_t*>(row + hoff) & (in ? cm_h : 0u);
+                if (APPLY) {
+                    vc = threshold_word<SMALL_T>(vc, fc, th);
+                    vh = threshold_word<SMALL_T>(vh, fh, th);
+                }
+                uint32_t vm = __shfl_up_sync(0xFFFFFFFFu, vc, 1);
+                uint32_t vq = __shfl_down_sync(0xFFFFFFFFu, vc, 1);
+                if (lane == 0) vm = vh;
+                if (lane == 31) vq = vh;
+                h[0] = __byte_perm(vm, vc, 0x0503) & 0x00FF00FFu;  // (x-1, x+1)
+                h[1] = __byte_perm(vc, 0u, 0x4240);                 // (x, x+2)
+                h[2] = __byte_perm(vc, 0u, 0x4341);                 // (x+1, x+3)
+                h[3] = __byte_perm(vc, vq, 0x0402) & 0x00FF00FFu;  // (x+2, x+4)
+            };
+            uint32_t ha[4], hb[4];
+            {
+                uint32_t fc = 0u, fh = 0u;
+                if (APPLY) flags_of(Y0 - 1, fc, fh);
+                load_row(0, fc, fh, ha);
+                if (APPLY) flags_of(Y0, fc, fh);
+                load_row(1, fc, fh, hb);
+            }
+#pragma unroll 1
+            for (int r0 = 0; r0 < nrows; r0 += NW_CHUNK) {
+                // Staged rows r0+2 .. r0+9: cell rows A and (from row yb on) B.
+                uint32_t fa_c = 0u, fa_h = 0u, fb_c = 0u, fb_h = 0u;
+                int yb = 0;
+                if (APPLY) {
+                    const int iy0 = Y0 + 1 + r0;
+                    flags_of(iy0, fa_c, fa_h);
+                    const int cya = (int)__umulhi((uint32_t)max(iy0 - ry0, 0), cell_magic);
+                    yb = ry0 + (cya + 1) * cell;
+                    if (yb <= iy0 + NW_CHUNK - 1) flags_of(yb, fb_c, fb_h);
+                }
+                uint32_t smask = 0u;  // bit 4 r + 2 pair + lane half
+#pragma unroll
+                for (int r = 0; r < NW_CHUNK; ++r) {
+                    if (r0 + r >= nrows) break;
+                    uint32_t hc[4];
+                    const bool b_row = APPLY && Y0 + 1 + r0 + r >= yb;
+                    load_row(r0 + r + 2, b_row ? fb_c : fa_c, b_row ? fb_h : fa_h, hc);
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) {
+                        const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(ha[pr], ha[1 + pr], ha[2 + pr]),
+                                                           __vimax3_u16x2(hb[pr], hb[2 + pr], hc[pr]),
+                                                           __vimax3_u16x2(hc[1 + pr], hc[2 + pr], hc[2 + pr]));
+                        // Lane bit 15 set when centre > neighbours (values <= 255).
+                        const uint32_t keep = (hb[1 + pr] + 0x7FFF7FFFu - nb) & 0x80008000u;
+                        const int bit = 2 * (2 * r + pr);
+                        smask |= ((keep >> 15) & 1u) << bit | (keep >> 31) << (bit + 1);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        ha[q] = hb[q];
+                        hb[q] = hc[q];
+                    }
+                }
+                // Append the chunk's survivors: a warp scan of the per-lane counts.
+                const int mine = __popc(smask);
+                int incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                int slot = n + incl - mine;
+                n += __shfl_sync(0xFFFFFFFFu, incl, 31);
+                while (smask) {
+                    const int bit = __ffs((int)smask) - 1;
+                    smask &= smask - 1u;
+                    // bit = 2 (2 row + pair) + half: column 4 lane + pair + 2 half
+                    queue[slot++] = q_entry(r0 + (bit >> 2), 4 * lane + ((bit >> 1) & 1) + 2 * (bit & 1));
+                }
+            }
+        }
+        // The score buffer is free: fetch the next tile's score box.
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0 && tn < n_tiles) issue_s(nxt);
+        ok = mbar_wait(&mbar[w][1], par);
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            if (lane == 0) {
+                atomicOr(call->status, OF_DEV_TIMEOUT);
+                mbar_wait(&mbar[w][1], par, OF_WAIT_LIMIT_NS / 8);
+                if (tn < n_tiles) mbar_wait(&mbar[w][0], par ^ 1u, OF_WAIT_LIMIT_NS / 8);
+            }
+            __syncwarp();
+            return;
+        }
+        if (n > 0) harris_phase<32>(sI, queue, n, I, X0, Y0, knum, kden, lane);
+        fence_proxy_async_smem();
+        __syncwarp();  // every lane is done with the image box and the queue
+        if (lane == 0 && tn < n_tiles) issue_i(nxt);
+        cur = nxt;
+        t = tn;
+    }
+}
+
+template <bool APPLY, bool SMALL_T>
+static void launch_nms_warp_t(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
+                              int n_tiles, const CUtensorMap* img_maps, const CUtensorMap* score_maps,
+                              const Call* call, int t_hi, int t_lo, int border, int cell, int grid, int order,
+                              void* stream) {
+    const uint32_t magic = 0xFFFFFFFFu / (uint32_t)cell + 1u;
+    k_nms_warp<APPLY, SMALL_T><<<grid, DET_THREADS, NW_DYN, (cudaStream_t)stream>>>(
+        imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, magic,
+        order);
+}
+
+void launch_nms_warp(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list, int n_tiles,
+                     const CUtensorMap* img_maps, const CUtensorMap* score_maps, const Call* call, int t_hi,
+                     int t_lo, int border, int cell, int grid, int order, void* stream, bool apply) {
+    if (n_tiles <= 0) return;
+    const int warps = (n_tiles + NW_WARPS - 1) / NW_WARPS;
+    grid = grid < warps ? grid : warps;
+    apply = apply && t_hi != t_lo;
+    if (!apply)
+        launch_nms_warp_t<false, true>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call,
+                                       t_hi, t_lo, border, cell, grid, order, stream);
+    else if (t_hi - t_lo + 1 <= 128)
+        launch_nms_warp_t<true, true>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call,
+                                      t_hi, t_lo, border, cell, grid, order, stream);
+    else
+        launch_nms_warp_t<true, false>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call,
+                                       t_hi, t_lo, border, cell, grid, order, stream);
+}
+
+// Resident blocks per SM of the per-warp NMS kernel (also raises its dynamic shared-memory limit).
+int nms_warp_blocks_per_sm() {
+    int n = 0, m = 0;
+    const cudaError_t e0 = cudaFuncSetAttribute(k_nms_warp<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, NW_DYN);
+    const cudaError_t e1 = cudaFuncSetAttribute(k_nms_warp<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, NW_DYN);
+    const cudaError_t e2 = cudaFuncSetAttribute(k_nms_warp<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, NW_DYN);
+    if (e0 != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nms_warp<true, true>, DET_THREADS, NW_DYN) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_nms_warp<false, true>, DET_THREADS, NW_DYN) != cudaSuccess)
+        return 1;
+    n = n < m ? n : m;
+    return n < 1 ? 1 : n;
+}
+
 template <bool FINAL, int TH>
 void launch_nms_t(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list, int n_tiles,
                   const CUtensorMap* img_maps, const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,
@@ -449,6 +752,7 @@ static cudaError_t nms_occupancy(int* n) {
 }
 
 int nms_blocks_per_sm(int tile_h, bool final_scores) {
+    if (tile_h == 32 && final_scores) return nms_warp_blocks_per_sm();
     int n = 0;
     cudaError_t e;
     if (final_scores)

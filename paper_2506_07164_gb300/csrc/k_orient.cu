@@ -160,15 +160,29 @@ void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t*
     k_inspect_cells<<<64, 256, 0, (cudaStream_t)stream>>>(imgs, img, t_hi, t_lo, dst);
 }
 
-// Score-map copies: the map's offset scores back to S(p) (nonzero bytes + off).
-__global__ void k_inspect_score(uint8_t* d, int64_t n, int off) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        if (d[i]) d[i] = (uint8_t)(d[i] + off);
+// S(p) from a dense copy of a map: 0 outside proposed tiles and below t_hi in
+// flagged cells, else the offset score + t_lo - 1 (idempotent on final maps).
+__global__ void k_inspect_score_final(const Img* imgs, int img, uint8_t* d, int w, int h, int t_hi, int t_lo,
+                                      int border, int cell) {
+    const Img& I = imgs[img];
+    const int rw = w - 2 * border, rh = h - 2 * border;
+    if (rw <= 0 || rh <= 0) return;
+    const int64_t n = (int64_t)rw * rh;
+    const int th = t_hi - t_lo + 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = border + (int)(i % rw), y = border + (int)(i / rw);
+        uint8_t* p = d + (size_t)y * w + x;
+        int v = *p;
+        if (v == 0) continue;
+        if (t_hi != t_lo && v < th && I.cell[(size_t)((y - border) / cell) * I.ncx + (x - border) / cell]) v = 0;
+        if (I.pmask && I.pmask[(size_t)((y - border) >> 5) * 4 * I.tiles_x + ((x - I.tile_x0) >> 5)] == 0) v = 0;
+        *p = (uint8_t)(v ? v + t_lo - 1 : 0);
+    }
 }
 
-void launch_inspect_score(uint8_t* dst, int64_t n, int off, void* stream) {
-    if (n <= 0 || off == 0) return;
-    k_inspect_score<<<256, 256, 0, (cudaStream_t)stream>>>(dst, n, off);
+void launch_inspect_score_final(const Img* imgs, int img, uint8_t* d, int w, int h, int t_hi, int t_lo, int border,
+                                int cell, void* stream) {
+    k_inspect_score_final<<<256, 256, 0, (cudaStream_t)stream>>>(imgs, img, d, w, h, t_hi, t_lo, border, cell);
 }
 
 void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream) {

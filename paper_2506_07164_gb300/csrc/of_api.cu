@@ -292,6 +292,12 @@ bool cell_form(const Plan* P) {
 bool strip_form(const Plan* P) { return P->strip_ok && P->tun.fast_cell_tiles == 4; }
 bool warp_form(const Plan* P) { return P->tun.fast_cell_tiles == 3 && P->apply_flags; }
 bool fast_sets_flags(const Plan* P) { return strip_form(P) || (!cell_form(P) && !P->apply_flags); }
+// The per-warp NMS kernel (32-row tiles) applies the flags to its staged
+// score words itself; the pass then only sets flags where FAST did not (for
+// images with proposal tiles at least: FAST skips their flags).
+bool nms_applies(const Plan* P) {
+    return P->tun.nms_tile_h == 32 && !cell_form(P) && P->s.t_hi != P->s.t_lo;
+}
 
 int plan_fast_bps(const Plan* P) {
     if (P->aligned_ok && P->tun.fast_cell_tiles == 2) return fast_aligned_blocks_per_sm();
@@ -414,26 +420,28 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                             H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st, fast_sets_flags(P), 32);
             break;
         case 2: {
-            if (!cell_form(P))
-                launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list, G.n_bands,
-                                  s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st,
-                                  strip_form(P) ? 2 : fast_sets_flags(P) ? 0 : 1, true);
+            if (!cell_form(P)) {
+                const int flags = strip_form(P) ? 2 : fast_sets_flags(P) ? 0 : 1;
+                const bool apply = !nms_applies(P);
+                if (flags || apply)
+                    launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list,
+                                      G.n_bands, s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st, flags, apply);
+            }
             const bool fin = true;
-            if (P->tun.nms_tile_h == 64)
+            if (P->tun.nms_tile_h == 32)
+                launch_nms_warp(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
+                                P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
+                                H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, nms_applies(P));
+            else if (P->tun.nms_tile_h == 64)
                 launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list,
                                   G.nms64_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
                                   s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, fin,
                                   64);
-            else if (P->tun.nms_tile_h == FT_HS[0])  // same tiling as the 128-row FAST tiles
+            else  // 128 rows: the tiling of the 128-row FAST tiles
                 launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gft(0) + G.ftall_off[0], G.n_list,
                                   G.ftall_tiles[0], P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi,
                                   s.t_lo, s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st,
                                   fin, FT_HS[0]);
-            else
-                launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list,
-                                  G.det_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
-                                  s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, fin,
-                                  32);
             break;
         }
         case 3:
@@ -1377,7 +1385,7 @@ int of_set_tuning(of_handle* H, const of_frame* frames, int n_frames, int levels
         t->nms_blocks_per_sm < 1 ||
         (t->nms_tile_h != 32 && t->nms_tile_h != 64 && t->nms_tile_h != 128) ||
         (t->fast_tile_h != 32 && t->fast_tile_h != 64 && t->fast_tile_h != FT_HS[0] && t->fast_tile_h != FT_HS[1]) ||
-        t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h, false) || (t->fast_order != 0 && t->fast_order != 1) ||
+        t->nms_blocks_per_sm > nms_blocks_per_sm(t->nms_tile_h, true) || (t->fast_order != 0 && t->fast_order != 1) ||
         (t->nms_order != 0 && t->nms_order != 1) || t->stream_groups < 1 || t->stream_groups > kMaxGroups ||
         t->fast_cell_tiles < 0 || t->fast_cell_tiles > 4)
         return fail(OF_ERR_ARG, "tuning field out of range");
@@ -1619,7 +1627,9 @@ int64_t of_inspect(of_handle* H, int what, int frame, int level, void* dst, int6
             OF_CK(cudaMemcpy2DAsync(d + (size_t)s.border * I.w + s.border, I.w,
                                     I.score + (size_t)s.border * I.spitch + s.border, I.spitch, rw,
                                     rh, cudaMemcpyDeviceToDevice, st));
-        ofk::launch_inspect_score(d, bytes, s.t_lo - 1, st);  // the maps hold s - (t_lo - 1)
+        // The maps hold s - (t_lo - 1); the thresholds may still be pending (NMS applies them itself).
+        ofk::launch_inspect_score_final(P->d_img(), frame * nl + level, d, I.w, I.h, s.t_hi, s.t_lo, s.border,
+                                        s.cell, st);
         OF_CK(cudaGetLastError());
     } else if (what == OF_BUF_CELLT) {
         ofk::launch_inspect_cells(P->d_img(), frame * nl + level, s.t_hi, s.t_lo, d, st);

@@ -171,16 +171,29 @@ void launch_nms_harris(const Img* imgs, const int32_t* img_list, const int32_t* 
                        const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo,
                        int border, int cell, int grid, int order, void* stream,
                        bool final_scores = false, int tile_h = 32);
+// Resident blocks per SM of the NMS kernel a plan launches for tile_h (32 with
+// final scores: the per-warp kernel).
 int nms_blocks_per_sm(int tile_h, bool final_scores);
+// Per-warp NMS + Harris on the 128 x 32 detect tiles.  apply: the maps hold
+// FAST's offset scores and the cell flags are set (cells of 8 or more rows);
+// the kernel applies the per-cell thresholds to the staged words itself.
+// Otherwise the maps hold S(p).  Scores outside proposed tiles count as 0.
+void launch_nms_warp(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list, int n_tiles,
+                     const CUtensorMap* img_maps, const CUtensorMap* score_maps, const Call* call, int t_hi,
+                     int t_lo, int border, int cell, int grid, int order, void* stream, bool apply);
+int nms_warp_blocks_per_sm();
 void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, void* stream);
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
 // Slots [slot_begin, slot_end) of images [img_begin, img_begin + n_img) (one frame group).
 void launch_orient_range(const Img* imgs, int img_begin, int n_img, int slot_begin, int slot_end, const Call* call,
                          void* stream);
+// S(p) of image `img` from a dense w x h copy of its map (offset scores):
+// the per-cell thresholds and proposal tiles applied, t_lo - 1 added back.
+void launch_inspect_score_final(const Img* imgs, int img, uint8_t* d, int w, int h, int t_hi, int t_lo, int border,
+                                int cell, void* stream);
 void launch_inspect_cells(const Img* imgs, int img, int t_hi, int t_lo, uint8_t* dst,
                           void* stream);
 void launch_inspect_cands(const Img* imgs, int img, int n, uint8_t* dst, void* stream);
-void launch_inspect_score(uint8_t* dst, int64_t n, int off, void* stream);
 int select_smem_bytes(int max_quota);
 // Paper ablation variants (k_ablation.cu); returns the number of launches.
 int launch_variant(int fast_v, int harris_v, const uint8_t* img, int w, int h, int pitch, int t, int border,

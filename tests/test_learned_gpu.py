@@ -168,16 +168,18 @@ def test_partial_proposal_same_under_every_fast_form():
     fr = [(t, t.shape[1], t.shape[0], t.stride(0)) for t in dev]
     det = ofg.Detector(1920, 1080, max_levels=8, max_features=1000, max_batch=2, fast_t_lo=7)
     got = []
-    for form in (0, 1, 2, 3, 4):
+    # Every FAST form with the block NMS kernel, then forms 0, 1 and 4 with the
+    # per-warp NMS kernel (32-row tiles), which applies the thresholds itself.
+    for form, nms_h in ((0, 64), (1, 64), (2, 64), (3, 64), (4, 64), (0, 32), (1, 32), (4, 32)):
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
-                           stream_groups=1, fast_cell_tiles=form, nms_tile_h=64, fast_tile_h=128)
+                           stream_groups=1, fast_cell_tiles=form, nms_tile_h=nms_h, fast_tile_h=128)
         det.set_tuning(dev, tun, levels=8, fast_t=20, n_features=1000)
         st = ofg.of_detect_learned(det.h, fr, 8, 1.2, 20, 0.04, 1000, net.net, meta["threshold"],
                                    meta["min_confidence"], meta["dilate"], det.out, det.counts)
         assert 0 < st["proposed"] < st["tiles"], st
         torch.cuda.synchronize()
         got.append(det.batch_results(2, 1000))
-    for k in (1, 2, 3, 4):
+    for k in range(1, len(got)):
         for a, b in zip(got[0], got[k]):
             assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), k
     det.close()

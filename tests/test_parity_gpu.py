@@ -226,8 +226,9 @@ def test_per_warp_fast_forms_other_borders_and_cells(border, cell):
     ora = [oracle.detect(im, levels=4, scale=1.2, fast_t=21, fast_t_lo=6, n_features=400, border=border, cell=cell,
                          radius=radius) for im in imgs]
     for form in (3, 4):
+        # Form 4 with the per-warp NMS kernel (it applies the thresholds), form 3 with the block kernel.
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
-                           stream_groups=2, fast_cell_tiles=form, nms_tile_h=64, fast_tile_h=32)
+                           stream_groups=2, fast_cell_tiles=form, nms_tile_h={3: 64, 4: 32}[form], fast_tile_h=32)
         det.set_tuning(dev, tun, levels=4, scale=1.2, fast_t=21, n_features=400)
         det.detect_batch(dev, levels=4, scale=1.2, fast_t=21, n_features=400)
         torch.cuda.synchronize()
@@ -457,8 +458,9 @@ def test_cell_sizes_both_fast_forms(cell):
     dev = torch.from_numpy(img).cuda()
     det = ofg.Detector(900, 700, max_levels=3, max_features=600, fast_t_lo=6, cell=cell)
     ora = oracle.detect(img, levels=3, scale=1.2, fast_t=22, fast_t_lo=6, n_features=600, cell=cell)
+    # nms_h 32: the per-warp NMS kernel, which applies the cell thresholds itself after forms 0, 3 and 4
     for form, nms_h, fast_h in ((0, 32, 32), (1, 64, 32), (0, 64, 64), (0, 128, 128), (0, 32, 256), (1, 128, 32),
-                                (2, 64, 32), (3, 64, 32), (4, 64, 32)):
+                                (2, 64, 32), (3, 64, 32), (4, 64, 32), (1, 32, 32), (3, 32, 32), (4, 32, 32)):
         tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
                            stream_groups=1, fast_cell_tiles=form, nms_tile_h=nms_h, fast_tile_h=fast_h)
         det.set_tuning([dev], tun, levels=3, scale=1.2, fast_t=22, n_features=600)
