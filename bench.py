@@ -299,7 +299,7 @@ FAST_OPS_PER_PX = 40.5
 # levels, divided by the frames.  Valid while the kernels' code
 # (kernels_sha1) and the per-stage launch choices below are the ones captured;
 # otherwise the line reports null.
-STAGE_TRAFFIC = {"code_sha1": "4472753352e8bd97efe6b35df646859ee9fcf15e", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 64}, "l2_bytes_per_frame": {"pyramid": 24169070, "fast": 30096538, "nms_harris": 52124423, "select": 3258757, "orient": 2455777}, "dram_bytes_per_frame": {"pyramid": 7737716, "fast": 12119084, "nms_harris": 22750364, "select": 1481184, "orient": 530344}}
+STAGE_TRAFFIC = {"code_sha1": "3adfce6df75e369e911d44d4b5c787cca1569399", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 32}, "l2_bytes_per_frame": {"pyramid": 24129916, "fast": 30055492, "nms_harris": 37321938, "select": 3253813, "orient": 2455290}, "dram_bytes_per_frame": {"pyramid": 7740540, "fast": 12113236, "nms_harris": 14523904, "select": 1479620, "orient": 530348}}
 
 
 def code_sha1(path):
@@ -814,8 +814,12 @@ def main():
     pool.close()
 
     # Per frame group: one resize per level after the first, FAST, the threshold
-    # pass (general FAST form only), NMS + Harris, top-N, orientation.
-    per_group = (LEVELS - 1) + 4 + (0 if int(tuning.get("fast_cell_tiles", 0)) in (1, 2) else 1)
+    # pass (FAST forms 0, 3, 4; after the per-warp NMS kernel, which applies the
+    # thresholds itself, only where the FAST form leaves the flags to it: forms
+    # 0 and 3), NMS + Harris, top-N, orientation.
+    form = int(tuning.get("fast_cell_tiles", 0))
+    has_pass = form in (0, 3) or (form == 4 and int(tuning.get("nms_tile_h", 64)) != 32)
+    per_group = (LEVELS - 1) + 4 + (1 if has_pass else 0)
     kernels_per_step = per_group * int(tuning.get("stream_groups", 1))
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,

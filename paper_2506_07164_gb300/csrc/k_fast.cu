@@ -152,6 +152,18 @@ __device__ __forceinline__ uint32_t ring_ipair_score(const uint32_t (*e)[8], uin
     return pair_score(q, e[3][C + 3], kb);
 }
 
+// The same score with the 7 staged rows held in a rotating window: row k of
+// the ring (dy = k - 3) is slot (r + k) % 7.  r is a compile-time constant
+// once the caller's row loop is unrolled.
+template <int C>
+__device__ __forceinline__ uint32_t ring_ipair_score_rot(const uint32_t (*hw)[8], int r, uint32_t kb) {
+    uint32_t q[16];
+#define OF_LOAD_RRING(i, dx, dy) q[i] = hw[(r + 3 + (dy)) % 7][(dx) + C + 3];
+    OF_RING(OF_LOAD_RRING)
+#undef OF_LOAD_RRING
+    return pair_score(q, hw[(r + 3) % 7][C + 3], kb);
+}
+
 // Store the bytes of v selected by mask (0xFF per byte) at d: one word store
 // when all four are selected, else byte stores (the other bytes may belong
 // to a tile another block writes at the same time).
@@ -440,15 +452,18 @@ int fast_blocks_per_sm(int tile_h, bool flags) {
 // other shared-memory buffer while the lanes score the current one;
 // completion on the warp's own mbarrier, so a warp never waits for another
 // warp's tile.  A lane scores 4 pixels (two interleaved pairs) of every row,
-// in unrolled chunks of FW_CHUNK rows (the staged-row window is rebuilt at
-// the start of each chunk: 6 rows of words again, but the unrolled body stays
-// small enough for the instruction cache -- 8-row chunks ran 6% faster than
-// 16-row ones, a single 33-row chunk 24% slower).  The score map is as the general kernel's; the cell
+// in unrolled chunks of FW_CHUNK = 7 rows over a rotating window of 7 staged
+// rows (slot (k mod 7) holds staged row k's words, so the slots line up again
+// after each chunk and every staged row's words are built once).  The short
+// unrolled body fits the instruction cache: 8-row chunks that rebuilt the
+// window's 6 shared rows ran 6 % faster than 16-row chunks and a single
+// 33-row chunk 24 % slower; the rotating 7-row window is 2 % faster again.  The score map is as the general kernel's; the cell
 // flags are left to the threshold pass.
 
 constexpr int FW_WARPS = DET_THREADS / 32;
 constexpr int FW_DYN = FW_WARPS * 2 * FAST_BUF + 128;  // two buffers per warp + alignment slack
-constexpr int FW_CHUNK = 8;                              // output rows per unrolled chunk
+constexpr int FW_CHUNK = 7;                              // output rows per unrolled chunk (= window rows)
+static_assert(FW_CHUNK == 7, "the rotating window holds the 7 staged rows of one output row");
 
 __global__ void __launch_bounds__(DET_THREADS, 2)
 k_fast_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ prefix,
@@ -518,18 +533,18 @@ k_fast_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, cons
         const uint32_t colmask = range_mask4(x, border, I.w - border) & lane_on;
         uint8_t* const sdst = I.score + x;
         const size_t spitch = (size_t)I.spitch;
+        const uint8_t* const srow = s + SROW + HALO_X + 4 * lane;  // staged row of output row -3
+        uint32_t hw[7][8];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) staged_row_words(srow + k * SROW, hw[k]);
 #pragma unroll 1
         for (int r0 = 0; r0 < nrows; r0 += FW_CHUNK) {
-            uint32_t hw[FW_CHUNK + 6][8];
-            const uint8_t* const srow = s + (r0 + 1) * SROW + HALO_X + 4 * lane;  // staged row of output row r0 - 3
-#pragma unroll
-            for (int k = 0; k < 7; ++k) staged_row_words(srow + k * SROW, hw[k]);
 #pragma unroll
             for (int r = 0; r < FW_CHUNK; ++r) {
                 if (r0 + r >= nrows) break;
-                if (r > 0) staged_row_words(srow + (r + 6) * SROW, hw[r + 6]);
-                const uint32_t s0 = ring_ipair_score<0>(hw + r, kb);  // 512 + offset score per lane
-                const uint32_t s1 = ring_ipair_score<1>(hw + r, kb);
+                staged_row_words(srow + (r0 + r + 6) * SROW, hw[(r + 6) % FW_CHUNK]);
+                const uint32_t s0 = ring_ipair_score_rot<0>(hw, r, kb);  // 512 + offset score per lane
+                const uint32_t s1 = ring_ipair_score_rot<1>(hw, r, kb);
                 if (colmask != 0u)
                     *reinterpret_cast<uint32_t*>(sdst + (size_t)(Y0 + r0 + r) * spitch) =
                         __byte_perm(s0, s1, 0x6240) & colmask;
@@ -654,17 +669,18 @@ k_fast_cstrip(const Img* __restrict__ imgs, const int32_t* __restrict__ list, co
         }
         uint32_t mx0 = 0u, mx1 = 0u;
         const uint8_t* const srow = s + SROW + HALO_X + 4 * lane;  // staged row of output row -3
+        // Rotating window of 7 staged rows: each staged row's words are built once.
+        uint32_t hw[7][8];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) staged_row_words(srow + k * SROW, hw[k]);
 #pragma unroll 1
         for (int r0 = 0; r0 < nrows; r0 += FW_CHUNK) {
-            uint32_t hw[FW_CHUNK + 6][8];
-#pragma unroll
-            for (int k = 0; k < 7; ++k) staged_row_words(srow + (r0 + k) * SROW, hw[k]);
 #pragma unroll
             for (int r = 0; r < FW_CHUNK; ++r) {
                 if (r0 + r >= nrows) break;
-                if (r > 0) staged_row_words(srow + (r0 + r + 6) * SROW, hw[r + 6]);
-                const uint32_t s0 = ring_ipair_score<0>(hw + r, kb);  // 512 + offset score per lane
-                const uint32_t s1 = ring_ipair_score<1>(hw + r, kb);
+                staged_row_words(srow + (r0 + r + 6) * SROW, hw[(r + 6) % FW_CHUNK]);
+                const uint32_t s0 = ring_ipair_score_rot<0>(hw, r, kb);  // 512 + offset score per lane
+                const uint32_t s1 = ring_ipair_score_rot<1>(hw, r, kb);
                 mx0 = __vimax3_u16x2(mx0, s0, s0);
                 mx1 = __vimax3_u16x2(mx1, s1, s1);
                 if (colmask != 0u)

@@ -428,14 +428,16 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
 // X0+128..X0+131); the 3x3 test's outer neighbours come from lanes +-1.
 // A chunk of NW_CHUNK output rows reads 8 new staged rows, which lie in at
 // most two cell rows for cells of 8 or more rows.  Otherwise the maps hold
-// S(p) and only the detect region is masked.
+// S(p).  Bytes outside the detect region, and outside the proposed tiles of
+// an image that has them, are zeroed in the staged score box first (in the
+// words of lanes whose word is not wholly inside).
 
 constexpr int NW_QCAP = TILE_W * TILE_H / 4;             // strict maxima are never adjacent
 constexpr int NW_SBUF = (S_BOX + 127) / 128 * 128;       // 5504
 constexpr int NW_BYTES = NW_SBUF + I_BOX + 2 * NW_QCAP;  // per warp: score box, image box, queue
 constexpr int NW_WARPS = DET_THREADS / 32;
 constexpr int NW_DYN = NW_WARPS * NW_BYTES + 128;        // + alignment slack
-constexpr int NW_CHUNK = 8;                              // output rows per unrolled chunk
+constexpr int NW_CHUNK = 8;                              // output rows per unrolled chunk (one bit each per byte)
 static_assert(NW_BYTES % 128 == 0 && NW_SBUF % 128 == 0, "TMA destinations on 128-byte boundaries");
 static_assert(TILE_H % NW_CHUNK == 0, "whole chunks per tile");
 
@@ -461,9 +463,21 @@ __device__ __forceinline__ uint32_t word_flags(const WordCells& c, const uint32_
     return (c.ma && crow[c.ca] ? c.ma : 0u) | (c.mb && crow[c.ca + 1] ? c.mb : 0u);
 }
 
+// Each byte of the result: the sign (bit 7) of the same byte of g, replicated
+// (prmt's sign-extending byte selectors 8..11).
+__device__ __forceinline__ uint32_t sign_bytes(uint32_t g) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(g), "r"(0u), "r"(0xBA98u));
+    return r;
+}
+
+// The bytes of v below th cleared where fm is 0xFF (flagged cells).  For
+// th <= 128, bit 7 of ((b | 0x80) - th) | b is set exactly when b >= th (no
+// borrow leaves a byte), as in bytes_ge, and its sign replicated is the mask.
 template <bool SMALL_T>
 __device__ __forceinline__ uint32_t threshold_word(uint32_t v, uint32_t fm, uint32_t th) {
-    return v & ((SMALL_T ? bytes_ge(v, th) : bytes_ge_any(v, th)) | ~fm);
+    const uint32_t ge = SMALL_T ? sign_bytes(((v | 0x80808080u) - th * 0x01010101u) | v) : bytes_ge_any(v, th);
+    return v & (ge | ~fm);
 }
 
 template <bool APPLY, bool SMALL_T>
@@ -540,34 +554,68 @@ k_nms_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const
         }
         if (!skip) {
             const int rx0 = border, rx1 = I.w - border, ry0 = border, ry1 = I.h - border;
-            const int lox = max(rx0, X0 - 1), hix = min(rx1, X0 + TILE_W + 1);
             const int xc = X0 + 4 * lane;
             const int xh = lane == 0 ? X0 - 4 : X0 + TILE_W;  // the halo word (used by lanes 0 and 31)
-            const uint32_t cm_c = range_mask4(xc, lox, hix), cm_h = range_mask4(xh, lox, hix);
             const int nrows = min(TILE_H, ry1 - Y0);
             const uint8_t* const srow = sS + HALO_X + 4 * lane;
             const int hoff = xh - xc;
+            // Zero the staged bytes outside the detect region, and outside the
+            // proposed tiles of an image that has them, in the words the 3x3 test
+            // reads (staged rows 0 .. nrows + 1; a lane's word, and the halo word of
+            // lanes 0 and 31), so that the row loop needs no masks.  Staged row 0 is
+            // image row Y0 - 1, rows 1 .. nrows lie in the region, row nrows + 1 is
+            // Y0 + nrows.  A word lies in one proposal tile (tile_x0, X0: multiples of 16).
+            {
+                const uint8_t* const pmask = I.pmask;
+                const bool top_in = Y0 - 1 >= ry0, bot_in = Y0 + nrows < ry1;
+                auto sanitize = [&](int x, int off) {
+                    const uint32_t m = range_mask4(x, rx0, rx1);
+                    uint32_t m0 = top_in ? m : 0u, m1 = m, m2 = bot_in ? m : 0u;
+                    if (pmask && m) {
+                        const int px = (x - I.tile_x0) >> 5, py = (Y0 - ry0) >> 5;
+                        auto on = [&](int yy) {
+                            return yy >= 0 && yy < I.tiles_y && px >= 0 && px < 4 * I.tiles_x &&
+                                   pmask[(size_t)yy * 4 * I.tiles_x + px] != 0;
+                        };
+                        if (!on(top_in ? (Y0 - 1 - ry0) >> 5 : -1)) m0 = 0u;
+                        if (!on(py)) m1 = 0u;
+                        if (!on(bot_in ? (Y0 + nrows - ry0) >> 5 : -1)) m2 = 0u;
+                    }
+                    uint32_t* p = reinterpret_cast<uint32_t*>(sS + HALO_X + off);
+                    if (m0 != 0xFFFFFFFFu) p[0] &= m0;
+                    if (m1 != 0xFFFFFFFFu)
+                        for (int k = 1; k <= nrows; ++k) p[k * (SROW / 4)] &= m1;
+                    if (m2 != 0xFFFFFFFFu) p[(nrows + 1) * (SROW / 4)] &= m2;
+                };
+                sanitize(xc, 4 * lane);
+                if (lane == 0 || lane == 31) sanitize(xh, xh - X0);
+                __syncwarp();
+            }
             WordCells wc_c{0u, 0u, 0}, wc_h{0u, 0u, 0};
             const uint32_t* cellp = I.cell;
             const int ncx = I.ncx;
             if (APPLY) {
-                wc_c = word_cells(xc, cm_c, lox, rx0, cell, cell_magic);
-                wc_h = word_cells(xh, cm_h, lox, rx0, cell, cell_magic);
+                wc_c = word_cells(xc, range_mask4(xc, rx0, rx1), rx0, rx0, cell, cell_magic);
+                wc_h = word_cells(xh, range_mask4(xh, rx0, rx1), rx0, rx0, cell, cell_magic);
             }
-            // Flag masks of staged row iy (APPLY): cell row of iy (rows outside the region are masked anyway).
+            // Flag masks of staged row iy (APPLY): cell row of iy (rows outside the region hold zeros).
             auto flags_of = [&](int iy, uint32_t& fc, uint32_t& fh) {
                 const int cy = (int)__umulhi((uint32_t)max(iy - ry0, 0), cell_magic);
                 const uint32_t* crow = cellp + (size_t)min(cy, I.ncy - 1) * ncx;
                 fc = word_flags(wc_c, crow);
                 fh = word_flags(wc_h, crow);
             };
-            // Staged row k (image row Y0 - 1 + k) as the four pair words of the 3x3 test.
-            auto load_row = [&](int k, uint32_t fc, uint32_t fh, uint32_t (&h)[4]) {
-                const int iy = Y0 - 1 + k;
-                const bool in = iy >= ry0 && iy < ry1;
+            // Staged row k (image row Y0 - 1 + k) reduced to what the 3x3 test takes
+            // from it for the pixel pairs (x, x+2) and (x+1, x+3) in 16-bit lanes: the
+            // centres, the maxima of the left and right neighbours (the centre row's
+            // part) and the maxima of all three (an adjacent row's part).
+            struct Row3 {
+                uint32_t ctr[2], side[2], all[2];
+            };
+            auto load_row = [&](int k, uint32_t fc, uint32_t fh) {
                 const uint8_t* row = srow + k * SROW;
-                uint32_t vc = *reinterpret_cast<const uint32_t*>(row) & (in ? cm_c : 0u);
-                uint32_t vh = *reinterpret_cast<const uint32_t*>(row + hoff) & (in ? cm_h : 0u);
+                uint32_t vc = *reinterpret_cast<const uint32_t*>(row);
+                uint32_t vh = *reinterpret_cast<const uint32_t*>(row + hoff);
                 if (APPLY) {
                     vc = threshold_word<SMALL_T>(vc, fc, th);
                     vh = threshold_word<SMALL_T>(vh, fh, th);
@@ -576,18 +624,26 @@ k_nms_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const
                 uint32_t vq = __shfl_down_sync(0xFFFFFFFFu, vc, 1);
                 if (lane == 0) vm = vh;
                 if (lane == 31) vq = vh;
-                h[0] = __byte_perm(vm, vc, 0x0503) & 0x00FF00FFu;  // (x-1, x+1)
-                h[1] = __byte_perm(vc, 0u, 0x4240);                 // (x, x+2)
-                h[2] = __byte_perm(vc, 0u, 0x4341);                 // (x+1, x+3)
-                h[3] = __byte_perm(vc, vq, 0x0402) & 0x00FF00FFu;  // (x+2, x+4)
+                const uint32_t h0 = __byte_perm(vm, vc, 0x0503) & 0x00FF00FFu;  // (x-1, x+1)
+                const uint32_t h1 = __byte_perm(vc, 0u, 0x4240);                 // (x, x+2)
+                const uint32_t h2 = __byte_perm(vc, 0u, 0x4341);                 // (x+1, x+3)
+                const uint32_t h3 = __byte_perm(vc, vq, 0x0402) & 0x00FF00FFu;  // (x+2, x+4)
+                Row3 o;
+                o.ctr[0] = h1;
+                o.ctr[1] = h2;
+                o.side[0] = __vimax3_u16x2(h0, h2, h2);
+                o.side[1] = __vimax3_u16x2(h1, h3, h3);
+                o.all[0] = __vimax3_u16x2(h0, h1, h2);
+                o.all[1] = __vimax3_u16x2(h1, h2, h3);
+                return o;
             };
-            uint32_t ha[4], hb[4];
+            Row3 ra, rb;  // staged rows of the output row's upper neighbours and of the row itself
             {
                 uint32_t fc = 0u, fh = 0u;
                 if (APPLY) flags_of(Y0 - 1, fc, fh);
-                load_row(0, fc, fh, ha);
+                ra = load_row(0, fc, fh);
                 if (APPLY) flags_of(Y0, fc, fh);
-                load_row(1, fc, fh, hb);
+                rb = load_row(1, fc, fh);
             }
 #pragma unroll 1
             for (int r0 = 0; r0 < nrows; r0 += NW_CHUNK) {
@@ -601,28 +657,19 @@ k_nms_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const
                     yb = ry0 + (cya + 1) * cell;
                     if (yb <= iy0 + NW_CHUNK - 1) flags_of(yb, fb_c, fb_h);
                 }
-                uint32_t smask = 0u;  // bit 4 r + 2 pair + lane half
+                // Survivor bits: byte j (pair j >> 1, lane half j & 1) bit r (chunk row r).
+                uint32_t smask = 0u;
 #pragma unroll
                 for (int r = 0; r < NW_CHUNK; ++r) {
                     if (r0 + r >= nrows) break;
-                    uint32_t hc[4];
                     const bool b_row = APPLY && Y0 + 1 + r0 + r >= yb;
-                    load_row(r0 + r + 2, b_row ? fb_c : fa_c, b_row ? fb_h : fa_h, hc);
-#pragma unroll
-                    for (int pr = 0; pr < 2; ++pr) {
-                        const uint32_t nb = __vimax3_u16x2(__vimax3_u16x2(ha[pr], ha[1 + pr], ha[2 + pr]),
-                                                           __vimax3_u16x2(hb[pr], hb[2 + pr], hc[pr]),
-                                                           __vimax3_u16x2(hc[1 + pr], hc[2 + pr], hc[2 + pr]));
-                        // Lane bit 15 set when centre > neighbours (values <= 255).
-                        const uint32_t keep = (hb[1 + pr] + 0x7FFF7FFFu - nb) & 0x80008000u;
-                        const int bit = 2 * (2 * r + pr);
-                        smask |= ((keep >> 15) & 1u) << bit | (keep >> 31) << (bit + 1);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        ha[q] = hb[q];
-                        hb[q] = hc[q];
-                    }
+                    const Row3 rc = load_row(r0 + r + 2, b_row ? fb_c : fa_c, b_row ? fb_h : fa_h);
+                    // Lane bit 15 set when the centre > its 8 neighbours (values <= 255).
+                    const uint32_t k0 = rb.ctr[0] + 0x7FFF7FFFu - __vimax3_u16x2(ra.all[0], rb.side[0], rc.all[0]);
+                    const uint32_t k1 = rb.ctr[1] + 0x7FFF7FFFu - __vimax3_u16x2(ra.all[1], rb.side[1], rc.all[1]);
+                    smask |= (__byte_perm(k0, k1, 0x7531) & 0x80808080u) >> (7 - r);
+                    ra = rb;
+                    rb = rc;
                 }
                 // Append the chunk's survivors: a warp scan of the per-lane counts.
                 const int mine = __popc(smask);
@@ -637,8 +684,8 @@ k_nms_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const
                 while (smask) {
                     const int bit = __ffs((int)smask) - 1;
                     smask &= smask - 1u;
-                    // bit = 2 (2 row + pair) + half: column 4 lane + pair + 2 half
-                    queue[slot++] = q_entry(r0 + (bit >> 2), 4 * lane + ((bit >> 1) & 1) + 2 * (bit & 1));
+                    const int j = bit >> 3;  // column 4 lane + pair + 2 half
+                    queue[slot++] = q_entry(r0 + (bit & 7), 4 * lane + (j >> 1) + 2 * (j & 1));
                 }
             }
         }

@@ -423,7 +423,9 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
             if (!cell_form(P)) {
                 const int flags = strip_form(P) ? 2 : fast_sets_flags(P) ? 0 : 1;
                 const bool apply = !nms_applies(P);
-                if (flags || apply)
+                // Flags of images with proposal tiles only (flags 2, no apply): the
+                // learned path launches that pass itself (learned_flag_pass).
+                if (apply || flags == 1)
                     launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list,
                                       G.n_bands, s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * 8, st, flags, apply);
             }
@@ -458,6 +460,18 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
 //   0 clear counters and cell flags, resize levels 1..L-1 (pyramid)
 //   1 FAST score + cell flags      2 NMS + Harris keys
 //   3 top-N per level              4 orientation + output records
+// Learned path, between FAST and NMS: the cell flags of the images with
+// proposal tiles, which the cell-row strip kernel leaves to the threshold
+// pass, when the stage-2 graphs run no pass (the per-warp NMS kernel applies
+// the thresholds itself).
+void learned_flag_pass(of_handle* H, Plan* P, cudaStream_t st) {
+    if (cell_form(P) || !strip_form(P) || !nms_applies(P)) return;
+    const Plan::Group& G = P->groups[1][0];
+    const Settings& s = P->s;
+    launch_cell_apply(P->d_img(), P->d_dl() + G.dl_begin, P->d_grp() + G.rp_off, G.n_list, G.n_bands, s.t_hi, s.t_lo,
+                      s.border, s.cell, H->n_sms * 8, st, 2, false);
+}
+
 void enqueue_stages(of_handle* H, Plan* P, int first, int last, cudaStream_t st) {
     for (int stage = first; stage < last; ++stage) {
         if (stage == 0) cudaMemsetAsync(H->arena, 0, P->lay.zero_end, st);
@@ -1488,7 +1502,13 @@ int of_detect_learned(of_handle* H, const of_frame* frames, int n_frames, int le
         rc = launch_propose(P->d_img(), P->d_dl(), d_pp, n_list, d_logit, P->lbuf + P->off_pos,
                             P->lbuf + P->off_mask, threshold, min_confidence, dilate, d_stats, st);
     if (rc != OF_OK) return rc;
-    for (int k = 1; k < kStages; ++k) OF_CK(cudaGraphLaunch(P->stage_exec[k], st));
+    for (int k = 1; k < kStages; ++k) {
+        if (k == 2) {
+            learned_flag_pass(H, P, st);
+            OF_CK(cudaGetLastError());
+        }
+        OF_CK(cudaGraphLaunch(P->stage_exec[k], st));
+    }
     H->last = P;
     if (stats) {
         OF_CK(cudaMemcpyAsync(H->h_count + 4, d_stats, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));

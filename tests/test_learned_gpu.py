@@ -247,13 +247,16 @@ def _oracle_on_tiles(img, masks, levels=8, scale=1.2, n_features=1000, border=19
     return rows
 
 
-def test_full_frame_fallback_below_min_confidence():
+@pytest.mark.parametrize("tuned", [False, True])
+def test_full_frame_fallback_below_min_confidence(tuned):
     """A min_confidence between the images' confidences sends some (frame,
     level) images to the full-frame fallback and leaves the others on their
     proposed tiles.  The inspected tile masks follow the network's logits
     (threshold, dilation, all ones where the image fell back); fallen-back
     images give exactly the plain path's records for that level; and every
-    frame equals the oracle restricted to the kept tiles."""
+    frame equals the oracle restricted to the kept tiles.  tuned: the cell-row
+    strip FAST kernel and the per-warp NMS kernel, which zeroes the scores
+    outside the proposed tiles itself (else the untuned plan's kernels)."""
     import json
 
     meta = json.load(open(learned.DEFAULT_META))
@@ -264,6 +267,10 @@ def test_full_frame_fallback_below_min_confidence():
     fr = [(t, t.shape[1], t.shape[0], t.stride(0)) for t in dev]
     N, L = 1000, 8
     det = ofg.Detector(1920, 1080, max_levels=L, max_features=N, max_batch=2, fast_t_lo=7)
+    if tuned:
+        tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
+                           stream_groups=1, fast_cell_tiles=4, nms_tile_h=32, fast_tile_h=32)
+        det.set_tuning(dev, tun, levels=L, fast_t=20, n_features=N)
 
     def tile_buf(what, f, lvl, dtype):
         raw, dims = det.inspect(what, f, lvl)

@@ -168,12 +168,16 @@ def test_cell_aligned_tiles(cell):
 
 def test_per_warp_general_tiles():
     """k_fast_warp: one 128 x 32 detect tile per warp item, one 160 x 40 box from
-    (X0 - 16, Y0 - 4); chunks of FW_CHUNK rows, chunk r0 reading staged rows
-    r0 + 1 .. r0 + FW_CHUNK + 6."""
+    (X0 - 16, Y0 - 4); output row r (0..31) reads staged rows r + 1 .. r + 7 through a
+    rotating window of FW_CHUNK = 7 slots (slot = staged row mod 7, aligned at every
+    chunk start)."""
     b = 19
     chunk = source_constants("of_internal.h", "k_fast.cu")["FW_CHUNK"]
+    assert chunk == 7
+    for r in range(32):
+        assert r + 1 >= 0 and r + 7 < IMG_BOX_ROWS
     for r0 in range(0, 32, chunk):
-        assert r0 + 1 >= 0 and r0 + 1 + chunk + 6 - 1 < IMG_BOX_ROWS
+        assert r0 % chunk == 0  # slot (r0 + k) % 7 == k % 7 at each chunk start
     assert HALO_X - 4 >= 0 and HALO_X + 4 * 31 + 7 < SROW
     for w, h in det_levels(b):
         tile_x0 = b & ~15
@@ -205,3 +209,33 @@ def test_cell_row_strips(cell):
                     if b <= xx < w - b:
                         assert 0 <= (xx - b) // cell - cx0 < 32
         assert b + ncy * cell >= h - b
+
+
+@pytest.mark.parametrize("cell", range(8, 41))
+def test_per_warp_nms_tiles(cell):
+    """k_nms_warp: per warp one 160 x 34 score box from (X0 - 16, Y0 - 1) and one 160 x 40
+    image box from (X0 - 16, Y0 - 4) on the 128 x 32 detect tiles.  The 3x3 test reads staged
+    score rows 0 .. 33 at word offsets HALO_X + 4 lane and the halo words HALO_X - 4 (lane 0)
+    and HALO_X + 128 (lane 31); Harris reads image rows ly .. ly + 8 and words w0 .. w0 + 2.
+    A chunk of NW_CHUNK output rows reads NW_CHUNK new staged rows, which lie in at most two
+    cell rows (cells of 8 or more rows); the queue holds every possible survivor; two blocks'
+    buffers fit one SM's shared memory."""
+    c = source_constants("of_internal.h", "k_nms_harris.cu")
+    chunk, qcap, nbytes, dyn = c["NW_CHUNK"], c["NW_QCAP"], c["NW_BYTES"], c["NW_DYN"]
+    assert c["S_BOX"] == SCORE_BOX_ROWS * SROW and c["I_BOX"] == IMG_BOX_ROWS * SROW
+    assert 32 + 1 < SCORE_BOX_ROWS                      # staged rows 0 .. 33
+    assert HALO_X - 4 >= 0 and HALO_X + TILE_W + 3 < SROW
+    for ly in range(32):
+        assert ly + 8 < IMG_BOX_ROWS
+    for lx in range(TILE_W):
+        w0 = (HALO_X + lx - 4) >> 2
+        assert w0 >= 0 and 4 * (w0 + 2) + 3 < SROW
+    assert qcap >= TILE_W * 32 // 4                     # strict maxima: at most one per 2 x 2 block
+    assert nbytes % 128 == 0 and c["NW_SBUF"] % 128 == 0
+    assert 2 * (dyn + 1024 + 8 * 16) <= 228 * 1024      # 2 blocks per SM, 1 KB reserved per block
+    # New staged rows of the chunk starting at output row r0: image rows Y0 + 1 + r0 .. Y0 + r0 + chunk.
+    b = 19
+    for y0 in range(b, b + 4 * cell, 32):
+        for r0 in range(0, 32, chunk):
+            rows = range(y0 + 1 + r0, y0 + 1 + r0 + chunk)
+            assert len({(y - b) // cell for y in rows}) <= 2
