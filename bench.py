@@ -299,7 +299,7 @@ FAST_OPS_PER_PX = 40.5
 # levels, divided by the frames.  Valid while the kernels' code
 # (kernels_sha1) and the per-stage launch choices below are the ones captured;
 # otherwise the line reports null.
-STAGE_TRAFFIC = {"code_sha1": "3adfce6df75e369e911d44d4b5c787cca1569399", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 32}, "l2_bytes_per_frame": {"pyramid": 24129916, "fast": 30055492, "nms_harris": 37321938, "select": 3253813, "orient": 2455290}, "dram_bytes_per_frame": {"pyramid": 7740540, "fast": 12113236, "nms_harris": 14523904, "select": 1479620, "orient": 530348}}
+STAGE_TRAFFIC = {"code_sha1": "87a137cd58ce75ed5cdd4868662cfcd4472c737d", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 32}, "l2_bytes_per_frame": {"pyramid": 24302823, "fast": 30152656, "nms_harris": 37627292, "select": 3254276, "orient": 2463354}, "dram_bytes_per_frame": {"pyramid": 7751308, "fast": 12116184, "nms_harris": 14628144, "select": 1479588, "orient": 530316}}
 
 
 def code_sha1(path):
