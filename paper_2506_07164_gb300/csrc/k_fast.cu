@@ -575,7 +575,7 @@ int fast_warp_blocks_per_sm() {
 
 // ---------------------------------------------------------------------------
 // Cell-row strips with per-warp pipelines: the general layout, with the cell
-// flags set exactly and cheaply (the threshold pass then only applies them).
+// flags set exactly and cheaply (NMS, or the threshold pass, then applies them).
 //
 // A work item is one cell row (cell <= 33 rows) of one 128-column detect tile
 // column of one image: x in [X0, X0 + 128), y in [y0, y0 + cell), y0 =
@@ -589,6 +589,9 @@ int fast_warp_blocks_per_sm() {
 // shared with the neighbouring strips).  Images with proposal tiles (the
 // learned path) get their flags from the threshold pass instead, which sees
 // only proposed pixels; nothing in the row loop depends on the proposal.
+// An image's last tile column often holds few region columns (18..52 on
+// three of the eight 1080p levels): with at most 64 (32) of them the lanes
+// form 2 (4) row groups over the first 64 (32) columns, so fewer lanes idle.
 
 __global__ void __launch_bounds__(DET_THREADS, 2)
 k_fast_cstrip(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ prefix,
@@ -648,10 +651,19 @@ k_fast_cstrip(const Img* __restrict__ imgs, const int32_t* __restrict__ list, co
         const uint8_t* const s = wbuf + b * FAST_BUF;
         const int X0 = ti.x0, y0 = ti.y0;
         const int rx0 = border, rx1 = I.w - border;
-        const int x = X0 + 4 * lane;
-        const uint32_t colmask = range_mask4(x, rx0, rx1);
         const int nrows = min(cell, I.h - border - y0);
-        uint8_t* const sdst = I.score + (size_t)y0 * I.spitch + x;
+        // A tile column with at most 64 (32) columns of the detect region left:
+        // the lanes split into 2 (4) row groups that each score columns
+        // X0 .. X0+63 (X0+31) over hq = nrows / groups rows (rounded up).  The
+        // last group ends at the strip's last row, overlapping its neighbour
+        // when the rows do not divide (those rows are scored twice, identically).
+        const int lg = rx1 - X0 <= 32 ? 2 : rx1 - X0 <= 64 ? 1 : 0;
+        const int cl = lane & (31 >> lg);  // column lane
+        const int hq = (nrows + (1 << lg) - 1) >> lg;
+        const int ro = min((lane >> (5 - lg)) * hq, nrows - hq);  // the group's first row
+        const int x = X0 + 4 * cl;
+        const uint32_t colmask = range_mask4(x, rx0, rx1);
+        uint8_t* const sdst = I.score + (size_t)(y0 + ro) * I.spitch + x;
         const size_t spitch = (size_t)I.spitch;
         // Learned path: skip a strip with no proposed tile under it (at most 2 x 4
         // proposal tiles; lanes 0..7 look one up each).  The threshold pass zeroes
@@ -668,16 +680,16 @@ k_fast_cstrip(const Img* __restrict__ imgs, const int32_t* __restrict__ list, co
             }
         }
         uint32_t mx0 = 0u, mx1 = 0u;
-        const uint8_t* const srow = s + SROW + HALO_X + 4 * lane;  // staged row of output row -3
+        const uint8_t* const srow = s + (ro + 1) * SROW + HALO_X + 4 * cl;  // staged row of group row -3
         // Rotating window of 7 staged rows: each staged row's words are built once.
         uint32_t hw[7][8];
 #pragma unroll
         for (int k = 0; k < 6; ++k) staged_row_words(srow + k * SROW, hw[k]);
 #pragma unroll 1
-        for (int r0 = 0; r0 < nrows; r0 += FW_CHUNK) {
+        for (int r0 = 0; r0 < hq; r0 += FW_CHUNK) {
 #pragma unroll
             for (int r = 0; r < FW_CHUNK; ++r) {
-                if (r0 + r >= nrows) break;
+                if (r0 + r >= hq) break;
                 staged_row_words(srow + (r0 + r + 6) * SROW, hw[(r + 6) % FW_CHUNK]);
                 const uint32_t s0 = ring_ipair_score_rot<0>(hw, r, kb);  // 512 + offset score per lane
                 const uint32_t s1 = ring_ipair_score_rot<1>(hw, r, kb);
@@ -686,6 +698,14 @@ k_fast_cstrip(const Img* __restrict__ imgs, const int32_t* __restrict__ list, co
                 if (colmask != 0u)
                     *reinterpret_cast<uint32_t*>(sdst + (size_t)(r0 + r) * spitch) =
                         __byte_perm(s0, s1, 0x6240) & colmask;
+            }
+        }
+        if (lg) {  // the row groups' maxima per column (groups: lane bit 4, and bit 3 for four)
+            mx0 = __vimax3_u16x2(mx0, __shfl_xor_sync(0xFFFFFFFFu, mx0, 16), mx0);
+            mx1 = __vimax3_u16x2(mx1, __shfl_xor_sync(0xFFFFFFFFu, mx1, 16), mx1);
+            if (lg == 2) {
+                mx0 = __vimax3_u16x2(mx0, __shfl_xor_sync(0xFFFFFFFFu, mx0, 8), mx0);
+                mx1 = __vimax3_u16x2(mx1, __shfl_xor_sync(0xFFFFFFFFu, mx1, 8), mx1);
             }
         }
         if (cells && !pmask) {

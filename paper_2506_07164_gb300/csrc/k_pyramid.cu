@@ -153,8 +153,9 @@ void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, i
 //   h(r, x) = (4096 - 2ax) S[r][x0] + 2ax S[r][x0 + 1]           (< 2^20)
 //   v       = (4096 - 2ay) h(y0, x) + 2ay h(y0 + 1, x) + 2^23    (< 2^32)
 //   out     = v >> 24 = ((sum of the original products) + 2^21) >> 22.
-// h is one __dp2a_lo (two 16 x 8-bit products) on the byte pair picked by one
-// __byte_perm; out is byte 3 of v, so four outputs pack with three byte
+// h is one __dp2a_lo or __dp2a_hi (two 16 x 8-bit products) on a byte pair;
+// one __byte_perm picks the byte pairs of two outputs into the low and high
+// halves of a word; out is byte 3 of v, so four outputs pack with three byte
 // permutes.  Where a source index is clamped (x0 = w - 1, y0 = h - 1) the
 // tables give that sample's partner weight 0, so the zero fill of the TMA
 // box past the image edge never contributes.
@@ -175,10 +176,12 @@ __device__ __forceinline__ void hrow(const uint8_t* __restrict__ row, int wa, in
                                      const uint32_t (&wgt)[4], uint32_t (&h)[4]) {
     const uint32_t* rp = reinterpret_cast<const uint32_t*>(row);
     const uint32_t a0 = rp[wa], a1 = rp[wa + 1], b0 = rp[wb], b1 = rp[wb + 1];
-    h[0] = __dp2a_lo(wgt[0], __byte_perm(a0, a1, sel[0]), 0u);
-    h[1] = __dp2a_lo(wgt[1], __byte_perm(a0, a1, sel[1]), 0u);
-    h[2] = __dp2a_lo(wgt[2], __byte_perm(b0, b1, sel[2]), 0u);
-    h[3] = __dp2a_lo(wgt[3], __byte_perm(b0, b1, sel[3]), 0u);
+    // sel[0]: the byte pairs of outputs 0 and 1 in one word (low half, high half); sel[2]: outputs 2 and 3.
+    const uint32_t p01 = __byte_perm(a0, a1, sel[0]), p23 = __byte_perm(b0, b1, sel[2]);
+    h[0] = __dp2a_lo(wgt[0], p01, 0u);
+    h[1] = __dp2a_hi(wgt[1], p01, 0u);
+    h[2] = __dp2a_lo(wgt[2], p23, 0u);
+    h[3] = __dp2a_hi(wgt[3], p23, 0u);
 }
 
 __global__ void __launch_bounds__(RT_THREADS)
@@ -256,6 +259,8 @@ k_resize_tma(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix
                 const uint32_t o = (uint32_t)(xo[i] - 4 * (i < 2 ? wa : wb));
                 sel[i] = o | ((o + 1u) << 4);
             }
+            sel[0] |= sel[1] << 8;  // outputs 0 and 1 share one permute
+            sel[2] |= sel[3] << 8;
             // The job's fields, read once (the stores below could alias them).
             const int dpitch = J.dpitch;
             const int32_t* ytab = J.ytab + ti.y0;

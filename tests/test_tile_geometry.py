@@ -191,10 +191,22 @@ def test_per_warp_general_tiles():
 def test_cell_row_strips(cell):
     """k_fast_cstrip: one cell row of one 128-column detect tile column per warp item; one
     160 x 40 box from (X0 - 16, y0 - 4); output row r < cell reads staged rows r + 1 .. r + 7;
-    the strip's cells fit the flag word."""
+    the strip's cells fit the flag word.  A tile column with at most 64 (32) region columns
+    left splits the lanes into 2 (4) row groups of hq = ceil(nrows / groups) rows starting
+    at min(g hq, nrows - hq): every row is covered, none lies past the strip."""
     b = 19
     assert (cell - 1) + 7 < IMG_BOX_ROWS
     assert TILE_W // cell + 2 <= 32
+    for nrows in range(1, cell + 1):
+        for lg in (0, 1, 2):
+            G = 1 << lg
+            hq = -(-nrows // G)
+            covered = set()
+            for g in range(G):
+                ro = min(g * hq, nrows - hq)
+                assert 0 <= ro and ro + hq <= nrows
+                covered |= set(range(ro, ro + hq))
+            assert covered == set(range(nrows))
     for w, h in det_levels(b):
         tile_x0 = b & ~15
         tiles_x = ceil_div(w - b - tile_x0, TILE_W)
@@ -202,9 +214,13 @@ def test_cell_row_strips(cell):
         for tx in range(tiles_x):
             X0 = tile_x0 + tx * TILE_W
             assert (X0 - HALO_X) % 16 == 0
+            useful = w - b - X0
+            lg = 2 if useful <= 32 else 1 if useful <= 64 else 0
+            # The lanes' columns cover the tile column's region columns.
+            assert X0 + 4 * (32 >> lg) >= min(w - b, X0 + TILE_W)
             cx0 = (max(X0, b) - b) // cell
             for lane in range(32):
-                x = X0 + 4 * lane
+                x = X0 + 4 * (lane & (31 >> lg))
                 for xx in range(x, x + 4):
                     if b <= xx < w - b:
                         assert 0 <= (xx - b) // cell - cx0 < 32
