@@ -299,7 +299,7 @@ FAST_OPS_PER_PX = 40.5
 # levels, divided by the frames.  Valid while the kernels' code
 # (kernels_sha1) and the per-stage launch choices below are the ones captured;
 # otherwise the line reports null.
-STAGE_TRAFFIC = {"code_sha1": "87a137cd58ce75ed5cdd4868662cfcd4472c737d", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 32}, "l2_bytes_per_frame": {"pyramid": 24302823, "fast": 30152656, "nms_harris": 37627292, "select": 3254276, "orient": 2463354}, "dram_bytes_per_frame": {"pyramid": 7751308, "fast": 12116184, "nms_harris": 14628144, "select": 1479588, "orient": 530316}}
+STAGE_TRAFFIC = {"code_sha1": "1bf24bf36e8bfbfe4df16e6801c8357024922369", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 32}, "l2_bytes_per_frame": {"pyramid": 24139810, "fast": 30256980, "nms_harris": 37339760, "select": 3254386, "orient": 2456736}, "dram_bytes_per_frame": {"pyramid": 7740396, "fast": 12246948, "nms_harris": 14578644, "select": 1483052, "orient": 530332}}
 
 
 def code_sha1(path):
