@@ -125,64 +125,65 @@ k_cell_apply(const Img* __restrict__ imgs, const int32_t* __restrict__ list, con
             for (int i = tid; i < ncx; i += CA_THREADS) crow[i] = bflag[i];
             fl = bflag;
         }
-        if (!APPLY) continue;  // flags only: NMS applies them on its staged tiles
-        for (int s0 = 0; s0 < n_chunks; s0 += CA_SEG) {
-            const int s1 = min(s0 + CA_SEG, n_chunks);
-            __syncthreads();  // earlier readers of colmask are done
-            // Column mask of the segment: 0xFF where the column is in the region and its cell is flagged.
-            int any = 0;
-            for (int c = s0 + tid; c < s1; c += CA_THREADS) {
-                const int x = xb0 + 16 * c;
-                uint32_t w[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t m = 0u;
-                    if (cells) {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int xx = x + 4 * q + i;
-                            if (xx >= border && xx < rx1 && fl[(int)__umulhi((uint32_t)(xx - border), magic)])
-                                m |= 0xFFu << (8 * i);
+        if constexpr (APPLY) {  // else flags only: NMS applies them on its staged tiles
+            for (int s0 = 0; s0 < n_chunks; s0 += CA_SEG) {
+                const int s1 = min(s0 + CA_SEG, n_chunks);
+                __syncthreads();  // earlier readers of colmask are done
+                // Column mask of the segment: 0xFF where the column is in the region and its cell is flagged.
+                int any = 0;
+                for (int c = s0 + tid; c < s1; c += CA_THREADS) {
+                    const int x = xb0 + 16 * c;
+                    uint32_t w[4];
+    #pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t m = 0u;
+                        if (cells) {
+    #pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int xx = x + 4 * q + i;
+                                if (xx >= border && xx < rx1 && fl[(int)__umulhi((uint32_t)(xx - border), magic)])
+                                    m |= 0xFFu << (8 * i);
+                            }
                         }
+                        w[q] = m;
+                        any |= m != 0u;
                     }
-                    w[q] = m;
-                    any |= m != 0u;
+                    *reinterpret_cast<uint4*>(colmask + 16 * (c - s0)) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
-                *reinterpret_cast<uint4*>(colmask + 16 * (c - s0)) = make_uint4(w[0], w[1], w[2], w[3]);
-            }
-            // A segment with no flagged cell keeps its bytes (unless proposal tiles clear some).
-            if (!__syncthreads_or(any) && !pmask) continue;
-            for (int y = y0 + warp; y < y1; y += CA_THREADS / 32) {
-                uint8_t* srow = score + (size_t)y * spitch;
-                const int py = (y - border) >> 5;
-                for (int c0 = s0; c0 < s1; c0 += 128) {
-                    uint4 v[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int c = c0 + lane + 32 * k;
-                        if (c < s1) v[k] = *reinterpret_cast<const uint4*>(srow + xb0 + 16 * c);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int c = c0 + lane + 32 * k;
-                        if (c >= s1) continue;
-                        const int x = xb0 + 16 * c;
-                        uint4 nv;
-                        if (pmask && pmask[(size_t)py * 4 * tiles_x + ((x - tile_x0) >> 5)] == 0) {
-                            // Outside the proposed tiles the region's bytes become 0.
-                            nv.x = v[k].x & ~range_mask4(x, border, rx1);
-                            nv.y = v[k].y & ~range_mask4(x + 4, border, rx1);
-                            nv.z = v[k].z & ~range_mask4(x + 8, border, rx1);
-                            nv.w = v[k].w & ~range_mask4(x + 12, border, rx1);
-                        } else {
-                            const uint4 fm = *reinterpret_cast<const uint4*>(colmask + 16 * (c - s0));
-                            nv.x = apply_word<SMALL_T>(v[k].x, fm.x, th);
-                            nv.y = apply_word<SMALL_T>(v[k].y, fm.y, th);
-                            nv.z = apply_word<SMALL_T>(v[k].z, fm.z, th);
-                            nv.w = apply_word<SMALL_T>(v[k].w, fm.w, th);
+                // A segment with no flagged cell keeps its bytes (unless proposal tiles clear some).
+                if (!__syncthreads_or(any) && !pmask) continue;
+                for (int y = y0 + warp; y < y1; y += CA_THREADS / 32) {
+                    uint8_t* srow = score + (size_t)y * spitch;
+                    const int py = (y - border) >> 5;
+                    for (int c0 = s0; c0 < s1; c0 += 128) {
+                        uint4 v[4];
+    #pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int c = c0 + lane + 32 * k;
+                            if (c < s1) v[k] = *reinterpret_cast<const uint4*>(srow + xb0 + 16 * c);
                         }
-                        if (nv.x != v[k].x || nv.y != v[k].y || nv.z != v[k].z || nv.w != v[k].w)
-                            *reinterpret_cast<uint4*>(srow + x) = nv;
+    #pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int c = c0 + lane + 32 * k;
+                            if (c >= s1) continue;
+                            const int x = xb0 + 16 * c;
+                            uint4 nv;
+                            if (pmask && pmask[(size_t)py * 4 * tiles_x + ((x - tile_x0) >> 5)] == 0) {
+                                // Outside the proposed tiles the region's bytes become 0.
+                                nv.x = v[k].x & ~range_mask4(x, border, rx1);
+                                nv.y = v[k].y & ~range_mask4(x + 4, border, rx1);
+                                nv.z = v[k].z & ~range_mask4(x + 8, border, rx1);
+                                nv.w = v[k].w & ~range_mask4(x + 12, border, rx1);
+                            } else {
+                                const uint4 fm = *reinterpret_cast<const uint4*>(colmask + 16 * (c - s0));
+                                nv.x = apply_word<SMALL_T>(v[k].x, fm.x, th);
+                                nv.y = apply_word<SMALL_T>(v[k].y, fm.y, th);
+                                nv.z = apply_word<SMALL_T>(v[k].z, fm.z, th);
+                                nv.w = apply_word<SMALL_T>(v[k].w, fm.w, th);
+                            }
+                            if (nv.x != v[k].x || nv.y != v[k].y || nv.z != v[k].z || nv.w != v[k].w)
+                                *reinterpret_cast<uint4*>(srow + x) = nv;
+                        }
                     }
                 }
             }

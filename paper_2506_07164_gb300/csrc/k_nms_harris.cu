@@ -270,7 +270,6 @@ k_nms_harris(const Img* __restrict__ imgs, const int32_t* __restrict__ list,
     __shared__ int nq;
 
     const int tid = threadIdx.x;
-    const bool cells = t_hi != t_lo;
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
