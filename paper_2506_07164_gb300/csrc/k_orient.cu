@@ -6,7 +6,9 @@
 //     lane = column u, loop over rows v, warp reduction;
 //   - angle = atan2f(m01, m10) (both moments are exact int32, |m| < 2^24, so
 //     their float conversion is exact);
-//   - response = key / kden * (1 / (4*7*255))^4 in float64, stored as float.
+//   - response = key / kden * (1 / (4*7*255))^4, as key (float) times the
+//     host-rounded float (1/(4*7*255))^4 / kden (relative error below 3e-7);
+//   - level-0 coordinates from the plan's tables (x * scale^level rounded once).
 // Records are level-major in rank order: the slot of a kept keypoint is the
 // number of keypoints kept by the frame's earlier levels plus its rank.
 #include <cuda_runtime.h>
@@ -98,16 +100,23 @@ k_orient(const Img* __restrict__ imgs, int img_begin, int n_img, int slot_begin,
     if (lane == 0) {
         const uint64_t okey = I.kkey[rank];
         const int64_t key = (int64_t)(okey ^ 0x8000000000000000ull);
-        const double f = 1.0 / (4.0 * 7.0 * 255.0);
-        const double resp = ((double)key / (double)call->kden) * (f * f * f * f);
+        // response = key / kden * (1/(4*7*255))^4 in float: key as hi * 2^32 + lo
+        // (two 32-bit conversions), times the host-rounded scale -- no float64 here
+        // (the FP64 pipe was the orientation kernel's busiest unit).
+        const float keyf = fmaf((float)(int32_t)(key >> 32), 4294967296.0f, (float)(uint32_t)key);
         of_keypoint k;
-        k.x = (float)((double)x * I.lscale);
-        k.y = (float)((double)y * I.lscale);
+        if (I.fx) {
+            k.x = I.fx[x];
+            k.y = I.fy[y];
+        } else {
+            k.x = (float)((double)x * I.lscale);
+            k.y = (float)((double)y * I.lscale);
+        }
         k.x_l = x;
         k.y_l = y;
         k.level = I.level;
         k.fast_score = I.score[(size_t)y * I.spitch + x] + (call->t_lo - 1);  // the map holds s - (t_lo - 1)
-        k.response = (float)resp;
+        k.response = keyf * call->resp_scale;
         k.angle = (m10 == 0 && m01 == 0) ? 0.0f : atan2f((float)m01, (float)m10);
         k.A = a;
         k.B = b;

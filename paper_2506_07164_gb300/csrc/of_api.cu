@@ -211,6 +211,7 @@ struct Plan {
     std::vector<Resize> h_rs;
     std::vector<int> rs_begin;      // jobs of level l: [rs_begin[l], rs_begin[l+1])
     std::vector<int32_t> det_list, det_prefix, tables;
+    std::vector<float> ftables;  // level-0 coordinates per (level size, scale^level), float
     std::vector<int> rs_frame;      // frame of each resize job
     // Launch ranges of one group of frames: groups[k] splits the batch into k
     // groups (k = 1: everything; k > 1: the forked graph's branches).  Tile
@@ -239,7 +240,7 @@ struct Plan {
     int det_tiles = 0, max_quota = 0, total_slots = 0, n_img = 0;
     Call h_call{};
     uint8_t* dbuf = nullptr;
-    size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0;
+    size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0, off_ftab = 0;
     size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gft[2] = {0, 0}, off_gfal = 0,
            off_gcs = 0;
     size_t off_maps = 0;
@@ -600,6 +601,27 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     }
     P->total_slots = slot;
 
+    // Level-0 coordinate tables of the keypoint records (deduplicated per
+    // (length, scale^level)): the orientation kernel then needs no float64.
+    std::vector<std::pair<int, int>> ftab_idx(P->n_img);
+    {
+        std::map<std::pair<int, uint64_t>, int> ftab_of;
+        auto ftable = [&](int n, double ls) {
+            uint64_t bits = 0;
+            std::memcpy(&bits, &ls, sizeof(bits));
+            const auto key = std::make_pair(n, bits);
+            const auto it = ftab_of.find(key);
+            if (it != ftab_of.end()) return it->second;
+            const int at = (int)P->ftables.size();
+            for (int i = 0; i < n; ++i) P->ftables.push_back((float)((double)i * ls));
+            ftab_of[key] = at;
+            return at;
+        };
+        for (int i = 0; i < P->n_img; ++i)
+            ftab_idx[i] = std::make_pair(ftable(P->h_img[i].w, P->h_img[i].lscale),
+                                         ftable(P->h_img[i].h, P->h_img[i].lscale));
+    }
+
     // Resize jobs and their tables (deduplicated per (n_src, n_dst)).
     std::map<std::pair<int, int>, int> tab_of;
     auto table = [&](int n_src, int n_dst) {
@@ -773,6 +795,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     C.radius = s.radius;
     C.n_img = P->n_img;
     C.total_slots = P->total_slots;
+    C.resp_scale = ofh::response_scale(s.kden);
     C.status = H->d_counts + 4;
     P->tun.resize_tile_h = RS_TILE_HS[1];
     P->tun.resize_tma = 1;
@@ -835,6 +858,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->det_list.size(), 1), 16);
     P->off_tab = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->tables.size(), 1), 16);
+    P->off_ftab = off;
+    off = align_up(off + sizeof(float) * std::max<size_t>(P->ftables.size(), 1), 16);
     P->off_gdp = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_det.size(), 1), 16);
     P->off_grs = off;
@@ -858,6 +883,11 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
         free_plan(P);
         return fail(OF_ERR_CUDA, std::string("cudaMalloc(descriptors): ") + cudaGetErrorString(e));
     }
+    const float* d_ftab = reinterpret_cast<const float*>(P->dbuf + P->off_ftab);
+    for (int i = 0; i < P->n_img; ++i) {
+        P->h_img[i].fx = d_ftab + ftab_idx[i].first;
+        P->h_img[i].fy = d_ftab + ftab_idx[i].second;
+    }
     const int32_t* d_tab = reinterpret_cast<const int32_t*>(P->dbuf + P->off_tab);
     for (size_t i = 0; i < P->h_rs.size(); ++i) {
         P->h_rs[i].xtab = d_tab + tab_idx[i].first;
@@ -873,6 +903,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_maps, P->h_maps.data(), sizeof(CUtensorMap) * P->h_maps.size());
     put(P->off_dl, P->det_list.data(), sizeof(int32_t) * P->det_list.size());
     put(P->off_tab, P->tables.data(), sizeof(int32_t) * P->tables.size());
+    put(P->off_ftab, P->ftables.data(), sizeof(float) * P->ftables.size());
     put(P->off_gdp, P->gp_det.data(), sizeof(int32_t) * P->gp_det.size());
     put(P->off_grs, P->gp_rs.data(), sizeof(int32_t) * P->gp_rs.size());
     put(P->off_gfp, P->gp_fast.data(), sizeof(int32_t) * P->gp_fast.size());

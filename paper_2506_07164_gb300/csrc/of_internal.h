@@ -72,6 +72,11 @@ struct Img {
     int32_t ftiles_x;          // cell tiles per row of the cell-tile FAST kernel (0: not used)
     int32_t slot0;             // first output slot of this image (sum of earlier quotas)
     double lscale;             // scale^level
+    // Level-0 coordinates of the level's pixel columns and rows: fx[x] =
+    // (float)(x * scale^level), the product taken in float64 and rounded once
+    // (on the host).  Null: the orientation kernel computes them in float64.
+    const float* fx;
+    const float* fy;
     // Learned path: one byte per 32 x 32 proposal tile on the detect-tile grid
     // (4 * tiles_x columns, tiles_y rows, tile (px, py) covers x in
     // [tile_x0 + 32 px, +32), y in [border + 32 py, +32)); 0 = skip.  Null: all on.
@@ -110,6 +115,7 @@ struct Call {
     int32_t border, cell, radius;
     int32_t n_img;        // n_frames * levels
     int32_t total_slots;  // sum of quotas
+    float resp_scale;     // (1 / (4*7*255))^4 / kden, rounded to float: response = key * resp_scale
 };
 
 // Order in which a persistent block walks the tiles of a launch:

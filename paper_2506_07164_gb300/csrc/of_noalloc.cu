@@ -196,6 +196,7 @@ extern "C" int of_detect_level_noalloc(const uint8_t* img, int w, int h, int pit
     Cl.status = reinterpret_cast<int32_t*>(S + o_zero) + 4;  // a timeout shows up as *out_count < 0
     Cl.knum = knum;
     Cl.kden = kden;
+    Cl.resp_scale = ofh::response_scale(kden);
     Cl.n_frames = 1;
     Cl.levels = 1;
     Cl.n_features = n_features;

@@ -83,6 +83,11 @@ bool k_fraction(float k, int64_t* num, int64_t* den) {
     return true;
 }
 
+float response_scale(int64_t den) {
+    const double f = 1.0 / (4.0 * 7.0 * 255.0);
+    return (float)((f * f * f * f) / (double)den);
+}
+
 }  // namespace ofh
 
 extern "C" int of_plan_levels(int W, int H, int levels, float scale, int n_features, int32_t* ws,
