@@ -18,7 +18,8 @@
 // The gathered candidates are bitonic-sorted by R, descending.  The largest
 // images hold tens of thousands of candidates, so every scan over them keeps
 // SEL_UNROLL loads in flight per thread (the scans are latency-bound, not
-// bandwidth-bound), and the passes over key bytes do not read positions.
+// bandwidth-bound); the coarse passes load two keys per 16-byte load and read
+// the positions of the gathered candidates only.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -92,18 +93,25 @@ k_select(const Img* __restrict__ imgs, const Call* __restrict__ call, int sort_c
     __syncthreads();
 
     if (n > q) {
-        // Coarse pass: histogram of the key code.
-        for (int i0 = tid; i0 < n; i0 += SEL_UNROLL * SELECT_THREADS) {
-            uint64_t hi[SEL_UNROLL];
+        // Coarse pass: histogram of the key code, two keys per 16-byte load
+        // (the candidate arrays start on 256-byte boundaries).
+        const ulonglong2* ck2 = reinterpret_cast<const ulonglong2*>(I.ckey);
+        const int n2 = n >> 1;
+        for (int i0 = tid; i0 < n2; i0 += SEL_UNROLL * SELECT_THREADS) {
+            ulonglong2 v[SEL_UNROLL];
 #pragma unroll
             for (int k = 0; k < SEL_UNROLL; ++k) {
                 const int i = i0 + k * SELECT_THREADS;
-                hi[k] = i < n ? __ldg(I.ckey + i) : 0ull;
+                v[k] = i < n2 ? __ldg(ck2 + i) : make_ulonglong2(0ull, 0ull);
             }
 #pragma unroll
             for (int k = 0; k < SEL_UNROLL; ++k)
-                if (i0 + k * SELECT_THREADS < n) atomicAdd(&hist[key_code(hi[k])], 1u);
+                if (i0 + k * SELECT_THREADS < n2) {
+                    atomicAdd(&hist[key_code(v[k].x)], 1u);
+                    atomicAdd(&hist[key_code(v[k].y)], 1u);
+                }
         }
+        if ((n & 1) && tid == 0) atomicAdd(&hist[key_code(__ldg(I.ckey + n - 1))], 1u);
         __syncthreads();
         // Suffix sums: thread t owns bins [8t, 8t + 8); higher bins = better keys.
         constexpr int PER = SEL_BINS / SELECT_THREADS;
@@ -193,6 +201,39 @@ k_select(const Img* __restrict__ imgs, const Call* __restrict__ call, int sort_c
         const uint64_t pre_hi = st.pre_hi, msk_hi = st.msk_hi;
         const uint32_t pre_lo = st.pre_lo, msk_lo = st.msk_lo;
         const uint32_t code_b = (uint32_t)st.code_b;
+        if (coarse) {
+            // Two keys per 16-byte load; positions only for the candidates taken.
+            const ulonglong2* ck2 = reinterpret_cast<const ulonglong2*>(I.ckey);
+            const int n2 = (n + 1) >> 1;
+            for (int i0 = tid; i0 < n2; i0 += SEL_UNROLL * SELECT_THREADS) {
+                ulonglong2 v[SEL_UNROLL];
+#pragma unroll
+                for (int k = 0; k < SEL_UNROLL; ++k) {
+                    const int i = i0 + k * SELECT_THREADS;
+                    if (i < n2) {
+                        if (2 * i + 1 < n) v[k] = __ldg(ck2 + i);
+                        else v[k] = make_ulonglong2(__ldg(I.ckey + 2 * i), 0ull);
+                    } else {
+                        v[k] = make_ulonglong2(0ull, 0ull);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < SEL_UNROLL; ++k) {
+                    const int i = i0 + k * SELECT_THREADS;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint64_t key = h ? v[k].y : v[k].x;
+                        if (i < n2 && 2 * i + h < n && key_code(key) >= code_b) {
+                            const int pos = atomicAdd(&s_cnt, 1);
+                            if (pos < sort_cap) {
+                                skey[pos] = key;
+                                syx[pos] = __ldg(I.cyx + 2 * i + h);
+                            }
+                        }
+                    }
+                }
+            }
+        } else
         for (int i0 = tid; i0 < n; i0 += SEL_UNROLL * SELECT_THREADS) {
             uint64_t hi[SEL_UNROLL];
             uint32_t yx[SEL_UNROLL];
