@@ -89,8 +89,11 @@ typedef struct of_tuning {
                                      0: general FAST (fast_tile_h rows), then a threshold pass; 3: general
                                      FAST on 128 x 32 tiles with per-warp pipelines, then the pass; 4: the
                                      same on strips one cell row high, which also set the cell flags, then
-                                     the pass applies them (cells of 8..33 pixels) */
-    int32_t nms_tile_h;           /* NMS + Harris tile height: 32, 64 or 128 rows */
+                                     the pass applies them (cells of 8..33 pixels).  With nms_tile_h 32 the
+                                     NMS kernel applies the cell flags itself: the pass then only sets
+                                     flags where FAST does not */
+    int32_t nms_tile_h;           /* NMS + Harris tile height: 32 (per-warp kernel on the 128 x 32 detect
+                                     tiles), 64 or 128 rows (block kernels) */
     int32_t fast_tile_h;          /* general FAST tile height: 32, 64, 128 or 256 rows */
     int32_t candidates_tried;     /* configurations timed */
     float resize_ms, fast_ms, nms_ms;  /* best measured time of each tuned stage (all levels);
@@ -184,8 +187,8 @@ int64_t of_inspect(of_handle* h, int what, int frame, int level, void* dst, int6
  * launch configuration -- pyramid kernel (staged tiles of 32 or 64 rows, or
  * the persistent TMA kernel), persistent grid size and tile order of the FAST
  * and NMS kernels, the FAST tile height (32..256 rows) and NMS tile height
- * (32..128 rows), the FAST form (cell-tile kernel or general kernel +
- * threshold pass), and whether the frames run as one group or as 2..8 groups
+ * (32..128 rows), the FAST form (0..4, see of_tuning), and whether the frames
+ * run as one group or as 2..8 groups
  * on forked graph branches -- with CUDA events on these frames (reps
  * timed repetitions each, 1..100), keep the fastest for every later call with
  * the same shape, and run the batch once with it.  Arguments
