@@ -108,9 +108,9 @@ k_orient(const Img* __restrict__ imgs, int img_begin, int n_img, int slot_begin,
         if (I.fx) {
             k.x = I.fx[x];
             k.y = I.fy[y];
-        } else {
-            k.x = (float)((double)x * I.lscale);
-            k.y = (float)((double)y * I.lscale);
+        } else {  // no tables: a level-0 image (scale^0 = 1; the allocation-free entry point)
+            k.x = (float)x;
+            k.y = (float)y;
         }
         k.x_l = x;
         k.y_l = y;

@@ -74,7 +74,8 @@ struct Img {
     double lscale;             // scale^level
     // Level-0 coordinates of the level's pixel columns and rows: fx[x] =
     // (float)(x * scale^level), the product taken in float64 and rounded once
-    // (on the host).  Null: the orientation kernel computes them in float64.
+    // (on the host).  Null only for a level-0 image (the allocation-free entry
+    // point), whose coordinates are x and y themselves.
     const float* fx;
     const float* fy;
     // Learned path: one byte per 32 x 32 proposal tile on the detect-tile grid
