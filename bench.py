@@ -299,7 +299,7 @@ FAST_OPS_PER_PX = 40.5
 # levels, divided by the frames.  Valid while the kernels' code
 # (kernels_sha1) and the per-stage launch choices below are the ones captured;
 # otherwise the line reports null.
-STAGE_TRAFFIC = {"code_sha1": "331ccc37f647a52c71eb38eae85e0668020b3979", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 32}, "l2_bytes_per_frame": {"pyramid": 24140580, "fast": 30254682, "nms_harris": 37314614, "select": 2578267, "orient": 2479251}, "dram_bytes_per_frame": {"pyramid": 7741092, "fast": 12241248, "nms_harris": 14585316, "select": 1024736, "orient": 531220}}
+STAGE_TRAFFIC = {"code_sha1": "5143eca0819dc2e22ddf4dfee92bbe39474edc5c", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 32}, "l2_bytes_per_frame": {"pyramid": 24106350, "fast": 30283002, "nms_harris": 37436153, "select": 2577936, "orient": 2481392}, "dram_bytes_per_frame": {"pyramid": 7742368, "fast": 12246744, "nms_harris": 14594332, "select": 1024108, "orient": 531224}}
 
 
 def code_sha1(path):
