@@ -448,6 +448,32 @@ def test_frame_groups_equal_one_group_and_oracle():
     det.close()
 
 
+@pytest.mark.parametrize("t", [1, 20])
+def test_per_warp_nms_without_cell_fallback(t):
+    """The per-warp NMS kernel (32-row tiles) on maps without a per-cell fallback
+    (t_lo = t_hi: nothing to apply, the maps are the candidate scores) and at t = 1
+    (every positive score a candidate), after FAST forms 0, 1 and 4: the oracle's
+    keypoints, score maps and candidates on every level."""
+    img = synth.scene(1000, 700, 31 + t, background="pink")
+    dev = torch.from_numpy(img).cuda()
+    det = ofg.Detector(1000, 700, max_levels=3, max_features=800)
+    ora = oracle.detect(img, levels=3, scale=1.2, fast_t=t, n_features=800)
+    for form in (0, 1, 4):
+        tun = ofg.OfTuning(resize_tile_h=64, resize_tma=1, fast_blocks_per_sm=2, nms_blocks_per_sm=2,
+                           stream_groups=1, fast_cell_tiles=form, nms_tile_h=32, fast_tile_h=32)
+        det.set_tuning([dev], tun, levels=3, scale=1.2, fast_t=t, n_features=800)
+        det.detect_batch([dev], levels=3, scale=1.2, fast_t=t, n_features=800)
+        torch.cuda.synchronize()
+        compare_keypoints(det.batch_results(1, 800)[0], ora)
+        for level in range(3):
+            lev = oracle.pyramid_level(img, 3, 1.2, level)
+            sm, T, cands = oracle_cands(lev, 19, 30, t, t)
+            g_sm, _ = det.inspect(ofg.OF_BUF_SCORE, 0, level)
+            np.testing.assert_array_equal(g_sm.reshape(lev.shape), clipped(sm, t), err_msg=f"form {form} score {level}")
+            assert gpu_cands(det, 0, level) == cands, f"form {form} candidates {level}"
+    det.close()
+
+
 @pytest.mark.parametrize("cell", [8, 13, 15, 30, 31, 40])
 def test_cell_sizes_both_fast_forms(cell):
     """Both FAST forms -- the cell-tile kernel (cells of 8..30 pixels) and the
