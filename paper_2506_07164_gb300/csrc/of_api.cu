@@ -800,14 +800,18 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     P->tun.resize_tile_h = RS_TILE_HS[1];
     P->tun.resize_tma = 1;
     P->tun.stream_groups = 1;
-    // Untuned plans: a few frames per call are launch-bound, where the cell-tile
-    // form saves the threshold pass's launch; larger batches take the
-    // cell-row strips (form 4), the autotuner's choice on 1080p batches.
-    P->tun.fast_cell_tiles = (nf >= 4 && P->strip_ok) ? 4 : P->cell_tiles ? 1 : 0;
+    // Untuned plans.  Batches of 4 frames or more start from the autotuner's
+    // choice on 1080p batches: the cell-row strips (form 4, which set the cell
+    // flags) and the per-warp NMS kernel, which applies them (no threshold
+    // pass).  Fewer frames per call are launch-bound; there the cell-tile form
+    // with the block NMS kernel measured faster (0.144 against 0.150 ms for
+    // one 1080p frame per call).
+    const bool big = nf >= 4 && P->strip_ok;
+    P->tun.fast_cell_tiles = big ? 4 : P->cell_tiles ? 1 : 0;
     P->tun.fast_tile_h = 32;
     P->tun.fast_blocks_per_sm = plan_fast_bps(P);
-    P->tun.nms_tile_h = 64;
-    P->tun.nms_blocks_per_sm = nms_blocks_per_sm(64, true);
+    P->tun.nms_tile_h = big ? 32 : 64;
+    P->tun.nms_blocks_per_sm = nms_blocks_per_sm(P->tun.nms_tile_h, true);
     for (int i = 0; i < 2; ++i)  // raise the tall kernels' shared-memory limits before any capture
         for (int fl = 0; fl < 2; ++fl) fast_blocks_per_sm(FT_HS[i], fl != 0);
     for (int th = 32; th <= 128; th *= 2)
