@@ -62,6 +62,7 @@ def _oracle_detect(img):
 
 
 SERVE_SIZES = [(640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
+DISPARITIES = (4, 9, 14, 19)  # stereo pairs of the serving mix: right view = left shifted by one of these
 # The uneven-size batch: 64 frames drawn uniformly from these sizes, 8 levels each (~512 images).
 MIXED_SIZES = [(720, 540), (1080, 720), (1440, 1080), (1920, 1080)]
 MIXED_FRAMES = 64
@@ -81,10 +82,12 @@ def _gen_sized(args):
     return synth.scene(w, h, seed, background="pink")
 
 
-def serving_leg(pool, seconds: float, rate: float, seed: int = 0, clients: int = 1):
+def serving_leg(pool, seconds: float, rate: float, seed: int = 0, clients: int = 1, max_outstanding: int = 0):
     """Poisson arrivals at `rate` frames/s of the mixed-size workload (split
     over `clients` submitting threads), through the continuous-batching
-    server; returns latency percentiles and throughput."""
+    server; returns latency percentiles and throughput.  max_outstanding > 0:
+    a client waits while that many frames are submitted and not yet returned
+    (a bounded backlog when the offered rate exceeds what the server serves)."""
     import threading
 
     import numpy as np
@@ -93,6 +96,15 @@ def serving_leg(pool, seconds: float, rate: float, seed: int = 0, clients: int =
 
     frames = {sz: pool.map(_gen_sized, [(sz[0], sz[1], 500 + 10 * i + k) for k in range(3)])
               for i, sz in enumerate(SERVE_SIZES)}
+
+    def shifted(img, d):  # right view: the left one shifted by disparity d, last column repeated
+        right = np.empty_like(img)
+        right[:, : img.shape[1] - d] = img[:, d:]
+        right[:, img.shape[1] - d:] = img[:, -1:]
+        return right
+
+    # Right views made before timing, so the submitting threads only submit.
+    rights = {sz: [[shifted(img, d) for d in DISPARITIES] for img in frames[sz]] for sz in SERVE_SIZES}
     srv = ofg.of_server_create(max_w=3840, max_h=2160, levels=LEVELS, scale=SCALE, fast_t=FAST_T,
                                fast_t_lo=FAST_T_LO, harris_k=HARRIS_K, n_features=NFEAT, slots=4,
                                max_batch=16, memory_budget=12 << 30)
@@ -108,19 +120,20 @@ def serving_leg(pool, seconds: float, rate: float, seed: int = 0, clients: int =
             now = time.perf_counter()
             if t_next > now:
                 time.sleep(t_next - now)
+            while max_outstanding and sum(submitted) - len(done) > max_outstanding:
+                time.sleep(0.001)
+            if time.perf_counter() - t0 >= seconds:
+                break  # a backlog-bound client stops at the leg's end, not at its schedule's
             sz = SERVE_SIZES[int(rng.integers(0, len(SERVE_SIZES)))]
-            img = frames[sz][int(rng.integers(0, 3))]
             if rng.random() < 0.2:  # stereo pair: right view = left shifted by a seeded disparity
-                d = int(rng.integers(4, 24))
-                right = np.empty_like(img)
-                right[:, : img.shape[1] - d] = img[:, d:]
-                right[:, img.shape[1] - d:] = img[:, -1:]
-                ofg.of_server_submit(srv, img, tag=1)
+                k = int(rng.integers(0, 3))
+                right = rights[sz][k][int(rng.integers(0, len(DISPARITIES)))]
+                ofg.of_server_submit(srv, frames[sz][k], tag=1)
                 ofg.of_server_submit(srv, right, tag=2)
                 submitted[c] += 2
                 t_next += float(rng.exponential(2.0 / crate))
             else:
-                ofg.of_server_submit(srv, img, tag=0)
+                ofg.of_server_submit(srv, frames[sz][int(rng.integers(0, 3))], tag=0)
                 submitted[c] += 1
                 t_next += float(rng.exponential(1.0 / crate))
 
@@ -148,14 +161,17 @@ def serving_leg(pool, seconds: float, rate: float, seed: int = 0, clients: int =
     first = min(a for a, *_ in done)
     last = max(b for _, b, *_ in done)
     ok = sum(1 for d in done if d[2] >= 0)
-    return {"offered_rate_fps": round(sum(submitted) / seconds, 1), "client_threads": clients,
+    return {"offered_rate_fps": round(rate, 1), "submitted_fps": round(sum(submitted) / seconds, 1),
+            "client_threads": clients,
             "frames": len(done), "ok": ok,
             "frames_per_s": round(len(done) / (last - first), 1),
             "mpix_per_s": round(sum(d[4] for d in done) / (last - first) / 1e6, 1),
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
             "mean_ms": round(float(lat.mean()), 3), "mean_batch_frames": round(float(np.mean([d[3] for d in done])), 2),
             "batches": stats["batches"], "slots": 4, "memory_budget_bytes": 12 << 30,
-            "mix": "uniform over 640x480/1280x720/1920x1080/3840x2160; 20% of arrivals are stereo pairs",
+            "max_outstanding": max_outstanding or None,
+            "mix": "uniform over 640x480/1280x720/1920x1080/3840x2160; 20% of arrivals are stereo pairs "
+                   "(right view shifted by 4, 9, 14 or 19 px)",
             "seconds": seconds}
 
 
@@ -460,8 +476,9 @@ def main():
     ap.add_argument("--skip-plain", action="store_true", help="skip the per-frame path (profiling)")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serving leg duration (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=500.0, help="Poisson arrival rate, frames/s")
-    ap.add_argument("--serve-sat-rate", type=float, default=6000.0,
-                    help="offered rate of the saturated serving leg, frames/s (0: skip)")
+    ap.add_argument("--serve-sat-rate", type=float, default=20000.0,
+                    help="offered rate of the saturated serving leg, frames/s, with at most 512 frames "
+                         "outstanding (0: skip)")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-buffer path (profiling)")
     ap.add_argument("--skip-learned", action="store_true", help="skip the learned tile-proposal leg")
     ap.add_argument("--skip-ablation", action="store_true", help="skip the paper-variant ablation leg")
@@ -805,7 +822,8 @@ def main():
     if args.serve_seconds > 0:
         serving = serving_leg(pool, args.serve_seconds, args.serve_rate)
         if args.serve_sat_rate > 0:
-            serving_sat = serving_leg(pool, args.serve_seconds, args.serve_sat_rate, seed=1, clients=4)
+            serving_sat = serving_leg(pool, args.serve_seconds, args.serve_sat_rate, seed=1, clients=8,
+                                      max_outstanding=512)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -9,9 +9,14 @@
 //   - whenever a slot is free, admits the oldest queued request and every
 //     later queued request of the same resolution, in arrival order, while the
 //     batch still fits the slot's scratch and input bytes and max_batch;
-//   - launches the batch asynchronously on the slot's stream: host frames ->
-//     pinned staging -> device (one copy), the cached batch graph, device ->
-//     pinned results, an event.
+//   - launches the batch asynchronously on the slot's stream: one copy per
+//     frame from its pinned request buffer to the device, the cached batch
+//     graph, device -> pinned results, an event.
+// A submitting thread copies its frame straight into a pinned buffer from the
+// server's pool (reused after the frame's batch completes; grown up to a cap,
+// beyond which a request falls back to pageable memory and the slot's pinned
+// staging), so the host copies run on the callers' threads, not on the
+// dispatcher.
 // Requests that arrive while other batches are on the GPU are admitted as
 // soon as a slot and its memory free up, and batches on different slots run
 // concurrently on the device.  A batch's pyramids stay resident in its
@@ -52,7 +57,9 @@ size_t up16(size_t x) { return (x + 15) / 16 * 16; }
 struct Request {
     int64_t id = 0, tag = 0;
     int w = 0, h = 0;
-    std::vector<uint8_t> pixels;  // packed rows, w bytes each
+    uint8_t* pin = nullptr;       // pinned pool buffer holding the packed rows (w bytes each), or null:
+    size_t pin_cap = 0;
+    std::vector<uint8_t> pixels;  // the packed rows in pageable memory
     double t_submit = 0, t_launch = 0;
 };
 
@@ -93,6 +100,10 @@ struct of_server {
     int64_t next_id = 0;
     of_server_stats st{};
     std::string fatal;
+    // Pinned request buffers: free list (capacity, buffer) and bytes allocated.
+    std::mutex pool_mu;
+    std::vector<std::pair<size_t, uint8_t*>> pool_free;
+    size_t pool_bytes = 0, pool_cap = 0;
 };
 
 namespace {
@@ -100,6 +111,48 @@ namespace {
 int64_t batch_bytes(of_server* S, int w, int h, int n) {
     std::vector<int32_t> ws(n, w), hs(n, h);
     return of_batch_bytes(&S->hp, ws.data(), hs.data(), n, S->p.levels, S->p.scale, S->p.n_features);
+}
+
+// A pinned buffer of at least `need` bytes from the pool (the smallest that
+// fits), a new one while the pool is under its cap, else null.
+uint8_t* pool_take(of_server* S, size_t need, size_t* cap) {
+    {
+        std::lock_guard<std::mutex> lk(S->pool_mu);
+        int best = -1;
+        for (int i = 0; i < (int)S->pool_free.size(); ++i)
+            if (S->pool_free[i].first >= need && (best < 0 || S->pool_free[i].first < S->pool_free[best].first))
+                best = i;
+        if (best >= 0) {
+            uint8_t* b = S->pool_free[best].second;
+            *cap = S->pool_free[best].first;
+            S->pool_free.erase(S->pool_free.begin() + best);
+            return b;
+        }
+        if (S->pool_bytes + need > S->pool_cap) return nullptr;
+        S->pool_bytes += need;
+    }
+    void* b = nullptr;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != S->device) cudaSetDevice(S->device);
+    const cudaError_t e = cudaHostAlloc(&b, need, cudaHostAllocPortable);
+    if (prev >= 0 && prev != S->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(S->pool_mu);
+        S->pool_bytes -= need;
+        return nullptr;
+    }
+    *cap = need;
+    return static_cast<uint8_t*>(b);
+}
+
+void pool_give(of_server* S, Request& rq) {
+    if (!rq.pin) return;
+    std::lock_guard<std::mutex> lk(S->pool_mu);
+    S->pool_free.emplace_back(rq.pin_cap, rq.pin);
+    rq.pin = nullptr;
+    rq.pin_cap = 0;
 }
 
 // Completes every finished slot.  Called by the dispatcher only.
@@ -131,6 +184,7 @@ void reap(of_server* S) {
             if (c > 0) d.kpts.assign(sl.h_out + i * (size_t)nf, sl.h_out + i * (size_t)nf + c);
             out.push_back(std::move(d));
         }
+        for (Request& rq : sl.batch) pool_give(S, rq);  // the batch's copies are done
         sl.batch.clear();
         sl.busy = false;
         {
@@ -176,13 +230,20 @@ int launch(of_server* S, Slot& sl) {
     for (int i = 0; i < n; ++i) {
         Request& rq = sl.batch[i];
         rq.t_launch = t;
-        uint8_t* dst = sl.h_in + i * fbytes;
-        for (int y = 0; y < h; ++y) std::memcpy(dst + (size_t)y * pitch, rq.pixels.data() + (size_t)y * w, w);
-        std::vector<uint8_t>().swap(rq.pixels);
+        const uint8_t* src = rq.pin;
+        size_t spitch = (size_t)w;
+        if (!src) {  // pageable request: through the slot's pinned staging
+            uint8_t* dst = sl.h_in + i * fbytes;
+            for (int y = 0; y < h; ++y) std::memcpy(dst + (size_t)y * pitch, rq.pixels.data() + (size_t)y * w, w);
+            std::vector<uint8_t>().swap(rq.pixels);
+            src = dst;
+            spitch = (size_t)pitch;
+        }
+        if (cudaMemcpy2DAsync(sl.d_in + i * fbytes, pitch, src, spitch, w, h, cudaMemcpyHostToDevice, sl.stream) !=
+            cudaSuccess)
+            return OF_ERR_CUDA;
         frames[i] = of_frame{sl.d_in + i * fbytes, w, h, pitch};
     }
-    if (cudaMemcpyAsync(sl.d_in, sl.h_in, n * fbytes, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
-        return OF_ERR_CUDA;
     const int rc = of_detect_batch(sl.H, frames.data(), n, S->p.levels, S->p.scale, S->p.fast_t,
                                    S->p.harris_k, S->p.n_features, sl.d_out, sl.d_counts);
     if (rc != OF_OK) return rc;
@@ -212,7 +273,9 @@ void dispatcher(of_server* S) {
             }
             const int rc = launch(S, sl);
             if (rc != OF_OK) {
-                // Report every request of the failed batch.
+                // Report every request of the failed batch (its copies queued so far finish first).
+                cudaStreamSynchronize(sl.stream);
+                for (Request& rq : sl.batch) pool_give(S, rq);
                 std::lock_guard<std::mutex> lk(S->mu);
                 for (auto& rq : sl.batch) {
                     Done d;
@@ -338,6 +401,8 @@ of_server* of_server_create(const of_server_params* pin) {
         sl.in_cap = in_cap;
         sl.arena_cap = arena;
     }
+    // Pinned request buffers: enough for two full batches per slot, at most 2 GiB.
+    S->pool_cap = std::min((size_t)2 << 30, (size_t)2 * p.slots * p.max_batch * (size_t)p.max_w * p.max_h);
     S->st.slot_arena_bytes = arena;
     S->st.slot_input_bytes = (int64_t)in_cap;
     S->worker = std::thread(dispatcher, S);
@@ -351,8 +416,12 @@ void of_server_destroy(of_server* S) {
     if (S->worker.joinable()) S->worker.join();
     for (Slot& sl : S->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
+        for (Request& rq : sl.batch) pool_give(S, rq);
         free_slot(sl);
     }
+    for (Request& rq : S->queue) pool_give(S, rq);
+    for (auto& b : S->pool_free) cudaFreeHost(b.second);
+    S->pool_free.clear();
     delete S;
 }
 
@@ -363,8 +432,16 @@ int64_t of_server_submit(of_server* S, const uint8_t* img, int w, int h, int pit
     rq.tag = tag;
     rq.w = w;
     rq.h = h;
-    rq.pixels.resize((size_t)w * h);
-    for (int y = 0; y < h; ++y) std::memcpy(rq.pixels.data() + (size_t)y * w, img + (size_t)y * pitch, w);
+    const size_t need = (size_t)w * h;
+    rq.pin = pool_take(S, need, &rq.pin_cap);
+    uint8_t* dst = rq.pin;
+    if (!dst) {
+        rq.pixels.resize(need);
+        dst = rq.pixels.data();
+    }
+    if (pitch == w) std::memcpy(dst, img, need);
+    else
+        for (int y = 0; y < h; ++y) std::memcpy(dst + (size_t)y * w, img + (size_t)y * pitch, w);
     rq.t_submit = now_s();
     int64_t id;
     {
