@@ -149,7 +149,7 @@ def serving_leg(pool, seconds: float, rate: float, seed: int = 0, clients: int =
     for th in ths:
         th.start()
     while any(th.is_alive() for th in ths) or len(done) < sum(submitted):
-        for r, _ in ofg.of_server_poll(srv, 256, NFEAT, wait_ms=20):
+        for r, _ in ofg.of_server_poll(srv, 256, NFEAT, wait_ms=20, keypoints=False):
             done.append((r.t_submit, r.t_done, r.count, r.batch_frames, r.w * r.h))
         if not any(th.is_alive() for th in ths) and time.perf_counter() - wall0 > seconds + 60:
             break

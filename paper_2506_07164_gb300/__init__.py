@@ -58,7 +58,8 @@ class OfTuning(C.Structure):
     stream_groups (1..8): frame groups on forked graph branches; fast_cell_tiles:
     0 general FAST + threshold pass, 1 cell-tile kernel, 2 cell-aligned general kernel,
     3 general FAST with per-warp pipelines + threshold pass, 4 the same on cell-row strips
-    that also set the cell flags + the pass applying them;
+    that also set the cell flags + the pass applying them (with nms_tile_h 32 the per-warp
+    NMS kernel applies the flags itself and the pass only sets flags FAST leaves unset);
     fast_tile_h (32/64/128/256) and nms_tile_h (32/64/128): tile heights.  The last
     four fields report the autotuner's search (candidates, best stage times in ms)."""
 
@@ -374,15 +375,24 @@ def of_server_submit(s: int, img: np.ndarray, tag: int = 0) -> int:
     return _check(int(load().of_server_submit(s, img.ctypes.data, img.shape[1], img.shape[0], img.strides[0], tag)))
 
 
-def of_server_poll(s: int, max_results: int, n_features: int, wait_ms: int = 0):
-    """Returns a list of (OfServerResult, keypoints ndarray)."""
+_poll_buffers = {}
+
+
+def of_server_poll(s: int, max_results: int, n_features: int, wait_ms: int = 0, keypoints: bool = True):
+    """Returns a list of (OfServerResult, keypoints ndarray or None).  The
+    keypoints land in a buffer kept per (max_results, n_features) and are
+    copied out per result; keypoints=False returns the results only."""
     res = (OfServerResult * max_results)()
-    kp = np.zeros(max_results * n_features, KEYPOINT_DTYPE)
-    n = _check(load().of_server_poll(s, res, kp.ctypes.data, max_results, wait_ms))
+    kp = None
+    if keypoints:
+        kp = _poll_buffers.get((max_results, n_features))
+        if kp is None:
+            kp = _poll_buffers[(max_results, n_features)] = np.empty(max_results * n_features, KEYPOINT_DTYPE)
+    n = _check(load().of_server_poll(s, res, kp.ctypes.data if kp is not None else None, max_results, wait_ms))
     out = []
     for i in range(n):
         c = res[i].count
-        out.append((res[i], kp[i * n_features: i * n_features + max(c, 0)].copy()))
+        out.append((res[i], kp[i * n_features: i * n_features + max(c, 0)].copy() if kp is not None else None))
     return out
 
 
