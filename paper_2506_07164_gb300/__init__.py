@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import threading
 
 import numpy as np
 
@@ -375,19 +376,23 @@ def of_server_submit(s: int, img: np.ndarray, tag: int = 0) -> int:
     return _check(int(load().of_server_submit(s, img.ctypes.data, img.shape[1], img.shape[0], img.strides[0], tag)))
 
 
-_poll_buffers = {}
+_poll_local = threading.local()
 
 
 def of_server_poll(s: int, max_results: int, n_features: int, wait_ms: int = 0, keypoints: bool = True):
     """Returns a list of (OfServerResult, keypoints ndarray or None).  The
-    keypoints land in a buffer kept per (max_results, n_features) and are
-    copied out per result; keypoints=False returns the results only."""
+    keypoints land in a buffer the calling thread keeps per (max_results,
+    n_features) and are copied out per result; keypoints=False returns the
+    results only."""
     res = (OfServerResult * max_results)()
     kp = None
     if keypoints:
-        kp = _poll_buffers.get((max_results, n_features))
+        bufs = getattr(_poll_local, "bufs", None)
+        if bufs is None:
+            bufs = _poll_local.bufs = {}
+        kp = bufs.get((max_results, n_features))
         if kp is None:
-            kp = _poll_buffers[(max_results, n_features)] = np.empty(max_results * n_features, KEYPOINT_DTYPE)
+            kp = bufs[(max_results, n_features)] = np.empty(max_results * n_features, KEYPOINT_DTYPE)
     n = _check(load().of_server_poll(s, res, kp.ctypes.data if kp is not None else None, max_results, wait_ms))
     out = []
     for i in range(n):
