@@ -481,10 +481,9 @@ __device__ __forceinline__ uint32_t threshold_word(uint32_t v, uint32_t fm, uint
 
 template <bool APPLY, bool SMALL_T>
 __global__ void __launch_bounds__(DET_THREADS, 2)
-k_nms_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const int32_t* __restrict__ prefix,
-           int n_list, int n_tiles, const CUtensorMap* __restrict__ img_maps,
-           const CUtensorMap* __restrict__ score_maps, const Call* __restrict__ call, int t_hi, int t_lo,
-           int border, int cell, uint32_t cell_magic, int order) {
+k_nms_warp(const Img* __restrict__ imgs, const uint2* __restrict__ items, int n_tiles,
+           const CUtensorMap* __restrict__ img_maps, const CUtensorMap* __restrict__ score_maps,
+           const Call* __restrict__ call, int t_hi, int t_lo, int border, int cell, uint32_t cell_magic, int order) {
     extern __shared__ __align__(128) uint8_t nw_raw[];
     uint8_t* const dyn = nw_raw + ((128u - (smem_u32(nw_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t mbar[NW_WARPS][2];  // [0] score box, [1] image box
@@ -499,12 +498,9 @@ k_nms_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const
     }
     __syncwarp();
     const int nw = gridDim.x * NW_WARPS, gw = blockIdx.x * NW_WARPS + w;
-    auto locate = [&](int t) {
-        const int j = find_tile_job(prefix, n_list, t);
-        const int ii = __ldg(list + j);
-        const Img& I = imgs[ii];
-        const int tt = t - __ldg(prefix + j);
-        return NmsTile{ii, I.tile_x0 + (tt % I.tiles_x) * TILE_W, border + (tt / I.tiles_x) * TILE_H};
+    auto locate = [&](int t) {  // the plan's item table: (image, (y0 << 16) | x0)
+        const uint2 e = __ldg(items + t);
+        return NmsTile{(int)e.x, (int)(e.y & 0xFFFFu), (int)(e.y >> 16)};
     };
     auto issue_s = [&](const NmsTile& ti) {  // lane 0
         tensormap_acquire(score_maps + ti.img);
@@ -712,32 +708,30 @@ k_nms_warp(const Img* __restrict__ imgs, const int32_t* __restrict__ list, const
 }
 
 template <bool APPLY, bool SMALL_T>
-static void launch_nms_warp_t(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list,
-                              int n_tiles, const CUtensorMap* img_maps, const CUtensorMap* score_maps,
-                              const Call* call, int t_hi, int t_lo, int border, int cell, int grid, int order,
-                              void* stream) {
+static void launch_nms_warp_t(const Img* imgs, const uint2* items, int n_tiles, const CUtensorMap* img_maps,
+                              const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo, int border,
+                              int cell, int grid, int order, void* stream) {
     const uint32_t magic = 0xFFFFFFFFu / (uint32_t)cell + 1u;
     k_nms_warp<APPLY, SMALL_T><<<grid, DET_THREADS, NW_DYN, (cudaStream_t)stream>>>(
-        imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, magic,
-        order);
+        imgs, items, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell, magic, order);
 }
 
-void launch_nms_warp(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list, int n_tiles,
-                     const CUtensorMap* img_maps, const CUtensorMap* score_maps, const Call* call, int t_hi,
-                     int t_lo, int border, int cell, int grid, int order, void* stream, bool apply) {
+void launch_nms_warp(const Img* imgs, const uint2* items, int n_tiles, const CUtensorMap* img_maps,
+                     const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo, int border, int cell,
+                     int grid, int order, void* stream, bool apply) {
     if (n_tiles <= 0) return;
     const int warps = (n_tiles + NW_WARPS - 1) / NW_WARPS;
     grid = grid < warps ? grid : warps;
     apply = apply && t_hi != t_lo;
     if (!apply)
-        launch_nms_warp_t<false, true>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call,
-                                       t_hi, t_lo, border, cell, grid, order, stream);
+        launch_nms_warp_t<false, true>(imgs, items, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell,
+                                       grid, order, stream);
     else if (t_hi - t_lo + 1 <= 128)
-        launch_nms_warp_t<true, true>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call,
-                                      t_hi, t_lo, border, cell, grid, order, stream);
+        launch_nms_warp_t<true, true>(imgs, items, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell,
+                                      grid, order, stream);
     else
-        launch_nms_warp_t<true, false>(imgs, img_list, tile_prefix, n_list, n_tiles, img_maps, score_maps, call,
-                                       t_hi, t_lo, border, cell, grid, order, stream);
+        launch_nms_warp_t<true, false>(imgs, items, n_tiles, img_maps, score_maps, call, t_hi, t_lo, border, cell,
+                                       grid, order, stream);
 }
 
 // Resident blocks per SM of the per-warp NMS kernel (also raises its dynamic shared-memory limit).

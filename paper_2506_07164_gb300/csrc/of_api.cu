@@ -221,6 +221,7 @@ struct Plan {
         int dl_begin = 0, n_list = 0, det_tiles = 0, dp_off = 0;
         int fast_tiles = 0, fp_off = 0;             // cell-tile FAST: tiles and prefix offset in gp_fast
         int cs_strips = 0, cs_off = 0;              // cell-strip FAST: strips and prefix offset in gp_cstrip
+        int csi_off = 0, dti_off = 0;               // item tables: cell strips, 128 x 32 detect tiles
         int nms64_tiles = 0, np_off = 0;            // NMS with 64-row tiles: tiles and prefix offset in gp_nms64
         int ftall_tiles[2] = {0, 0}, ftall_off[2] = {0, 0};  // FAST on FT_HS[i]-row tiles: tiles, offset in gp_ftall[i]
         int fal_tiles = 0, fal_off = 0;             // cell-aligned FAST: tiles and prefix offset in gp_fal
@@ -231,6 +232,8 @@ struct Plan {
     };
     std::vector<Group> groups[kMaxGroups + 1];
     std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_ftall[2], gp_fal, gp_cstrip;
+    // Work-item tables of the per-warp kernels, per group: (image, (y0 << 16) | x0).
+    std::vector<uint2> items_cs, items_dt;
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
     bool apply_flags = false;    // the threshold pass can set the cell flags (else the general FAST kernel does)
     bool strip_ok = false;       // the cell size allows the cell-row strip kernel (cells of 8..33 pixels)
@@ -242,7 +245,7 @@ struct Plan {
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0, off_ftab = 0;
     size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gft[2] = {0, 0}, off_gfal = 0,
-           off_gcs = 0;
+           off_gcs = 0, off_ics = 0, off_idt = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -275,6 +278,8 @@ struct Plan {
     const int32_t* d_gfp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfp); }
     const int32_t* d_grp() const { return reinterpret_cast<const int32_t*>(dbuf + off_grp); }
     const int32_t* d_gcs() const { return reinterpret_cast<const int32_t*>(dbuf + off_gcs); }
+    const uint2* d_ics() const { return reinterpret_cast<const uint2*>(dbuf + off_ics); }
+    const uint2* d_idt() const { return reinterpret_cast<const uint2*>(dbuf + off_idt); }
     const int32_t* d_gnp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gnp); }
     const int32_t* d_gft(int i) const { return reinterpret_cast<const int32_t*>(dbuf + off_gft[i]); }
     const int32_t* d_gfal() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfal); }
@@ -393,9 +398,8 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                                     G.fal_tiles, P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
                                     H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
             else if (strip_form(P))
-                launch_fast_cstrip(P->d_img(), P->d_dl() + G.dl_begin, P->d_gcs() + G.cs_off, G.n_list, G.cs_strips,
-                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                                   H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
+                launch_fast_cstrip(P->d_img(), P->d_ics() + G.csi_off, G.cs_strips, P->d_maps(), P->d_call(), s.t_hi,
+                                   s.t_lo, s.border, s.cell, H->n_sms * P->tun.fast_blocks_per_sm, P->tun.fast_order, st);
             else if (cell_form(P))
                 launch_fast_cells(P->d_img(), P->d_dl() + G.dl_begin, P->d_gfp() + G.fp_off, G.n_list, G.fast_tiles,
                                   P->d_maps(), P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
@@ -432,9 +436,9 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
             }
             const bool fin = true;
             if (P->tun.nms_tile_h == 32)
-                launch_nms_warp(P->d_img(), P->d_dl() + G.dl_begin, P->d_gdp() + G.dp_off, G.n_list, G.det_tiles,
-                                P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo, s.border, s.cell,
-                                H->n_sms * P->tun.nms_blocks_per_sm, P->tun.nms_order, st, nms_applies(P));
+                launch_nms_warp(P->d_img(), P->d_idt() + G.dti_off, G.det_tiles, P->d_maps(), P->d_maps() + P->n_img,
+                                P->d_call(), s.t_hi, s.t_lo, s.border, s.cell, H->n_sms * P->tun.nms_blocks_per_sm,
+                                P->tun.nms_order, st, nms_applies(P));
             else if (P->tun.nms_tile_h == 64)
                 launch_nms_harris(P->d_img(), P->d_dl() + G.dl_begin, P->d_gnp() + G.np_off, G.n_list,
                                   G.nms64_tiles, P->d_maps(), P->d_maps() + P->n_img, P->d_call(), s.t_hi, s.t_lo,
@@ -732,8 +736,20 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             for (int i = 0; i < 2; ++i) G.ftall_off[i] = (int)P->gp_ftall[i].size();
             G.fal_off = (int)P->gp_fal.size();
             G.cs_off = (int)P->gp_cstrip.size();
+            G.csi_off = (int)P->items_cs.size();
+            G.dti_off = (int)P->items_dt.size();
             for (int j = j0; j < j1; ++j) {
                 const Img& I = P->h_img[P->det_list[j]];
+                const uint32_t ii = (uint32_t)P->det_list[j];
+                for (int ty = 0; ty < I.tiles_y; ++ty)  // tile t = ty * tiles_x + tx, as the prefixes count
+                    for (int tx = 0; tx < I.tiles_x; ++tx)
+                        P->items_dt.push_back(make_uint2(
+                            ii, ((uint32_t)(s.border + ty * TILE_H) << 16) | (uint32_t)(I.tile_x0 + tx * TILE_W)));
+                if (P->strip_ok)
+                    for (int cy = 0; cy < I.ncy; ++cy)
+                        for (int tx = 0; tx < I.tiles_x; ++tx)
+                            P->items_cs.push_back(make_uint2(
+                                ii, ((uint32_t)(s.border + cy * s.cell) << 16) | (uint32_t)(I.tile_x0 + tx * TILE_W)));
                 P->gp_nms64.push_back(G.nms64_tiles);
                 G.nms64_tiles += I.tiles_x * ((I.h - 2 * s.border + 63) / 64);
                 for (int i = 0; i < 2; ++i) {
@@ -882,6 +898,10 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_fal.size(), 1), 16);
     P->off_gcs = off;
     off = align_up(off + sizeof(int32_t) * std::max<size_t>(P->gp_cstrip.size(), 1), 16);
+    P->off_ics = off;
+    off = align_up(off + sizeof(uint2) * std::max<size_t>(P->items_cs.size(), 1), 16);
+    P->off_idt = off;
+    off = align_up(off + sizeof(uint2) * std::max<size_t>(P->items_dt.size(), 1), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -916,6 +936,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     for (int i = 0; i < 2; ++i) put(P->off_gft[i], P->gp_ftall[i].data(), sizeof(int32_t) * P->gp_ftall[i].size());
     put(P->off_gfal, P->gp_fal.data(), sizeof(int32_t) * P->gp_fal.size());
     put(P->off_gcs, P->gp_cstrip.data(), sizeof(int32_t) * P->gp_cstrip.size());
+    put(P->off_ics, P->items_cs.data(), sizeof(uint2) * P->items_cs.size());
+    put(P->off_idt, P->items_dt.data(), sizeof(uint2) * P->items_dt.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);

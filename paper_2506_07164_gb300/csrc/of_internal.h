@@ -163,9 +163,8 @@ int fast_warp_blocks_per_sm();
 // Cell-row strips (one cell row of one 128-column tile per warp item; cells
 // of 8..33 pixels): general FAST that also sets the cell flags exactly.
 constexpr int CS_MAX_CELL = 33;
-void launch_fast_cstrip(const Img* imgs, const int32_t* img_list, const int32_t* strip_prefix, int n_list,
-                        int n_strips, const CUtensorMap* maps, const Call* call, int t_hi, int t_lo, int border,
-                        int cell, int grid, int order, void* stream);
+void launch_fast_cstrip(const Img* imgs, const uint2* items, int n_strips, const CUtensorMap* maps, const Call* call,
+                        int t_hi, int t_lo, int border, int cell, int grid, int order, void* stream);
 int fast_cstrip_blocks_per_sm();
 // Threshold pass: flags 1: sets the cell flags (when the FAST kernel did
 // not), 2: only for images with proposal tiles, 0: never; apply: applies them
@@ -185,9 +184,9 @@ int nms_blocks_per_sm(int tile_h, bool final_scores);
 // FAST's offset scores and the cell flags are set (cells of 8 or more rows);
 // the kernel applies the per-cell thresholds to the staged words itself.
 // Otherwise the maps hold S(p).  Scores outside proposed tiles count as 0.
-void launch_nms_warp(const Img* imgs, const int32_t* img_list, const int32_t* tile_prefix, int n_list, int n_tiles,
-                     const CUtensorMap* img_maps, const CUtensorMap* score_maps, const Call* call, int t_hi,
-                     int t_lo, int border, int cell, int grid, int order, void* stream, bool apply);
+void launch_nms_warp(const Img* imgs, const uint2* items, int n_tiles, const CUtensorMap* img_maps,
+                     const CUtensorMap* score_maps, const Call* call, int t_hi, int t_lo, int border, int cell,
+                     int grid, int order, void* stream, bool apply);
 int nms_warp_blocks_per_sm();
 void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, void* stream);
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
