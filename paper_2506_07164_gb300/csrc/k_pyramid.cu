@@ -185,7 +185,7 @@ __device__ __forceinline__ void hrow(const uint8_t* __restrict__ row, int wa, in
 }
 
 __global__ void __launch_bounds__(RT_THREADS)
-k_resize_tma(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix, int n_jobs, int n_tiles,
+k_resize_tma(const Resize* __restrict__ jobs, const uint2* __restrict__ items, int n_tiles,
              const CUtensorMap* __restrict__ maps, const Call* __restrict__ call, int buf_bytes) {
     extern __shared__ __align__(128) uint8_t rdyn[];
     __shared__ __align__(8) uint64_t mbar[2];
@@ -201,10 +201,11 @@ k_resize_tma(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix
     }
     __syncthreads();
     auto issue = [&](int t, int b) {
-        const int j = find_job(prefix, n_jobs, t);
+        // Tile t from the plan's item table: (job, (Y0 << 16) | X0).
+        const uint2 e = __ldg(items + t);
+        const int j = (int)e.x;
         const Resize& J = jobs[j];
-        const int tt = t - __ldg(prefix + j);
-        const int X0 = (tt % J.tiles_x) * RS_TILE_W, Y0 = (tt / J.tiles_x) * RT_TILE_H;
+        const int X0 = (int)(e.y & 0xFFFFu), Y0 = (int)(e.y >> 16);
         const int sx0 = (__ldg(J.xtab + X0) >> 12) & ~15;
         const int sy0 = __ldg(J.ytab + Y0) >> 12;
         tinfo[b] = RsTile{j, X0, Y0, sx0, sy0};
@@ -301,12 +302,12 @@ k_resize_tma(const Resize* __restrict__ jobs, const int32_t* __restrict__ prefix
     }
 }
 
-void launch_resize_tma(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
-                       const CUtensorMap* maps, const Call* call, int buf_bytes, int grid, void* stream) {
+void launch_resize_tma(const Resize* jobs, const uint2* items, int n_tiles, const CUtensorMap* maps,
+                       const Call* call, int buf_bytes, int grid, void* stream) {
     if (n_tiles <= 0) return;
     grid = grid < n_tiles ? grid : n_tiles;
-    k_resize_tma<<<grid, RT_THREADS, 2 * buf_bytes + 128, (cudaStream_t)stream>>>(jobs, tile_prefix, n_jobs,
-                                                                                   n_tiles, maps, call, buf_bytes);
+    k_resize_tma<<<grid, RT_THREADS, 2 * buf_bytes + 128, (cudaStream_t)stream>>>(jobs, items, n_tiles, maps, call,
+                                                                                   buf_bytes);
 }
 
 // The kernel's dynamic shared-memory limit is raised once to the largest

@@ -229,11 +229,13 @@ struct Plan {
         int slot_begin = 0, slot_end = 0;
         std::vector<int> rs_job, rs_n;              // per level: first resize job, jobs
         std::vector<int> rsp_off[2], rs_tiles[2];   // per level and resize tile height
+        std::vector<int> rsi_off;                   // per level: offset of its 64-row tiles in items_rs
     };
     std::vector<Group> groups[kMaxGroups + 1];
     std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_ftall[2], gp_fal, gp_cstrip;
     // Work-item tables of the per-warp kernels, per group: (image, (y0 << 16) | x0).
     std::vector<uint2> items_cs, items_dt;
+    std::vector<uint2> items_rs;  // TMA resize tiles per group and level: (job in the level's launch, (Y0 << 16) | X0)
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
     bool apply_flags = false;    // the threshold pass can set the cell flags (else the general FAST kernel does)
     bool strip_ok = false;       // the cell size allows the cell-row strip kernel (cells of 8..33 pixels)
@@ -245,7 +247,7 @@ struct Plan {
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0, off_ftab = 0;
     size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gft[2] = {0, 0}, off_gfal = 0,
-           off_gcs = 0, off_ics = 0, off_idt = 0;
+           off_gcs = 0, off_ics = 0, off_idt = 0, off_irs = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -280,6 +282,7 @@ struct Plan {
     const int32_t* d_gcs() const { return reinterpret_cast<const int32_t*>(dbuf + off_gcs); }
     const uint2* d_ics() const { return reinterpret_cast<const uint2*>(dbuf + off_ics); }
     const uint2* d_idt() const { return reinterpret_cast<const uint2*>(dbuf + off_idt); }
+    const uint2* d_irs() const { return reinterpret_cast<const uint2*>(dbuf + off_irs); }
     const int32_t* d_gnp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gnp); }
     const int32_t* d_gft(int i) const { return reinterpret_cast<const int32_t*>(dbuf + off_gft[i]); }
     const int32_t* d_gfal() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfal); }
@@ -380,7 +383,7 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
                 if (nj <= 0) continue;
                 if (P->tun.resize_tma && P->rt_buf[l] > 0) {
                     static_assert(RS_TILE_HS[1] == RT_TILE_H, "TMA resize uses the 64-row tile prefix");
-                    launch_resize_tma(P->d_rs() + G.rs_job[l], P->d_grs() + G.rsp_off[1][l], nj, G.rs_tiles[1][l],
+                    launch_resize_tma(P->d_rs() + G.rs_job[l], P->d_irs() + G.rsi_off[l], G.rs_tiles[1][l],
                                       P->d_maps() + 2 * P->n_img + G.rs_job[l], P->d_call(), P->rt_buf[l],
                                       H->n_sms * P->rt_bps[l], st);
                 } else {
@@ -772,6 +775,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
             G.slot_end = f1 < nf ? P->h_img[f1 * nl].slot0 : P->total_slots;
             G.rs_job.assign(nl + 1, 0);
             G.rs_n.assign(nl + 1, 0);
+            G.rsi_off.assign(nl + 1, 0);
             for (int v = 0; v < 2; ++v) {
                 G.rsp_off[v].assign(nl + 1, 0);
                 G.rs_tiles[v].assign(nl + 1, 0);
@@ -783,6 +787,12 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
                 while (e < P->rs_begin[l + 1] && P->rs_frame[e] < f1) ++e;
                 G.rs_job[l] = b;
                 G.rs_n[l] = e - b;
+                G.rsi_off[l] = (int)P->items_rs.size();
+                for (int i = b; i < e; ++i)  // tile t = ty * tiles_x + tx of job i - b, as the prefixes count
+                    for (int ty = 0; ty < (P->h_rs[i].dh + RT_TILE_H - 1) / RT_TILE_H; ++ty)
+                        for (int tx = 0; tx < P->h_rs[i].tiles_x; ++tx)
+                            P->items_rs.push_back(make_uint2(
+                                (uint32_t)(i - b), ((uint32_t)(ty * RT_TILE_H) << 16) | (uint32_t)(tx * RS_TILE_W)));
                 for (int v = 0; v < 2; ++v) {
                     G.rsp_off[v][l] = (int)P->gp_rs.size();
                     int tiles = 0;
@@ -902,6 +912,8 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     off = align_up(off + sizeof(uint2) * std::max<size_t>(P->items_cs.size(), 1), 16);
     P->off_idt = off;
     off = align_up(off + sizeof(uint2) * std::max<size_t>(P->items_dt.size(), 1), 16);
+    P->off_irs = off;
+    off = align_up(off + sizeof(uint2) * std::max<size_t>(P->items_rs.size(), 1), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -938,6 +950,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_gcs, P->gp_cstrip.data(), sizeof(int32_t) * P->gp_cstrip.size());
     put(P->off_ics, P->items_cs.data(), sizeof(uint2) * P->items_cs.size());
     put(P->off_idt, P->items_dt.data(), sizeof(uint2) * P->items_dt.size());
+    put(P->off_irs, P->items_rs.data(), sizeof(uint2) * P->items_rs.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);

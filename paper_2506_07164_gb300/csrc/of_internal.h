@@ -134,8 +134,8 @@ __host__ __device__ __forceinline__ int tile_of(int order, int block, int grid, 
 namespace ofk {
 void launch_resize(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
                    int tile_h, void* stream);
-void launch_resize_tma(const Resize* jobs, const int32_t* tile_prefix, int n_jobs, int n_tiles,
-                       const CUtensorMap* maps, const Call* call, int buf_bytes, int grid, void* stream);
+void launch_resize_tma(const Resize* jobs, const uint2* items, int n_tiles, const CUtensorMap* maps,
+                       const Call* call, int buf_bytes, int grid, void* stream);
 int resize_tma_blocks_per_sm(int buf_bytes);  // also raises the kernel's shared-memory limit
 // General FAST on 128 x tile_h tiles (32, 64, 128 or 256 rows); flags: also
 // set the cell flags (else the threshold pass sets them).
