@@ -315,7 +315,7 @@ FAST_OPS_PER_PX = 40.5
 # levels, divided by the frames.  Valid while the kernels' code
 # (kernels_sha1) and the per-stage launch choices below are the ones captured;
 # otherwise the line reports null.
-STAGE_TRAFFIC = {"code_sha1": "5143eca0819dc2e22ddf4dfee92bbe39474edc5c", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 32}, "l2_bytes_per_frame": {"pyramid": 24106350, "fast": 30283002, "nms_harris": 37436153, "select": 2577936, "orient": 2481392}, "dram_bytes_per_frame": {"pyramid": 7742368, "fast": 12246744, "nms_harris": 14594332, "select": 1024108, "orient": 531224}}
+STAGE_TRAFFIC = {"code_sha1": "15beeae98e4bf634d86ea749ce057c562c4ff06e", "frames": 64, "tuning": {"resize_tma": 1, "resize_tile_h": 64, "fast_cell_tiles": 4, "fast_tile_h": 32, "nms_tile_h": 32}, "l2_bytes_per_frame": {"pyramid": 24196450, "fast": 30250878, "nms_harris": 37334777, "select": 2605176, "orient": 2479839}, "dram_bytes_per_frame": {"pyramid": 7743236, "fast": 12241556, "nms_harris": 14609800, "select": 1026060, "orient": 533236}}
 
 
 def code_sha1(path):

@@ -19,14 +19,19 @@ namespace ofk {
 
 __global__ void __launch_bounds__(ORIENT_WARPS * 32)
 k_orient(const Img* __restrict__ imgs, int img_begin, int n_img, int slot_begin, int slot_end,
-         const Call* __restrict__ call) {
+         const Call* __restrict__ call, const uint16_t* __restrict__ slot_img) {
     const int slot = slot_begin + blockIdx.x * ORIENT_WARPS + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (slot >= slot_end) return;
+    // The slot's image: from the plan's slot table, else a search over slot0.
     int lo = img_begin, hi = img_begin + n_img - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (imgs[mid].slot0 <= slot) lo = mid; else hi = mid - 1;
+    if (slot_img) {
+        lo = __ldg(slot_img + slot);
+    } else {
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (imgs[mid].slot0 <= slot) lo = mid; else hi = mid - 1;
+        }
     }
     const Img& I = imgs[lo];
     const int rank = slot - I.slot0;
@@ -134,15 +139,15 @@ k_orient(const Img* __restrict__ imgs, int img_begin, int n_img, int slot_begin,
 }
 
 void launch_orient_range(const Img* imgs, int img_begin, int n_img, int slot_begin, int slot_end, const Call* call,
-                         void* stream) {
+                         void* stream, const uint16_t* slot_img) {
     if (slot_end <= slot_begin || n_img <= 0) return;
     const int blocks = (slot_end - slot_begin + ORIENT_WARPS - 1) / ORIENT_WARPS;
     k_orient<<<blocks, ORIENT_WARPS * 32, 0, (cudaStream_t)stream>>>(imgs, img_begin, n_img, slot_begin, slot_end,
-                                                                       call);
+                                                                       call, slot_img);
 }
 
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream) {
-    launch_orient_range(imgs, 0, n_img, 0, total_slots, call, stream);
+    launch_orient_range(imgs, 0, n_img, 0, total_slots, call, stream, nullptr);
 }
 
 // ---------------------------------------------------------------- inspect

@@ -235,6 +235,7 @@ struct Plan {
     std::vector<int32_t> gp_det, gp_rs, gp_fast, gp_rows, gp_nms64, gp_ftall[2], gp_fal, gp_cstrip;
     // Work-item tables of the per-warp kernels, per group: (image, (y0 << 16) | x0).
     std::vector<uint2> items_cs, items_dt;
+    std::vector<uint16_t> slot_img;  // image of every output slot (orientation kernel)
     std::vector<uint2> items_rs;  // TMA resize tiles per group and level: (job in the level's launch, (Y0 << 16) | X0)
     bool cell_tiles = false;     // the cell size allows the cell-tile FAST kernel
     bool apply_flags = false;    // the threshold pass can set the cell flags (else the general FAST kernel does)
@@ -247,7 +248,7 @@ struct Plan {
     uint8_t* dbuf = nullptr;
     size_t off_call = 0, off_img = 0, off_rs = 0, off_dl = 0, off_tab = 0, off_ftab = 0;
     size_t off_gdp = 0, off_grs = 0, off_gfp = 0, off_grp = 0, off_gnp = 0, off_gft[2] = {0, 0}, off_gfal = 0,
-           off_gcs = 0, off_ics = 0, off_idt = 0, off_irs = 0;
+           off_gcs = 0, off_ics = 0, off_idt = 0, off_irs = 0, off_sli = 0;
     size_t off_maps = 0;
     std::vector<CUtensorMap> h_maps;  // [image maps | score maps] (n_img each) | resize source maps
     of_tuning tun{};  // launch configuration (defaults, or the autotuner's choice)
@@ -283,6 +284,7 @@ struct Plan {
     const uint2* d_ics() const { return reinterpret_cast<const uint2*>(dbuf + off_ics); }
     const uint2* d_idt() const { return reinterpret_cast<const uint2*>(dbuf + off_idt); }
     const uint2* d_irs() const { return reinterpret_cast<const uint2*>(dbuf + off_irs); }
+    const uint16_t* d_sli() const { return reinterpret_cast<const uint16_t*>(dbuf + off_sli); }
     const int32_t* d_gnp() const { return reinterpret_cast<const int32_t*>(dbuf + off_gnp); }
     const int32_t* d_gft(int i) const { return reinterpret_cast<const int32_t*>(dbuf + off_gft[i]); }
     const int32_t* d_gfal() const { return reinterpret_cast<const int32_t*>(dbuf + off_gfal); }
@@ -458,7 +460,8 @@ void enqueue_group_stage(of_handle* H, Plan* P, const Plan::Group& G, int stage,
             launch_select(P->d_img() + G.img_begin, G.n_img, P->d_call(), P->max_quota, st);
             break;
         case 4:
-            launch_orient_range(P->d_img(), G.img_begin, G.n_img, G.slot_begin, G.slot_end, P->d_call(), st);
+            launch_orient_range(P->d_img(), G.img_begin, G.n_img, G.slot_begin, G.slot_end, P->d_call(), st,
+                                P->n_img <= 65536 ? P->d_sli() : nullptr);
             break;
     }
 }
@@ -914,6 +917,14 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     off = align_up(off + sizeof(uint2) * std::max<size_t>(P->items_dt.size(), 1), 16);
     P->off_irs = off;
     off = align_up(off + sizeof(uint2) * std::max<size_t>(P->items_rs.size(), 1), 16);
+    // Output slot -> image (slots of image i: [slot0, slot0 + layout quota)).
+    P->slot_img.assign(std::max(P->total_slots, 1), 0);
+    for (int i = 0; i < P->n_img; ++i) {
+        const int e = i + 1 < P->n_img ? P->h_img[i + 1].slot0 : P->total_slots;
+        for (int k = P->h_img[i].slot0; k < e; ++k) P->slot_img[k] = (uint16_t)i;
+    }
+    P->off_sli = off;
+    off = align_up(off + sizeof(uint16_t) * P->slot_img.size(), 16);
     cudaError_t e = cudaMalloc(&P->dbuf, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -951,6 +962,7 @@ int build_plan(of_handle* H, const std::vector<FrameKey>& frames, const Settings
     put(P->off_ics, P->items_cs.data(), sizeof(uint2) * P->items_cs.size());
     put(P->off_idt, P->items_dt.data(), sizeof(uint2) * P->items_dt.size());
     put(P->off_irs, P->items_rs.data(), sizeof(uint2) * P->items_rs.size());
+    put(P->off_sli, P->slot_img.data(), sizeof(uint16_t) * P->slot_img.size());
     e = cudaMemcpy(P->dbuf, blob.data(), off, cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&P->stage[i], P->header_bytes);

@@ -192,7 +192,7 @@ void launch_select(const Img* imgs, int n_img, const Call* call, int max_quota, 
 void launch_orient(const Img* imgs, int n_img, const Call* call, int total_slots, void* stream);
 // Slots [slot_begin, slot_end) of images [img_begin, img_begin + n_img) (one frame group).
 void launch_orient_range(const Img* imgs, int img_begin, int n_img, int slot_begin, int slot_end, const Call* call,
-                         void* stream);
+                         void* stream, const uint16_t* slot_img = nullptr);
 // S(p) of image `img` from a dense w x h copy of its map (offset scores):
 // the per-cell thresholds and proposal tiles applied, t_lo - 1 added back.
 void launch_inspect_score_final(const Img* imgs, int img, uint8_t* d, int w, int h, int t_hi, int t_lo, int border,
