@@ -462,6 +462,29 @@ def run_reference(args, rank: int, world: int):
     return 0
 
 
+def parse_tuning(text):
+    """--tuning: a JSON object holding every field of TUNING_FIELDS as an integer.
+
+    The bench line's own "autotune" object is accepted as it is: the search
+    statistics it also holds (candidates, stage times) are dropped.  Other keys
+    and missing fields are errors; the library validates the values."""
+    stats = ("candidates_tried", "resize_ms", "fast_ms", "nms_ms")
+    try:
+        obj = json.loads(text)
+    except ValueError as e:
+        raise SystemExit(f"--tuning: not JSON ({e})")
+    if not isinstance(obj, dict):
+        raise SystemExit("--tuning: expected a JSON object")
+    unknown = sorted(set(obj) - set(TUNING_FIELDS) - set(stats))
+    missing = [k for k in TUNING_FIELDS if k not in obj]
+    if unknown or missing:
+        raise SystemExit(f"--tuning: unknown fields {unknown}, missing fields {missing}")
+    bad = [k for k in TUNING_FIELDS if isinstance(obj[k], bool) or not isinstance(obj[k], int)]
+    if bad:
+        raise SystemExit(f"--tuning: fields {bad} must be integers")
+    return {k: obj[k] for k in TUNING_FIELDS}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,8 +506,13 @@ def main():
     ap.add_argument("--skip-learned", action="store_true", help="skip the learned tile-proposal leg")
     ap.add_argument("--skip-ablation", action="store_true", help="skip the paper-variant ablation leg")
     ap.add_argument("--skip-mixed", action="store_true", help="skip the uneven-size batch leg")
+    ap.add_argument("--tuning", type=str, default=None,
+                    help="JSON object of every launch-configuration field (%s): installed with of_set_tuning "
+                         "instead of the autotuner's search, so that a profiling run launches what a timed "
+                         "run chose" % ", ".join(TUNING_FIELDS))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    fixed_tuning = parse_tuning(args.tuning) if args.tuning else None
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -526,10 +554,16 @@ def main():
     plain = ofg.Detector(W_, H_, max_levels=LEVELS, max_features=NFEAT, max_batch=1, fast_t_lo=FAST_T_LO,
                          stream=stream)
     frames = [(t, W_, H_, W_) for t in dev_frames]
-    # Autotune the batched plan once (launch configuration per stage), then time it.
+    # Autotune the batched plan once (launch configuration per stage), or install the
+    # given one, then time it.
     with torch.cuda.stream(stream):
-        tuning = ofg.of_autotune(batched.h, frames, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, batched.out,
-                                 batched.counts, reps=3).as_dict()
+        if fixed_tuning is None:
+            tuning = ofg.of_autotune(batched.h, frames, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, batched.out,
+                                     batched.counts, reps=3).as_dict()
+        else:
+            ofg.of_set_tuning(batched.h, frames, LEVELS, SCALE, FAST_T, HARRIS_K, NFEAT, batched.out,
+                              batched.counts, ofg.OfTuning(**fixed_tuning))
+            tuning = dict(fixed_tuning)
     torch.cuda.synchronize()
 
     def step_batched(events=None):
@@ -861,6 +895,7 @@ def main():
                 "pipelining": "two device input sets and handles; step k+1's H2D (copy stream) overlaps "
                               "step k's detection"},
         "autotune": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tuning.items()},
+        "tuning_source": "autotuned" if fixed_tuning is None else "fixed (--tuning)",
         "roofline": roofline,
         "mixed": mixed,
         "learned": learned_out,

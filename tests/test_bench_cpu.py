@@ -36,3 +36,21 @@ def test_code_hash_ignores_comments(tmp_path):
     assert bench.code_sha1(str(a)) == bench.code_sha1(str(b))
     b.write_text("int f() {\n    return 2;\n}\n")
     assert bench.code_sha1(str(a)) != bench.code_sha1(str(b))
+
+
+def test_tuning_option_takes_the_lines_autotune_object():
+    """--tuning accepts the "autotune" object a bench line printed (search
+    statistics dropped) and rejects anything that is not every field as an
+    integer, before any GPU work."""
+    line = {"resize_tile_h": 64, "fast_blocks_per_sm": 2, "nms_blocks_per_sm": 2, "fast_order": 0,
+            "nms_order": 0, "resize_tma": 1, "stream_groups": 8, "fast_cell_tiles": 4, "nms_tile_h": 32,
+            "fast_tile_h": 32, "candidates_tried": 61, "resize_ms": 0.4684, "fast_ms": 3.1161, "nms_ms": 1.132}
+    got = bench.parse_tuning(json.dumps(line))
+    assert list(got) == list(bench.TUNING_FIELDS)
+    assert all(got[k] == line[k] for k in bench.TUNING_FIELDS)
+    missing = dict(line)
+    del missing["stream_groups"]
+    for bad in ("[64]", "not json", json.dumps(missing), json.dumps(dict(line, extra=1)),
+                json.dumps(dict(line, fast_order=0.5)), json.dumps(dict(line, resize_tma=True))):
+        with pytest.raises(SystemExit):
+            bench.parse_tuning(bad)
