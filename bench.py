@@ -306,7 +306,7 @@ def summarize_clocks(path: str):
 # of an SM: 64 lane-ops per clock per SM.  Algorithmic work of the score: per
 # pixel pair, 2 x (16 + 16 + 8) three-input packed min/max operations of the
 # arc network plus 1 for the final score = 81, i.e. 40.5 per pixel of the
-# detect tiles.
+# detect regions (tile padding is not work the method asks for).
 ALU_LANES_PER_SM_CLK = 64
 FAST_OPS_PER_PX = 40.5
 # L2 (lts__t_bytes.sum) and DRAM (dram__bytes_read.sum + dram__bytes_write.sum)

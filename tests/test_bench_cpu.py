@@ -54,3 +54,32 @@ def test_tuning_option_takes_the_lines_autotune_object():
                 json.dumps(dict(line, fast_order=0.5)), json.dumps(dict(line, resize_tma=True))):
         with pytest.raises(SystemExit):
             bench.parse_tuning(bad)
+
+
+def test_algorithmic_work_of_the_1080p_workload():
+    """The per-frame figures the roofline fields divide by, for 1920x1080 with
+    8 levels at scale 1.2: level sizes from the oracle, detect regions counted
+    by masking each level with the border, and each stage's algorithmic bytes
+    (pyramid: read levels 0..6, write 1..7; FAST: read every level, write its
+    score map; floor: input, levels 1..7 written, every level read once, one
+    64-byte record per kept keypoint)."""
+    import numpy as np
+
+    import oracle
+
+    lw, lh, _ = oracle.level_sizes(1920, 1080, 8, 1.2)
+    lw, lh = [int(v) for v in lw], [int(v) for v in lh]
+    assert (lw[1], lh[1], lw[7], lh[7]) == (1600, 900, 536, 301)
+    b = bench.BORDER
+    px = [w * h for w, h in zip(lw, lh)]
+    det = sum(int(np.ones((h, w), bool)[b:h - b, b:w - b].sum()) for w, h in zip(lw, lh))
+    assert sum(px) == 6_419_321 and det == 5_905_941
+    assert bench.detect_region_pixels(lw, lh) == det
+    pyr, fast, nmsh, sel, orient = bench.stage_bytes(lw, lh, [10] * 8, [2] * 8)
+    assert pyr == sum(px) - px[-1] + sum(px) - px[0] == 10_603_706
+    assert fast == sum(px) + det == 12_325_262
+    assert nmsh == det + sum(px) + 12 * 80 and sel == 12 * 80 + 12 * 16 and orient == 866 * 16
+    assert bench.floor_bytes_per_frame(lw, lh, 1000) == px[0] + 2 * sum(px) - px[0] + 64_000 == 12_902_642
+    # FAST's work per frame against the integer-ALU peak (152 SMs x 64 lanes x 2.07 GHz).
+    assert abs(bench.FAST_OPS_PER_PX * det - 239.19e6) < 0.01e6
+    assert abs(152 * bench.ALU_LANES_PER_SM_CLK * 2070e6 - 20.137e12) < 0.001e12
