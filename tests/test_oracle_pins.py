@@ -441,3 +441,50 @@ def test_detect_degenerate_levels():
     assert all(k["level"] == 0 for k in kp)
     tiny = np.zeros((30, 30), np.uint8)
     assert len(oracle.detect(tiny, levels=3, n_features=10)) == 0
+
+
+# ----------------------------------------------------------------- symmetries
+def test_score_map_symmetries():
+    """Eq. 1 treats bright and dark alike, and the radius-3 ring of Fig. 2(a)
+    is closed under quarter turns and mirrors (each maps contiguous arcs to
+    contiguous arcs): the score map of the inverted, rotated or mirrored image
+    is the original map, unchanged, rotated or mirrored.  A one-sided
+    comparison, a wrong ring offset or an x/y swap breaks one of them."""
+    ring = set(RING)
+    assert {(dy, -dx) for dx, dy in RING} == ring and {(-dx, dy) for dx, dy in RING} == ring
+    img = synth.scene(72, 72, 4, n_rect=25, n_checker=4)  # square: the border maps onto itself
+    b = 3
+    s = oracle.score_map(img, b)
+    assert (s >= 20).sum() > 20
+    assert np.array_equal(oracle.score_map(255 - img, b), s)
+    for k in (1, 2, 3):
+        assert np.array_equal(oracle.score_map(np.ascontiguousarray(np.rot90(img, k)), b), np.rot90(s, k))
+    assert np.array_equal(oracle.score_map(np.ascontiguousarray(img[:, ::-1]), b), s[:, ::-1])
+    assert np.array_equal(oracle.score_map(np.ascontiguousarray(img[::-1]), b), s[::-1])
+
+
+def test_detect_quarter_turn_equivariance():
+    """One level and one threshold (the cell fallback then has nothing to
+    decide): a quarter turn of a square frame turns every keypoint with it.
+    With r[i, j] = img[j, n-1-i] (numpy's rot90), the point (x, y) moves to
+    (y, n-1-x), gx becomes gy and gy becomes -gx, so A and B trade places, C
+    changes sign and the Harris key (det - k trace^2) is unchanged; the
+    moments become (m01, -m10) and the angle turns by -90 degrees.  A
+    transposed operand, a Sobel sign or a swapped record field fails it."""
+    n = 160
+    img = synth.scene(n, n, 9, n_rect=40, n_checker=6)
+    kw = dict(levels=1, fast_t=20, fast_t_lo=20, n_features=1 << 20)
+    a = oracle.detect(img, **kw)
+    r = oracle.detect(np.ascontiguousarray(np.rot90(img)), **kw)
+    assert len(a) == len(r) > 20
+
+    def rec(k):
+        return (int(k["x_l"]), int(k["y_l"]), int(k["fast_score"]), int(k["key"]),
+                int(k["A"]), int(k["B"]), int(k["C"]), int(k["m10"]), int(k["m01"]))
+
+    turned = {(y, n - 1 - x, s, key, B, A, -C, m01, -m10) for x, y, s, key, A, B, C, m10, m01 in map(rec, a)}
+    assert turned == set(map(rec, r))
+    ang_a = {(int(k["y_l"]), n - 1 - int(k["x_l"])): float(k["angle"]) for k in a}
+    for k in r:
+        d = float(k["angle"]) - (ang_a[(int(k["x_l"]), int(k["y_l"]))] - math.pi / 2)
+        assert abs(math.remainder(d, 2 * math.pi)) < 1e-9
