@@ -117,3 +117,30 @@ def test_variant_detect_validates_before_any_device_work(lib):
             ofg.of_variant_detect(fv, hv, 16, 64, 64, 64, 20, 19, 0.04, 16, 16, 10)
     with pytest.raises(ofg.OfError):  # border < 4
         ofg.of_variant_detect(0, -1, 16, 64, 64, 64, 20, 3, 0.04, 16, 16, 10)
+
+
+@pytest.mark.parametrize("w,h", [(1920, 1080), (640, 480), (3840, 2160), (333, 217)])
+def test_batch_bytes_is_the_documented_layout(lib, w, h):
+    """of_batch_bytes (host-only) against the scratch layout of the arena,
+    built here from the oracle's level sizes and quotas: per (frame, level)
+    image the level (pitch rounded to 16 bytes; for level 0 the copy an
+    unaligned frame needs), its score map (same pitch), 12 bytes of candidate
+    key and position for each of ceil(rw/2) x ceil(rh/2) possible strict 3x3
+    maxima (they are never adjacent), 12 bytes per kept keypoint of the
+    level's quota, one uint32 flag word per cell and 4 int32 counters.  Every
+    buffer starts on 256 bytes, so a frame costs at most 8 levels x 6 buffers
+    x 255 bytes more, plus a small per-batch block."""
+    levels, scale, nf, border, cell = 8, 1.2, 1000, 19, 30
+    lw, lh, _ = oracle.level_sizes(w, h, levels, scale)
+    quota = oracle.level_quotas(nf, levels, scale)
+    frame = 0
+    for l in range(levels):
+        lwl, lhl = int(lw[l]), int(lh[l])
+        rw, rh = lwl - 2 * border, lhl - 2 * border
+        assert rw > 0 and rh > 0  # every level holds a detect region at these sizes
+        pitch = -(-lwl // 16) * 16
+        frame += 2 * pitch * lhl + 12 * (-(-rw // 2)) * (-(-rh // 2)) + 12 * int(quota[l])
+        frame += 4 * (-(-rw // cell)) * (-(-rh // cell)) + 16
+    for n in (1, 2, 5):
+        got = ofg.of_batch_bytes(ofg.OfParams(), [(w, h)] * n, levels, scale, nf)
+        assert 0 <= got - n * frame <= n * levels * 6 * 255 + 4096, (n, got, n * frame)
