@@ -84,6 +84,17 @@ def test_create_rejects_invalid_params(lib):
         ofg.of_create(max_w=100, max_h=100, harris_block=5)
 
 
+@pytest.mark.parametrize("bad", [dict(max_w=0), dict(max_h=-1), dict(slots=17), dict(slots=-2),
+                                 dict(max_batch=257), dict(memory_budget=0), dict(levels=17),
+                                 dict(n_features=8193), dict(n_features=-1)])
+def test_server_create_rejects_invalid_params(lib, bad):
+    # The serving loop validates its parameters before any CUDA call.
+    kw = dict(max_w=1920, max_h=1080, memory_budget=1 << 30)
+    kw.update(bad)
+    with pytest.raises(ofg.OfError, match="invalid of_server_params"):
+        ofg.of_server_create(**kw)
+
+
 def _header_struct_fields(name):
     text = open(os.path.join(ROOT, "include", "ofast.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
