@@ -95,6 +95,26 @@ def test_server_create_rejects_invalid_params(lib, bad):
         ofg.of_server_create(**kw)
 
 
+@pytest.mark.parametrize("bad,code", [
+    (dict(img=None), ofg.OF_ERR_ARG), (dict(out_count=None), ofg.OF_ERR_ARG),
+    (dict(out_kpts=None), ofg.OF_ERR_ARG), (dict(w=0), ofg.OF_ERR_ARG), (dict(pitch=1919), ofg.OF_ERR_ARG),
+    (dict(w=70000, pitch=70000), ofg.OF_ERR_ARG), (dict(fast_t=0), ofg.OF_ERR_ARG),
+    (dict(fast_t=256), ofg.OF_ERR_ARG), (dict(fast_t_lo=-1), ofg.OF_ERR_ARG), (dict(n_features=8193), ofg.OF_ERR_ARG),
+    (dict(harris_k=0.3), ofg.OF_ERR_ARG), (dict(harris_k=0.0403), ofg.OF_ERR_ARG),
+    (dict(w=3840, h=2160, pitch=3840), ofg.OF_ERR_TOO_LARGE), (dict(w=2304, h=2304, pitch=2304), ofg.OF_ERR_TOO_LARGE)])
+def test_noalloc_rejects_before_any_device_work(lib, bad, code):
+    # Every call here fails validation, which comes before the first CUDA call: the
+    # pointers are fake (aligned, never dereferenced).  The too-large frames need far
+    # more than the 16 MiB array: 2304 x 2304 holds a 5.3 MB score map and 1133^2
+    # candidate slots of 12 B (15.4 MB), 3840 x 2160 about 32 MB.
+    kw = dict(img=1 << 20, w=1920, h=1080, pitch=1920, fast_t=20, fast_t_lo=7, harris_k=0.04, n_features=1000,
+              out_kpts=2 << 20, out_count=3 << 20)
+    kw.update(bad)
+    with pytest.raises(ofg.OfError) as e:
+        ofg.of_detect_level_noalloc(**kw)
+    assert e.value.code == code
+
+
 def _header_struct_fields(name):
     text = open(os.path.join(ROOT, "include", "ofast.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
