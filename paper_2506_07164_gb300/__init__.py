@@ -356,6 +356,10 @@ def of_batch_bytes(params: OfParams, sizes, levels: int, scale: float, n_feature
     return _check(int(load().of_batch_bytes(C.byref(params), ws, hs, n, levels, scale, n_features)))
 
 
+# Records a server writes per polled result (its n_features; 1000 when left 0).
+_server_features: dict = {}
+
+
 def of_server_create(**kw) -> int:
     p = OfServerParams()
     for k, v in kw.items():
@@ -363,11 +367,13 @@ def of_server_create(**kw) -> int:
     s = load().of_server_create(C.byref(p))
     if not s:
         raise OfError(OF_ERR_ARG, of_last_error())
+    _server_features[s] = p.n_features or 1000
     return s
 
 
 def of_server_destroy(s: int) -> None:
     load().of_server_destroy(s)
+    _server_features.pop(s, None)
 
 
 def of_server_submit(s: int, img: np.ndarray, tag: int = 0) -> int:
@@ -384,6 +390,10 @@ def of_server_poll(s: int, max_results: int, n_features: int, wait_ms: int = 0, 
     keypoints land in a buffer the calling thread keeps per (max_results,
     n_features) and are copied out per result; keypoints=False returns the
     results only."""
+    nf = _server_features.get(s)
+    if keypoints and nf is not None and n_features != nf:
+        # The server writes result i's records at i * its own n_features.
+        raise ValueError(f"n_features {n_features} differs from the server's {nf}")
     res = (OfServerResult * max_results)()
     kp = None
     if keypoints:

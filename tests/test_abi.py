@@ -115,6 +115,14 @@ def test_noalloc_rejects_before_any_device_work(lib, bad, code):
     assert e.value.code == code
 
 
+def test_server_poll_refuses_a_keypoint_buffer_of_another_size(monkeypatch):
+    # The server writes result i's keypoints at i * its own n_features: a poll sized for
+    # another n_features is refused before the library is called (the handle is fake).
+    monkeypatch.setitem(ofg._server_features, 0x5EED, 500)
+    with pytest.raises(ValueError, match="differs"):
+        ofg.of_server_poll(0x5EED, 4, 100)
+
+
 def _header_struct_fields(name):
     text = open(os.path.join(ROOT, "include", "ofast.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
