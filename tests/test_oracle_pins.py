@@ -488,3 +488,20 @@ def test_detect_quarter_turn_equivariance():
     for k in r:
         d = float(k["angle"]) - (ang_a[(int(k["x_l"]), int(k["y_l"]))] - math.pi / 2)
         assert abs(math.remainder(d, 2 * math.pi)) < 1e-9
+
+
+def test_resize_and_pyramid_commute_with_transposition():
+    """Both axes follow the same sampling rule and the bilinear value is one
+    exact integer expression rounded once, so resizing the transposed image
+    gives the transposed result, and so does every level of the chain (sizes
+    are computed per axis).  An axis sampled with the other axis' size fails
+    it (swapped corner operands commute with transposition: the ramp golden
+    and the float64 bilinear bound catch those)."""
+    src = synth.scene(97, 61, 12, n_rect=20, n_checker=3)
+    for dw, dh in ((80, 50), (41, 60), (97, 61), (150, 33)):
+        assert np.array_equal(oracle.resize(np.ascontiguousarray(src.T), dh, dw), oracle.resize(src, dw, dh).T)
+    img = synth.scene(333, 217, 13, n_rect=40, n_checker=5)
+    for level in (1, 3, 5):
+        a = oracle.pyramid_level(img, 6, 1.2, level)
+        b = oracle.pyramid_level(np.ascontiguousarray(img.T), 6, 1.2, level)
+        assert np.array_equal(b, a.T)
